@@ -1,0 +1,196 @@
+"""FP64 CPU oracle of the BioFVM-B diffusion-decay step (ctypes over biofvm_oracle.c).
+
+TEST INFRASTRUCTURE ONLY: the test-suite, ``__graft_entry__.smoke()`` and the CPU-baseline
+leg of ``bench.py`` may import this package; the library in ``paper_2602_05017_gb300`` never
+does, and it shares no code with it.
+
+Every function follows one passage of the paper (arXiv 2602.05017):
+  * ``axis_coefficients`` -- Appendix A (a, b, c, constant_c, denom), with the readings
+    a_i = c_i = -D dt/dx^2 and b = 1 + lambda dt/3 on a one-voxel axis;
+  * ``thomas``            -- the TDMA of Sect. 2.1 (forward: divide, backward: negated axpy);
+  * ``sweep``             -- Algorithm 1 for one dimension over every line and substrate;
+  * ``dirichlet``         -- one of the four Dirichlet applications of the 7-stage solver (Sect. 2);
+  * ``sources``           -- the cell source/uptake update of the end-to-end run (Sect. 5.3),
+    in the implicit form of the cited BioFVM, agents sharing a voxel aggregated;
+  * ``step``              -- Src, B, X^-1, B, Y^-1, B, Z^-1, B, repeated n_steps times;
+  * ``adjoint_step``      -- reverse mode of ``step`` (symmetric 1D operators: A^-T = A^-1).
+
+Pins (tests/test_oracle_pins.py) tie it to dense LU solves, closed forms (uniform decay,
+cosine modes, D = 0), exact invariants (mass, maximum principle, Dirichlet steady state,
+sweep-order independence) and finite differences.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "biofvm_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_u8p = ctypes.POINTER(ctypes.c_uint8)
+_i64p = ctypes.POINTER(ctypes.c_longlong)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no FMA contraction, so x86 and Arm agree bit for bit)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(
+            ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c99", "-shared", "-fPIC",
+             _SRC, "-o", tmp])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def _get():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        i, d, L = ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+        lib.oracle_axis_coefficients.argtypes = [i, d, d, _dp, _dp, _dp, _dp, _dp]
+        lib.oracle_thomas.argtypes = [i, _dp, _dp, _dp, _dp]
+        lib.oracle_sweep.argtypes = [i, i, i, i, i, d, d, _dp, _dp, _dp]
+        lib.oracle_dirichlet.argtypes = [i, i, i, i, _u8p, _dp, _dp]
+        lib.oracle_sources.argtypes = [i, i, i, i, d, L, _i64p, _dp, _dp, _dp, _dp, _dp]
+        lib.oracle_step.argtypes = [i, i, i, i, d, d, _dp, _dp, _u8p, _dp, L, _i64p, _dp, _dp,
+                                    _dp, _dp, i, _dp]
+        lib.oracle_adjoint_step.argtypes = [i, i, i, i, d, d, _dp, _dp, _u8p, _dp, L, _i64p, _dp,
+                                            _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
+        for f in (lib.oracle_axis_coefficients, lib.oracle_thomas, lib.oracle_sweep,
+                  lib.oracle_dirichlet, lib.oracle_sources, lib.oracle_step,
+                  lib.oracle_adjoint_step):
+            f.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _f64(a, n=None):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    if n is not None and a.size != n:
+        raise ValueError(f"expected {n} values, got {a.size}")
+    return a
+
+
+def _ptr(a, t=_dp):
+    return None if a is None else a.ctypes.data_as(t)
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise ValueError(f"oracle {what} failed with code {rc}")
+
+
+class Problem:
+    """Grid, parameters, boundary and agents of one microenvironment (all FP64, host).
+
+    Field layout is ``rho[z, y, x, s]`` (substrates interleaved per voxel, x fastest of the axes).
+    """
+
+    def __init__(self, nx, ny, nz, ns, dx, dt, D, lam, dirichlet_on=None, dirichlet_value=None,
+                 voxel=None, secretion=None, target=None, uptake=None, weight=None):
+        self.nx, self.ny, self.nz, self.ns = int(nx), int(ny), int(nz), int(ns)
+        self.dx, self.dt = float(dx), float(dt)
+        self.D = _f64(D, self.ns)
+        self.lam = _f64(lam, self.ns)
+        if dirichlet_on is not None:
+            self.on = np.ascontiguousarray(np.asarray(dirichlet_on, dtype=np.uint8).reshape(-1))
+            self.val = _f64(dirichlet_value, self.ns)
+        else:
+            self.on, self.val = None, None
+        if voxel is not None and len(voxel) > 0:
+            self.voxel = np.ascontiguousarray(np.asarray(voxel, dtype=np.int64).reshape(-1))
+            na = self.voxel.size
+            self.sec = None if secretion is None else _f64(secretion, na * self.ns)
+            self.tgt = None if target is None else _f64(target, na * self.ns)
+            self.upt = None if uptake is None else _f64(uptake, na * self.ns)
+            self.w = None if weight is None else _f64(weight, na)
+        else:
+            self.voxel = None
+            self.sec = self.tgt = self.upt = self.w = None
+
+    @property
+    def shape(self):
+        return (self.nz, self.ny, self.nx, self.ns)
+
+    @property
+    def n_agents(self):
+        return 0 if self.voxel is None else int(self.voxel.size)
+
+    def _field(self, rho):
+        a = np.array(rho, dtype=np.float64, order="C", copy=True)
+        if a.size != self.nx * self.ny * self.nz * self.ns:
+            raise ValueError("field has the wrong size")
+        return a.reshape(self.shape)
+
+    def _agents(self):
+        return (self.n_agents, _ptr(self.voxel, _i64p), _ptr(self.sec), _ptr(self.tgt),
+                _ptr(self.upt), _ptr(self.w))
+
+    def sweep(self, axis, rho):
+        out = self._field(rho)
+        _check(_get().oracle_sweep(axis, self.nx, self.ny, self.nz, self.ns, self.dx, self.dt,
+                                   _ptr(self.D), _ptr(self.lam), _ptr(out)), "sweep")
+        return out
+
+    def dirichlet(self, rho):
+        out = self._field(rho)
+        _check(_get().oracle_dirichlet(self.nx, self.ny, self.nz, self.ns, _ptr(self.on, _u8p),
+                                       _ptr(self.val), _ptr(out)), "dirichlet")
+        return out
+
+    def sources(self, rho):
+        out = self._field(rho)
+        _check(_get().oracle_sources(self.nx, self.ny, self.nz, self.ns, self.dt, *self._agents(),
+                                     _ptr(out)), "sources")
+        return out
+
+    def step(self, rho, n_steps=1):
+        out = self._field(rho)
+        _check(_get().oracle_step(self.nx, self.ny, self.nz, self.ns, self.dx, self.dt,
+                                  _ptr(self.D), _ptr(self.lam), _ptr(self.on, _u8p),
+                                  _ptr(self.val), *self._agents(), int(n_steps), _ptr(out)), "step")
+        return out
+
+    def adjoint_step(self, rho_in, gbar_out):
+        """Adjoint of one step: returns (gbar_in, dD, dlambda, dsecretion, duptake)."""
+        rho_in = self._field(rho_in)
+        gout = self._field(gbar_out)
+        gin = np.zeros_like(gout)
+        dD = np.zeros(self.ns)
+        dl = np.zeros(self.ns)
+        na = self.n_agents
+        dsec = np.zeros(na * self.ns)
+        dupt = np.zeros(na * self.ns)
+        _check(_get().oracle_adjoint_step(
+            self.nx, self.ny, self.nz, self.ns, self.dx, self.dt, _ptr(self.D), _ptr(self.lam),
+            _ptr(self.on, _u8p), _ptr(self.val), *self._agents(), _ptr(rho_in), _ptr(gout),
+            _ptr(gin), _ptr(dD), _ptr(dl), _ptr(dsec) if na else None,
+            _ptr(dupt) if na else None), "adjoint_step")
+        return gin, dD, dl, dsec.reshape(na, self.ns), dupt.reshape(na, self.ns)
+
+
+def axis_coefficients(n, r, lam3):
+    """Appendix A for one axis: returns (a, b, c, denom, cprime), each of length n."""
+    arrs = [np.zeros(n) for _ in range(5)]
+    _check(_get().oracle_axis_coefficients(int(n), float(r), float(lam3),
+                                           *[_ptr(x) for x in arrs]), "axis_coefficients")
+    return tuple(arrs)
+
+
+def thomas(a, b, c, d):
+    """Solve one tridiagonal system with the TDMA of Sect. 2.1 (returns a new array)."""
+    a, b, c = _f64(a), _f64(b), _f64(c)
+    x = _f64(d).copy()
+    n = x.size
+    if not (a.size == b.size == c.size == n):
+        raise ValueError("a, b, c, d must have the same length")
+    _check(_get().oracle_thomas(n, _ptr(a), _ptr(b), _ptr(c), _ptr(x)), "thomas")
+    return x

@@ -1,0 +1,210 @@
+"""Seeded synthetic workloads shaped like the paper's benchmark cubes (Sect. 4.3, Table 1).
+
+This module only draws inputs: grids, parameters, initial fields, agents, probes.  It holds
+none of the method's arithmetic, imports neither the CUDA library nor the oracle, and is the
+one module both sides of every parity test share.
+
+The paper's workloads are cubic microenvironments of a given side and substrate count; no
+public dataset is involved.  The five workloads below keep the paper's dx-scale resolution and
+substrate counts but are sized for one GPU (the 4% liver cube, 500^3 x 2, lies between the
+second and the third).  Random draws use NumPy's PCG64 (``numpy.random.default_rng``) with
+seed 2602050170 + k for workload k.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import List, Optional
+
+import numpy as np
+
+SEED_BASE = 2602050170
+TARGET_DENSITY = 38.0
+
+
+@dataclass
+class Workload:
+    """One microenvironment: grid, parameters, boundary, initial field and agents (FP64 host)."""
+    name: str
+    nx: int
+    ny: int
+    nz: int
+    ns: int
+    dx: float
+    dt: float
+    D: np.ndarray
+    lam: np.ndarray
+    n_steps: int
+    rho0: Optional[np.ndarray] = None            # [nz, ny, nx, ns]
+    dirichlet_on: Optional[np.ndarray] = None     # [ns] uint8, None => all zero-flux
+    dirichlet_value: Optional[np.ndarray] = None  # [ns]
+    voxel: Optional[np.ndarray] = None            # [n_agents] int64, index (z*ny + y)*nx + x
+    secretion: Optional[np.ndarray] = None        # [n_agents, ns]
+    target: Optional[np.ndarray] = None           # [n_agents, ns]
+    uptake: Optional[np.ndarray] = None           # [n_agents, ns]
+    weight: Optional[np.ndarray] = None           # [n_agents] or None (=> 1)
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def shape(self):
+        return (self.nz, self.ny, self.nx, self.ns)
+
+    @property
+    def n_vs(self):
+        """Voxel-substrate count (the unit of the throughput metric)."""
+        return self.nx * self.ny * self.nz * self.ns
+
+    @property
+    def n_agents(self):
+        return 0 if self.voxel is None else int(self.voxel.size)
+
+    def oracle_kwargs(self):
+        return dict(nx=self.nx, ny=self.ny, nz=self.nz, ns=self.ns, dx=self.dx, dt=self.dt,
+                    D=self.D, lam=self.lam, dirichlet_on=self.dirichlet_on,
+                    dirichlet_value=self.dirichlet_value, voxel=self.voxel,
+                    secretion=self.secretion, target=self.target, uptake=self.uptake,
+                    weight=self.weight)
+
+
+def _loguniform(rng, lo, hi, size):
+    return np.exp(rng.uniform(np.log(lo), np.log(hi), size=size))
+
+
+def random_agents(rng, nvox, ns, n_agents, kind="mixed", rate=(1e-3, 10.0)):
+    """Agents at seeded random voxels (repeats allowed).
+
+    kind="mixed": each agent is a source (secretion ~ logU[rate], uptake 0) or a sink
+    (uptake ~ logU[rate], secretion 0) with probability 1/2, per substrate; target 38.
+    """
+    voxel = rng.integers(0, nvox, size=n_agents, dtype=np.int64)
+    rates = _loguniform(rng, rate[0], rate[1], (n_agents, ns))
+    is_src = rng.random((n_agents, ns)) < 0.5
+    sec = np.where(is_src, rates, 0.0)
+    upt = np.where(is_src, 0.0, rates)
+    tgt = np.full((n_agents, ns), TARGET_DENSITY)
+    return voxel, sec, tgt, upt
+
+
+def gaussian_blobs(rng, nx, ny, nz, ns, dx, n_blobs=64, sigma=(100.0, 400.0), amp=(0.0, 38.0),
+                   dtype=np.float64):
+    """Sum of seeded Gaussian blobs (centres uniform in the box, sigma in um, amplitude)."""
+    out = np.zeros((nz, ny, nx, ns), dtype=dtype)
+    cx = rng.uniform(0, nx * dx, n_blobs)
+    cy = rng.uniform(0, ny * dx, n_blobs)
+    cz = rng.uniform(0, nz * dx, n_blobs)
+    sg = rng.uniform(sigma[0], sigma[1], n_blobs)
+    am = rng.uniform(amp[0], amp[1], (n_blobs, ns))
+    xs = (np.arange(nx) + 0.5) * dx
+    ys = (np.arange(ny) + 0.5) * dx
+    zs = (np.arange(nz) + 0.5) * dx
+    for b in range(n_blobs):
+        gx = np.exp(-0.5 * ((xs - cx[b]) / sg[b]) ** 2)
+        gy = np.exp(-0.5 * ((ys - cy[b]) / sg[b]) ** 2)
+        gz = np.exp(-0.5 * ((zs - cz[b]) / sg[b]) ** 2)
+        # only planes/rows where the blob is above 1e-30 of its peak are touched
+        kz = np.nonzero(gz > 1e-30)[0]
+        ky = np.nonzero(gy > 1e-30)[0]
+        if kz.size == 0 or ky.size == 0:
+            continue
+        z0, z1, y0, y1 = kz[0], kz[-1] + 1, ky[0], ky[-1] + 1
+        plane = (gy[y0:y1, None] * gx[None, :])  # [y, x]
+        for z in range(z0, z1):
+            w = gz[z] * plane
+            out[z, y0:y1, :, :] += (w[:, :, None] * am[b][None, None, :]).astype(dtype)
+    return out
+
+
+# --------------------------------------------------------------------------------------------
+# The five workloads.  `shape` overrides the grid (parity tests at reduced size keep every
+# other recipe); `with_field=False` skips the initial field for callers that draw their own.
+# --------------------------------------------------------------------------------------------
+
+def workload(k: int, shape=None, n_agents=None, with_field=True, field_dtype=np.float64,
+             seed=None) -> Workload:
+    rng = np.random.default_rng(SEED_BASE + k if seed is None else seed)
+    if k == 1:
+        nx, ny, nz = shape or (50, 50, 50)
+        w = Workload("lod_fp64_50c_s1", nx, ny, nz, 1, 20.0, 0.01, np.array([1e5]),
+                     np.array([0.1]), 100)
+        if with_field:
+            w.rho0 = rng.uniform(0.0, 38.0, w.shape).astype(field_dtype)
+        na = 200 if n_agents is None else n_agents
+        w.voxel = rng.integers(0, nx * ny * nz, size=na, dtype=np.int64)
+        w.secretion = np.full((na, 1), 10.0)
+        w.target = np.full((na, 1), TARGET_DENSITY)
+        w.uptake = np.full((na, 1), 1.0)
+        return w
+    if k == 2:
+        nx, ny, nz = shape or (400, 400, 400)
+        w = Workload("lod_400c_s4", nx, ny, nz, 4, 20.0, 0.01,
+                     np.array([1e5, 1e3, 5e2, 1e2]), np.array([0.1, 0.01, 0.4, 1e-3]), 100)
+        if with_field:
+            w.rho0 = rng.uniform(0.0, 38.0, w.shape).astype(field_dtype)
+        na = 1_000_000 if n_agents is None else n_agents
+        w.voxel, w.secretion, w.target, w.uptake = random_agents(rng, nx * ny * nz, 4, na)
+        return w
+    if k == 3:
+        nx, ny, nz = shape or (1200, 1200, 1200)
+        w = Workload("lod_fp32_1200c_s2_dirichlet", nx, ny, nz, 2, 20.0, 0.01,
+                     np.array([1e5, 1e3]), np.array([0.1, 0.01]), 20)
+        w.dirichlet_on = np.array([1, 0], dtype=np.uint8)
+        w.dirichlet_value = np.array([TARGET_DENSITY, 0.0])
+        if with_field:
+            w.rho0 = gaussian_blobs(rng, nx, ny, nz, 2, w.dx, dtype=field_dtype)
+        na = 10_000_000 if n_agents is None else n_agents
+        w.voxel, w.secretion, w.target, w.uptake = random_agents(rng, nx * ny * nz, 2, na)
+        return w
+    if k == 5:
+        nx, ny, nz = shape or (128, 128, 128)
+        w = Workload("adjoint_128c_s2", nx, ny, nz, 2, 20.0, 0.01, np.array([1e5, 1e3]),
+                     np.array([0.1, 0.01]), 200)
+        if with_field:
+            w.rho0 = rng.uniform(0.0, 38.0, w.shape).astype(field_dtype)
+        nvox = nx * ny * nz
+        na = max(1, nvox // 100) if n_agents is None else n_agents
+        w.voxel = rng.choice(nvox, size=na, replace=False).astype(np.int64)
+        w.secretion = _loguniform(rng, 1e-3, 10.0, (na, 2))
+        w.target = np.full((na, 2), TARGET_DENSITY)
+        w.uptake = np.zeros((na, 2))
+        n_probe = min(4096, nvox * 2)
+        flat = rng.choice(nvox * 2, size=n_probe, replace=False)
+        w.extra["probe_index"] = flat.astype(np.int64)       # flat index into [nz,ny,nx,ns]
+        w.extra["probe_target"] = rng.uniform(0.0, 38.0, n_probe)
+        w.extra["checkpoint_every"] = 20
+        return w
+    raise ValueError(f"unknown workload {k}")
+
+
+def batched_workloads(n_env=256, edge=(32, 192), ns=(1, 8), seed=None, n_steps=50,
+                      with_field=True, field_dtype=np.float32) -> List[Workload]:
+    """Many independent microenvironments of uneven cubic size and substrate count."""
+    rng = np.random.default_rng(SEED_BASE + 4 if seed is None else seed)
+    envs = []
+    for e in range(n_env):
+        n = int(rng.integers(edge[0], edge[1] + 1))
+        s = int(rng.integers(ns[0], ns[1] + 1))
+        D = _loguniform(rng, 1e2, 1e5, s)
+        lam = _loguniform(rng, 1e-3, 1.0, s)
+        w = Workload(f"env{e}", n, n, n, s, 20.0, 0.01, D, lam, n_steps)
+        if with_field:
+            w.rho0 = rng.uniform(0.0, 38.0, w.shape).astype(field_dtype)
+        na = max(1, (n * n * n) // 64)
+        w.voxel, w.secretion, w.target, w.uptake = random_agents(rng, n * n * n, s, na)
+        envs.append(w)
+    return envs
+
+
+def random_problem(rng, nx, ny, nz, ns, n_agents=0, dirichlet=False, dx=20.0, dt=0.01,
+                   D_range=(1e2, 1e5), lam_range=(1e-3, 1.0)) -> Workload:
+    """A small random problem for edge-case parity tests (any shape, optional Dirichlet)."""
+    D = _loguniform(rng, D_range[0], D_range[1], ns)
+    lam = _loguniform(rng, lam_range[0], lam_range[1], ns)
+    w = Workload(f"rand_{nx}x{ny}x{nz}_s{ns}", nx, ny, nz, ns, dx, dt, D, lam, 1)
+    w.rho0 = rng.uniform(0.0, 38.0, w.shape)
+    if dirichlet:
+        w.dirichlet_on = (rng.random(ns) < 0.5).astype(np.uint8)
+        w.dirichlet_on[0] = 1
+        w.dirichlet_value = rng.uniform(0.0, 38.0, ns)
+    if n_agents:
+        w.voxel, w.secretion, w.target, w.uptake = random_agents(rng, nx * ny * nz, ns, n_agents)
+        w.weight = rng.uniform(0.5, 1.5, n_agents)
+    return w
