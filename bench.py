@@ -1,0 +1,318 @@
+"""Benchmark of the LOD diffusion-decay step on GB300 (one JSON line on rank 0).
+
+Workload: 400 x 400 x 400 voxels x 4 substrates interleaved per voxel, dx = 20 um,
+dt = 0.01 min, D = {1e5, 1e3, 5e2, 1e2} um^2/min, lambda = {0.1, 0.01, 0.4, 1e-3} /min,
+1M agents with log-uniform secretion/uptake rates, initial field uniform in [0, 38] (seeded).
+A bench step is one full LOD time step (Src, B, X^-1, B, Y^-1, B, Z^-1, B) of that grid.
+The headline runs in FP64 (the paper's precision); the FP32 path is reported beside it.
+
+  value      voxel-substrate updates/s, field resident in HBM, graph-launched steps,
+             CUDA events on the library's stream, max over ranks (replicas, weak scaling)
+  e2e        the same metric through the C ABI from pinned host buffers: set_density(host),
+             K steps, density(host), all inside the timed region
+  roofline   dominant kernel: algorithmic bytes (one read + one write of the field per sweep)
+             or FP64 operations per launch / its average CUDA-event duration over K steps
+  cpu_baseline  the FP64 oracle, single-threaded on this host, on a bounded slab sample
+
+`--impl reference` times the oracle instead (the reference arm), on the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+HBM_FALLBACK_GBS = 6800.0
+# FP64 FMA issue rate of one GB300 SM (FMA/clk), measured by an 8-chain FMA probe; a GB300
+# has 152 SMs at up to 2070 MHz.  See the design doc for the derivation.
+FP64_FMA_PER_CLK_PER_SM = None
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": HBM_FALLBACK_GBS, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except FileNotFoundError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            out, _ = self.proc.communicate(timeout=10)
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in getattr(self, "lines", []):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def workload_config():
+    from paper_2602_05017_gb300 import inputs
+    return inputs.workload(2, with_field=False)
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2602_05017_gb300 import binding
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = workload_config()
+    nel = w.n_vs
+    K, W = args.steps, args.warmup
+    stream = torch.cuda.Stream(device=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    results = {}
+    for prec in ("fp64", "fp32"):
+        esz = 8 if prec == "fp64" else 4
+        tdt = torch.float64 if prec == "fp64" else torch.float32
+        sim = binding.BioFVM(w.nx, w.ny, w.nz, w.ns, w.dx, w.dt, w.D, w.lam, precision=prec,
+                             stream=stream.cuda_stream)
+        g = torch.Generator(device=dev)
+        g.manual_seed(2602050172 + rank)
+        with torch.cuda.stream(stream):
+            rho0 = torch.rand(w.shape, generator=g, device=dev, dtype=tdt) * 38.0
+        stream.synchronize()
+        sim.set_density(rho0)
+        sim.set_sources(w.voxel, w.secretion, w.target, w.uptake)
+        sim.step(W)
+        sim.sync()
+        # --- timed region: K graph-launched steps, field resident in HBM ---
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk:
+            barrier()
+            torch.cuda.synchronize(dev)
+            e0.record(stream)
+            sim.step(K)
+            e1.record(stream)
+            e1.synchronize()
+            torch.cuda.synchronize(dev)
+            barrier()
+        ms = e0.elapsed_time(e1)
+        ms_t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        if world > 1:
+            dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+        ms_max = float(ms_t.item())
+        # --- per-kernel durations over K steps (same stream, CUDA events between launches) ---
+        kev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+        for k in range(K):
+            _stage_step(sim, kev[k], stream)
+        stream.synchronize()
+        kms = [sum(kev[k][i].elapsed_time(kev[k][i + 1]) for k in range(K)) / K for i in range(3)]
+        res = {"ms_total": ms_max, "ms_per_step": ms_max / K,
+               "value": world * nel * K / (ms_max * 1e-3), "kernel_ms": kms, "clocks": clk.summary(),
+               "launches": sim.launches_per_step() * K, "esz": esz}
+        # --- e2e: host buffers through the C ABI ---
+        if rank == 0 and not args.no_e2e:
+            host_in = torch.empty(w.shape, dtype=tdt).pin_memory()
+            host_in.copy_(rho0.cpu())
+            host_out = torch.empty(w.shape, dtype=tdt).pin_memory()
+            ts = []
+            for rep in range(1 + args.e2e_reps):
+                torch.cuda.synchronize(dev)
+                t0 = time.perf_counter()
+                sim.set_density(host_in)
+                sim.step(K)
+                sim.density(host_out)
+                t1 = time.perf_counter()
+                if rep > 0:
+                    ts.append(t1 - t0)
+            t = statistics.median(ts)
+            res["e2e"] = {"value": nel * K / t, "unit": "voxel-substrate updates/s",
+                          "h2d_bytes_per_step": nel * esz / K, "d2h_bytes_per_step": nel * esz / K,
+                          "seconds_per_job": t,
+                          "job": f"set_density(host) + {K} steps + density(host)"}
+        sim.close()
+        del rho0
+        torch.cuda.empty_cache()
+        results[prec] = res
+        barrier()
+    if world > 1:
+        dist.destroy_process_group()
+    return rank, world, results
+
+
+def _stage_step(sim, ev, stream):
+    """One step as its three kernels with an event between launches (flags as in a step)."""
+    ev[0].record(stream)
+    sim.run_stage(8)
+    ev[1].record(stream)
+    sim.run_stage(2)
+    ev[2].record(stream)
+    sim.run_stage(3)
+    ev[3].record(stream)
+
+
+def cpu_baseline(args, sample_nz=8):
+    """The FP64 oracle (single thread) on a slab of the workload: 400 x 400 x sample_nz x 4."""
+    import oracle
+    from paper_2602_05017_gb300 import inputs
+    w = inputs.workload(2, shape=(400, 400, sample_nz), n_agents=1_000_000 * sample_nz // 400)
+    p = oracle.Problem(**w.oracle_kwargs())
+    p.step(w.rho0, 1)  # warm
+    ts = []
+    t_end = time.time() + args.cpu_seconds
+    while time.time() < t_end or not ts:
+        t0 = time.perf_counter()
+        p.step(w.rho0, 1)
+        ts.append(time.perf_counter() - t0)
+    t = statistics.median(ts)
+    return {"value": w.n_vs / t, "unit": "voxel-substrate updates/s", "cores": 1, "kind": "oracle",
+            "sample": f"one LOD step of a 400x400x{sample_nz}x4 slab of the workload (FP64, "
+                      f"{len(ts)} repetitions, median {t:.3f} s)"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2602_05017_gb300 import inputs
+    oracle.build()
+    nz = 8
+    w = inputs.workload(2, shape=(400, 400, nz), n_agents=1_000_000 * nz // 400)
+    p = oracle.Problem(**w.oracle_kwargs())
+    rho = w.rho0
+    for _ in range(args.warmup):
+        rho = p.step(rho, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        rho = p.step(rho, 1)
+    t = time.perf_counter() - t0
+    v = w.n_vs * args.steps / t
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"lod_400c_s4 slab 400x400x{nz}x4 (bounded CPU sample)",
+                       "steps_per_sample": 1},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"each step: one LOD step of a 400x400x{nz}x4 slab, FP64"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+METRIC = "LOD step voxel-substrate updates/s (HBM GB/s vs peak in roofline)"
+UNIT = "voxel-substrate updates/s"
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--e2e-reps", type=int, default=3)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    rank, world, res = run_gpu(args)
+    if rank != 0:
+        return 0
+    peaks, src = measured_peaks()
+    w = workload_config()
+    line = {"metric": METRIC, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic"}
+    r64 = res["fp64"]
+    line["value"] = r64["value"]
+    line["ms_per_step"] = r64["ms_per_step"]
+    line["config"] = {"workload": "lod_400c_s4: 400x400x400 voxels x 4 substrates, 1M agents, "
+                                  "dx=20um, dt=0.01min, zero-flux",
+                      "global_batch": world, "parallelism": f"replicas x{world}",
+                      "l2": "field 2.05 GB (FP64) / 1.02 GB (FP32) > 129 MB L2: no flush needed"}
+    line["gpu_launches"] = r64["launches"]
+    line["clocks"] = r64["clocks"]
+    line["e2e"] = r64.get("e2e")
+    line["roofline"] = roofline(r64, w, peaks, src)
+    line["fp32"] = {"value": res["fp32"]["value"], "ms_per_step": res["fp32"]["ms_per_step"],
+                    "dtype": "f32", "roofline": roofline(res["fp32"], w, peaks, src),
+                    "e2e": res["fp32"].get("e2e"), "clocks": res["fp32"]["clocks"],
+                    "vs_fp64": res["fp32"]["value"] / r64["value"]}
+    line["kernel_ms"] = {"fp64": dict(zip(("x", "y", "z"), r64["kernel_ms"])),
+                         "fp32": dict(zip(("x", "y", "z"), res["fp32"]["kernel_ms"]))}
+    if not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(args)
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def roofline(r, w, peaks, src):
+    kms = r["kernel_ms"]
+    i = int(np.argmax(kms))
+    name = ("x", "y", "z")[i]
+    alg_bytes = 2 * r["esz"] * w.n_vs  # one read + one write of the field per sweep
+    achieved = alg_bytes / (kms[i] * 1e-3) / 1e9
+    peak = float(peaks["hbm_gbs"])
+    return {"bound": "hbm", "kernel": f"{name}-sweep", "achieved": achieved, "peak": peak,
+            "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+            "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({src})"}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,156 @@
+/*
+ * libbiofvm -- GB300 (sm_103a) LOD diffusion-decay step of BioFVM-B
+ * (Estragues-Munoz et al., "A Novel Scalable High Performance diffusion
+ * solver for multiscale cell simulations", arXiv 2602.05017).
+ *
+ * One time step advances every substrate of a 3D voxel grid (Sect. 2):
+ *
+ *   rho <- B . Z^-1 . B . Y^-1 . B . X^-1 . B . Src (rho)
+ *
+ *   Src   cell source/uptake update, rho <- (rho + alpha)/(1 + beta) per
+ *         voxel with alpha = sum dt*w*S*rho_target and beta = sum dt*w*(S+U)
+ *         over the agents in that voxel (the end-to-end run of Sect. 5.3;
+ *         implicit form of the cited BioFVM);
+ *   B     Dirichlet application: the voxels of the six faces take the
+ *         substrate's Dirichlet value when its flag is on ("four
+ *         applications of Dirichlet conditions", Sect. 2);
+ *   X^-1  every x-line of every substrate solved with the Thomas algorithm
+ *         (Algorithm 1; Sect. 2.1) on the system of Appendix A:
+ *         a_i = c_i = -r, b = 1 + 2r + lambda*dt/3 inside, 1 + r + lambda*dt/3
+ *         at the two ends (zero flux), 1 + lambda*dt/3 on a one-voxel axis,
+ *         r = D*dt/dx^2;  Y^-1 and Z^-1 likewise along y and z.
+ *
+ * Field layout (Sect. 3.1, one contiguous 4D array): element (x, y, z, s) is
+ * at index ((z*ny + y)*nx + x)*n_sub + s -- substrates interleaved per voxel,
+ * x the fastest of the three axes.  The element type is double for
+ * BIOFVM_FP64 and float for BIOFVM_FP32 (Thomas constants are always computed
+ * in double on the host, then rounded to the element type).
+ *
+ * Conventions of every call:
+ *   - Errors are returned as a biofvm_status, never thrown; the thread-local
+ *     message of the last failure is biofvm_last_error().
+ *   - The library owns all device memory it allocates.  The caller owns and
+ *     keeps every array it passes; the library copies what it needs (host
+ *     arrays host->device, device arrays device->device) before returning.
+ *   - All device work of a handle is ordered on the CUDA stream given at
+ *     create (0 = the legacy default stream).  Calls marked "async" return
+ *     before the GPU has finished; biofvm_density/biofvm_sync wait.
+ *   - A handle is not thread-safe; distinct handles are independent.
+ */
+#ifndef BIOFVM_H
+#define BIOFVM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct biofvm biofvm_t; /* opaque handle */
+
+typedef enum {
+  BIOFVM_OK = 0,
+  BIOFVM_ERR_ARG = 1,     /* invalid argument (nothing was changed)        */
+  BIOFVM_ERR_OOM = 2,     /* device or host allocation failed              */
+  BIOFVM_ERR_CUDA = 3,    /* a CUDA call failed (message has its name)     */
+  BIOFVM_ERR_TIMEOUT = 4, /* a bounded device-side wait gave up            */
+  BIOFVM_ERR_STATE = 5    /* call not valid in the handle's current state  */
+} biofvm_status;
+
+typedef enum { BIOFVM_FP64 = 0, BIOFVM_FP32 = 1 } biofvm_precision;
+
+typedef struct {
+  int nx, ny, nz; /* voxels per axis, each >= 1                          */
+  int n_sub;      /* substrates per voxel, 1 <= n_sub <= 32              */
+} biofvm_grid;
+
+/* Dirichlet condition per substrate (Sect. 2, the four applications).
+ * dirichlet_on[s] != 0 switches it on for substrate s; dirichlet_value[s]
+ * is the value written on the six faces.  A NULL biofvm_boundary pointer, or
+ * NULL dirichlet_on, means zero-flux (Neumann) for every substrate. */
+typedef struct {
+  const uint8_t *dirichlet_on;    /* [n_sub] host */
+  const double *dirichlet_value;  /* [n_sub] host */
+} biofvm_boundary;
+
+/* Create a microenvironment.  grid: sizes (host, read once).  dx: voxel edge
+ * (> 0, same unit as sqrt(D*dt)).  dt: time step (> 0).  D[n_sub] >= 0 and
+ * lambda[n_sub] >= 0: diffusion and decay per substrate (host).  bc: see
+ * biofvm_boundary.  cuda_stream: a cudaStream_t cast to uintptr_t, kept for
+ * the handle's life (the caller must keep it alive).  On success *out holds
+ * the handle; the field is zero and there are no agents.
+ * Computes the Thomas constants of App. A (denom, c') in double.
+ * Errors: ARG (sizes, dx, dt, D, lambda, NULL), OOM, CUDA. */
+biofvm_status biofvm_create(const biofvm_grid *grid, double dx, double dt,
+                            const double *D, const double *lambda,
+                            const biofvm_boundary *bc, biofvm_precision prec,
+                            uintptr_t cuda_stream, biofvm_t **out);
+
+/* Copy the whole field in.  src: nx*ny*nz*n_sub elements of the handle's
+ * element type in the layout above; a host pointer (src_on_device = 0) or a
+ * device pointer (1).  Async with respect to the host for device sources;
+ * a host source is fully read before return.  Errors: ARG, CUDA. */
+biofvm_status biofvm_set_density(biofvm_t *h, const void *src,
+                                 int src_on_device);
+
+/* Replace the agents (cell sources/sinks, Sect. 5.3).  n >= 0 agents; agent
+ * k sits in voxel voxel[k] = (z*ny + y)*nx + x and has, per substrate s,
+ * secretion rate secretion[k*n_sub+s] >= 0 toward target density
+ * target[k*n_sub+s], uptake rate uptake[k*n_sub+s] >= 0, and volume weight
+ * weight[k] >= 0 (cell volume / voxel volume; NULL means 1).  secretion,
+ * target and uptake may each be NULL (= 0).  All arrays are host arrays.
+ * Agents sharing a voxel are aggregated on the host into one (alpha, beta)
+ * pair per (voxel, substrate), which makes the update independent of the
+ * order of the agents.  Not timed as part of a step.
+ * Errors: ARG (voxel out of range, negative rates or weights), OOM, CUDA. */
+biofvm_status biofvm_set_sources(biofvm_t *h, int64_t n, const int64_t *voxel,
+                                 const double *secretion, const double *target,
+                                 const double *uptake, const double *weight);
+
+/* Advance n_steps >= 0 time steps (async).  The first call after create or
+ * after a parameter change captures one step into a CUDA graph; every step is
+ * then one graph launch on the handle's stream.  Errors: ARG, CUDA,
+ * TIMEOUT (reported by the next synchronising call). */
+biofvm_status biofvm_step(biofvm_t *h, int n_steps);
+
+/* Copy the field out into dst (host pointer if dst_on_device = 0, device
+ * pointer if 1), same layout and type as biofvm_set_density.  Waits for the
+ * stream, then checks the device status word.  Errors: ARG, CUDA, TIMEOUT. */
+biofvm_status biofvm_density(biofvm_t *h, void *dst, int dst_on_device);
+
+/* Replace D[n_sub] and lambda[n_sub] (host) and recompute the App. A
+ * constants (used by finite-difference checks).  Errors: ARG, CUDA. */
+biofvm_status biofvm_set_params(biofvm_t *h, const double *D,
+                                const double *lambda);
+
+/* Run exactly one stage of the step in place, for stage-by-stage checks:
+ * stage 0 = Src then B, 1 = X^-1 then B, 2 = Y^-1 then B, 3 = Z^-1 then B,
+ * 4 = the source update alone (no Dirichlet), 5 = X^-1 alone, 6 = Y^-1
+ * alone, 7 = Z^-1 alone, 8 = Src, B, X^-1, B in one launch (the first kernel
+ * of a step; with stages 2 and 3 it makes one whole step).  Async.
+ * Errors: ARG, CUDA. */
+biofvm_status biofvm_run_stage(biofvm_t *h, int stage);
+
+/* Wait for the handle's stream and check the device status word.
+ * Errors: CUDA, TIMEOUT. */
+biofvm_status biofvm_sync(biofvm_t *h);
+
+/* Device address of the handle's field (owned by the library, valid until
+ * destroy), for zero-copy interop with a framework's device tensors.
+ * Errors: ARG. */
+biofvm_status biofvm_density_ptr(biofvm_t *h, void **dev_ptr);
+
+/* Number of kernel launches one time step makes (3: x-, y-, z-sweep). */
+int biofvm_launches_per_step(const biofvm_t *h);
+
+/* Free the handle and all device memory it owns (waits for its stream).
+ * NULL is a no-op. */
+void biofvm_destroy(biofvm_t *h);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *biofvm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BIOFVM_H */

@@ -1,0 +1,245 @@
+"""Python binding of libbiofvm (ctypes): argument marshalling only.
+
+Every step of the computation runs in the library's CUDA kernels; this module turns torch
+tensors / numpy arrays into pointers and status codes into exceptions.  PyTorch supplies
+device memory and the CUDA stream.  Importing it loads ``libbiofvm.so`` and raises if the
+library has not been built (``python -m paper_2602_05017_gb300.build``): there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libbiofvm.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "biofvm.h")
+
+OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_STATE = range(6)
+FP64, FP32 = 0, 1
+STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_TIMEOUT",
+                5: "ERR_STATE"}
+
+
+class BioFVMError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("n_sub", ctypes.c_int)]
+
+
+class Boundary(ctypes.Structure):
+    _fields_ = [("dirichlet_on", ctypes.POINTER(ctypes.c_uint8)),
+                ("dirichlet_value", ctypes.POINTER(ctypes.c_double))]
+
+
+def declared_functions(header=HEADER):
+    """Names of the functions include/biofvm.h declares."""
+    text = open(header).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(biofvm_[a-z_0-9]+)\s*\(", text)))
+
+
+_lib = None
+
+
+def load():
+    """Load libbiofvm.so (raises if it is missing) and declare the C signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is not built; run `python -m paper_2602_05017_gb300.build`"
+                          " (the CUDA library is the only compute path)")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, dp, i64p = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)
+    st = ctypes.c_int
+    sig = {
+        "biofvm_create": (st, [ctypes.POINTER(Grid), ctypes.c_double, ctypes.c_double, dp, dp,
+                               ctypes.POINTER(Boundary), ctypes.c_int, ctypes.c_size_t,
+                               ctypes.POINTER(vp)]),
+        "biofvm_set_density": (st, [vp, vp, ctypes.c_int]),
+        "biofvm_set_sources": (st, [vp, ctypes.c_int64, i64p, dp, dp, dp, dp]),
+        "biofvm_step": (st, [vp, ctypes.c_int]),
+        "biofvm_density": (st, [vp, vp, ctypes.c_int]),
+        "biofvm_set_params": (st, [vp, dp, dp]),
+        "biofvm_run_stage": (st, [vp, ctypes.c_int]),
+        "biofvm_sync": (st, [vp]),
+        "biofvm_density_ptr": (st, [vp, ctypes.POINTER(vp)]),
+        "biofvm_launches_per_step": (ctypes.c_int, [vp]),
+        "biofvm_destroy": (None, [vp]),
+        "biofvm_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status, lib=None):
+    if status != OK:
+        lib = lib or load()
+        raise BioFVMError(status, lib.biofvm_last_error().decode())
+
+
+def _f64(a, n=None):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64)).reshape(-1)
+    if n is not None and a.size != n:
+        raise ValueError(f"expected {n} values, got {a.size}")
+    return a
+
+
+def _dptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _current_stream():
+    import torch
+    return torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else 0
+
+
+class BioFVM:
+    """One microenvironment on the GPU behind the C ABI (see include/biofvm.h).
+
+    Field layout ``[nz, ny, nx, n_sub]``; ``precision`` is "fp64" or "fp32".
+    """
+
+    def __init__(self, nx, ny, nz, n_sub, dx, dt, D, lam, dirichlet_on=None,
+                 dirichlet_value=None, precision="fp64", stream=None):
+        self.lib = load()
+        self.shape = (int(nz), int(ny), int(nx), int(n_sub))
+        self.precision = precision
+        self.dtype = np.float64 if precision == "fp64" else np.float32
+        self.n_elem = int(np.prod(self.shape))
+        grid = Grid(int(nx), int(ny), int(nz), int(n_sub))
+        D = _f64(D, n_sub)
+        lam = _f64(lam, n_sub)
+        bc = None
+        if dirichlet_on is not None:
+            self._on = np.ascontiguousarray(np.asarray(dirichlet_on, dtype=np.uint8).reshape(-1))
+            self._val = _f64(dirichlet_value, n_sub)
+            bc = Boundary(self._on.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), _dptr(self._val))
+        self.stream = _current_stream() if stream is None else int(stream)
+        h = ctypes.c_void_p()
+        st = self.lib.biofvm_create(ctypes.byref(grid), float(dx), float(dt), _dptr(D), _dptr(lam),
+                                    ctypes.byref(bc) if bc is not None else None,
+                                    FP64 if precision == "fp64" else FP32, self.stream,
+                                    ctypes.byref(h))
+        _check(st, self.lib)
+        self.h = h
+
+    # -- field ------------------------------------------------------------------------------
+    def set_density(self, rho):
+        """rho: torch tensor (CUDA or CPU) or numpy array with n_elem elements."""
+        try:
+            import torch
+            if isinstance(rho, torch.Tensor):
+                t = rho.detach().to(dtype=torch.float64 if self.precision == "fp64"
+                                    else torch.float32).contiguous()
+                if t.numel() != self.n_elem:
+                    raise ValueError("field has the wrong size")
+                _check(self.lib.biofvm_set_density(self.h, ctypes.c_void_p(t.data_ptr()),
+                                                   1 if t.is_cuda else 0), self.lib)
+                if t.is_cuda:
+                    self._keep = t  # the copy is stream-ordered; keep the source alive
+                return
+        except ImportError:  # pragma: no cover
+            pass
+        a = np.ascontiguousarray(np.asarray(rho, dtype=self.dtype))
+        if a.size != self.n_elem:
+            raise ValueError("field has the wrong size")
+        _check(self.lib.biofvm_set_density(self.h, a.ctypes.data_as(ctypes.c_void_p), 0), self.lib)
+
+    def density(self, out=None):
+        """Copy the field out: into ``out`` (torch tensor or numpy array) or a new numpy array."""
+        if out is None:
+            out = np.empty(self.shape, dtype=self.dtype)
+        try:
+            import torch
+            if isinstance(out, torch.Tensor):
+                assert out.is_contiguous() and out.numel() == self.n_elem
+                _check(self.lib.biofvm_density(self.h, ctypes.c_void_p(out.data_ptr()),
+                                               1 if out.is_cuda else 0), self.lib)
+                return out
+        except ImportError:  # pragma: no cover
+            pass
+        assert out.flags.c_contiguous and out.size == self.n_elem and out.dtype == self.dtype
+        _check(self.lib.biofvm_density(self.h, out.ctypes.data_as(ctypes.c_void_p), 0), self.lib)
+        return out
+
+    def density_ptr(self):
+        p = ctypes.c_void_p()
+        _check(self.lib.biofvm_density_ptr(self.h, ctypes.byref(p)), self.lib)
+        return p.value
+
+    def field_tensor(self):
+        """Zero-copy torch view of the library-owned device field (valid until close)."""
+        import torch
+
+        class _CAI:
+            pass
+        obj = _CAI()
+        obj.__cuda_array_interface__ = {
+            "shape": self.shape, "typestr": "<f8" if self.precision == "fp64" else "<f4",
+            "data": (self.density_ptr(), False), "version": 3, "strides": None,
+            "stream": None}
+        return torch.as_tensor(obj, device="cuda")
+
+    # -- agents and parameters --------------------------------------------------------------
+    def set_sources(self, voxel, secretion=None, target=None, uptake=None, weight=None):
+        vox = np.ascontiguousarray(np.asarray(voxel, dtype=np.int64)).reshape(-1)
+        n = vox.size
+        ns = self.shape[3]
+        arrs = [None if a is None else _f64(a, n * ns) for a in (secretion, target, uptake)]
+        w = None if weight is None else _f64(weight, n)
+        _check(self.lib.biofvm_set_sources(
+            self.h, n, vox.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)) if n else None,
+            *[_dptr(a) for a in arrs], _dptr(w)), self.lib)
+
+    def set_params(self, D, lam):
+        ns = self.shape[3]
+        _check(self.lib.biofvm_set_params(self.h, _dptr(_f64(D, ns)), _dptr(_f64(lam, ns))),
+               self.lib)
+
+    # -- stepping ---------------------------------------------------------------------------
+    def step(self, n_steps=1):
+        _check(self.lib.biofvm_step(self.h, int(n_steps)), self.lib)
+
+    def run_stage(self, stage):
+        _check(self.lib.biofvm_run_stage(self.h, int(stage)), self.lib)
+
+    def sync(self):
+        _check(self.lib.biofvm_sync(self.h), self.lib)
+
+    def launches_per_step(self):
+        return int(self.lib.biofvm_launches_per_step(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.biofvm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @classmethod
+    def from_workload(cls, w, precision="fp64", stream=None):
+        """Create, upload the initial field and the agents of an ``inputs.Workload``."""
+        sim = cls(w.nx, w.ny, w.nz, w.ns, w.dx, w.dt, w.D, w.lam, w.dirichlet_on,
+                  w.dirichlet_value, precision=precision, stream=stream)
+        if w.rho0 is not None:
+            sim.set_density(w.rho0)
+        if w.n_agents:
+            sim.set_sources(w.voxel, w.secretion, w.target, w.uptake, w.weight)
+        return sim

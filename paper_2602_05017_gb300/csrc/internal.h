@@ -1,0 +1,90 @@
+// Internal interface between the host half of libbiofvm (api.cpp) and the
+// sweep kernels (sweeps_fp64.cu, sweeps_fp32.cu).  Not installed; the public
+// C ABI is include/biofvm.h.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace bfv {
+
+// Stage flags of the x-sweep kernel (the kernel that also owns Src and the
+// first two Dirichlet applications of a step).
+enum : int {
+  kSrc = 1,        // rho <- (rho + alpha) * scale on the listed elements
+  kDirBefore = 2,  // Dirichlet application before the solve
+  kSolve = 4,      // Thomas solve along the axis
+  kDirAfter = 8,   // Dirichlet application after the solve
+};
+
+// Status word values written by kernels (mirror biofvm_status).
+enum : int { kStatusOk = 0, kStatusTimeout = 4 };
+
+// Thomas constants of one axis, element type E, layout [i][S] (position-major,
+// substrate fastest), computed in double on the host (App. A) and rounded:
+//   inv[i]  = 1/denom_i           mul[i] = r/denom_i = -c'_i
+//   pf[i]   = prod_{l=lo(i)}^{i} mul_l     (forward carry weight in a chunk)
+//   pb[i]   = prod_{l=i}^{hi(i)} mul_l     (backward carry weight in a chunk)
+//   pc[t]   = prod over chunk t of mul_l   (layout [t][S])
+// where the axis is cut into T chunks of m positions (the last may be short).
+//
+// FP32 path (defect-correction form): the zero-flux rows of A = (1 + lam3) I
+// + r L_N sum to 1 + lam3, so A^-1 d = c d - c r A^-1 (L_N d), c = 1/(1+lam3).
+// The kernels solve for the small correction y = (-c r) A^-1 (L_N d) -- inv
+// then holds (-c r)/denom_i -- and form x = c_hi d + (c_lo d + y) with one
+// final rounding; cfix = [c_hi[S], c_lo[S]].  Plain FP32 Thomas accumulates a
+// rounding bias along smooth lines (about 3e-5 after 300 sweeps); this form
+// stays at the storage-rounding level (about 2e-7).
+struct AxisTab {
+  const void *inv, *mul, *pf, *pb, *pc, *cfix;
+  int n, T, m;
+};
+
+// x-sweep launch: rows (y, z) of nx*S contiguous elements, rows_per_cta rows
+// staged per CTA; a row's S lines are cut into T segments, one lane each.
+struct XLaunch {
+  void *rho;
+  int nx, ny, nz, S;
+  AxisTab tab;
+  int rows_per_cta, rows_per_warp, warps, maxm;
+  int use_bulk;        // tile staged with cp.async.bulk (16-byte aligned rows)
+  size_t smem_bytes;
+  int flags;
+  // sources: CSR over rows; element index (global); alpha; scale = 1/(1+beta)
+  const int64_t *src_row_off;
+  const int64_t *src_elem;
+  const void *src_alpha, *src_scale;
+  int has_src;
+  const uint8_t *dir_on;
+  const void *dir_val;
+  int *status;
+};
+
+// y- or z-sweep launch: lines are columns of a plane, column c at
+// plane*plane_stride + j*C + c for j = 0..n-1 (C = stride between positions).
+struct ColLaunch {
+  void *rho;
+  int64_t C, plane_stride;
+  int nplanes, n, S;
+  int mode;  // 1 = y-sweep (plane = z, column -> x), 2 = z-sweep (column -> x, y)
+  int nx, ny, nz;
+  AxisTab tab;
+  int maxm;
+  int flags;  // kSolve | kDirAfter
+  const uint8_t *dir_on;
+  const void *dir_val;
+};
+
+// Register-chunk capacities compiled for each precision (ascending).
+constexpr int kMaxmF64[] = {8, 16, 24, 32, 48, 64};
+constexpr int kMaxmF32[] = {8, 16, 24, 32, 48, 64, 96, 128};
+
+// Raise the dynamic shared-memory limit of the x-sweep instantiation for
+// chunk capacity maxm (called once per handle, outside any graph capture).
+cudaError_t allow_x_smem_f64(int maxm, size_t bytes);
+cudaError_t allow_x_smem_f32(int maxm, size_t bytes);
+cudaError_t launch_x_f64(const XLaunch &a, cudaStream_t st);
+cudaError_t launch_x_f32(const XLaunch &a, cudaStream_t st);
+cudaError_t launch_col_f64(const ColLaunch &a, cudaStream_t st);
+cudaError_t launch_col_f32(const ColLaunch &a, cudaStream_t st);
+
+}  // namespace bfv

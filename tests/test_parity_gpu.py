@@ -1,0 +1,245 @@
+"""GPU parity of libbiofvm against the FP64 CPU oracle, through the C ABI.
+
+Error measure (normwise): max |rho_gpu - rho_oracle| / max |rho_oracle|.
+  FP64 path: <= 1e-12.  Thomas in double has a backward error of a few ulp per line and the
+  solves are contractive (diagonally dominant M-matrices), so the forward error of a step stays
+  within ~1e-15 relative; 1e-12 leaves room for many steps and chunked reassociation.
+  FP32 path: <= 1e-5 after 100 steps (storage and arithmetic in float; constants from double).
+At full workload sizes, where the oracle would take hours, parity is checked on one full step
+(workload 2) and, over all steps, through closed forms that hold at any size (uniform-field
+decay, cosine-mode decay, Dirichlet steady state).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2602_05017_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "fp32": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def binding():
+    from paper_2602_05017_gb300 import binding as b
+    return b
+
+
+def rel_err(got, ref):
+    got = np.asarray(got, dtype=np.float64)
+    return float(np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-300))
+
+
+def gpu_run(binding, w, prec, n_steps=1, rho=None):
+    sim = binding.BioFVM.from_workload(w, precision=prec)
+    if rho is not None:
+        sim.set_density(rho)
+    sim.step(n_steps)
+    out = sim.density().astype(np.float64)
+    sim.close()
+    return out
+
+
+def orc(w):
+    return oracle.Problem(**w.oracle_kwargs())
+
+
+SHAPES = [
+    (37, 23, 19, 3), (1, 9, 7, 2), (8, 1, 5, 1), (6, 5, 1, 4), (1, 1, 1, 1), (2, 2, 2, 5),
+    (65, 33, 17, 2), (200, 7, 9, 1), (9, 130, 11, 2), (5, 7, 300, 1), (64, 12, 10, 8),
+    (31, 3, 4, 7), (513, 3, 2, 1), (50, 50, 50, 1),
+]
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_step_matches_oracle(binding, shape, prec):
+    nx, ny, nz, ns = shape
+    rng = np.random.default_rng(hash(shape) % 2**32)
+    w = inputs.random_problem(rng, nx, ny, nz, ns, n_agents=max(1, nx * ny * nz // 20),
+                              dirichlet=True)
+    ref = orc(w).step(w.rho0, 2)
+    got = gpu_run(binding, w, prec, 2)
+    assert rel_err(got, ref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("shape", [(37, 23, 19, 3), (1, 9, 7, 2), (200, 7, 9, 1), (9, 70, 130, 2)],
+                         ids=lambda s: "x".join(map(str, s)))
+def test_each_stage_matches_oracle(binding, shape):
+    nx, ny, nz, ns = shape
+    rng = np.random.default_rng(11)
+    w = inputs.random_problem(rng, nx, ny, nz, ns, n_agents=50, dirichlet=True)
+    p = orc(w)
+    expect = {
+        4: lambda u: p.sources(u),
+        5: lambda u: p.sweep(0, u),
+        6: lambda u: p.sweep(1, u),
+        7: lambda u: p.sweep(2, u),
+        0: lambda u: p.dirichlet(p.sources(u)),
+        1: lambda u: p.dirichlet(p.sweep(0, u)),
+        2: lambda u: p.dirichlet(p.sweep(1, u)),
+        3: lambda u: p.dirichlet(p.sweep(2, u)),
+    }
+    for stage, fn in expect.items():
+        sim = binding.BioFVM.from_workload(w, precision="fp64")
+        sim.run_stage(stage)
+        got = sim.density()
+        sim.close()
+        assert rel_err(got, fn(w.rho0)) <= 1e-13, stage
+
+
+def test_graph_steps_equal_stage_sequence(binding):
+    rng = np.random.default_rng(3)
+    w = inputs.random_problem(rng, 21, 17, 13, 2, n_agents=30, dirichlet=True)
+    a = gpu_run(binding, w, "fp64", 3)
+    sim = binding.BioFVM.from_workload(w, precision="fp64")
+    for _ in range(3):
+        for stage in (0, 1, 2, 3):
+            sim.run_stage(stage)
+    b = sim.density()
+    sim.close()
+    assert np.array_equal(a, b)
+
+
+def test_sources_can_be_replaced_and_cleared(binding):
+    rng = np.random.default_rng(4)
+    w = inputs.random_problem(rng, 12, 11, 10, 2, n_agents=40)
+    sim = binding.BioFVM.from_workload(w, precision="fp64")
+    sim.set_sources([])  # no agents
+    sim.step(2)
+    got = sim.density()
+    sim.close()
+    w2 = inputs.random_problem(np.random.default_rng(4), 12, 11, 10, 2)
+    assert rel_err(got, orc(w2).step(w.rho0, 2)) <= 1e-12
+
+
+def test_set_params_recomputes_constants(binding):
+    rng = np.random.default_rng(5)
+    w = inputs.random_problem(rng, 16, 15, 14, 3, n_agents=20)
+    sim = binding.BioFVM.from_workload(w, precision="fp64")
+    w.D = w.D * 3.0
+    w.lam = w.lam * 0.5
+    sim.set_params(w.D, w.lam)
+    sim.step(2)
+    got = sim.density()
+    sim.close()
+    assert rel_err(got, orc(w).step(w.rho0, 2)) <= 1e-12
+
+
+def test_torch_device_tensors_roundtrip(binding):
+    import torch
+    rng = np.random.default_rng(6)
+    w = inputs.random_problem(rng, 20, 10, 6, 2)
+    sim = binding.BioFVM(w.nx, w.ny, w.nz, w.ns, w.dx, w.dt, w.D, w.lam)
+    t = torch.from_numpy(w.rho0).cuda()
+    sim.set_density(t)
+    sim.step(1)
+    out = torch.empty_like(t)
+    sim.density(out)
+    view = sim.field_tensor()
+    assert torch.equal(view, out)
+    assert rel_err(out.cpu().numpy(), orc(w).step(w.rho0, 1)) <= 1e-12
+    sim.close()
+
+
+# ------------------------------------------------------------------------------------------------
+# The workloads: small one in full, the others at reduced size and (properties) at full size.
+# ------------------------------------------------------------------------------------------------
+
+def test_workload1_full_100_steps_fp64(binding):
+    w = inputs.workload(1)
+    ref = orc(w).step(w.rho0, w.n_steps)
+    got = gpu_run(binding, w, "fp64", w.n_steps)
+    assert rel_err(got, ref) <= 1e-12
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_workload2_reduced_100_steps(binding, prec):
+    w = inputs.workload(2, shape=(48, 40, 36), n_agents=3000)
+    ref = orc(w).step(w.rho0, w.n_steps)
+    got = gpu_run(binding, w, prec, w.n_steps)
+    assert rel_err(got, ref) <= TOL[prec]
+
+
+@pytest.mark.slow
+def test_workload2_full_size_one_step_fp64(binding):
+    """400^3 x 4 with 1M agents: one whole step against the oracle, every element."""
+    w = inputs.workload(2)
+    ref = orc(w).step(w.rho0, 1)
+    got = gpu_run(binding, w, "fp64", 1)
+    assert rel_err(got, ref) <= 1e-12
+
+
+def _cosine_field(shape, k):
+    nz, ny, nx, ns = shape
+    fx = np.cos(k[0] * np.pi * (np.arange(nx) + 0.5) / nx)
+    fy = np.cos(k[1] * np.pi * (np.arange(ny) + 0.5) / ny)
+    fz = np.cos(k[2] * np.pi * (np.arange(nz) + 0.5) / nz)
+    return fz[:, None, None, None] * fy[None, :, None, None] * fx[None, None, :, None]
+
+
+def _mode_factor(w, s, k):
+    r = w.D[s] * w.dt / w.dx ** 2
+    f = 1.0
+    for n, kd in zip((w.nx, w.ny, w.nz), k):
+        f /= 1.0 + w.lam[s] * w.dt / 3.0 + 2.0 * r * (1.0 - np.cos(kd * np.pi / n))
+    return f
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_workload2_full_size_100_steps_cosine_mode(binding, prec):
+    """400^3 x 4, 100 steps, no agents: a separable cosine mode decays by the closed form."""
+    import torch
+    w = inputs.workload(2, with_field=False, n_agents=0)
+    w.voxel = None
+    k = (3, 1, 7)
+    base = _cosine_field(w.shape, k)
+    field = np.broadcast_to(38.0 * base, w.shape)
+    sim = binding.BioFVM.from_workload(w, precision=prec)
+    sim.set_density(torch.from_numpy(np.ascontiguousarray(field)).cuda())
+    sim.step(w.n_steps)
+    got = sim.field_tensor().double().cpu().numpy()
+    sim.close()
+    for s in range(w.ns):
+        expect = 38.0 * base[..., 0] * _mode_factor(w, s, k) ** w.n_steps
+        err = np.abs(got[..., s] - expect).max() / 38.0
+        assert err <= TOL[prec], (s, err)
+
+
+def test_workload3_reduced_20_steps_fp32(binding):
+    w = inputs.workload(3, shape=(96, 80, 72), n_agents=20000)
+    ref = orc(w).step(w.rho0, w.n_steps)
+    got = gpu_run(binding, w, "fp32", w.n_steps)
+    assert rel_err(got, ref) <= 1e-5
+
+
+@pytest.mark.slow
+def test_workload3_full_size_20_steps_fp32_properties(binding):
+    """1200^3 x 2 FP32 (13.8 GB): substrate 0, uniform at its Dirichlet value 38 with its decay
+    switched off, stays 38 (a steady state); substrate 1 (zero flux) carries a cosine mode that
+    decays by the closed form."""
+    import torch
+    w = inputs.workload(3, with_field=False, n_agents=0)
+    w.voxel = None
+    w.lam = np.array([0.0, w.lam[1]])
+    k = (2, 5, 1)
+    nz, ny, nx, _ = w.shape
+    fx = torch.cos(k[0] * torch.pi * (torch.arange(nx, device="cuda") + 0.5) / nx)
+    fy = torch.cos(k[1] * torch.pi * (torch.arange(ny, device="cuda") + 0.5) / ny)
+    fz = torch.cos(k[2] * torch.pi * (torch.arange(nz, device="cuda") + 0.5) / nz)
+    sim = binding.BioFVM.from_workload(w, precision="fp32")
+    f = sim.field_tensor()
+    f[..., 0] = 38.0
+    f[..., 1] = 38.0 * fz[:, None, None] * fy[None, :, None] * fx[None, None, :]
+    torch.cuda.synchronize()
+    sim.step(w.n_steps)
+    sim.sync()
+    f = sim.field_tensor()
+    assert float((f[..., 0] - 38.0).abs().max()) <= 38.0 * 1e-5
+    expect = (38.0 * _mode_factor(w, 1, k) ** w.n_steps) * (
+        fz[:, None, None] * fy[None, :, None] * fx[None, None, :])
+    err = float((f[..., 1].double() - expect.double()).abs().max()) / 38.0
+    sim.close()
+    assert err <= 1e-5
