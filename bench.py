@@ -94,9 +94,15 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+SHAPE = None  # --shape overrides the grid (profiling a smaller case of the same recipe)
+
+
 def workload_config():
     from paper_2602_05017_gb300 import inputs
-    return inputs.workload(2, with_field=False)
+    if SHAPE is None:
+        return inputs.workload(2, with_field=False)
+    nvox = SHAPE[0] * SHAPE[1] * SHAPE[2]
+    return inputs.workload(2, shape=SHAPE, with_field=False, n_agents=nvox // 64)
 
 
 def run_gpu(args):
@@ -121,7 +127,7 @@ def run_gpu(args):
             dist.barrier()
 
     results = {}
-    for prec in ("fp64", "fp32"):
+    for prec in args.only or ("fp64", "fp32"):
         esz = 8 if prec == "fp64" else 4
         tdt = torch.float64 if prec == "fp64" else torch.float32
         sim = binding.BioFVM(w.nx, w.ny, w.nz, w.ns, w.dx, w.dt, w.D, w.lam, precision=prec,
@@ -186,9 +192,57 @@ def run_gpu(args):
         torch.cuda.empty_cache()
         results[prec] = res
         barrier()
+    if not args.no_batch and not args.shape and not args.only:
+        results["fp32_batched"] = run_batched(args, stream, dev)
     if world > 1:
         dist.destroy_process_group()
     return rank, world, results
+
+
+def run_batched(args, stream, dev):
+    """256 uneven FP32 microenvironments, 50 steps per launch, tiles from the autotuner."""
+    import torch
+
+    from paper_2602_05017_gb300 import autotune, binding, inputs
+    envs = inputs.batched_workloads(n_env=args.batch_envs, with_field=False,
+                                    n_steps=args.batch_steps)
+    cache_path = autotune.default_cache_path()
+    if os.path.exists(cache_path):
+        cache, tuned = autotune.load(cache_path), "cache"
+    else:
+        cache, tuned = autotune.tune("fp32", reps=2), "tuned in this run"
+    shapes = autotune.tile_shapes(envs, cache)
+    b = binding.BioFVMBatch(envs, precision="fp32", tile_m=shapes, stream=stream.cuda_stream)
+    g = torch.Generator(device=dev)
+    g.manual_seed(2602050174)
+    for sim, w in zip(b.envs, envs):
+        with torch.cuda.stream(stream):
+            sim.field_tensor().uniform_(0.0, 38.0, generator=g)
+        sim.set_sources(w.voxel, w.secretion, w.target, w.uptake)
+    stream.synchronize()
+    b.step(args.warmup)
+    b.sync()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    K = args.batch_steps
+    with ClockSampler(dev.index or 0) as clk:
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        b.step(K)
+        e1.record(stream)
+        e1.synchronize()
+    b.sync()
+    ms = e0.elapsed_time(e1)
+    n_vs = b.n_vs
+    out = {"value": n_vs * K / (ms * 1e-3), "unit": UNIT, "dtype": "f32", "ms_per_step": ms / K,
+           "steps": K, "n_env": len(envs), "voxel_substrates": n_vs,
+           "launches": 1, "grid": b.grid(), "tiles": tuned,
+           "alg_GBps": 24.0 * n_vs * K / (ms * 1e-3) / 1e9, "clocks": clk.summary(),
+           "workload": "256 cubes, edge U{32..192}, 1-8 substrates, D logU[1e2,1e5], "
+                       "lambda logU[1e-3,1], agents 1 per 64 voxels, zero-flux"}
+    b.close()
+    torch.cuda.empty_cache()
+    return out
 
 
 def _stage_step(sim, ev, stream):
@@ -266,13 +320,25 @@ def main():
     ap.add_argument("--e2e-reps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-envs", type=int, default=256)
+    ap.add_argument("--batch-steps", type=int, default=50)
+    ap.add_argument("--shape", type=int, nargs=3, metavar=("NX", "NY", "NZ"),
+                    help="smaller grid of the same recipe (profiling only; not a bench line)")
+    ap.add_argument("--only", nargs="+", choices=["fp64", "fp32"],
+                    help="run only these precisions (profiling only; not a bench line)")
     args = ap.parse_args()
+    global SHAPE
+    SHAPE = tuple(args.shape) if args.shape else None
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
     rank, world, res = run_gpu(args)
     if rank != 0:
+        return 0
+    if args.only or args.shape:  # profiling run: per-precision numbers only
+        print(json.dumps({"profiling_run": True, "shape": SHAPE, "results": res}), flush=True)
         return 0
     peaks, src = measured_peaks()
     w = workload_config()
@@ -294,6 +360,10 @@ def main():
                     "dtype": "f32", "roofline": roofline(res["fp32"], w, peaks, src),
                     "e2e": res["fp32"].get("e2e"), "clocks": res["fp32"]["clocks"],
                     "vs_fp64": res["fp32"]["value"] / r64["value"]}
+    if "fp32_batched" in res:
+        bt = dict(res["fp32_batched"])
+        bt["vs_fp64"] = bt["value"] / r64["value"]
+        line["fp32_batched"] = bt
     line["kernel_ms"] = {"fp64": dict(zip(("x", "y", "z"), r64["kernel_ms"])),
                          "fp32": dict(zip(("x", "y", "z"), res["fp32"]["kernel_ms"]))}
     if not args.no_cpu:

@@ -131,6 +131,28 @@ biofvm_status biofvm_set_params(biofvm_t *h, const double *D,
  * Errors: ARG, CUDA. */
 biofvm_status biofvm_run_stage(biofvm_t *h, int stage);
 
+/* One time step, like biofvm_step(h, 1), that also writes the forward states
+ * the adjoint of that step needs into `saved` (device, 4*nx*ny*nz*n_sub
+ * elements of the handle's type, layout [4][field]): [0] the source output
+ * (before its Dirichlet application), [1] the X^-1 output, [2] the Y^-1
+ * output, [3] the Z^-1 output (each before the B that follows it).  Async.
+ * Errors: ARG, CUDA. */
+biofvm_status biofvm_step_save(biofvm_t *h, void *saved);
+
+/* Reverse mode of one step (the stages of Sect. 2 transposed; each 1D matrix
+ * of App. A is symmetric, so the adjoint sweeps are the forward sweeps run in
+ * the order Z, Y, X).  grad_out: adjoint of the step's output; grad_in:
+ * receives the adjoint of the step's input (may equal grad_out); saved: the
+ * states biofvm_step_save wrote for this step.  All three are device arrays
+ * in the field layout and type.  ACCUMULATES (+=) into device FP64 arrays:
+ * dD[n_sub], dlambda[n_sub] (reduced in a fixed order: bit-reproducible), and,
+ * if dsecretion is not NULL, dsecretion[n_agents*n_sub], the gradient with
+ * respect to each agent's secretion rate (agents as last passed to
+ * biofvm_set_sources).  The first call allocates the adjoint field and a
+ * small reduction buffer.  Async.  Errors: ARG, OOM, CUDA. */
+biofvm_status biofvm_adjoint_step(biofvm_t *h, const void *grad_out, void *grad_in, double *dD,
+                                  double *dlambda, double *dsecretion, const void *saved);
+
 /* Wait for the handle's stream and check the device status word.
  * Errors: CUDA, TIMEOUT. */
 biofvm_status biofvm_sync(biofvm_t *h);
@@ -142,6 +164,49 @@ biofvm_status biofvm_density_ptr(biofvm_t *h, void **dev_ptr);
 
 /* Number of kernel launches one time step makes (3: x-, y-, z-sweep). */
 int biofvm_launches_per_step(const biofvm_t *h);
+
+/* ------------------------------------------------------------------------
+ * Batched microenvironments: many independent grids of uneven size and
+ * substrate count, advanced together by ONE persistent kernel launch per
+ * biofvm_batch_step call (all environments, all steps; captured in a CUDA
+ * graph).  Each environment is an ordinary handle (zero-flux boundaries)
+ * reachable through biofvm_batch_env, so biofvm_set_density,
+ * biofvm_set_sources, biofvm_density (and even biofvm_step) work on it.
+ * ---------------------------------------------------------------------- */
+typedef struct biofvm_batch biofvm_batch_t;
+
+/* Create n_env >= 1 environments: grids[e] (host), dx[e], dt[e], and
+ * D_flat / lambda_flat holding the n_sub of environment 0, then of
+ * environment 1, ... (host).  tile_m: NULL or [n_env][3] chunk lengths of the
+ * partitioned solve along x, y, z per environment (<= 0 picks a default; each
+ * axis must give at most 8 chunks of at most 48 positions) -- the tile shapes
+ * an autotuner chooses.  All environments share `prec` and the stream.
+ * Errors: ARG, OOM, CUDA (with the failing environment in the message). */
+biofvm_status biofvm_batch_create(int n_env, const biofvm_grid *grids, const double *dx,
+                                  const double *dt, const double *D_flat,
+                                  const double *lambda_flat, biofvm_precision prec,
+                                  uintptr_t cuda_stream, const int *tile_m,
+                                  biofvm_batch_t **out);
+
+/* The handle of environment e (owned by the batch; do not destroy it). */
+biofvm_status biofvm_batch_env(biofvm_batch_t *b, int e, biofvm_t **env);
+
+/* Advance every environment n_steps >= 0 steps in one persistent launch
+ * (async).  Work items (step, sweep, environment, tile of 32 lines) are
+ * spread over a resident grid; each waits, with a bounded spin, for the
+ * previous sweep of its own environment.  Errors: ARG, CUDA; a timed-out wait
+ * is reported by biofvm_batch_sync as TIMEOUT. */
+biofvm_status biofvm_batch_step(biofvm_batch_t *b, int n_steps);
+
+/* Wait for the batch's stream and check its status word.  Errors: CUDA,
+ * TIMEOUT. */
+biofvm_status biofvm_batch_sync(biofvm_batch_t *b);
+
+/* CTAs of the persistent batched launch (resident at once). */
+int biofvm_batch_grid(const biofvm_batch_t *b);
+
+/* Free the batch and every environment (waits for the stream). */
+void biofvm_batch_destroy(biofvm_batch_t *b);
 
 /* Free the handle and all device memory it owns (waits for its stream).
  * NULL is a no-op. */

@@ -1,0 +1,119 @@
+"""Autotuner for the tile shapes of the batched persistent step.
+
+The tunable shape of an environment is the chunk length of the partitioned Thomas solve along
+each axis (a line of n voxels is cut into ceil(n/m) chunks, one warp each, at most 8): it sets
+the registers per thread, the warps per tile and the length of the serial recurrences.  For each
+class (edge-length bucket, substrate count) the tuner builds a batch of identical environments
+large enough to fill the GPU, times the candidates with CUDA events (y/z chunk first, then x),
+and records the fastest in a JSON cache.  ``tile_shapes`` maps any list of environments to
+per-environment chunk lengths from that cache.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+import time
+
+import numpy as np
+
+from . import inputs
+
+N_BUCKETS = (32, 64, 96, 128, 160, 192)
+MAX_CHUNKS = 8     # warps of the batched CTA
+MAX_CHUNK = 48     # largest register chunk compiled for the batched kernel
+
+
+def candidates(n):
+    """Valid chunk lengths for an axis of n voxels (at most MAX_CHUNKS chunks)."""
+    lo = max(4, math.ceil(n / MAX_CHUNKS))
+    out = sorted({min(c, MAX_CHUNK, n) for c in (lo, math.ceil(1.5 * lo), 2 * lo, 3 * lo)})
+    return [c for c in out if c >= math.ceil(n / MAX_CHUNKS)]
+
+
+def _bucket(n):
+    return min(N_BUCKETS, key=lambda b: (abs(b - n), b))
+
+
+def _time_batch(binding, torch, envs, tile_m, precision, steps, reps):
+    b = binding.BioFVMBatch(envs, precision=precision, tile_m=tile_m)
+    try:
+        for e in b.envs:
+            f = e.field_tensor()
+            f.uniform_(0.0, 38.0)
+        torch.cuda.synchronize()
+        b.step(1)
+        b.sync()
+        best = float("inf")
+        st = torch.cuda.current_stream()
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            b.step(steps)
+            e1.record(st)
+            b.sync()
+            best = min(best, e0.elapsed_time(e1) / steps)
+        return b.n_vs / (best * 1e-3)
+    finally:
+        b.close()
+
+
+def tune(precision="fp32", n_buckets=N_BUCKETS, subs=range(1, 9), target_vs=1.2e8, steps=3,
+         reps=3, path=None, log=None):
+    """Time the candidates of every class; returns and (if path) writes the cache."""
+    import torch
+
+    from . import binding
+    cache = {"version": 1, "precision": precision, "device": torch.cuda.get_device_name(),
+             "when": time.strftime("%Y-%m-%dT%H:%M:%S"), "classes": {}}
+    for n in n_buckets:
+        for S in subs:
+            k = max(1, min(32, int(target_vs // (n ** 3 * S))))
+            envs = [inputs.Workload(f"tune{n}_{S}", n, n, n, S, 20.0, 0.01, np.full(S, 1e4),
+                                    np.full(S, 0.1), 1) for _ in range(k)]
+            cands = candidates(n)
+            m_x = cands[0]
+            best_yz, best_rate = cands[0], -1.0
+            for myz in cands:
+                rate = _time_batch(binding, torch, envs, [[m_x, myz, myz]] * k, precision, steps,
+                                   reps)
+                if rate > best_rate:
+                    best_yz, best_rate = myz, rate
+            best_x = m_x
+            for mx in cands[1:]:
+                rate = _time_batch(binding, torch, envs, [[mx, best_yz, best_yz]] * k, precision,
+                                   steps, reps)
+                if rate > best_rate:
+                    best_x, best_rate = mx, rate
+            cache["classes"][f"{n},{S}"] = {"m": [best_x, best_yz, best_yz],
+                                            "vs_per_s": best_rate, "envs": k}
+            if log:
+                log(f"tune n={n} S={S}: m={[best_x, best_yz, best_yz]} {best_rate:.3e} vs/s")
+    if path:
+        with open(path, "w") as f:
+            json.dump(cache, f, indent=1)
+    return cache
+
+
+def load(path):
+    with open(path) as f:
+        return json.load(f)
+
+
+def tile_shapes(envs, cache):
+    """Per-environment [m_x, m_y, m_z] from a cache (nearest class), kept valid for each axis."""
+    out = []
+    for w in envs:
+        entry = cache["classes"].get(f"{_bucket(max(w.nx, w.ny, w.nz))},{min(max(w.ns, 1), 8)}")
+        m = entry["m"] if entry else [0, 0, 0]
+        row = []
+        for mm, n in zip(m, (w.nx, w.ny, w.nz)):
+            lo = math.ceil(n / MAX_CHUNKS)
+            row.append(int(min(MAX_CHUNK, max(mm, lo, 1))) if mm > 0 else 0)
+        out.append(row)
+    return out
+
+
+def default_cache_path():
+    return os.path.join(os.path.dirname(os.path.abspath(__file__)), "tune_cache.json")

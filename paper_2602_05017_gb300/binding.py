@@ -73,6 +73,16 @@ def load():
         "biofvm_sync": (st, [vp]),
         "biofvm_density_ptr": (st, [vp, ctypes.POINTER(vp)]),
         "biofvm_launches_per_step": (ctypes.c_int, [vp]),
+        "biofvm_step_save": (st, [vp, vp]),
+        "biofvm_adjoint_step": (st, [vp, vp, vp, vp, vp, vp, vp]),
+        "biofvm_batch_create": (st, [ctypes.c_int, ctypes.POINTER(Grid), dp, dp, dp, dp,
+                                     ctypes.c_int, ctypes.c_size_t,
+                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(vp)]),
+        "biofvm_batch_env": (st, [vp, ctypes.c_int, ctypes.POINTER(vp)]),
+        "biofvm_batch_step": (st, [vp, ctypes.c_int]),
+        "biofvm_batch_sync": (st, [vp]),
+        "biofvm_batch_grid": (ctypes.c_int, [vp]),
+        "biofvm_batch_destroy": (None, [vp]),
         "biofvm_destroy": (None, [vp]),
         "biofvm_last_error": (ctypes.c_char_p, []),
     }
@@ -113,12 +123,17 @@ class BioFVM:
     """
 
     def __init__(self, nx, ny, nz, n_sub, dx, dt, D, lam, dirichlet_on=None,
-                 dirichlet_value=None, precision="fp64", stream=None):
+                 dirichlet_value=None, precision="fp64", stream=None, _handle=None):
         self.lib = load()
         self.shape = (int(nz), int(ny), int(nx), int(n_sub))
         self.precision = precision
         self.dtype = np.float64 if precision == "fp64" else np.float32
         self.n_elem = int(np.prod(self.shape))
+        self._owned = _handle is None
+        if _handle is not None:  # an environment of a batch (the batch owns it)
+            self.stream = stream
+            self.h = _handle
+            return
         grid = Grid(int(nx), int(ny), int(nz), int(n_sub))
         D = _f64(D, n_sub)
         lam = _f64(lam, n_sub)
@@ -213,6 +228,34 @@ class BioFVM:
     def step(self, n_steps=1):
         _check(self.lib.biofvm_step(self.h, int(n_steps)), self.lib)
 
+    def _dev(self, t, n, dtype):
+        import torch
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
+            raise ValueError("expected a contiguous CUDA tensor")
+        if t.dtype != dtype or t.numel() != n:
+            raise ValueError(f"expected {n} elements of {dtype}, got {t.numel()} of {t.dtype}")
+        return ctypes.c_void_p(t.data_ptr())
+
+    def _field_dtype(self):
+        import torch
+        return torch.float64 if self.precision == "fp64" else torch.float32
+
+    def step_save(self, saved):
+        """One step that also writes the adjoint's forward states into `saved` (4 fields)."""
+        _check(self.lib.biofvm_step_save(self.h, self._dev(saved, 4 * self.n_elem,
+                                                              self._field_dtype())), self.lib)
+
+    def adjoint_step(self, grad_out, grad_in, dD, dlam, dsec, saved):
+        """Reverse mode of one step; accumulates into dD, dlam (and dsec if given), FP64 CUDA."""
+        import torch
+        fd = self._field_dtype()
+        ns = self.shape[3]
+        _check(self.lib.biofvm_adjoint_step(
+            self.h, self._dev(grad_out, self.n_elem, fd), self._dev(grad_in, self.n_elem, fd),
+            self._dev(dD, ns, torch.float64), self._dev(dlam, ns, torch.float64),
+            None if dsec is None else self._dev(dsec, dsec.numel(), torch.float64),
+            self._dev(saved, 4 * self.n_elem, fd)), self.lib)
+
     def run_stage(self, stage):
         _check(self.lib.biofvm_run_stage(self.h, int(stage)), self.lib)
 
@@ -224,7 +267,8 @@ class BioFVM:
 
     def close(self):
         if getattr(self, "h", None):
-            self.lib.biofvm_destroy(self.h)
+            if self._owned:
+                self.lib.biofvm_destroy(self.h)
             self.h = None
 
     def __del__(self):  # pragma: no cover
@@ -243,3 +287,63 @@ class BioFVM:
         if w.n_agents:
             sim.set_sources(w.voxel, w.secretion, w.target, w.uptake, w.weight)
         return sim
+
+
+class BioFVMBatch:
+    """Many microenvironments advanced by one persistent launch per step() call.
+
+    envs: list of ``inputs.Workload`` (grids, dx, dt, D, lambda; zero-flux).  tile_m: optional
+    [n_env][3] chunk lengths (x, y, z) -- from ``autotune`` -- else library defaults.
+    """
+
+    def __init__(self, envs, precision="fp32", tile_m=None, stream=None):
+        self.lib = load()
+        n = len(envs)
+        grids = (Grid * n)(*[Grid(w.nx, w.ny, w.nz, w.ns) for w in envs])
+        dx = _f64([w.dx for w in envs])
+        dt = _f64([w.dt for w in envs])
+        D = _f64(np.concatenate([np.asarray(w.D, dtype=np.float64) for w in envs]))
+        lam = _f64(np.concatenate([np.asarray(w.lam, dtype=np.float64) for w in envs]))
+        tm = None
+        if tile_m is not None:
+            self._tm = np.ascontiguousarray(np.asarray(tile_m, dtype=np.int32).reshape(n, 3))
+            tm = self._tm.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        self.stream = _current_stream() if stream is None else int(stream)
+        h = ctypes.c_void_p()
+        _check(self.lib.biofvm_batch_create(n, grids, _dptr(dx), _dptr(dt), _dptr(D), _dptr(lam),
+                                            FP64 if precision == "fp64" else FP32, self.stream,
+                                            tm, ctypes.byref(h)), self.lib)
+        self.h = h
+        self.precision = precision
+        self.envs = []
+        for e, w in enumerate(envs):
+            eh = ctypes.c_void_p()
+            _check(self.lib.biofvm_batch_env(self.h, e, ctypes.byref(eh)), self.lib)
+            self.envs.append(BioFVM(w.nx, w.ny, w.nz, w.ns, w.dx, w.dt, w.D, w.lam,
+                                    precision=precision, stream=self.stream, _handle=eh))
+
+    @property
+    def n_vs(self):
+        return sum(e.n_elem for e in self.envs)
+
+    def step(self, n_steps=1):
+        _check(self.lib.biofvm_batch_step(self.h, int(n_steps)), self.lib)
+
+    def sync(self):
+        _check(self.lib.biofvm_batch_sync(self.h), self.lib)
+
+    def grid(self):
+        return int(self.lib.biofvm_batch_grid(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            for e in self.envs:
+                e.h = None
+            self.lib.biofvm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -12,11 +12,14 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
 
 #include "../../include/biofvm.h"
+#include "batch_args.h"
+#include "pipe_args.h"
 #include "internal.h"
 
 using namespace bfv;
@@ -64,6 +67,17 @@ cudaError_t dev_alloc(DevBuf &b, size_t bytes) {
 struct ColPlan {
   int T = 1, m = 1, maxm = 8;
 };
+// Persistent TMA pipeline of one sweep (used when rows are 16-byte aligned and
+// a ring of >= 2 stages fits in shared memory; otherwise the plain kernels).
+struct PipePlan {
+  int use = 0, T = 1, m = 1, maxm = 8;
+  int box_rows = 0, nbox = 0, rows_per_tile = 0, pitch = 0;
+  int stages = 0, tab_in_smem = 0, grid = 0;
+  int64_t stage_elems = 0, ntiles = 0;
+  size_t smem = 0;
+  CUtensorMap map[2]{};  // y/z: [0] the field, [1] the adjoint field
+  int have_map[2]{};
+};
 struct XPlan {
   int T = 1, m = 1, maxm = 8, rows_per_warp = 1, warps = 1, rows_per_cta = 1, use_bulk = 0;
   size_t smem = 0;
@@ -87,11 +101,22 @@ struct biofvm {
   DevBuf rho, tab[3], dir_on_d, dir_val_d, status;
   XPlan xp;
   ColPlan cp[3];  // [1] = y, [2] = z
+  PipePlan pp[3];
+  int num_sms = 0;
+  int pipe_enabled = 1;
+  int forced = 0;  // chunk lengths fixed by the caller (batched environments)
+  unsigned generation = 0;  // bumped when kernel arguments change (sources, constants)
   // sources
   int64_t n_entries = 0;
   DevBuf src_row_off, src_elem, src_alpha, src_scale;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
+  // adjoint: the adjoint field, reduction partials, agents on the device
+  DevBuf adj, partial, ag_elem, ag_entry, ag_weight, ag_target;
+  int reduce_blocks = 0;
+  bool agents_on_device = false;
+  std::vector<int64_t> h_voxel, h_src_elem;
+  std::vector<double> h_weight, h_target;
 };
 
 namespace {
@@ -172,14 +197,24 @@ int pick_maxm(int m, bool fp64) {
 }
 
 // Threads a column-sweep CTA may use for a chunk capacity (mirrors ColBound).
-int col_bound_threads(int maxm, size_t) {
-  const int regs = 2 * maxm + 64;
+int col_bound_threads(int maxm, size_t esz) {
+  const int regs = maxm * (int)esz / 4 + 64;
   const int raw = 65536 / regs;
   return std::min(1024, raw) / 32 * 32;
 }
 
-bool plan_col(int n, bool fp64, ColPlan &p) {
+bool plan_col(int n, bool fp64, ColPlan &p, int forced_m = 0) {
   const size_t esz = fp64 ? 8 : 4;
+  if (forced_m > 0) {
+    const int m = std::min(forced_m, n);
+    const int T = (n + m - 1) / m;
+    const int maxm = pick_maxm(m, fp64);
+    if (maxm == 0 || T * 32 > col_bound_threads(maxm, esz)) return false;
+    p.T = T;
+    p.m = m;
+    p.maxm = maxm;
+    return true;
+  }
   for (int target = 32; target <= 128; target *= 2) {
     int T = (n + target - 1) / target;
     if (T < 1) T = 1;
@@ -197,7 +232,7 @@ bool plan_col(int n, bool fp64, ColPlan &p) {
   return false;
 }
 
-bool plan_x(int nx, int S, bool fp64, XPlan &p) {
+bool plan_x(int nx, int S, bool fp64, XPlan &p, int forced_m = 0) {
   const size_t esz = fp64 ? 8 : 4;
   const int Tmax = 32 / S;
   if (Tmax < 1) return false;
@@ -210,8 +245,9 @@ bool plan_x(int nx, int S, bool fp64, XPlan &p) {
     T = std::min(Tmax, (nx + largest - 1) / largest);
     m = (nx + T - 1) / T;
   }
+  if (forced_m > 0) m = std::min(forced_m, nx);
   T = (nx + m - 1) / m;
-  if (m > largest) return false;
+  if (m > largest || T > Tmax) return false;
   p.T = T;
   p.m = m;
   p.maxm = pick_maxm(m, fp64);
@@ -232,6 +268,130 @@ bool plan_x(int nx, int S, bool fp64, XPlan &p) {
     }
   }
   return false;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// Tensor map of axis 1/2 over `field` ([nplanes][n][C] elements, box 32 x
+// box_rows) into pp[axis].map[buf].
+bool encode_pipe_map(biofvm *h, int axis, int buf, void *field) {
+  PipePlan &p = h->pp[axis];
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc) return false;
+  const int64_t nx = h->g.nx, ny = h->g.ny, nz = h->g.nz, S = h->g.n_sub;
+  const int64_t C = axis == 1 ? nx * S : nx * ny * S;
+  const int64_t n = axis == 1 ? ny : nz, nplanes = axis == 1 ? nz : 1;
+  const size_t esz = h->esz;
+  cuuint64_t dims[3] = {(cuuint64_t)C, (cuuint64_t)n, (cuuint64_t)nplanes};
+  cuuint64_t strides[2] = {(cuuint64_t)(C * esz), (cuuint64_t)(C * esz * n)};
+  cuuint32_t box[3] = {32, (cuuint32_t)p.box_rows, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(&p.map[buf],
+                   esz == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                   field, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  p.have_map[buf] = r == CUDA_SUCCESS;
+  return p.have_map[buf] != 0;
+}
+
+// Bank-conflict degree of 32 lanes reading column c at (c/S)*pitch + c%S
+// (x tiles): the largest number of lanes that share a bank (FP32) or a bank
+// pair within a half warp (FP64).
+int x_tile_conflicts(int pitch, int S, int lanes, size_t esz) {
+  int worst = 0;
+  if (esz == 4) {
+    int cnt[32] = {0};
+    for (int c = 0; c < lanes; c++) worst = std::max(worst, ++cnt[((c / S) * pitch + c % S) & 31]);
+  } else {
+    for (int half = 0; half < 2; half++) {
+      int cnt[16] = {0};
+      for (int c = half * 16; c < std::min(lanes, half * 16 + 16); c++)
+        worst = std::max(worst, ++cnt[((c / S) * pitch + c % S) & 15]);
+    }
+  }
+  return worst;
+}
+
+// Plan the pipelined sweep of axis 0 (x), 1 (y) or 2 (z); leaves pp.use = 0
+// when the plain kernels have to be used instead.
+void plan_pipe(biofvm *h, int axis) {
+  PipePlan &p = h->pp[axis];
+  p = PipePlan{};
+  const int64_t nx = h->g.nx, ny = h->g.ny, nz = h->g.nz, S = h->g.n_sub;
+  const size_t esz = h->esz;
+  const int n = axis_len(h, axis);
+  ColPlan cp;
+  if (!plan_col(n, esz == 8, cp)) return;
+  if ((cp.T + 1) * 32 > pipe_max_threads(cp.maxm, esz)) return;
+  p.T = cp.T;
+  p.m = cp.m;
+  p.maxm = cp.maxm;
+  if (axis == 0) {
+    const int64_t rowlen = nx * S;
+    if ((rowlen * (int64_t)esz) % 16 != 0 || S > 32) return;
+    p.rows_per_tile = (int)(32 / S);
+    const int align = (int)(16 / esz);  // pitch in elements keeps every row 16-byte aligned
+    int best = 1 << 30;
+    for (int64_t pitch = (rowlen + align - 1) / align * align; pitch <= rowlen + 64; pitch += align) {
+      const int d = x_tile_conflicts((int)(pitch % 64), (int)S, p.rows_per_tile * (int)S, esz);
+      if (d < best) {
+        best = d;
+        p.pitch = (int)pitch;
+      }
+    }
+    p.stage_elems = (int64_t)p.rows_per_tile * p.pitch;
+    p.ntiles = (ny * nz + p.rows_per_tile - 1) / p.rows_per_tile;
+  } else {
+    const int64_t C = axis == 1 ? nx * S : nx * ny * S;
+    const int nplanes = axis == 1 ? (int)nz : 1;
+    if ((C * (int64_t)esz) % 16 != 0 || C > (int64_t)0x7fffffff || nplanes > 65535) return;
+    p.nbox = (n + 255) / 256;
+    p.box_rows = (n + p.nbox - 1) / p.nbox;
+    p.stage_elems = (int64_t)p.nbox * p.box_rows * 32;
+    p.ntiles = (int64_t)nplanes * ((C + 31) / 32);
+  }
+  const size_t stage = (size_t)p.stage_elems * esz;
+  const size_t tab = (size_t)pipe_tab_elems_host(n, (int)S, p.T) * esz;  // staged in shared memory
+  const size_t scratch = 2 * (size_t)p.T * 32 * esz + 16 + 2 * 8 * 8;
+  for (int ns = 4; ns >= 2 && !p.stages; ns--)
+    if (ns * stage + tab + scratch <= kMaxDynamicSmem) p.stages = ns;
+  if (!p.stages) return;
+  p.tab_in_smem = 1;
+  p.smem = p.stages * stage + tab + scratch;
+  if (axis != 0 && !encode_pipe_map(h, axis, 0, h->rho.p)) return;
+  // the attribute is per kernel, shared by every handle: always the opt-in maximum
+  const cudaError_t e = esz == 8 ? allow_pipe_smem_f64(p.maxm, kMaxDynamicSmem)
+                                 : allow_pipe_smem_f32(p.maxm, kMaxDynamicSmem);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  const int threads = (p.T + 1) * 32;
+  const int regs = p.maxm * (int)esz / 4 + 96;
+  int per_sm = (int)std::min<size_t>({kMaxDynamicSmem / p.smem, (size_t)(2048 / threads),
+                                      (size_t)(65536 / (threads * regs))});
+  per_sm = std::max(per_sm, 1);
+  p.grid = (int)std::min<int64_t>(p.ntiles, (int64_t)h->num_sms * per_sm);
+  p.use = 1;
 }
 
 // ---------------------------------------------------------------------------
@@ -257,11 +417,26 @@ biofvm_status upload_doubles(biofvm *h, DevBuf &b, const std::vector<double> &v)
   return BIOFVM_OK;
 }
 
+// The chunk partition of an axis, shared by its tables and every kernel that
+// solves along it: the pipelined plan's when the pipeline runs that axis.
+void axis_partition(const biofvm *h, int axis, int &T, int &m) {
+  if (h->pp[axis].use) {
+    T = h->pp[axis].T;
+    m = h->pp[axis].m;
+  } else if (axis == 0) {
+    T = h->xp.T;
+    m = h->xp.m;
+  } else {
+    T = h->cp[axis].T;
+    m = h->cp[axis].m;
+  }
+}
+
 biofvm_status upload_constants(biofvm *h) {
   std::vector<double> t;
   for (int axis = 0; axis < 3; axis++) {
-    const int T = axis == 0 ? h->xp.T : h->cp[axis].T;
-    const int m = axis == 0 ? h->xp.m : h->cp[axis].m;
+    int T, m;
+    axis_partition(h, axis, T, m);
     axis_tables(h, axis, T, m, h->prec == BIOFVM_FP32, t);
     biofvm_status st = upload_doubles(h, h->tab[axis], t);
     if (st) return st;
@@ -272,6 +447,7 @@ biofvm_status upload_constants(biofvm *h) {
     h->graph = nullptr;
     h->gexec = nullptr;
   }
+  h->generation++;
   return BIOFVM_OK;
 }
 
@@ -285,19 +461,70 @@ AxisTab axis_tab(const biofvm *h, int axis) {
   t.pf = base + 2 * blk;
   t.pb = base + 3 * blk;
   t.pc = base + 4 * blk;
-  t.cfix = base + 4 * blk + (size_t)(axis == 0 ? h->xp.T : h->cp[axis].T) * S * h->esz;
+  int T, m;
+  axis_partition(h, axis, T, m);
+  t.cfix = base + 4 * blk + (size_t)T * S * h->esz;
   t.n = n;
-  t.T = axis == 0 ? h->xp.T : h->cp[axis].T;
-  t.m = axis == 0 ? h->xp.m : h->cp[axis].m;
+  t.T = T;
+  t.m = m;
   return t;
 }
 
 // ---------------------------------------------------------------------------
 // Kernel launches.
 // ---------------------------------------------------------------------------
-cudaError_t launch_x(const biofvm *h, int flags, cudaStream_t st) {
+// Launch the pipelined sweep of `axis` on `field` (buf selects the y/z tensor map).
+cudaError_t launch_pipe(const biofvm *h, int axis, int flags, cudaStream_t st, void *field,
+                        int buf) {
+  const PipePlan &p = h->pp[axis];
+  PipeArgs b{};
+  b.mode = axis;
+  b.n = axis_len(h, axis);
+  b.S = h->g.n_sub;
+  b.nx = h->g.nx;
+  b.ny = h->g.ny;
+  b.nz = h->g.nz;
+  b.ntiles = p.ntiles;
+  b.C = axis == 1 ? (int64_t)h->g.nx * h->g.n_sub : (int64_t)h->g.nx * h->g.ny * h->g.n_sub;
+  b.tiles_per_plane = (int)((b.C + 31) / 32);
+  b.nplanes = axis == 1 ? h->g.nz : 1;
+  b.box_rows = p.box_rows;
+  b.nbox = p.nbox;
+  b.rows_per_tile = p.rows_per_tile;
+  b.rowlen = h->g.nx * h->g.n_sub;
+  b.pitch = p.pitch;
+  b.nrows = (int64_t)h->g.ny * h->g.nz;
+  b.field = field;
+  b.stages = p.stages;
+  b.tab_in_smem = p.tab_in_smem;
+  b.stage_elems = p.stage_elems;
+  b.tab = axis_tab(h, axis);
+  b.tab.T = p.T;
+  b.tab.m = p.m;
+  b.flags = flags;
+  if (!h->any_dir) b.flags &= ~(kDirBefore | kDirAfter);
+  b.src_row_off = static_cast<const int64_t *>(h->src_row_off.p);
+  b.src_elem = static_cast<const int64_t *>(h->src_elem.p);
+  b.src_alpha = h->src_alpha.p;
+  b.src_scale = h->src_scale.p;
+  b.has_src = h->n_entries > 0;
+  b.dir_on = static_cast<const uint8_t *>(h->dir_on_d.p);
+  b.dir_val = h->dir_val_d.p;
+  b.status = static_cast<int *>(h->status.p);
+  const CUtensorMap &map = p.map[axis == 0 ? 0 : buf];
+  return h->prec == BIOFVM_FP64 ? launch_pipe_f64(map, b, p.maxm, p.grid, p.smem, st)
+                                : launch_pipe_f32(map, b, p.maxm, p.grid, p.smem, st);
+}
+
+bool pipe_ok(const biofvm *h, int axis, int flags, int buf) {
+  const PipePlan &p = h->pp[axis];
+  return p.use && (flags & kSolve) && (axis == 0 || p.have_map[buf]);
+}
+
+cudaError_t launch_x(const biofvm *h, int flags, cudaStream_t st, void *field = nullptr) {
+  if (pipe_ok(h, 0, flags, 0)) return launch_pipe(h, 0, flags, st, field ? field : h->rho.p, 0);
   XLaunch a{};
-  a.rho = h->rho.p;
+  a.rho = field ? field : h->rho.p;
   a.nx = h->g.nx;
   a.ny = h->g.ny;
   a.nz = h->g.nz;
@@ -322,9 +549,9 @@ cudaError_t launch_x(const biofvm *h, int flags, cudaStream_t st) {
   return h->prec == BIOFVM_FP64 ? launch_x_f64(a, st) : launch_x_f32(a, st);
 }
 
-cudaError_t launch_col(const biofvm *h, int axis, int flags, cudaStream_t st) {
+cudaError_t launch_col(const biofvm *h, int axis, int flags, cudaStream_t st, int buf = 0) {
   ColLaunch a{};
-  a.rho = h->rho.p;
+  a.rho = buf ? h->adj.p : h->rho.p;
   const int64_t nx = h->g.nx, ny = h->g.ny, nz = h->g.nz, S = h->g.n_sub;
   if (axis == 1) {
     a.C = nx * S;
@@ -349,6 +576,7 @@ cudaError_t launch_col(const biofvm *h, int axis, int flags, cudaStream_t st) {
   if (!h->any_dir) a.flags &= ~kDirAfter;
   a.dir_on = static_cast<const uint8_t *>(h->dir_on_d.p);
   a.dir_val = h->dir_val_d.p;
+  if (pipe_ok(h, axis, flags, buf)) return launch_pipe(h, axis, flags, st, a.rho, buf);
   return h->prec == BIOFVM_FP64 ? launch_col_f64(a, st) : launch_col_f32(a, st);
 }
 
@@ -384,12 +612,17 @@ void destroy_impl(biofvm *h) {
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   if (h->graph) cudaGraphDestroy(h->graph);
   for (DevBuf *b : {&h->rho, &h->tab[0], &h->tab[1], &h->tab[2], &h->dir_on_d, &h->dir_val_d,
-                    &h->status, &h->src_row_off, &h->src_elem, &h->src_alpha, &h->src_scale})
+                    &h->status, &h->src_row_off, &h->src_elem, &h->src_alpha, &h->src_scale,
+                    &h->adj, &h->partial, &h->ag_elem, &h->ag_entry, &h->ag_weight,
+                    &h->ag_target})
     b->release();
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   delete h;
 }
 
+biofvm_status create_impl(const biofvm_grid *grid, double dx, double dt, const double *D,
+                          const double *lambda, const biofvm_boundary *bc, biofvm_precision prec,
+                          uintptr_t cuda_stream, const int *force_m, biofvm_t **out);
 }  // namespace
 
 // ===========================================================================
@@ -402,6 +635,17 @@ const char *biofvm_last_error(void) { return g_last_error.c_str(); }
 biofvm_status biofvm_create(const biofvm_grid *grid, double dx, double dt, const double *D,
                             const double *lambda, const biofvm_boundary *bc,
                             biofvm_precision prec, uintptr_t cuda_stream, biofvm_t **out) {
+  return create_impl(grid, dx, dt, D, lambda, bc, prec, cuda_stream, nullptr, out);
+}
+
+}  // extern "C"
+
+namespace {
+// biofvm_create with optional chunk lengths force_m[3] (x, y, z): the batched
+// kernel needs every environment's partition to fit its CTA; no pipelines then.
+biofvm_status create_impl(const biofvm_grid *grid, double dx, double dt, const double *D,
+                          const double *lambda, const biofvm_boundary *bc, biofvm_precision prec,
+                          uintptr_t cuda_stream, const int *force_m, biofvm_t **out) {
   g_last_error.clear();
   if (!out) return fail(BIOFVM_ERR_ARG, "out is NULL");
   *out = nullptr;
@@ -452,12 +696,14 @@ biofvm_status biofvm_create(const biofvm_grid *grid, double dx, double dt, const
   h->prec = prec;
   h->esz = fp64 ? 8 : 4;
   h->nel = (size_t)g.nx * g.ny * g.nz * g.n_sub;
-  if (!plan_x(g.nx, g.n_sub, fp64, h->xp)) {
+  h->forced = force_m != nullptr;
+  if (!plan_x(g.nx, g.n_sub, fp64, h->xp, force_m ? force_m[0] : 0)) {
     delete h;
     return fail(BIOFVM_ERR_ARG, "x lines too long for the x-sweep tile (nx*n_sub = %d)",
                 g.nx * g.n_sub);
   }
-  if (!plan_col(g.ny, fp64, h->cp[1]) || !plan_col(g.nz, fp64, h->cp[2])) {
+  if (!plan_col(g.ny, fp64, h->cp[1], force_m ? force_m[1] : 0) ||
+      !plan_col(g.nz, fp64, h->cp[2], force_m ? force_m[2] : 0)) {
     delete h;
     return fail(BIOFVM_ERR_ARG, "y or z lines too long for the column sweep (ny=%d nz=%d)", g.ny,
                 g.nz);
@@ -496,12 +742,18 @@ biofvm_status biofvm_create(const biofvm_grid *grid, double dx, double dt, const
     destroy_impl(h);
     return fail(BIOFVM_ERR_CUDA, "initialising device memory failed: %s", cudaGetErrorString(e));
   }
-  e = fp64 ? allow_x_smem_f64(h->xp.maxm, h->xp.smem) : allow_x_smem_f32(h->xp.maxm, h->xp.smem);
+  // the attribute is per kernel, shared by every handle: always the opt-in maximum
+  e = fp64 ? allow_x_smem_f64(h->xp.maxm, kMaxDynamicSmem)
+           : allow_x_smem_f32(h->xp.maxm, kMaxDynamicSmem);
   if (e != cudaSuccess) {
     destroy_impl(h);
     return fail(BIOFVM_ERR_CUDA, "x-sweep shared memory of %zu bytes refused: %s", h->xp.smem,
                 cudaGetErrorString(e));
   }
+  h->num_sms = prop.multiProcessorCount;
+  if (const char *env = getenv("BIOFVM_PIPELINE")) h->pipe_enabled = atoi(env) != 0;
+  if (h->pipe_enabled && !h->forced)
+    for (int axis = 0; axis < 3; axis++) plan_pipe(h, axis);
   if ((st = upload_doubles(h, h->dir_val_d, h->dir_val)) != BIOFVM_OK ||
       (st = upload_constants(h)) != BIOFVM_OK) {
     std::string msg = g_last_error;
@@ -512,6 +764,9 @@ biofvm_status biofvm_create(const biofvm_grid *grid, double dx, double dt, const
   *out = h;
   return BIOFVM_OK;
 }
+}  // namespace
+
+extern "C" {
 
 biofvm_status biofvm_set_density(biofvm_t *h, const void *src, int src_on_device) {
   if (!h || !src) return fail(BIOFVM_ERR_ARG, "NULL handle or source");
@@ -636,6 +891,15 @@ biofvm_status biofvm_set_sources(biofvm_t *h, int64_t n, const int64_t *voxel,
     if (st) return st;
   }
   h->n_entries = (int64_t)u;
+  // agents as the adjoint needs them (moved to the device on first use)
+  h->h_voxel.assign(voxel, voxel + n);
+  h->h_weight.clear();
+  if (weight) h->h_weight.assign(weight, weight + n);
+  h->h_target.assign((size_t)n * S, 0.0);
+  if (target) std::copy(target, target + (size_t)n * S, h->h_target.begin());
+  h->h_src_elem = elem;
+  h->agents_on_device = false;
+  h->generation++;
   if (h->graph) {  // kernel arguments changed
     cudaGraphExecDestroy(h->gexec);
     cudaGraphDestroy(h->graph);
@@ -690,6 +954,360 @@ biofvm_status biofvm_run_stage(biofvm_t *h, int stage) {
   return BIOFVM_OK;
 }
 
+biofvm_status biofvm_step_save(biofvm_t *h, void *saved) {
+  if (!h || !saved) return fail(BIOFVM_ERR_ARG, "NULL handle or saved buffer");
+  CK(cudaSetDevice(h->device));
+  const size_t bytes = h->nel * h->esz;
+  char *sv = static_cast<char *>(saved);
+  cudaStream_t st = h->stream;
+  CK(launch_x(h, kSrc, st));
+  CK(cudaMemcpyAsync(sv, h->rho.p, bytes, cudaMemcpyDeviceToDevice, st));
+  if (h->any_dir) CK(launch_x(h, kDirAfter, st));
+  CK(launch_x(h, kSolve, st));
+  CK(cudaMemcpyAsync(sv + bytes, h->rho.p, bytes, cudaMemcpyDeviceToDevice, st));
+  if (h->any_dir) CK(launch_x(h, kDirAfter, st));
+  CK(launch_col(h, 1, kSolve, st));
+  CK(cudaMemcpyAsync(sv + 2 * bytes, h->rho.p, bytes, cudaMemcpyDeviceToDevice, st));
+  if (h->any_dir) CK(launch_x(h, kDirAfter, st));
+  CK(launch_col(h, 2, kSolve, st));
+  CK(cudaMemcpyAsync(sv + 3 * bytes, h->rho.p, bytes, cudaMemcpyDeviceToDevice, st));
+  if (h->any_dir) CK(launch_x(h, kDirAfter, st));
+  return BIOFVM_OK;
+}
+
+biofvm_status biofvm_adjoint_step(biofvm_t *h, const void *grad_out, void *grad_in, double *dD,
+                                  double *dlambda, double *dsecretion, const void *saved) {
+  if (!h || !grad_out || !grad_in || !dD || !dlambda || !saved)
+    return fail(BIOFVM_ERR_ARG, "NULL handle, gradient or saved-state pointer");
+  CK(cudaSetDevice(h->device));
+  cudaStream_t st = h->stream;
+  const size_t bytes = h->nel * h->esz;
+  const int S = h->g.n_sub;
+  // lazily: adjoint field (+ its tensor maps), reduction scratch, device agents
+  if (!h->adj.p) {
+    if (dev_alloc(h->adj, bytes) != cudaSuccess)
+      return fail(BIOFVM_ERR_OOM, "device allocation of the adjoint field failed");
+    for (int axis = 1; axis <= 2; axis++)
+      if (h->pp[axis].use) encode_pipe_map(h, axis, 1, h->adj.p);  // x tiles need no map
+  }
+  if (!h->partial.p) {
+    h->reduce_blocks = 4 * h->num_sms;
+    if (dev_alloc(h->partial, (size_t)h->reduce_blocks * 2 * S * sizeof(double)) != cudaSuccess)
+      return fail(BIOFVM_ERR_OOM, "device allocation of the reduction scratch failed");
+  }
+  const int64_t na = (int64_t)h->h_voxel.size();
+  if (!h->agents_on_device && na > 0) {
+    std::vector<int64_t> el((size_t)na * S), en((size_t)na * S);
+    for (int64_t k = 0; k < na; k++)
+      for (int s = 0; s < S; s++) {
+        const int64_t e = h->h_voxel[k] * S + s;
+        auto it = std::lower_bound(h->h_src_elem.begin(), h->h_src_elem.end(), e);
+        el[k * S + s] = e;
+        en[k * S + s] = (it != h->h_src_elem.end() && *it == e) ? (it - h->h_src_elem.begin()) : -1;
+      }
+    if (dev_alloc(h->ag_elem, el.size() * 8) != cudaSuccess ||
+        dev_alloc(h->ag_entry, en.size() * 8) != cudaSuccess ||
+        dev_alloc(h->ag_target, h->h_target.size() * 8) != cudaSuccess ||
+        dev_alloc(h->ag_weight, h->h_weight.size() * 8) != cudaSuccess)
+      return fail(BIOFVM_ERR_OOM, "device allocation of the agent arrays failed");
+    CK(cudaMemcpy(h->ag_elem.p, el.data(), el.size() * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->ag_entry.p, en.data(), en.size() * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->ag_target.p, h->h_target.data(), h->h_target.size() * 8,
+                  cudaMemcpyHostToDevice));
+    if (!h->h_weight.empty())
+      CK(cudaMemcpy(h->ag_weight.p, h->h_weight.data(), h->h_weight.size() * 8,
+                    cudaMemcpyHostToDevice));
+    h->agents_on_device = true;
+  }
+  const char *sv = static_cast<const char *>(saved);
+  const int mask = kDirAfter | kMaskZero;
+  auto reduce = [&](int axis, const void *u) -> cudaError_t {
+    ReduceLaunch r{};
+    r.mu = h->adj.p;
+    r.u = u;
+    r.nel = (long long)h->nel;
+    r.S = S;
+    r.stride = axis == 0 ? S : axis == 1 ? (long long)h->g.nx * S : (long long)h->g.nx * h->g.ny * S;
+    r.n_axis = axis_len(h, axis);
+    r.nblocks = h->reduce_blocks;
+    r.used = (long long)r.nblocks * kReduceThreads / S * S;
+    r.partial = static_cast<double *>(h->partial.p);
+    r.scale_lambda = -h->dt / 3.0;
+    r.scale_D = -h->dt / (h->dx * h->dx);
+    r.dlambda = dlambda;
+    r.dD = dD;
+    return h->prec == BIOFVM_FP64 ? launch_adj_reduce_f64(r, st) : launch_adj_reduce_f32(r, st);
+  };
+  CK(cudaMemcpyAsync(h->adj.p, grad_out, bytes, cudaMemcpyDeviceToDevice, st));
+  if (h->any_dir) CK(launch_x(h, mask, st, h->adj.p));
+  CK(launch_col(h, 2, kSolve, st, 1));
+  CK(reduce(2, sv + 3 * bytes));
+  if (h->any_dir) CK(launch_x(h, mask, st, h->adj.p));
+  CK(launch_col(h, 1, kSolve, st, 1));
+  CK(reduce(1, sv + 2 * bytes));
+  if (h->any_dir) CK(launch_x(h, mask, st, h->adj.p));
+  CK(launch_x(h, kSolve, st, h->adj.p));
+  CK(reduce(0, sv + bytes));
+  if (h->any_dir) CK(launch_x(h, mask, st, h->adj.p));
+  SrcAdjLaunch a{};
+  a.gbar = h->adj.p;
+  a.u1 = sv;
+  a.elem = static_cast<const int64_t *>(h->ag_elem.p);
+  a.entry = static_cast<const int64_t *>(h->ag_entry.p);
+  a.weight = h->h_weight.empty() ? nullptr : static_cast<const double *>(h->ag_weight.p);
+  a.target = static_cast<const double *>(h->ag_target.p);
+  a.n = na * S;
+  a.src_elem = static_cast<const int64_t *>(h->src_elem.p);
+  a.src_scale = h->src_scale.p;
+  a.n_entries = h->n_entries;
+  a.dt = h->dt;
+  a.S = S;
+  a.dsec = dsecretion;
+  CK(h->prec == BIOFVM_FP64 ? launch_src_adjoint_f64(a, st) : launch_src_adjoint_f32(a, st));
+  CK(cudaMemcpyAsync(grad_in, h->adj.p, bytes, cudaMemcpyDeviceToDevice, st));
+  return BIOFVM_OK;
+}
+
 void biofvm_destroy(biofvm_t *h) { destroy_impl(h); }
+
+}  // extern "C"
+
+// ===========================================================================
+// Batched environments: one persistent launch advances all of them.
+// ===========================================================================
+struct biofvm_batch {
+  std::vector<biofvm *> env;
+  std::vector<unsigned> env_gen;
+  biofvm_precision prec = BIOFVM_FP32;
+  cudaStream_t stream = nullptr, cap_stream = nullptr;
+  int device = 0, maxm = 8, grid = 0;
+  int64_t per_step = 0;
+  DevBuf envs_d, tile_off_d, done_d, flags_d;  // flags: [0] abort, [1] status
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  int graph_steps = -1;
+};
+
+namespace {
+
+void batch_drop_graph(biofvm_batch *b) {
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->gexec = nullptr;
+  b->graph = nullptr;
+  b->graph_steps = -1;
+}
+
+void batch_destroy_impl(biofvm_batch *b) {
+  if (!b) return;
+  cudaSetDevice(b->device);
+  cudaStreamSynchronize(b->stream);
+  batch_drop_graph(b);
+  for (biofvm *h : b->env) destroy_impl(h);
+  for (DevBuf *d : {&b->envs_d, &b->tile_off_d, &b->done_d, &b->flags_d}) d->release();
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  delete b;
+}
+
+// Environment descriptors (device pointers of every environment's field,
+// constants and sources) and the tile prefix sums.
+biofvm_status batch_upload(biofvm_batch *b) {
+  const int ne = (int)b->env.size();
+  std::vector<BatchEnv> d(ne);
+  std::vector<int64_t> off(3 * (size_t)(ne + 1), 0);
+  for (int e = 0; e < ne; e++) {
+    const biofvm *h = b->env[e];
+    BatchEnv &x = d[e];
+    x.field = h->rho.p;
+    x.nx = h->g.nx;
+    x.ny = h->g.ny;
+    x.nz = h->g.nz;
+    x.S = h->g.n_sub;
+    for (int axis = 0; axis < 3; axis++) {
+      const AxisTab t = axis_tab(h, axis);
+      x.tab[axis] = t.inv;
+      x.T[axis] = t.T;
+      x.m[axis] = t.m;
+    }
+    x.rows_per_tile = 32 / x.S;
+    const int64_t nrows = (int64_t)x.ny * x.nz, rowlen = (int64_t)x.nx * x.S;
+    x.tiles[0] = (nrows + x.rows_per_tile - 1) / x.rows_per_tile;
+    x.tiles[1] = (int64_t)x.nz * ((rowlen + 31) / 32);
+    x.tiles[2] = (rowlen * x.ny + 31) / 32;
+    x.src_row_off = static_cast<const int64_t *>(h->src_row_off.p);
+    x.src_elem = static_cast<const int64_t *>(h->src_elem.p);
+    x.src_alpha = h->src_alpha.p;
+    x.src_scale = h->src_scale.p;
+    x.has_src = h->n_entries > 0;
+    for (int ph = 0; ph < 3; ph++) off[ph * (ne + 1) + e + 1] = off[ph * (ne + 1) + e] + x.tiles[ph];
+    b->env_gen[e] = h->generation;
+  }
+  b->per_step = off[0 * (ne + 1) + ne] + off[1 * (ne + 1) + ne] + off[2 * (ne + 1) + ne];
+  CK(cudaMemcpy(b->envs_d.p, d.data(), d.size() * sizeof(BatchEnv), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(b->tile_off_d.p, off.data(), off.size() * 8, cudaMemcpyHostToDevice));
+  batch_drop_graph(b);
+  return BIOFVM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+biofvm_status biofvm_batch_create(int n_env, const biofvm_grid *grids, const double *dx,
+                                  const double *dt, const double *D_flat,
+                                  const double *lambda_flat, biofvm_precision prec,
+                                  uintptr_t cuda_stream, const int *tile_m,
+                                  biofvm_batch_t **out) {
+  g_last_error.clear();
+  if (!out) return fail(BIOFVM_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (n_env < 1 || !grids || !dx || !dt || !D_flat || !lambda_flat)
+    return fail(BIOFVM_ERR_ARG, "n_env must be >= 1 and every array non-NULL");
+  biofvm_batch *b = new (std::nothrow) biofvm_batch();
+  if (!b) return fail(BIOFVM_ERR_OOM, "host allocation failed");
+  b->prec = prec;
+  b->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  int64_t off = 0;
+  for (int e = 0; e < n_env; e++) {
+    const biofvm_grid &g = grids[e];
+    int m[3];
+    const int ns[3] = {g.nx, g.ny, g.nz};
+    for (int a = 0; a < 3; a++) {
+      int want = tile_m ? tile_m[3 * e + a] : 0;
+      if (want <= 0) want = std::max(8, (ns[a] + kBatchWarps - 1) / kBatchWarps);  // default
+      m[a] = std::min(want, std::max(ns[a], 1));
+      if ((ns[a] + m[a] - 1) / m[a] > kBatchWarps || m[a] > 48) {
+        batch_destroy_impl(b);
+        return fail(BIOFVM_ERR_ARG,
+                    "environment %d axis %d: chunk length %d gives more than %d chunks or "
+                    "exceeds 48", e, a, m[a], kBatchWarps);
+      }
+    }
+    if (g.n_sub < 1 || g.n_sub > 32) {
+      batch_destroy_impl(b);
+      return fail(BIOFVM_ERR_ARG, "environment %d: n_sub must be in [1, 32]", e);
+    }
+    biofvm *h = nullptr;
+    biofvm_status st = create_impl(&g, dx[e], dt[e], D_flat + off, lambda_flat + off, nullptr,
+                                   prec, cuda_stream, m, &h);
+    if (st != BIOFVM_OK) {
+      std::string msg = g_last_error;
+      batch_destroy_impl(b);
+      return fail(st, "environment %d: %s", e, msg.c_str());
+    }
+    b->env.push_back(h);
+    b->env_gen.push_back(0);
+    for (int a = 0; a < 3; a++) b->maxm = std::max(b->maxm, m[a]);
+    off += g.n_sub;
+  }
+  for (int c : kBatchMaxm)
+    if (c >= b->maxm) {
+      b->maxm = c;
+      break;
+    }
+  b->device = b->env[0]->device;
+  const bool fp64 = prec == BIOFVM_FP64;
+  int per_sm = 0;
+  cudaError_t e = fp64 ? batch_occupancy_f64(b->maxm, &per_sm) : batch_occupancy_f32(b->maxm, &per_sm);
+  if (e != cudaSuccess || per_sm < 1) {
+    batch_destroy_impl(b);
+    return fail(BIOFVM_ERR_CUDA, "batched kernel occupancy query failed");
+  }
+  b->grid = per_sm * b->env[0]->num_sms;  // every CTA resident (the schedule relies on it)
+  if (dev_alloc(b->envs_d, (size_t)n_env * sizeof(BatchEnv)) != cudaSuccess ||
+      dev_alloc(b->tile_off_d, 3 * (size_t)(n_env + 1) * 8) != cudaSuccess ||
+      dev_alloc(b->done_d, 3 * (size_t)n_env * sizeof(unsigned)) != cudaSuccess ||
+      dev_alloc(b->flags_d, 2 * sizeof(int)) != cudaSuccess) {
+    batch_destroy_impl(b);
+    return fail(BIOFVM_ERR_OOM, "device allocation of the batch descriptors failed");
+  }
+  if ((e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaMemset(b->flags_d.p, 0, 2 * sizeof(int))) != cudaSuccess) {
+    batch_destroy_impl(b);
+    return fail(BIOFVM_ERR_CUDA, "batch set-up failed: %s", cudaGetErrorString(e));
+  }
+  biofvm_status st = batch_upload(b);
+  if (st != BIOFVM_OK) {
+    std::string msg = g_last_error;
+    batch_destroy_impl(b);
+    g_last_error = msg;
+    return st;
+  }
+  *out = b;
+  return BIOFVM_OK;
+}
+
+biofvm_status biofvm_batch_env(biofvm_batch_t *b, int e, biofvm_t **env) {
+  if (!b || !env || e < 0 || e >= (int)b->env.size())
+    return fail(BIOFVM_ERR_ARG, "bad batch handle, environment index or output");
+  *env = b->env[e];
+  return BIOFVM_OK;
+}
+
+biofvm_status biofvm_batch_step(biofvm_batch_t *b, int n_steps) {
+  if (!b) return fail(BIOFVM_ERR_ARG, "NULL batch handle");
+  if (n_steps < 0) return fail(BIOFVM_ERR_ARG, "n_steps must be >= 0");
+  if (n_steps == 0) return BIOFVM_OK;
+  CK(cudaSetDevice(b->device));
+  bool stale = false;
+  for (size_t e = 0; e < b->env.size(); e++) stale |= b->env[e]->generation != b->env_gen[e];
+  if (stale) {
+    CK(cudaStreamSynchronize(b->stream));  // descriptors are read by launches in flight
+    biofvm_status st = batch_upload(b);
+    if (st) return st;
+  }
+  if (!b->gexec || b->graph_steps != n_steps) {
+    batch_drop_graph(b);
+    const int ne = (int)b->env.size();
+    BatchArgs a{};
+    a.env = static_cast<const BatchEnv *>(b->envs_d.p);
+    a.n_env = ne;
+    a.n_steps = n_steps;
+    a.tile_off = static_cast<const int64_t *>(b->tile_off_d.p);
+    a.per_step = b->per_step;
+    a.done = static_cast<unsigned *>(b->done_d.p);
+    a.abort_flag = static_cast<int *>(b->flags_d.p);
+    a.status = static_cast<int *>(b->flags_d.p) + 1;
+    const int grid = (int)std::min<int64_t>(b->grid, b->per_step * n_steps);
+    CK(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e1 = cudaMemsetAsync(b->done_d.p, 0, 3 * (size_t)ne * sizeof(unsigned), b->cap_stream);
+    cudaError_t e2 = cudaMemsetAsync(b->flags_d.p, 0, sizeof(int), b->cap_stream);  // abort flag
+    cudaError_t e3 = b->prec == BIOFVM_FP64 ? launch_batch_f64(a, b->maxm, grid, b->cap_stream)
+                                            : launch_batch_f32(a, b->maxm, grid, b->cap_stream);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e4 = cudaStreamEndCapture(b->cap_stream, &graph);
+    for (cudaError_t ee : {e1, e2, e3, e4})
+      if (ee != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return fail(BIOFVM_ERR_CUDA, "batch graph capture failed: %s", cudaGetErrorString(ee));
+      }
+    cudaError_t e5 = cudaGraphInstantiate(&b->gexec, graph, 0);
+    if (e5 != cudaSuccess) {
+      cudaGraphDestroy(graph);
+      return fail(BIOFVM_ERR_CUDA, "cudaGraphInstantiate failed: %s", cudaGetErrorString(e5));
+    }
+    b->graph = graph;
+    b->graph_steps = n_steps;
+  }
+  CK(cudaGraphLaunch(b->gexec, b->stream));
+  return BIOFVM_OK;
+}
+
+biofvm_status biofvm_batch_sync(biofvm_batch_t *b) {
+  if (!b) return fail(BIOFVM_ERR_ARG, "NULL batch handle");
+  CK(cudaSetDevice(b->device));
+  CK(cudaStreamSynchronize(b->stream));
+  int st = 0;
+  CK(cudaMemcpy(&st, static_cast<int *>(b->flags_d.p) + 1, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st != kStatusOk) {
+    CK(cudaMemset(b->flags_d.p, 0, 2 * sizeof(int)));
+    return fail(BIOFVM_ERR_TIMEOUT, "a bounded wait of the batched kernel timed out");
+  }
+  return BIOFVM_OK;
+}
+
+int biofvm_batch_grid(const biofvm_batch_t *b) { return b ? b->grid : 0; }
+
+void biofvm_batch_destroy(biofvm_batch_t *b) { batch_destroy_impl(b); }
 
 }  // extern "C"

@@ -1,0 +1,32 @@
+// Descriptors of the batched persistent step (batch.cuh), shared with the host.
+#pragma once
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace bfv {
+
+// One environment: its field, per-axis constants (the same blocks and chunk
+// partition as its single-grid handle) and its aggregated sources.
+struct BatchEnv {
+  void *field;
+  int nx, ny, nz, S;
+  const void *tab[3];  // per axis: inv, mul, pf, pb [n][S]; pc [T][S]; cfix [2][S]
+  int T[3], m[3];
+  int rows_per_tile;    // x tiles: floor(32/S) rows of S lines each
+  int64_t tiles[3];     // tiles per phase
+  const int64_t *src_row_off, *src_elem;
+  const void *src_alpha, *src_scale;
+  int has_src;
+};
+
+struct BatchArgs {
+  const BatchEnv *env;
+  int n_env, n_steps;
+  const int64_t *tile_off;  // [3][n_env + 1] prefix sums of tiles per phase
+  int64_t per_step;         // tiles of one step
+  unsigned int *done;       // [3][n_env] completed tiles (cumulative over steps)
+  int *abort_flag, *status;
+};
+
+}  // namespace bfv

@@ -2,6 +2,7 @@
 // sweep kernels (sweeps_fp64.cu, sweeps_fp32.cu).  Not installed; the public
 // C ABI is include/biofvm.h.
 #pragma once
+#include <cuda.h>  // CUtensorMap (type only; the encoder is fetched at run time)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -14,6 +15,7 @@ enum : int {
   kDirBefore = 2,  // Dirichlet application before the solve
   kSolve = 4,      // Thomas solve along the axis
   kDirAfter = 8,   // Dirichlet application after the solve
+  kMaskZero = 16,  // Dirichlet applications write 0 (the adjoint of B: dB/du = mask)
 };
 
 // Status word values written by kernels (mirror biofvm_status).
@@ -74,6 +76,45 @@ struct ColLaunch {
   const void *dir_val;
 };
 
+// Persistent TMA-pipelined sweep (pipe.cuh): tiles of 32 lines x n positions
+// through a ring of shared-memory stages.
+struct PipeArgs;
+
+// Opt-in dynamic shared memory per CTA on sm_100-class GPUs (227 KB).
+constexpr size_t kMaxDynamicSmem = 232448;
+
+// Threads per block of the adjoint reduction.
+constexpr int kReduceThreads = 256;
+
+// Adjoint parameter-gradient reduction of one sweep (adjoint.cuh).
+struct ReduceLaunch {
+  const void *mu, *u;           // adjoint after the sweep, forward sweep output
+  long long nel, stride, used;  // elements; element stride along the axis; threads used
+  int S, n_axis, nblocks;
+  double *partial;              // [nblocks][2][S] scratch
+  double scale_lambda, scale_D; // -dt/3, -dt/dx^2
+  double *dlambda, *dD;         // [S] accumulated (device)
+};
+// Adjoint of the source update (adjoint.cuh).
+struct SrcAdjLaunch {
+  void *gbar;
+  const void *u1;                      // forward source output
+  const int64_t *elem, *entry;         // [n] per (agent, substrate)
+  const double *weight, *target;       // [n/S] or NULL, [n]
+  long long n;
+  const int64_t *src_elem;             // aggregated entries
+  const void *src_scale;               // 1/(1+beta) per entry
+  long long n_entries;
+  double dt;
+  int S;
+  double *dsec;                        // [n] accumulated (device) or NULL
+};
+
+// Batched persistent step (batch.cuh).
+struct BatchArgs;
+constexpr int kBatchMaxm[] = {8, 16, 24, 32, 48};
+constexpr int kBatchWarps = 8;  // chunks per line at most (256-thread CTAs)
+
 // Register-chunk capacities compiled for each precision (ascending).
 constexpr int kMaxmF64[] = {8, 16, 24, 32, 48, 64};
 constexpr int kMaxmF32[] = {8, 16, 24, 32, 48, 64, 96, 128};
@@ -86,5 +127,26 @@ cudaError_t launch_x_f64(const XLaunch &a, cudaStream_t st);
 cudaError_t launch_x_f32(const XLaunch &a, cudaStream_t st);
 cudaError_t launch_col_f64(const ColLaunch &a, cudaStream_t st);
 cudaError_t launch_col_f32(const ColLaunch &a, cudaStream_t st);
+cudaError_t allow_pipe_smem_f64(int maxm, size_t bytes);
+cudaError_t allow_pipe_smem_f32(int maxm, size_t bytes);
+cudaError_t launch_pipe_f64(const CUtensorMap &map, const PipeArgs &a, int maxm, int grid,
+                            size_t smem, cudaStream_t st);
+cudaError_t launch_pipe_f32(const CUtensorMap &map, const PipeArgs &a, int maxm, int grid,
+                            size_t smem, cudaStream_t st);
+cudaError_t launch_adj_reduce_f64(const ReduceLaunch &a, cudaStream_t st);
+cudaError_t launch_adj_reduce_f32(const ReduceLaunch &a, cudaStream_t st);
+cudaError_t launch_src_adjoint_f64(const SrcAdjLaunch &a, cudaStream_t st);
+cudaError_t launch_src_adjoint_f32(const SrcAdjLaunch &a, cudaStream_t st);
+cudaError_t launch_batch_f64(const BatchArgs &a, int maxm, int grid, cudaStream_t st);
+cudaError_t launch_batch_f32(const BatchArgs &a, int maxm, int grid, cudaStream_t st);
+cudaError_t batch_occupancy_f64(int maxm, int *out);
+cudaError_t batch_occupancy_f32(int maxm, int *out);
+// Largest CTA the pipelined sweep with chunk capacity maxm may use.
+int pipe_max_threads(int maxm, size_t esz);
+// Shared-memory constants of the pipelined sweep (elements): [4][S][npad] + pc + cfix.
+inline int pipe_tab_elems_host(int n, int S, int T) {
+  const int npad = (n + 31) / 32 * 32 + 1;
+  return 4 * S * npad + T * S + 2 * S;
+}
 
 }  // namespace bfv

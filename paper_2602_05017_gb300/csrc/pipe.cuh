@@ -1,0 +1,402 @@
+// Persistent, TMA-pipelined sweep kernel for sm_103a (x, y and z sweeps).
+//
+// Same arithmetic as the plain kernels of sweeps.cuh -- partitioned Thomas of
+// Algorithm 1 on the App. A system, FP32 in defect-correction form -- but
+// every tile of 32 independent lines ("columns") x n positions moves through
+// a ring of shared-memory stages:
+//
+//   warp 0, lane 0 (producer): TMA loads of tile k+NS-1 (cp.async.bulk.tensor
+//     boxes for y/z tiles, one cp.async.bulk per row for x tiles) completing
+//     on mbarrier `full`; once the consumers have written tile k back into its
+//     stage (mbarrier `done`), the bulk store of that tile; the stage is
+//     reloaded after the store has finished reading it;
+//   warps 1..T (consumers): chunk t of every column of the staged tile, in
+//     registers.  x tiles first get the source update and the first Dirichlet
+//     application in shared memory.  Halos and chunk carries cross warps
+//     through shared memory between named barriers that only consumers join.
+//
+// The grid is persistent (tiles strided by gridDim.x), so loads of later
+// tiles overlap the solve and the store of earlier ones.  The axis constants
+// are staged once per CTA when they fit.
+//
+// Every mbarrier wait is bounded (mbar_wait_bounded): on a timeout the status
+// word is set, the consumers agree to stop through an AND-reducing barrier (no
+// named barrier is left waiting), and the producer drains (bounded) the loads
+// still in flight before the CTA exits.
+#pragma once
+#include <cuda.h>
+
+#include "pipe_args.h"
+#include "sweeps.cuh"
+
+namespace bfv {
+
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int c0, int c1,
+                                            int c2, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(dst)),
+      "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap *map, int c0, int c1, int c2,
+                                             const void *src) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
+          map),
+      "r"(c0), "r"(c1), "r"(c2), "r"(smem_addr(src))
+      : "memory");
+}
+__device__ __forceinline__ void bulk_wait_read_all() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+// Barrier 1 over the consumer warps only.
+__device__ __forceinline__ void consumers_sync(int nthreads) {
+  asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+}
+// Barrier 1 over the consumers with an AND of `ok` (uniform result).
+__device__ __forceinline__ bool consumers_all(bool ok, int nthreads) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 p, %1, 0;\n\t"
+      "bar.red.and.pred q, 1, %2, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)ok), "r"(nthreads)
+      : "memory");
+  return r != 0;
+}
+
+template <typename E, int MAXM>
+struct PipeBound {  // chunk registers + about 96 for addressing, carries, constants
+  static constexpr int regs = MAXM * (int)sizeof(E) / 4 + 96;
+  static constexpr int raw = 65536 / regs;
+  static constexpr int threads = (raw >= 1024 ? 1024 : raw) / 32 * 32;
+};
+
+// Shared-memory constants of the pipelined kernel: inv, mul, pf, pb stored
+// substrate-major [S][n_pad] (n_pad = 1 mod 32, so lanes of different
+// substrates read different banks and each thread walks its own row with
+// compile-time offsets), then pc [T][S] and cfix [2][S] as in global memory.
+__host__ __device__ inline int pipe_npad(int n) { return (n + 31) / 32 * 32 + 1; }
+__host__ __device__ inline int pipe_tab_elems(int n, int S, int T) {
+  return 4 * S * pipe_npad(n) + T * S + 2 * S;
+}
+
+// One chunk of one column: e = L_N d (FP32), forward elimination, carry in,
+// back substitution, carry in, c d + y (FP32), Dirichlet, write-back.
+// FULL: the chunk has exactly MAXM positions (no per-position guards).
+// PS > 0: compile-time stride between positions in the staged tile.
+template <typename E, int MAXM, bool FULL, int PS>
+__device__ __forceinline__ void pipe_chunk(E *p, const int ps_rt, const int len, const int lo,
+                                           const int n, const int t, const int T, const int lane,
+                                           const E *Ti, const E *Tm, const E *Tf, const E *Tb,
+                                           const E *Tpc, const int S, const int s, const E chi,
+                                           const E clo, E *s_end, E *s_beg, const int ncons,
+                                           const bool dir, const bool face, const E dval) {
+  const int ps = PS > 0 ? PS : ps_rt;
+  E v[MAXM];
+#pragma unroll
+  for (int i = 0; i < MAXM; i++)
+    if (FULL || i < len) v[i] = p[i * ps];
+  if constexpr (kDefect<E>) {
+    // e = L_N d.  At the two ends of the line the zero-flux rows equal the
+    // interior formula with a mirrored ghost value (d_{-1} = d_0,
+    // d_n = d_{n-1}), so no position needs a branch.
+    E prev = E(0), after = E(0);
+    if (len > 0) {
+      prev = lo > 0 ? p[-ps] : v[0];
+      // (the last value is re-read from the tile: selecting v[len-1] would
+      // index the register array dynamically)
+      const E last = FULL ? v[MAXM - 1] : p[(len - 1) * ps];
+      after = lo + len < n ? p[(FULL ? MAXM : len) * ps] : last;
+    }
+#pragma unroll
+    for (int i = 0; i < MAXM; i++)
+      if (FULL || i < len) {
+        const E cur = v[i];
+        const E nxt = (i + 1 < MAXM && (FULL || i + 1 < len)) ? v[i + 1] : after;
+        v[i] = (cur - prev) + (cur - nxt);
+        prev = cur;
+      }
+  }
+  E g = E(0);
+#pragma unroll
+  for (int i = 0; i < MAXM; i++)
+    if (FULL || i < len) {
+      g = fma(Tm[i], g, v[i] * Ti[i]);
+      v[i] = g;
+    }
+  s_end[t * 32 + lane] = g;
+  consumers_sync(ncons);
+  if (t > 0) {  // chunk 0 enters with a zero carry
+    E carry = E(0), w = E(1);
+    for (int u = t - 1; u >= 0; u--) {
+      carry = fma(w, s_end[u * 32 + lane], carry);
+      w = w * Tpc[u * S + s];
+    }
+#pragma unroll
+    for (int i = 0; i < MAXM; i++)
+      if (FULL || i < len) v[i] = fma(Tf[i], carry, v[i]);
+  }
+  E x = E(0);
+#pragma unroll
+  for (int i = MAXM - 1; i >= 0; i--)
+    if (FULL || i < len) {
+      x = fma(Tm[i], x, v[i]);
+      v[i] = x;
+    }
+  s_beg[t * 32 + lane] = x;
+  consumers_sync(ncons);
+  if (t + 1 < T) {  // the last chunk enters with a zero carry
+    E carry = E(0), w = E(1);
+    for (int u = t + 1; u < T; u++) {
+      carry = fma(w, s_beg[u * 32 + lane], carry);
+      w = w * Tpc[u * S + s];
+    }
+#pragma unroll
+    for (int i = 0; i < MAXM; i++)
+      if (FULL || i < len) v[i] = fma(Tb[i], carry, v[i]);
+  }
+  if constexpr (kDefect<E>) {  // x = c_hi d + (c_lo d + y), d from the staged tile
+#pragma unroll
+    for (int i = 0; i < MAXM; i++)
+      if (FULL || i < len) {
+        const E d = p[i * ps];
+        v[i] = fma(chi, d, fma(clo, d, v[i]));
+      }
+  }
+  if (dir && len > 0) {
+#pragma unroll
+    for (int i = 0; i < MAXM; i++)
+      if ((FULL || i < len) && (face || lo + i == 0 || lo + i == n - 1)) v[i] = dval;
+  }
+  consumers_sync(ncons);  // every halo read of this tile is done before any write-back
+#pragma unroll
+  for (int i = 0; i < MAXM; i++)
+    if (FULL || i < len) p[i * ps] = v[i];
+}
+
+// MODE 0: x tiles (per-row bulk copies, Src and B before the solve);
+// MODE 1: y/z tiles (tensor boxes).
+template <typename E, int MAXM, int MODE>
+__global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
+    sweep_pipe_kernel(const __grid_constant__ CUtensorMap map, const PipeArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  const int T = a.tab.T, m = a.tab.m, n = a.n, S = a.S, NS = a.stages;
+  const int64_t stage_elems = a.stage_elems;
+  const int npad = pipe_npad(n);
+  E *stage0 = reinterpret_cast<E *>(smem_raw);
+  E *tab = stage0 + NS * stage_elems;
+  E *s_inv = tab, *s_mul = tab + S * npad, *s_pf = s_mul + S * npad, *s_pb = s_pf + S * npad;
+  E *s_pc = s_pb + S * npad, *s_cfix = s_pc + T * S;
+  E *s_end = s_cfix + 2 * S;
+  E *s_beg = s_end + T * 32;
+  uint64_t *full = reinterpret_cast<uint64_t *>(
+      (reinterpret_cast<uintptr_t>(s_beg + T * 32) + 15) & ~uintptr_t(15));
+  uint64_t *done = full + NS;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long first = blockIdx.x;
+  const long long count = (a.ntiles - first + gridDim.x - 1) / gridDim.x;
+  const int ncons = T * 32;
+  E *field = static_cast<E *>(a.field);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NS; s++) {
+      mbar_init(&full[s], 1);
+      mbar_init(&done[s], ncons);
+    }
+    fence_mbar_init();
+    fence_proxy_async_smem();
+  }
+  {  // constants: global [n][S] -> shared [S][npad] (transposed), then pc and cfix
+    const E *g = static_cast<const E *>(a.tab.inv);
+    const int nS = n * S;
+    for (int q = threadIdx.x; q < 4 * nS; q += blockDim.x) {
+      const int which = q / nS, r = q - which * nS, i = r / S, ss = r - i * S;
+      tab[which * S * npad + ss * npad + i] = __ldg(g + q);
+    }
+    for (int q = threadIdx.x; q < T * S + 2 * S; q += blockDim.x) s_pc[q] = __ldg(g + 4 * nS + q);
+  }
+  __syncthreads();
+
+  if (warp == 0) {  // ------------------------------------------------ producer
+    if (lane != 0) return;
+    auto rows_of = [&](long long tile) {
+      const long long r0 = tile * a.rows_per_tile;
+      return (int)min((long long)a.rows_per_tile, a.nrows - r0);
+    };
+    auto issue_load = [&](long long k, int s) {
+      const long long tile = first + k * gridDim.x;
+      E *dst = stage0 + s * stage_elems;
+      if constexpr (MODE == 0) {
+        const int rows = rows_of(tile);
+        const uint32_t rb = (uint32_t)(a.rowlen * sizeof(E));
+        mbar_arrive_expect_tx(&full[s], rb * rows);
+        for (int r = 0; r < rows; r++)
+          bulk_g2s(dst + (size_t)r * a.pitch, field + (tile * a.rows_per_tile + r) * a.rowlen, rb,
+                   &full[s]);
+      } else {
+        const int plane = (int)(tile / a.tiles_per_plane);
+        const int c0 = (int)(tile % a.tiles_per_plane) * 32;
+        mbar_arrive_expect_tx(&full[s], (uint32_t)(stage_elems * sizeof(E)));
+        for (int b = 0; b < a.nbox; b++)
+          tma_load_3d(dst + (size_t)b * a.box_rows * 32, &map, c0, b * a.box_rows, plane, &full[s]);
+      }
+    };
+    auto issue_store = [&](long long k, int s) {
+      const long long tile = first + k * gridDim.x;
+      const E *src = stage0 + s * stage_elems;
+      if constexpr (MODE == 0) {
+        const int rows = rows_of(tile);
+        const uint32_t rb = (uint32_t)(a.rowlen * sizeof(E));
+        for (int r = 0; r < rows; r++)
+          bulk_s2g(field + (tile * a.rows_per_tile + r) * a.rowlen, src + (size_t)r * a.pitch, rb);
+      } else {
+        const int plane = (int)(tile / a.tiles_per_plane);
+        const int c0 = (int)(tile % a.tiles_per_plane) * 32;
+        for (int b = 0; b < a.nbox; b++)
+          tma_store_3d(&map, c0, b * a.box_rows, plane, src + (size_t)b * a.box_rows * 32);
+      }
+      bulk_commit();
+    };
+    const long long pre = count < NS ? count : NS;
+    for (long long k = 0; k < pre; k++) issue_load(k, (int)k);
+    long long k = 0;
+    bool ok = true;
+    for (; k < count; k++) {
+      const int s = (int)(k % NS);
+      if (!(ok = mbar_wait_bounded(&done[s], (uint32_t)((k / NS) & 1), a.status))) break;
+      issue_store(k, s);
+      if (k + NS < count) {
+        bulk_wait_read_all();  // the stage is free once the store has read it
+        issue_load(k + NS, s);
+      }
+    }
+    if (!ok) {  // drain the loads still in flight (bounded) before exiting
+      for (long long j = k; j < count && j < k + NS; j++)
+        mbar_wait_bounded(&full[j % NS], (uint32_t)((j / NS) & 1), a.status);
+    }
+    bulk_wait_all();
+    return;
+  }
+
+  // ---------------------------------------------------------------- consumers
+  const int t = warp - 1;
+  const int ctid = threadIdx.x - 32;
+  const int lo = t * m;
+  const int len_full = min(m, n - lo);
+  const int colbase = MODE == 0 ? (lane / S) * a.pitch + lane % S : lane;
+  const int ps_rt = MODE == 0 ? S : 32;
+  const bool dir_after = (a.flags & kDirAfter) != 0;
+  for (long long k = 0; k < count; k++) {
+    const int st = (int)(k % NS);
+    bool ok = mbar_wait_bounded(&full[st], (uint32_t)((k / NS) & 1), a.status);
+    if (!consumers_all(ok, ncons)) break;
+    const long long tile = first + k * gridDim.x;
+    E *const stg = stage0 + st * stage_elems;
+    int s;
+    bool active, face = false;
+    if constexpr (MODE == 0) {
+      const long long r0 = tile * a.rows_per_tile;
+      const int rows = (int)min((long long)a.rows_per_tile, a.nrows - r0);
+      s = lane % S;
+      const long long row = r0 + lane / S;
+      active = lane < a.rows_per_tile * S && lane / S < rows;
+      {
+        const int y = (int)(row % a.ny), z = (int)(row / a.ny);
+        face = y == 0 || y == a.ny - 1 || z == 0 || z == a.nz - 1;
+      }
+      // Src then B on the staged rows, before any solve
+      if ((a.flags & kSrc) && a.has_src) {
+        const long long e0 = a.src_row_off[r0], e1 = a.src_row_off[r0 + rows];
+        for (long long e = e0 + ctid; e < e1; e += ncons) {
+          const long long el = a.src_elem[e];
+          const long long rr = el / a.rowlen;
+          E *q = stg + (rr - r0) * a.pitch + (el - rr * a.rowlen);
+          *q = (*q + ldg<E>(a.src_alpha, e)) * ldg<E>(a.src_scale, e);
+        }
+      }
+      if (a.flags & kDirBefore) {  // consumer warp t takes rows t, t+T, ...
+        for (int rr = t; rr < rows; rr += T) {
+          const long long gr = r0 + rr;
+          const int y = (int)(gr % a.ny), z = (int)(gr / a.ny);
+          E *tr = stg + (size_t)rr * a.pitch;
+          if (y == 0 || y == a.ny - 1 || z == 0 || z == a.nz - 1) {
+            for (int kk = lane; kk < a.rowlen; kk += 32) {
+              const int ss = kk % S;
+              if (a.dir_on[ss]) tr[kk] = dir_value<E>(a.flags, a.dir_val, ss);
+            }
+          } else {
+            for (int kk = lane; kk < 2 * S; kk += 32) {
+              const int ss = kk % S;
+              if (a.dir_on[ss])
+                tr[kk < S ? ss : (a.nx - 1) * S + ss] = dir_value<E>(a.flags, a.dir_val, ss);
+            }
+          }
+        }
+      }
+      if ((a.flags & (kSrc | kDirBefore)) != 0) consumers_sync(ncons);
+    } else {
+      const int plane = (int)(tile / a.tiles_per_plane);
+      const long long c = (tile % a.tiles_per_plane) * 32 + lane;
+      active = c < a.C;
+      s = (int)(c % S);
+      if (dir_after) {
+        if (a.mode == 1) {
+          const int x0 = (int)(c / S);
+          face = (x0 == 0 || x0 == a.nx - 1 || plane == 0 || plane == a.nz - 1);
+        } else {
+          const long long vox = c / S;
+          const int x0 = (int)(vox % a.nx), y = (int)(vox / a.nx);
+          face = (x0 == 0 || x0 == a.nx - 1 || y == 0 || y == a.ny - 1);
+        }
+      }
+    }
+    const int len = active ? len_full : 0;
+    E *p = stg + colbase + lo * ps_rt;
+    const int rowoff = s * npad + lo;
+    const bool dir = dir_after && a.dir_on[s];
+    const E dval = dir ? dir_value<E>(a.flags, a.dir_val, s) : E(0);
+    const E chi = s_cfix[s], clo = s_cfix[S + s];
+    if (len == MAXM)
+      pipe_chunk<E, MAXM, true, MODE == 0 ? 0 : 32>(p, ps_rt, len, lo, n, t, T, lane,
+                                                    s_inv + rowoff, s_mul + rowoff, s_pf + rowoff,
+                                                    s_pb + rowoff, s_pc, S, s, chi, clo, s_end,
+                                                    s_beg, ncons, dir, face, dval);
+    else
+      pipe_chunk<E, MAXM, false, MODE == 0 ? 0 : 32>(p, ps_rt, len, lo, n, t, T, lane,
+                                                     s_inv + rowoff, s_mul + rowoff, s_pf + rowoff,
+                                                     s_pb + rowoff, s_pc, S, s, chi, clo, s_end,
+                                                     s_beg, ncons, dir, face, dval);
+    fence_proxy_async_smem();  // generic-proxy writes -> visible to the bulk store
+    mbar_arrive(&done[st]);
+  }
+}
+
+template <typename E, int MAXM>
+cudaError_t allow_pipe_smem(size_t bytes) {
+  cudaError_t e = cudaFuncSetAttribute(sweep_pipe_kernel<E, MAXM, 0>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(sweep_pipe_kernel<E, MAXM, 1>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <typename E, int MAXM>
+cudaError_t launch_pipe_one(const CUtensorMap &map, const PipeArgs &a, int grid, size_t smem,
+                            cudaStream_t st) {
+  if ((a.tab.T + 1) * 32 > PipeBound<E, MAXM>::threads) return cudaErrorInvalidConfiguration;
+  if (a.mode == 0)
+    sweep_pipe_kernel<E, MAXM, 0><<<grid, (a.tab.T + 1) * 32, smem, st>>>(map, a);
+  else
+    sweep_pipe_kernel<E, MAXM, 1><<<grid, (a.tab.T + 1) * 32, smem, st>>>(map, a);
+  return cudaGetLastError();
+}
+
+}  // namespace bfv

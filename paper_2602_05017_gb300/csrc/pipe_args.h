@@ -1,0 +1,47 @@
+// Arguments of the persistent TMA-pipelined sweep kernel (pipe.cuh).
+#pragma once
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace bfv {
+
+// A tile is 32 "columns" (independent lines) x n positions along the axis.
+//
+//   mode 0 (x-sweep): a column is one (row, substrate) pair of
+//     rows_per_tile = floor(32/S) consecutive rows (y, z); the rows are
+//     staged with one cp.async.bulk each into shared memory at a padded
+//     `pitch` (elements) chosen on the host so that the 32 lanes of a warp
+//     hit 32 different banks; element (column c, position x) sits at
+//     (c/S)*pitch + x*S + c%S.
+//   mode 1 / 2 (y- / z-sweep): a column is one of 32 consecutive (x, s) or
+//     (x, y, s) entries of a plane; the tile [n][32] is staged with
+//     cp.async.bulk.tensor boxes of box_rows x 32; element (c, j) sits at
+//     j*32 + c.
+//
+// Tile k of a CTA is tile blockIdx.x + k*gridDim.x of ntiles.
+struct PipeArgs {
+  int mode, n, S, nx, ny, nz;
+  int64_t ntiles;
+  // mode 1 / 2
+  int64_t C;
+  int tiles_per_plane, nplanes, box_rows, nbox;
+  // mode 0
+  int rows_per_tile, rowlen, pitch;
+  int64_t nrows;
+  void *field;
+  // ring of stages
+  int stages, tab_in_smem;
+  int64_t stage_elems;
+  AxisTab tab;
+  int flags;
+  // mode 0: sources (CSR over rows) and the Dirichlet application before the solve
+  const int64_t *src_row_off, *src_elem;
+  const void *src_alpha, *src_scale;
+  int has_src;
+  const uint8_t *dir_on;
+  const void *dir_val;
+  int *status;
+};
+
+}  // namespace bfv

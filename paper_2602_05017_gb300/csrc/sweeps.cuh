@@ -106,6 +106,13 @@ __device__ __forceinline__ E ldg(const void *p, long long i) {
   return __ldg(static_cast<const E *>(p) + i);
 }
 
+// Value a Dirichlet application writes: the substrate's value, or 0 for the
+// adjoint mask.
+template <typename E>
+__device__ __forceinline__ E dir_value(int flags, const void *dir_val, int s) {
+  return (flags & kMaskZero) ? E(0) : ldg<E>(dir_val, s);
+}
+
 // FP32 kernels solve in defect-correction form (see AxisTab); FP64 solves
 // the plain system.
 template <typename E>
@@ -201,13 +208,13 @@ __global__ void __launch_bounds__(256) x_sweep_kernel(const XLaunch a) {
       if (face) {
         for (int k = lane; k < rowlen; k += 32) {
           const int s = k % S;
-          if (a.dir_on[s]) tr[k] = ldg<E>(a.dir_val, s);
+          if (a.dir_on[s]) tr[k] = dir_value<E>(a.flags, a.dir_val, s);
         }
       } else {
         for (int k = lane; k < 2 * S; k += 32) {
           const int s = k % S;
           const int idx = (k < S) ? s : (nx - 1) * S + s;
-          if (a.dir_on[s]) tr[idx] = ldg<E>(a.dir_val, s);
+          if (a.dir_on[s]) tr[idx] = dir_value<E>(a.flags, a.dir_val, s);
         }
       }
     }
@@ -305,7 +312,7 @@ __global__ void __launch_bounds__(256) x_sweep_kernel(const XLaunch a) {
     if ((a.flags & kDirAfter) && active && a.dir_on[s]) {
       const long long row = row0 + r;
       const int y = (int)(row % a.ny), z = (int)(row / a.ny);
-      const E val = ldg<E>(a.dir_val, s);
+      const E val = dir_value<E>(a.flags, a.dir_val, s);
       if (y == 0 || y == a.ny - 1 || z == 0 || z == a.nz - 1) {
 #pragma unroll
         for (int i = 0; i < MAXM; i++)
@@ -329,7 +336,7 @@ __global__ void __launch_bounds__(256) x_sweep_kernel(const XLaunch a) {
       E *tr = tile + (size_t)r * rowlen;
       for (int k = lane; k < rowlen; k += 32) {
         const int s = k % S, x = k / S;
-        if (a.dir_on[s] && (face || x == 0 || x == nx - 1)) tr[k] = ldg<E>(a.dir_val, s);
+        if (a.dir_on[s] && (face || x == 0 || x == nx - 1)) tr[k] = dir_value<E>(a.flags, a.dir_val, s);
       }
     }
   }
@@ -366,8 +373,6 @@ __global__ void __launch_bounds__(ColBound<E, MAXM>::threads) col_sweep_kernel(c
   extern __shared__ __align__(128) unsigned char smem_raw[];
   E *s_end = reinterpret_cast<E *>(smem_raw);  // [T][32] forward chunk ends
   E *s_beg = s_end + a.tab.T * 32;             // [T][32] backward chunk starts
-  E *s_first = s_beg + a.tab.T * 32;           // [T][32] chunk first values (FP32 halo)
-  E *s_last = s_first + a.tab.T * 32;          // [T][32] chunk last values (FP32 halo)
   const int lane = threadIdx.x, t = threadIdx.y;
   const int T = a.tab.T, m = a.tab.m, n = a.n, S = a.S;
   const long long c = (long long)blockIdx.x * 32 + lane;
@@ -379,28 +384,19 @@ __global__ void __launch_bounds__(ColBound<E, MAXM>::threads) col_sweep_kernel(c
   const long long C = a.C;
 
   E v[MAXM];
-  E dd[kDefect<E> ? MAXM : 1];  // FP32: the right-hand side, kept for the final sum
 #pragma unroll
   for (int i = 0; i < MAXM; i++)
     if (i < len) v[i] = col[(long long)(lo + i) * C];
   if constexpr (kDefect<E>) {
-    E last = E(0);
+    // e = L_N d in place; halo values are read from the neighbouring chunks'
+    // rows (not yet overwritten: every thread writes its own rows last)
+    E prev = (len > 0 && lo > 0) ? col[(long long)(lo - 1) * C] : E(0);
+    const E after = (len > 0 && lo + len < n) ? col[(long long)(lo + len) * C] : E(0);
 #pragma unroll
     for (int i = 0; i < MAXM; i++)
       if (i < len) {
-        dd[i] = v[i];
-        if (i == len - 1) last = v[i];
-      }
-    s_first[t * 32 + lane] = (len > 0) ? v[0] : E(0);
-    s_last[t * 32 + lane] = last;
-    __syncthreads();
-    E prev = (t > 0) ? s_last[(t - 1) * 32 + lane] : E(0);
-    const E after = (t + 1 < T) ? s_first[(t + 1) * 32 + lane] : E(0);
-#pragma unroll
-    for (int i = 0; i < MAXM; i++)
-      if (i < len) {
-        const E cur = dd[i];
-        const E nxt = (i + 1 < MAXM && i + 1 < len) ? dd[i + 1] : after;
+        const E cur = v[i];
+        const E nxt = (i + 1 < MAXM && i + 1 < len) ? v[i + 1] : after;
         v[i] = second_difference(cur, prev, nxt, lo + i, n);
         prev = cur;
       }
@@ -446,7 +442,10 @@ __global__ void __launch_bounds__(ColBound<E, MAXM>::threads) col_sweep_kernel(c
     const E chi = ldg<E>(a.tab.cfix, s), clo = ldg<E>(a.tab.cfix, S + s);
 #pragma unroll
     for (int i = 0; i < MAXM; i++)
-      if (i < len) v[i] = fma(chi, dd[i], fma(clo, dd[i], v[i]));
+      if (i < len) {
+        const E d = col[(long long)(lo + i) * C];  // the right-hand side (L2-resident)
+        v[i] = fma(chi, d, fma(clo, d, v[i]));
+      }
   }
 
   if ((a.flags & kDirAfter) && len > 0 && a.dir_on[s]) {
@@ -459,7 +458,7 @@ __global__ void __launch_bounds__(ColBound<E, MAXM>::threads) col_sweep_kernel(c
       const int x0 = (int)(vox % a.nx), y = (int)(vox / a.nx);
       face = (x0 == 0 || x0 == a.nx - 1 || y == 0 || y == a.ny - 1);
     }
-    const E val = ldg<E>(a.dir_val, s);
+    const E val = dir_value<E>(a.flags, a.dir_val, s);
 #pragma unroll
     for (int i = 0; i < MAXM; i++)
       if (i < len && (face || lo + i == 0 || lo + i == n - 1)) v[i] = val;
@@ -491,7 +490,7 @@ template <typename E, int MAXM>
 cudaError_t launch_col_one(const ColLaunch &a, cudaStream_t st) {
   auto k = col_sweep_kernel<E, MAXM>;
   if (a.tab.T * 32 > ColBound<E, MAXM>::threads) return cudaErrorInvalidConfiguration;
-  const size_t smem = (kDefect<E> ? 4 : 2) * (size_t)a.tab.T * 32 * sizeof(E);
+  const size_t smem = 2 * (size_t)a.tab.T * 32 * sizeof(E);
   dim3 grid((unsigned)((a.C + 31) / 32), (unsigned)a.nplanes);
   dim3 block(32, (unsigned)a.tab.T);
   k<<<grid, block, smem, st>>>(a);

@@ -1,5 +1,8 @@
 // FP32 instantiations of the sweep kernels (element type float; the Thomas
 // constants are computed in double on the host and rounded to float).
+#include "adjoint.cuh"
+#include "batch.cuh"
+#include "pipe.cuh"
 #include "sweeps.cuh"
 
 namespace bfv {
@@ -43,6 +46,81 @@ cudaError_t allow_x_smem_f32(int maxm, size_t bytes) {
     case 64: return allow_x_smem<float, 64>(bytes);
     case 96: return allow_x_smem<float, 96>(bytes);
     case 128: return allow_x_smem<float, 128>(bytes);
+  }
+  return cudaErrorInvalidValue;
+}
+
+
+cudaError_t allow_pipe_smem_f32(int maxm, size_t bytes) {
+  switch (maxm) {
+    case 8: return allow_pipe_smem<float, 8>(bytes);
+    case 16: return allow_pipe_smem<float, 16>(bytes);
+    case 24: return allow_pipe_smem<float, 24>(bytes);
+    case 32: return allow_pipe_smem<float, 32>(bytes);
+    case 48: return allow_pipe_smem<float, 48>(bytes);
+    case 64: return allow_pipe_smem<float, 64>(bytes);
+    case 96: return allow_pipe_smem<float, 96>(bytes);
+    case 128: return allow_pipe_smem<float, 128>(bytes);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_pipe_f32(const CUtensorMap &map, const PipeArgs &a, int maxm, int grid,
+                            size_t smem, cudaStream_t st) {
+  switch (maxm) {
+    case 8: return launch_pipe_one<float, 8>(map, a, grid, smem, st);
+    case 16: return launch_pipe_one<float, 16>(map, a, grid, smem, st);
+    case 24: return launch_pipe_one<float, 24>(map, a, grid, smem, st);
+    case 32: return launch_pipe_one<float, 32>(map, a, grid, smem, st);
+    case 48: return launch_pipe_one<float, 48>(map, a, grid, smem, st);
+    case 64: return launch_pipe_one<float, 64>(map, a, grid, smem, st);
+    case 96: return launch_pipe_one<float, 96>(map, a, grid, smem, st);
+    case 128: return launch_pipe_one<float, 128>(map, a, grid, smem, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+
+cudaError_t launch_adj_reduce_f32(const ReduceLaunch &a, cudaStream_t st) {
+  adj_reduce_kernel<float><<<a.nblocks, kReduceThreads, 0, st>>>(
+      static_cast<const float *>(a.mu), static_cast<const float *>(a.u), a.nel, a.S, a.stride,
+      a.n_axis, a.used, a.partial);
+  adj_reduce_final_kernel<float><<<1, 32, 0, st>>>(a.partial, a.nblocks, a.S, a.scale_lambda, a.scale_D,
+                                            a.dlambda, a.dD);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_src_adjoint_f32(const SrcAdjLaunch &a, cudaStream_t st) {
+  if (a.dsec && a.n > 0)
+    src_adjoint_agents_kernel<float><<<(unsigned)((a.n + 255) / 256), 256, 0, st>>>(
+        static_cast<const float *>(a.gbar), static_cast<const float *>(a.u1), a.elem, a.entry,
+        static_cast<const float *>(a.src_scale), a.weight, a.target, a.n, a.dt, a.S, a.dsec);
+  if (a.n_entries > 0)
+    src_adjoint_scale_kernel<float><<<(unsigned)((a.n_entries + 255) / 256), 256, 0, st>>>(
+        static_cast<float *>(a.gbar), a.src_elem, static_cast<const float *>(a.src_scale),
+        a.n_entries);
+  return cudaGetLastError();
+}
+
+
+cudaError_t launch_batch_f32(const BatchArgs &a, int maxm, int grid, cudaStream_t st) {
+  switch (maxm) {
+    case 8: return launch_batch_one<float, 8>(a, grid, st);
+    case 16: return launch_batch_one<float, 16>(a, grid, st);
+    case 24: return launch_batch_one<float, 24>(a, grid, st);
+    case 32: return launch_batch_one<float, 32>(a, grid, st);
+    case 48: return launch_batch_one<float, 48>(a, grid, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t batch_occupancy_f32(int maxm, int *out) {
+  switch (maxm) {
+    case 8: return batch_blocks_per_sm<float, 8>(out);
+    case 16: return batch_blocks_per_sm<float, 16>(out);
+    case 24: return batch_blocks_per_sm<float, 24>(out);
+    case 32: return batch_blocks_per_sm<float, 32>(out);
+    case 48: return batch_blocks_per_sm<float, 48>(out);
   }
   return cudaErrorInvalidValue;
 }

@@ -1,4 +1,7 @@
 // FP64 instantiations of the sweep kernels (element type double).
+#include "adjoint.cuh"
+#include "batch.cuh"
+#include "pipe.cuh"
 #include "sweeps.cuh"
 
 namespace bfv {
@@ -36,6 +39,83 @@ cudaError_t allow_x_smem_f64(int maxm, size_t bytes) {
     case 32: return allow_x_smem<double, 32>(bytes);
     case 48: return allow_x_smem<double, 48>(bytes);
     case 64: return allow_x_smem<double, 64>(bytes);
+  }
+  return cudaErrorInvalidValue;
+}
+
+
+cudaError_t allow_pipe_smem_f64(int maxm, size_t bytes) {
+  switch (maxm) {
+    case 8: return allow_pipe_smem<double, 8>(bytes);
+    case 16: return allow_pipe_smem<double, 16>(bytes);
+    case 24: return allow_pipe_smem<double, 24>(bytes);
+    case 32: return allow_pipe_smem<double, 32>(bytes);
+    case 48: return allow_pipe_smem<double, 48>(bytes);
+    case 64: return allow_pipe_smem<double, 64>(bytes);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_pipe_f64(const CUtensorMap &map, const PipeArgs &a, int maxm, int grid,
+                            size_t smem, cudaStream_t st) {
+  switch (maxm) {
+    case 8: return launch_pipe_one<double, 8>(map, a, grid, smem, st);
+    case 16: return launch_pipe_one<double, 16>(map, a, grid, smem, st);
+    case 24: return launch_pipe_one<double, 24>(map, a, grid, smem, st);
+    case 32: return launch_pipe_one<double, 32>(map, a, grid, smem, st);
+    case 48: return launch_pipe_one<double, 48>(map, a, grid, smem, st);
+    case 64: return launch_pipe_one<double, 64>(map, a, grid, smem, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+int pipe_max_threads(int maxm, size_t esz) {  // mirrors PipeBound
+  const int regs = maxm * (int)esz / 4 + 96;
+  const int raw = 65536 / regs;
+  return (raw >= 1024 ? 1024 : raw) / 32 * 32;
+}
+
+
+cudaError_t launch_adj_reduce_f64(const ReduceLaunch &a, cudaStream_t st) {
+  adj_reduce_kernel<double><<<a.nblocks, kReduceThreads, 0, st>>>(
+      static_cast<const double *>(a.mu), static_cast<const double *>(a.u), a.nel, a.S, a.stride,
+      a.n_axis, a.used, a.partial);
+  adj_reduce_final_kernel<double><<<1, 32, 0, st>>>(a.partial, a.nblocks, a.S, a.scale_lambda, a.scale_D,
+                                            a.dlambda, a.dD);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_src_adjoint_f64(const SrcAdjLaunch &a, cudaStream_t st) {
+  if (a.dsec && a.n > 0)
+    src_adjoint_agents_kernel<double><<<(unsigned)((a.n + 255) / 256), 256, 0, st>>>(
+        static_cast<const double *>(a.gbar), static_cast<const double *>(a.u1), a.elem, a.entry,
+        static_cast<const double *>(a.src_scale), a.weight, a.target, a.n, a.dt, a.S, a.dsec);
+  if (a.n_entries > 0)
+    src_adjoint_scale_kernel<double><<<(unsigned)((a.n_entries + 255) / 256), 256, 0, st>>>(
+        static_cast<double *>(a.gbar), a.src_elem, static_cast<const double *>(a.src_scale),
+        a.n_entries);
+  return cudaGetLastError();
+}
+
+
+cudaError_t launch_batch_f64(const BatchArgs &a, int maxm, int grid, cudaStream_t st) {
+  switch (maxm) {
+    case 8: return launch_batch_one<double, 8>(a, grid, st);
+    case 16: return launch_batch_one<double, 16>(a, grid, st);
+    case 24: return launch_batch_one<double, 24>(a, grid, st);
+    case 32: return launch_batch_one<double, 32>(a, grid, st);
+    case 48: return launch_batch_one<double, 48>(a, grid, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t batch_occupancy_f64(int maxm, int *out) {
+  switch (maxm) {
+    case 8: return batch_blocks_per_sm<double, 8>(out);
+    case 16: return batch_blocks_per_sm<double, 16>(out);
+    case 24: return batch_blocks_per_sm<double, 24>(out);
+    case 32: return batch_blocks_per_sm<double, 32>(out);
+    case 48: return batch_blocks_per_sm<double, 48>(out);
   }
   return cudaErrorInvalidValue;
 }

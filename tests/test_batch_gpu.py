@@ -1,0 +1,123 @@
+"""Batched persistent step (biofvm_batch_*) against the FP64 oracle, environment by environment,
+plus the autotuner's cache plumbing."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2602_05017_gb300 import autotune, inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "fp32": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def binding():
+    from paper_2602_05017_gb300 import binding as b
+    return b
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def _envs(seed, shapes):
+    rng = np.random.default_rng(seed)
+    out = []
+    for (nx, ny, nz, ns) in shapes:
+        w = inputs.random_problem(rng, nx, ny, nz, ns, n_agents=max(1, nx * ny * nz // 30))
+        out.append(w)
+    return out
+
+
+SHAPES = [(33, 17, 9, 3), (8, 40, 21, 1), (50, 50, 50, 4), (7, 5, 3, 8), (64, 9, 30, 2),
+          (1, 12, 12, 2), (20, 20, 1, 5), (96, 11, 13, 6)]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_batch_matches_oracle_per_environment(binding, prec):
+    envs = _envs(1, SHAPES)
+    b = binding.BioFVMBatch(envs, precision=prec)
+    for sim, w in zip(b.envs, envs):
+        sim.set_density(w.rho0)
+        sim.set_sources(w.voxel, w.secretion, w.target, w.uptake, w.weight)
+    b.step(4)
+    b.sync()
+    for sim, w in zip(b.envs, envs):
+        ref = oracle.Problem(**w.oracle_kwargs()).step(w.rho0, 4)
+        assert rel(sim.density(), ref) <= TOL[prec], w.name
+    b.close()
+
+
+def test_batch_with_explicit_tile_shapes_and_repeated_calls(binding):
+    envs = _envs(2, [(48, 40, 36, 2), (25, 31, 19, 4), (64, 64, 8, 1)])
+    shapes = [[m, m, m] for m in (8, 12, 16)]
+    b = binding.BioFVMBatch(envs, precision="fp64", tile_m=shapes)
+    for sim, w in zip(b.envs, envs):
+        sim.set_density(w.rho0)
+        sim.set_sources(w.voxel, w.secretion, w.target, w.uptake, w.weight)
+    b.step(2)
+    b.step(3)  # a second graph for another step count, the field carried over
+    b.sync()
+    for sim, w in zip(b.envs, envs):
+        ref = oracle.Problem(**w.oracle_kwargs()).step(w.rho0, 5)
+        assert rel(sim.density(), ref) <= 1e-12
+    b.close()
+
+
+def test_batch_sources_changed_between_launches(binding):
+    envs = _envs(3, [(30, 20, 10, 2), (12, 12, 12, 3)])
+    b = binding.BioFVMBatch(envs, precision="fp64")
+    for sim, w in zip(b.envs, envs):
+        sim.set_density(w.rho0)
+    b.step(1)
+    mid = [sim.density() for sim in b.envs]
+    for sim, w in zip(b.envs, envs):
+        sim.set_sources(w.voxel, w.secretion, w.target, w.uptake, w.weight)
+    b.step(2)
+    b.sync()
+    for sim, w, m in zip(b.envs, envs, mid):
+        ref = oracle.Problem(**w.oracle_kwargs()).step(m, 2)
+        assert rel(sim.density(), ref) <= 1e-12
+    b.close()
+
+
+def test_batch_rejects_invalid_tile_shapes(binding):
+    envs = _envs(4, [(100, 10, 10, 1)])
+    with pytest.raises(binding.BioFVMError):
+        binding.BioFVMBatch(envs, tile_m=[[8, 8, 8]])  # 100/8 -> 13 chunks > 8
+
+
+def test_batched_workload_recipe_reduced(binding):
+    """The batched recipe (uneven cubes, 1-8 substrates, log-uniform D and lambda, agents 1 per
+    64 voxels) with 12 environments of edge 16-48, 10 steps, FP32 vs the FP64 oracle."""
+    envs = inputs.batched_workloads(n_env=12, edge=(16, 48), n_steps=10, field_dtype=np.float64)
+    b = binding.BioFVMBatch(envs, precision="fp32")
+    for sim, w in zip(b.envs, envs):
+        sim.set_density(w.rho0)
+        sim.set_sources(w.voxel, w.secretion, w.target, w.uptake, w.weight)
+    b.step(10)
+    b.sync()
+    for sim, w in zip(b.envs, envs):
+        ref = oracle.Problem(**w.oracle_kwargs()).step(w.rho0, 10)
+        assert rel(sim.density(), ref) <= 1e-5, w.name
+    b.close()
+
+
+def test_autotuner_cache_roundtrip(binding, tmp_path):
+    cache = autotune.tune("fp32", n_buckets=(32,), subs=(2,), target_vs=2e6, steps=1, reps=1,
+                          path=str(tmp_path / "c.json"))
+    loaded = autotune.load(str(tmp_path / "c.json"))
+    assert loaded["classes"].keys() == cache["classes"].keys()
+    envs = _envs(5, [(30, 33, 31, 2), (32, 32, 32, 2)])
+    shapes = autotune.tile_shapes(envs, loaded)
+    b = binding.BioFVMBatch(envs, precision="fp32", tile_m=shapes)
+    for sim, w in zip(b.envs, envs):
+        sim.set_density(w.rho0)
+    b.step(2)
+    b.sync()
+    for sim, w in zip(b.envs, envs):
+        ref = oracle.Problem(**w.oracle_kwargs()).step(w.rho0, 2)
+        assert rel(sim.density(), ref) <= 1e-5
+    b.close()

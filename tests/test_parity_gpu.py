@@ -243,3 +243,19 @@ def test_workload3_full_size_20_steps_fp32_properties(binding):
     err = float((f[..., 1].double() - expect.double()).abs().max()) / 38.0
     sim.close()
     assert err <= 1e-5
+
+
+@pytest.mark.parametrize("pipeline", ["0", "1"])
+@pytest.mark.parametrize("shape", [(40, 36, 28, 4), (64, 300, 9, 2), (8, 8, 520, 1), (16, 70, 70, 3)],
+                         ids=lambda s: "x".join(map(str, s)) if isinstance(s, tuple) else s)
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_sweep_paths_match_oracle(binding, monkeypatch, shape, pipeline, prec):
+    """Both sweep implementations (plain kernels and the persistent TMA pipeline,
+    chosen at create through BIOFVM_PIPELINE) against the oracle, with Dirichlet faces."""
+    monkeypatch.setenv("BIOFVM_PIPELINE", pipeline)
+    nx, ny, nz, ns = shape
+    rng = np.random.default_rng(17)
+    w = inputs.random_problem(rng, nx, ny, nz, ns, n_agents=100, dirichlet=True)
+    ref = orc(w).step(w.rho0, 3)
+    got = gpu_run(binding, w, prec, 3)
+    assert rel_err(got, ref) <= TOL[prec]
