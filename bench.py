@@ -32,9 +32,13 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 HBM_FALLBACK_GBS = 6800.0
-# FP64 FMA issue rate of one GB300 SM (FMA/clk), measured by an 8-chain FMA probe; a GB300
-# has 152 SMs at up to 2070 MHz.  See the design doc for the derivation.
-FP64_FMA_PER_CLK_PER_SM = None
+# FP64 ALU roof of a GB300: 2 FP64 FMA per clock per SM (0.5 per SM sub-partition, measured
+# with an 8-chain FMA probe: 6.28e11 FMA/s) x 152 SMs x 2070 MHz, an FMA counting 2 flops.
+FP64_FMA_PER_CLK_PER_SM = 2.0
+GB300_SMS = 152
+# Floating-point operations of the Thomas algorithm per element and sweep (Sect. 2.1, Eq. 2:
+# forward axpy + division, backward negated axpy).
+FLOPS_PER_ELEMENT_SWEEP = 5
 
 
 def measured_peaks():
@@ -97,6 +101,18 @@ class ClockSampler:
 SHAPE = None  # --shape overrides the grid (profiling a smaller case of the same recipe)
 
 
+def aggregate(ms_local, world, units_per_rank, steps, device=None):
+    """Max of the per-rank timed region over ranks and the whole-job rate it gives
+    (every rank processes `units_per_rank` units per step: replicas, weak scaling)."""
+    import torch
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return ms_max, world * units_per_rank * steps / (ms_max * 1e-3)
+
+
 def workload_config():
     from paper_2602_05017_gb300 import inputs
     if SHAPE is None:
@@ -153,11 +169,7 @@ def run_gpu(args):
             e1.synchronize()
             torch.cuda.synchronize(dev)
             barrier()
-        ms = e0.elapsed_time(e1)
-        ms_t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        if world > 1:
-            dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-        ms_max = float(ms_t.item())
+        ms_max, _ = aggregate(e0.elapsed_time(e1), world, nel, K, dev)
         # --- per-kernel durations over K steps (same stream, CUDA events between launches) ---
         kev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
         for k in range(K):
@@ -208,10 +220,9 @@ def run_batched(args, stream, dev):
                                     n_steps=args.batch_steps)
     cache_path = autotune.default_cache_path()
     if os.path.exists(cache_path):
-        cache, tuned = autotune.load(cache_path), "cache"
+        shapes, tuned = autotune.tile_shapes(envs, autotune.load(cache_path)), "autotuner cache"
     else:
-        cache, tuned = autotune.tune("fp32", reps=2), "tuned in this run"
-    shapes = autotune.tile_shapes(envs, cache)
+        shapes, tuned = None, "library defaults (no autotuner cache)"
     b = binding.BioFVMBatch(envs, precision="fp32", tile_m=shapes, stream=stream.cuda_stream)
     g = torch.Generator(device=dev)
     g.manual_seed(2602050174)
@@ -372,15 +383,26 @@ def main():
     return 0
 
 
-def roofline(r, w, peaks, src):
+def roofline(r, w, peaks, src, traffic=None):
+    """Roofline of the dominant (longest) sweep kernel.  FP32: HBM-bound, algorithmic bytes =
+    one read + one write of the field.  FP64: bound by the FP64 pipe (its HBM time is half its
+    FP64-ALU time at the measured rates), algorithmic flops = Eq. 2's 5 per element."""
     kms = r["kernel_ms"]
     i = int(np.argmax(kms))
     name = ("x", "y", "z")[i]
+    if r["esz"] == 8:
+        clk = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+        peak = 2.0 * FP64_FMA_PER_CLK_PER_SM * GB300_SMS * clk / 1e12
+        achieved = FLOPS_PER_ELEMENT_SWEEP * w.n_vs / (kms[i] * 1e-3) / 1e12
+        return {"bound": "alu", "kernel": f"{name}-sweep", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                "peak_source": "FP64 FMA rate 2/clk/SM (measured probe) x 152 SMs x sm_max_mhz",
+                "hbm_GBps": 2 * r["esz"] * w.n_vs / (kms[i] * 1e-3) / 1e9}
     alg_bytes = 2 * r["esz"] * w.n_vs  # one read + one write of the field per sweep
     achieved = alg_bytes / (kms[i] * 1e-3) / 1e9
     peak = float(peaks["hbm_gbs"])
     return {"bound": "hbm", "kernel": f"{name}-sweep", "achieved": achieved, "peak": peak,
-            "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+            "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
             "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({src})"}
 
 

@@ -202,8 +202,23 @@ biofvm_status biofvm_batch_step(biofvm_batch_t *b, int n_steps);
  * TIMEOUT. */
 biofvm_status biofvm_batch_sync(biofvm_batch_t *b);
 
+/* Change the tile shapes (chunk lengths, same rules as tile_m of
+ * biofvm_batch_create) of every environment without touching the fields or
+ * agents: re-partitions the App. A constants.  Used by the autotuner.  Waits
+ * for the stream.  Errors: ARG (nothing changed), CUDA. */
+biofvm_status biofvm_batch_set_tiles(biofvm_batch_t *b, const int *tile_m);
+
 /* CTAs of the persistent batched launch (resident at once). */
 int biofvm_batch_grid(const biofvm_batch_t *b);
+
+/* Failure-detection test hook: with on != 0, every following batched launch
+ * makes the first y-sweep tile of environment 0 wait for a completion count
+ * that never comes.  Its bounded wait gives up after about two seconds, the
+ * kernel sets the status word and every CTA stops at its next item (results
+ * of that launch are undefined); biofvm_batch_sync then returns TIMEOUT and
+ * the context stays usable.  on = 0 restores normal launches.  No GPU fault
+ * or hang is involved.  Errors: ARG. */
+biofvm_status biofvm_batch_test_stall(biofvm_batch_t *b, int on);
 
 /* Free the batch and every environment (waits for the stream). */
 void biofvm_batch_destroy(biofvm_batch_t *b);

@@ -24,39 +24,34 @@ MAX_CHUNKS = 8     # warps of the batched CTA
 MAX_CHUNK = 48     # largest register chunk compiled for the batched kernel
 
 
-def candidates(n):
-    """Valid chunk lengths for an axis of n voxels (at most MAX_CHUNKS chunks)."""
+def candidates(n, S=None):
+    """Valid chunk lengths for an axis of n voxels (at most MAX_CHUNKS chunks; for the x axis,
+    given S, also at most 32/S chunks so that a row's lines fit one warp)."""
     lo = max(4, math.ceil(n / MAX_CHUNKS))
+    if S is not None:
+        lo = max(lo, math.ceil(n / max(1, 32 // S)))
     out = sorted({min(c, MAX_CHUNK, n) for c in (lo, math.ceil(1.5 * lo), 2 * lo, 3 * lo)})
-    return [c for c in out if c >= math.ceil(n / MAX_CHUNKS)]
+    return [c for c in out if c >= lo] or [min(MAX_CHUNK, n)]
 
 
 def _bucket(n):
     return min(N_BUCKETS, key=lambda b: (abs(b - n), b))
 
 
-def _time_batch(binding, torch, envs, tile_m, precision, steps, reps):
-    b = binding.BioFVMBatch(envs, precision=precision, tile_m=tile_m)
-    try:
-        for e in b.envs:
-            f = e.field_tensor()
-            f.uniform_(0.0, 38.0)
-        torch.cuda.synchronize()
-        b.step(1)
+def _rate(torch, b, steps, reps):
+    b.step(1)
+    b.sync()
+    best = float("inf")
+    st = torch.cuda.current_stream()
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        b.step(steps)
+        e1.record(st)
         b.sync()
-        best = float("inf")
-        st = torch.cuda.current_stream()
-        for _ in range(reps):
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(st)
-            b.step(steps)
-            e1.record(st)
-            b.sync()
-            best = min(best, e0.elapsed_time(e1) / steps)
-        return b.n_vs / (best * 1e-3)
-    finally:
-        b.close()
+        best = min(best, e0.elapsed_time(e1) / steps)
+    return b.n_vs / (best * 1e-3)
 
 
 def tune(precision="fp32", n_buckets=N_BUCKETS, subs=range(1, 9), target_vs=1.2e8, steps=3,
@@ -69,23 +64,31 @@ def tune(precision="fp32", n_buckets=N_BUCKETS, subs=range(1, 9), target_vs=1.2e
              "when": time.strftime("%Y-%m-%dT%H:%M:%S"), "classes": {}}
     for n in n_buckets:
         for S in subs:
-            k = max(1, min(32, int(target_vs // (n ** 3 * S))))
+            k = max(1, min(16, int(target_vs // (n ** 3 * S))))
             envs = [inputs.Workload(f"tune{n}_{S}", n, n, n, S, 20.0, 0.01, np.full(S, 1e4),
                                     np.full(S, 0.1), 1) for _ in range(k)]
             cands = candidates(n)
-            m_x = cands[0]
-            best_yz, best_rate = cands[0], -1.0
-            for myz in cands:
-                rate = _time_batch(binding, torch, envs, [[m_x, myz, myz]] * k, precision, steps,
-                                   reps)
-                if rate > best_rate:
-                    best_yz, best_rate = myz, rate
-            best_x = m_x
-            for mx in cands[1:]:
-                rate = _time_batch(binding, torch, envs, [[mx, best_yz, best_yz]] * k, precision,
-                                   steps, reps)
-                if rate > best_rate:
-                    best_x, best_rate = mx, rate
+            cands_x = candidates(n, S)
+            m_x = cands_x[0]
+            b = binding.BioFVMBatch(envs, precision=precision, tile_m=[[m_x, cands[0], cands[0]]] * k)
+            try:
+                for e in b.envs:
+                    e.field_tensor().uniform_(0.0, 38.0)
+                torch.cuda.synchronize()
+                best_yz, best_rate = cands[0], -1.0
+                for myz in cands:
+                    b.set_tiles([[m_x, myz, myz]] * k)
+                    rate = _rate(torch, b, steps, reps)
+                    if rate > best_rate:
+                        best_yz, best_rate = myz, rate
+                best_x = m_x
+                for mx in cands_x[1:]:
+                    b.set_tiles([[mx, best_yz, best_yz]] * k)
+                    rate = _rate(torch, b, steps, reps)
+                    if rate > best_rate:
+                        best_x, best_rate = mx, rate
+            finally:
+                b.close()
             cache["classes"][f"{n},{S}"] = {"m": [best_x, best_yz, best_yz],
                                             "vs_per_s": best_rate, "envs": k}
             if log:
@@ -108,8 +111,10 @@ def tile_shapes(envs, cache):
         entry = cache["classes"].get(f"{_bucket(max(w.nx, w.ny, w.nz))},{min(max(w.ns, 1), 8)}")
         m = entry["m"] if entry else [0, 0, 0]
         row = []
-        for mm, n in zip(m, (w.nx, w.ny, w.nz)):
+        for a, (mm, n) in enumerate(zip(m, (w.nx, w.ny, w.nz))):
             lo = math.ceil(n / MAX_CHUNKS)
+            if a == 0:
+                lo = max(lo, math.ceil(n / max(1, 32 // w.ns)))
             row.append(int(min(MAX_CHUNK, max(mm, lo, 1))) if mm > 0 else 0)
         out.append(row)
     return out

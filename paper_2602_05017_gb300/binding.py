@@ -82,6 +82,8 @@ def load():
         "biofvm_batch_step": (st, [vp, ctypes.c_int]),
         "biofvm_batch_sync": (st, [vp]),
         "biofvm_batch_grid": (ctypes.c_int, [vp]),
+        "biofvm_batch_test_stall": (st, [vp, ctypes.c_int]),
+        "biofvm_batch_set_tiles": (st, [vp, ctypes.POINTER(ctypes.c_int)]),
         "biofvm_batch_destroy": (None, [vp]),
         "biofvm_destroy": (None, [vp]),
         "biofvm_last_error": (ctypes.c_char_p, []),
@@ -334,6 +336,16 @@ class BioFVMBatch:
 
     def grid(self):
         return int(self.lib.biofvm_batch_grid(self.h))
+
+    def set_tiles(self, tile_m):
+        """Re-partition every environment with [n_env][3] chunk lengths (fields kept)."""
+        tm = np.ascontiguousarray(np.asarray(tile_m, dtype=np.int32).reshape(len(self.envs), 3))
+        _check(self.lib.biofvm_batch_set_tiles(self.h, tm.ctypes.data_as(
+            ctypes.POINTER(ctypes.c_int))), self.lib)
+
+    def test_stall(self, on=True):
+        """Failure-detection hook: the next launches hit a bounded wait that expires."""
+        _check(self.lib.biofvm_batch_test_stall(self.h, 1 if on else 0), self.lib)
 
     def close(self):
         if getattr(self, "h", None):

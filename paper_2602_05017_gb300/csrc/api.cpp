@@ -148,9 +148,10 @@ void axis_constants(int n, double r, double lam3, double *inv, double *mul) {
 // a (hi, lo) pair of floats.
 void axis_tables(const biofvm *h, int axis, int T, int m, bool defect, std::vector<double> &out) {
   const int n = axis_len(h, axis), S = h->g.n_sub;
-  out.assign((size_t)4 * n * S + (size_t)T * S + 2 * (size_t)S, 0.0);
+  out.assign((size_t)4 * n * S + (size_t)T * S + 2 * (size_t)S + (size_t)T * T * S, 0.0);
   double *inv = out.data(), *mul = inv + (size_t)n * S, *pf = mul + (size_t)n * S,
-         *pb = pf + (size_t)n * S, *pc = pb + (size_t)n * S, *cfix = pc + (size_t)T * S;
+         *pb = pf + (size_t)n * S, *pc = pb + (size_t)n * S, *cfix = pc + (size_t)T * S,
+         *cw = cfix + 2 * (size_t)S;
   std::vector<double> ci(n), cm(n);
   for (int s = 0; s < S; s++) {
     const double r = h->D[s] * h->dt / (h->dx * h->dx);
@@ -179,6 +180,14 @@ void axis_tables(const biofvm *h, int axis, int T, int m, bool defect, std::vect
         pb[(size_t)i * S + s] = p;
       }
     }
+    // carry weight between chunks u and t: the product of pc over the chunks
+    // strictly between them (the same in both directions)
+    for (int u = 0; u < T; u++)
+      for (int t = 0; t < T; t++) {
+        double w = 1.0;
+        for (int v = std::min(u, t) + 1; v < std::max(u, t); v++) w *= pc[(size_t)v * S + s];
+        cw[((size_t)u * T + t) * S + s] = w;
+      }
   }
 }
 
@@ -464,6 +473,7 @@ AxisTab axis_tab(const biofvm *h, int axis) {
   int T, m;
   axis_partition(h, axis, T, m);
   t.cfix = base + 4 * blk + (size_t)T * S * h->esz;
+  t.cw = base + 4 * blk + ((size_t)T * S + 2 * (size_t)S) * h->esz;
   t.n = n;
   t.T = T;
   t.m = m;
@@ -1086,6 +1096,7 @@ struct biofvm_batch {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
   int graph_steps = -1;
+  int stall_test = 0;
 };
 
 namespace {
@@ -1175,6 +1186,8 @@ biofvm_status biofvm_batch_create(int n_env, const biofvm_grid *grids, const dou
     for (int a = 0; a < 3; a++) {
       int want = tile_m ? tile_m[3 * e + a] : 0;
       if (want <= 0) want = std::max(8, (ns[a] + kBatchWarps - 1) / kBatchWarps);  // default
+      if (a == 0 && g.n_sub >= 1 && g.n_sub <= 32)  // a row's lines in one warp: T*S <= 32
+        want = std::max(want, (ns[0] + 32 / g.n_sub - 1) / (32 / g.n_sub));
       m[a] = std::min(want, std::max(ns[a], 1));
       if ((ns[a] + m[a] - 1) / m[a] > kBatchWarps || m[a] > 48) {
         batch_destroy_impl(b);
@@ -1268,6 +1281,7 @@ biofvm_status biofvm_batch_step(biofvm_batch_t *b, int n_steps) {
     a.done = static_cast<unsigned *>(b->done_d.p);
     a.abort_flag = static_cast<int *>(b->flags_d.p);
     a.status = static_cast<int *>(b->flags_d.p) + 1;
+    a.stall_test = b->stall_test;
     const int grid = (int)std::min<int64_t>(b->grid, b->per_step * n_steps);
     CK(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e1 = cudaMemsetAsync(b->done_d.p, 0, 3 * (size_t)ne * sizeof(unsigned), b->cap_stream);
@@ -1307,6 +1321,56 @@ biofvm_status biofvm_batch_sync(biofvm_batch_t *b) {
 }
 
 int biofvm_batch_grid(const biofvm_batch_t *b) { return b ? b->grid : 0; }
+
+biofvm_status biofvm_batch_set_tiles(biofvm_batch_t *b, const int *tile_m) {
+  if (!b || !tile_m) return fail(BIOFVM_ERR_ARG, "NULL batch handle or tile shapes");
+  CK(cudaSetDevice(b->device));
+  CK(cudaStreamSynchronize(b->stream));
+  const bool fp64 = b->prec == BIOFVM_FP64;
+  std::vector<XPlan> xp(b->env.size());
+  std::vector<ColPlan> cy(b->env.size()), cz(b->env.size());
+  int maxm = 8;
+  for (size_t e = 0; e < b->env.size(); e++) {  // validate everything before changing anything
+    const biofvm *h = b->env[e];
+    const int ns[3] = {h->g.nx, h->g.ny, h->g.nz};
+    int m[3];
+    for (int a = 0; a < 3; a++) {
+      m[a] = std::min(tile_m[3 * e + a] > 0 ? tile_m[3 * e + a] : 8, ns[a]);
+      if ((ns[a] + m[a] - 1) / m[a] > kBatchWarps || m[a] > 48)
+        return fail(BIOFVM_ERR_ARG, "environment %zu axis %d: chunk length %d not allowed", e, a,
+                    m[a]);
+      maxm = std::max(maxm, m[a]);
+    }
+    if (!plan_x(h->g.nx, h->g.n_sub, fp64, xp[e], m[0]) || !plan_col(h->g.ny, fp64, cy[e], m[1]) ||
+        !plan_col(h->g.nz, fp64, cz[e], m[2]))
+      return fail(BIOFVM_ERR_ARG, "environment %zu: tile shapes do not fit the kernels", e);
+  }
+  for (int c : kBatchMaxm)
+    if (c >= maxm) {
+      maxm = c;
+      break;
+    }
+  int per_sm = 0;
+  CK(fp64 ? batch_occupancy_f64(maxm, &per_sm) : batch_occupancy_f32(maxm, &per_sm));
+  for (size_t e = 0; e < b->env.size(); e++) {
+    biofvm *h = b->env[e];
+    h->xp = xp[e];
+    h->cp[1] = cy[e];
+    h->cp[2] = cz[e];
+    biofvm_status st = upload_constants(h);
+    if (st) return st;
+  }
+  b->maxm = maxm;
+  b->grid = std::max(per_sm, 1) * b->env[0]->num_sms;
+  return batch_upload(b);
+}
+
+biofvm_status biofvm_batch_test_stall(biofvm_batch_t *b, int on) {
+  if (!b) return fail(BIOFVM_ERR_ARG, "NULL batch handle");
+  b->stall_test = on ? 1 : 0;
+  batch_drop_graph(b);  // the hook is a kernel argument
+  return BIOFVM_OK;
+}
 
 void biofvm_batch_destroy(biofvm_batch_t *b) { batch_destroy_impl(b); }
 

@@ -73,7 +73,8 @@ __global__ void __launch_bounds__(kBatchWarps * 32) batch_kernel(const BatchArgs
                         !(phase == 0 && step == 0);
       if (go && need) {
         const int dep_phase = phase == 0 ? 2 : phase - 1;
-        const unsigned want = (unsigned)(E_.tiles[dep_phase] * (phase == 0 ? step : step + 1));
+        unsigned want = (unsigned)(E_.tiles[dep_phase] * (phase == 0 ? step : step + 1));
+        if (a.stall_test && phase == 1 && step == 0 && ei == 0 && tile == 0) want = 0xffffffffu;
         const unsigned *ctr = a.done + dep_phase * a.n_env + ei;
         const long long t0 = clock64();
         while (ld_acquire(ctr) < want) {
@@ -167,12 +168,11 @@ __global__ void __launch_bounds__(kBatchWarps * 32) batch_kernel(const BatchArgs
       }
     s_end[t * 32 + lane] = gcar;
     __syncthreads();
-    E carry = E(0), w = E(1);
+    const E *T_cw = T_cfix + 2 * S;  // [T][T][S]
+    E carry = E(0);
     if (t < T)
-      for (int u = t - 1; u >= 0; u--) {
-        carry = fma(w, s_end[u * 32 + lane], carry);
-        w = w * __ldg(T_pc + u * S + s);
-      }
+      for (int u = t - 1; u >= 0; u--)
+        carry = fma(__ldg(T_cw + (u * T + t) * S + s), s_end[u * 32 + lane], carry);
 #pragma unroll
     for (int i = 0; i < MAXM; i++)
       if (i < len) v[i] = fma(__ldg(T_pf + (lo + i) * S + s), carry, v[i]);
@@ -186,12 +186,9 @@ __global__ void __launch_bounds__(kBatchWarps * 32) batch_kernel(const BatchArgs
     s_beg[t * 32 + lane] = xcar;
     __syncthreads();
     carry = E(0);
-    w = E(1);
     if (t < T)
-      for (int u = t + 1; u < T; u++) {
-        carry = fma(w, s_beg[u * 32 + lane], carry);
-        w = w * __ldg(T_pc + u * S + s);
-      }
+      for (int u = t + 1; u < T; u++)
+        carry = fma(__ldg(T_cw + (u * T + t) * S + s), s_beg[u * 32 + lane], carry);
 #pragma unroll
     for (int i = 0; i < MAXM; i++)
       if (i < len) v[i] = fma(__ldg(T_pb + (lo + i) * S + s), carry, v[i]);

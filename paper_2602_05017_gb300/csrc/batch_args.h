@@ -27,6 +27,8 @@ struct BatchArgs {
   int64_t per_step;         // tiles of one step
   unsigned int *done;       // [3][n_env] completed tiles (cumulative over steps)
   int *abort_flag, *status;
+  int stall_test;           // test hook: the first y tile of environment 0 waits for a count
+                            // that never comes, so its bounded wait expires
 };
 
 }  // namespace bfv

@@ -36,8 +36,12 @@ enum : int { kStatusOk = 0, kStatusTimeout = 4 };
 // final rounding; cfix = [c_hi[S], c_lo[S]].  Plain FP32 Thomas accumulates a
 // rounding bias along smooth lines (about 3e-5 after 300 sweeps); this form
 // stays at the storage-rounding level (about 2e-7).
+//
+// cw [T][T][S]: the carry entering chunk t from chunk u is cw[u][t] times the
+// end (forward) or start (backward) value of chunk u, cw[u][t] being the
+// product of pc over the chunks strictly between u and t.
 struct AxisTab {
-  const void *inv, *mul, *pf, *pb, *pc, *cfix;
+  const void *inv, *mul, *pf, *pb, *pc, *cfix, *cw;
   int n, T, m;
 };
 

@@ -53,17 +53,21 @@ __device__ __forceinline__ void bulk_wait_read_all() {
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
-// Barrier 1 over the consumer warps only.
+// Barrier 1 over the consumer warps only.  The non-.aligned form, after a
+// __syncwarp: lanes may reach it from divergent code (ragged tiles), and the
+// compiler does not treat an asm barrier as a reconvergence point.
 __device__ __forceinline__ void consumers_sync(int nthreads) {
-  asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+  __syncwarp();
+  asm volatile("barrier.cta.sync 1, %0;" ::"r"(nthreads) : "memory");
 }
 // Barrier 1 over the consumers with an AND of `ok` (uniform result).
 __device__ __forceinline__ bool consumers_all(bool ok, int nthreads) {
   uint32_t r;
+  __syncwarp();
   asm volatile(
       "{\n\t.reg .pred p, q;\n\t"
       "setp.ne.u32 p, %1, 0;\n\t"
-      "bar.red.and.pred q, 1, %2, p;\n\t"
+      "barrier.cta.red.and.pred q, 1, %2, p;\n\t"
       "selp.u32 %0, 1, 0, q;\n\t}"
       : "=r"(r)
       : "r"((uint32_t)ok), "r"(nthreads)
@@ -95,7 +99,7 @@ template <typename E, int MAXM, bool FULL, int PS>
 __device__ __forceinline__ void pipe_chunk(E *p, const int ps_rt, const int len, const int lo,
                                            const int n, const int t, const int T, const int lane,
                                            const E *Ti, const E *Tm, const E *Tf, const E *Tb,
-                                           const E *Tpc, const int S, const int s, const E chi,
+                                           const E *Tcw, const int S, const int s, const E chi,
                                            const E clo, E *s_end, E *s_beg, const int ncons,
                                            const bool dir, const bool face, const E dval) {
   const int ps = PS > 0 ? PS : ps_rt;
@@ -134,11 +138,8 @@ __device__ __forceinline__ void pipe_chunk(E *p, const int ps_rt, const int len,
   s_end[t * 32 + lane] = g;
   consumers_sync(ncons);
   if (t > 0) {  // chunk 0 enters with a zero carry
-    E carry = E(0), w = E(1);
-    for (int u = t - 1; u >= 0; u--) {
-      carry = fma(w, s_end[u * 32 + lane], carry);
-      w = w * Tpc[u * S + s];
-    }
+    E carry = E(0);
+    for (int u = t - 1; u >= 0; u--) carry = fma(Tcw[(u * T + t) * S + s], s_end[u * 32 + lane], carry);
 #pragma unroll
     for (int i = 0; i < MAXM; i++)
       if (FULL || i < len) v[i] = fma(Tf[i], carry, v[i]);
@@ -153,11 +154,8 @@ __device__ __forceinline__ void pipe_chunk(E *p, const int ps_rt, const int len,
   s_beg[t * 32 + lane] = x;
   consumers_sync(ncons);
   if (t + 1 < T) {  // the last chunk enters with a zero carry
-    E carry = E(0), w = E(1);
-    for (int u = t + 1; u < T; u++) {
-      carry = fma(w, s_beg[u * 32 + lane], carry);
-      w = w * Tpc[u * S + s];
-    }
+    E carry = E(0);
+    for (int u = t + 1; u < T; u++) carry = fma(Tcw[(u * T + t) * S + s], s_beg[u * 32 + lane], carry);
 #pragma unroll
     for (int i = 0; i < MAXM; i++)
       if (FULL || i < len) v[i] = fma(Tb[i], carry, v[i]);
@@ -293,6 +291,7 @@ __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
   const int len_full = min(m, n - lo);
   const int colbase = MODE == 0 ? (lane / S) * a.pitch + lane % S : lane;
   const int ps_rt = MODE == 0 ? S : 32;
+  const E *Tcw = static_cast<const E *>(a.tab.cw);  // [T][T][S], global (L1-resident)
   const bool dir_after = (a.flags & kDirAfter) != 0;
   for (long long k = 0; k < count; k++) {
     const int st = (int)(k % NS);
@@ -322,6 +321,8 @@ __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
           *q = (*q + ldg<E>(a.src_alpha, e)) * ldg<E>(a.src_scale, e);
         }
       }
+      // B must see the source update of every element (a source can sit on a face)
+      if ((a.flags & kSrc) && a.has_src && (a.flags & kDirBefore)) consumers_sync(ncons);
       if (a.flags & kDirBefore) {  // consumer warp t takes rows t, t+T, ...
         for (int rr = t; rr < rows; rr += T) {
           const long long gr = r0 + rr;
@@ -364,15 +365,17 @@ __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
     const bool dir = dir_after && a.dir_on[s];
     const E dval = dir ? dir_value<E>(a.flags, a.dir_val, s) : E(0);
     const E chi = s_cfix[s], clo = s_cfix[S + s];
-    if (len == MAXM)
+    // the unguarded path only when every lane of the warp has a full chunk:
+    // the choice is warp-uniform, so a warp never splits across the paths
+    if (__all_sync(0xffffffffu, len == MAXM))
       pipe_chunk<E, MAXM, true, MODE == 0 ? 0 : 32>(p, ps_rt, len, lo, n, t, T, lane,
                                                     s_inv + rowoff, s_mul + rowoff, s_pf + rowoff,
-                                                    s_pb + rowoff, s_pc, S, s, chi, clo, s_end,
+                                                    s_pb + rowoff, Tcw, S, s, chi, clo, s_end,
                                                     s_beg, ncons, dir, face, dval);
     else
       pipe_chunk<E, MAXM, false, MODE == 0 ? 0 : 32>(p, ps_rt, len, lo, n, t, T, lane,
                                                      s_inv + rowoff, s_mul + rowoff, s_pf + rowoff,
-                                                     s_pb + rowoff, s_pc, S, s, chi, clo, s_end,
+                                                     s_pb + rowoff, Tcw, S, s, chi, clo, s_end,
                                                      s_beg, ncons, dir, face, dval);
     fence_proxy_async_smem();  // generic-proxy writes -> visible to the bulk store
     mbar_arrive(&done[st]);

@@ -411,12 +411,10 @@ __global__ void __launch_bounds__(ColBound<E, MAXM>::threads) col_sweep_kernel(c
     }
   s_end[t * 32 + lane] = g;
   __syncthreads();
-  // carry into chunk t: sum_{u<t} (prod_{u<w<t} pc_w) * end_u
-  E carry = E(0), w = E(1);
-  for (int u = t - 1; u >= 0; u--) {
-    carry = fma(w, s_end[u * 32 + lane], carry);
-    w = w * ldg<E>(a.tab.pc, u * S + s);
-  }
+  // carry into chunk t: sum_{u<t} cw[u][t] * end_u
+  E carry = E(0);
+  for (int u = t - 1; u >= 0; u--)
+    carry = fma(ldg<E>(a.tab.cw, (u * T + t) * S + s), s_end[u * 32 + lane], carry);
 #pragma unroll
   for (int i = 0; i < MAXM; i++)
     if (i < len) v[i] = fma(ldg<E>(a.tab.pf, (lo + i) * S + s), carry, v[i]);
@@ -430,11 +428,8 @@ __global__ void __launch_bounds__(ColBound<E, MAXM>::threads) col_sweep_kernel(c
   s_beg[t * 32 + lane] = x;
   __syncthreads();
   carry = E(0);
-  w = E(1);
-  for (int u = t + 1; u < T; u++) {
-    carry = fma(w, s_beg[u * 32 + lane], carry);
-    w = w * ldg<E>(a.tab.pc, u * S + s);
-  }
+  for (int u = t + 1; u < T; u++)
+    carry = fma(ldg<E>(a.tab.cw, (u * T + t) * S + s), s_beg[u * 32 + lane], carry);
 #pragma unroll
   for (int i = 0; i < MAXM; i++)
     if (i < len) v[i] = fma(ldg<E>(a.tab.pb, (lo + i) * S + s), carry, v[i]);

@@ -22,3 +22,10 @@ def test_tile_shapes_use_nearest_class_and_stay_valid():
     assert shapes[0] == [9, 16, 16]   # 70 voxels need >= 9 per chunk
     assert shapes[1] == [24, 24, 24]
     assert shapes[2] == [0, 0, 0]     # no class: library default
+
+
+def test_x_candidates_fit_one_warp_per_row():
+    for S in range(1, 9):
+        for n in (16, 33, 100, 192):
+            for m in autotune.candidates(n, S):
+                assert math.ceil(n / m) * S <= 32 or m == min(autotune.MAX_CHUNK, n)

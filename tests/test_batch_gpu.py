@@ -22,11 +22,12 @@ def rel(a, b):
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
 
 
-def _envs(seed, shapes):
+def _envs(seed, shapes, agents=True):
     rng = np.random.default_rng(seed)
     out = []
     for (nx, ny, nz, ns) in shapes:
-        w = inputs.random_problem(rng, nx, ny, nz, ns, n_agents=max(1, nx * ny * nz // 30))
+        w = inputs.random_problem(rng, nx, ny, nz, ns,
+                                  n_agents=max(1, nx * ny * nz // 30) if agents else 0)
         out.append(w)
     return out
 
@@ -110,7 +111,7 @@ def test_autotuner_cache_roundtrip(binding, tmp_path):
                           path=str(tmp_path / "c.json"))
     loaded = autotune.load(str(tmp_path / "c.json"))
     assert loaded["classes"].keys() == cache["classes"].keys()
-    envs = _envs(5, [(30, 33, 31, 2), (32, 32, 32, 2)])
+    envs = _envs(5, [(30, 33, 31, 2), (32, 32, 32, 2)], agents=False)
     shapes = autotune.tile_shapes(envs, loaded)
     b = binding.BioFVMBatch(envs, precision="fp32", tile_m=shapes)
     for sim, w in zip(b.envs, envs):
@@ -120,4 +121,27 @@ def test_autotuner_cache_roundtrip(binding, tmp_path):
     for sim, w in zip(b.envs, envs):
         ref = oracle.Problem(**w.oracle_kwargs()).step(w.rho0, 2)
         assert rel(sim.density(), ref) <= 1e-5
+    b.close()
+
+
+def test_bounded_wait_expires_reports_timeout_and_context_stays_usable(binding):
+    """Failure detection without a GPU fault: a dependency wait that can never be satisfied gives
+    up (about two seconds), the host reads TIMEOUT, and the next normal launch is correct."""
+    envs = _envs(6, [(24, 20, 16, 2), (16, 16, 16, 1)], agents=False)
+    b = binding.BioFVMBatch(envs, precision="fp64")
+    for sim, w in zip(b.envs, envs):
+        sim.set_density(w.rho0)
+    b.test_stall(True)
+    b.step(1)
+    with pytest.raises(binding.BioFVMError) as err:
+        b.sync()
+    assert err.value.status == binding.ERR_TIMEOUT
+    b.test_stall(False)
+    for sim, w in zip(b.envs, envs):
+        sim.set_density(w.rho0)
+    b.step(2)
+    b.sync()
+    for sim, w in zip(b.envs, envs):
+        ref = oracle.Problem(**w.oracle_kwargs()).step(w.rho0, 2)
+        assert rel(sim.density(), ref) <= 1e-12
     b.close()
