@@ -223,6 +223,35 @@ biofvm_status biofvm_batch_test_stall(biofvm_batch_t *b, int on);
 /* Free the batch and every environment (waits for the stream). */
 void biofvm_batch_destroy(biofvm_batch_t *b);
 
+/* ------------------------------------------------------------------------
+ * Allocation-free variant of the adjoint's parameter-gradient reduction.
+ * The paper has no counterpart: it serves callers that cannot call
+ * cudaMalloc -- code inside a host framework that owns all device memory
+ * through its own pool or arena, processes under a fixed device-memory
+ * budget, or loops where allocating is not allowed.
+ *
+ * For one sweep with adjoint field mu and forward sweep output u (device
+ * arrays, the field layout, double for BIOFVM_FP64 or float for BIOFVM_FP32)
+ * along `axis` (0 = x, 1 = y, 2 = z) of an nx x ny x nz grid of n_sub
+ * substrates, ACCUMULATES into device doubles
+ *     dlambda[s] += -(dt/3)    * sum_elements(s) mu * u
+ *     dD[s]      += -(dt/dx^2) * sum_lines(s) sum_i (mu_{i+1}-mu_i)(u_{i+1}-u_i)
+ * exactly as biofvm_adjoint_step does for each of its three sweeps, on
+ * cuda_stream (async).  It calls no allocator: its per-block partial sums
+ * live in one file-scope device array of 256 KB (512 blocks x 2 sums x 32
+ * substrates, FP64) that every GPU loading the library holds until the
+ * process exits.  Every call overwrites all the partials it reads, so
+ * nothing carries over from the previous call; calls whose kernels overlap
+ * on the GPU (other streams, other host threads) race on that array.  The
+ * first call on each device looks the array's address up
+ * (cudaGetSymbolAddress, once per device): make that first call before any
+ * stream capture.  Limits: 1 <= n_sub <= 32 (larger is rejected with
+ * BIOFVM_ERR_ARG).  Errors: ARG, CUDA. */
+biofvm_status biofvm_param_grad_noalloc(const void *mu, const void *u, int nx, int ny, int nz,
+                                        int n_sub, int axis, biofvm_precision prec, double dt,
+                                        double dx, double *dD, double *dlambda,
+                                        uintptr_t cuda_stream);
+
 /* Free the handle and all device memory it owns (waits for its stream).
  * NULL is a no-op. */
 void biofvm_destroy(biofvm_t *h);

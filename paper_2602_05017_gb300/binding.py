@@ -85,6 +85,10 @@ def load():
         "biofvm_batch_test_stall": (st, [vp, ctypes.c_int]),
         "biofvm_batch_set_tiles": (st, [vp, ctypes.POINTER(ctypes.c_int)]),
         "biofvm_batch_destroy": (None, [vp]),
+        "biofvm_param_grad_noalloc": (st, [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                           ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                           ctypes.c_double, ctypes.c_double, vp, vp,
+                                           ctypes.c_size_t]),
         "biofvm_destroy": (None, [vp]),
         "biofvm_last_error": (ctypes.c_char_p, []),
     }

@@ -635,6 +635,10 @@ biofvm_status create_impl(const biofvm_grid *grid, double dx, double dt, const d
                           uintptr_t cuda_stream, const int *force_m, biofvm_t **out);
 }  // namespace
 
+namespace bfv {
+void set_error_message(const char *msg) { g_last_error = msg ? msg : ""; }
+}  // namespace bfv
+
 // ===========================================================================
 // C ABI
 // ===========================================================================

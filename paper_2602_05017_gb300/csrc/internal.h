@@ -137,6 +137,9 @@ cudaError_t launch_pipe_f64(const CUtensorMap &map, const PipeArgs &a, int maxm,
                             size_t smem, cudaStream_t st);
 cudaError_t launch_pipe_f32(const CUtensorMap &map, const PipeArgs &a, int maxm, int grid,
                             size_t smem, cudaStream_t st);
+// Sets the thread-local message biofvm_last_error() returns.
+void set_error_message(const char *msg);
+
 cudaError_t launch_adj_reduce_f64(const ReduceLaunch &a, cudaStream_t st);
 cudaError_t launch_adj_reduce_f32(const ReduceLaunch &a, cudaStream_t st);
 cudaError_t launch_src_adjoint_f64(const SrcAdjLaunch &a, cudaStream_t st);
