@@ -143,7 +143,7 @@ def run_gpu(args):
             dist.barrier()
 
     results = {}
-    for prec in args.only or ("fp64", "fp32"):
+    for prec in ([] if args.batch_only else (args.only or ("fp64", "fp32"))):
         esz = 8 if prec == "fp64" else 4
         tdt = torch.float64 if prec == "fp64" else torch.float32
         sim = binding.BioFVM(w.nx, w.ny, w.nz, w.ns, w.dx, w.dt, w.D, w.lam, precision=prec,
@@ -257,13 +257,14 @@ def run_batched(args, stream, dev):
 
 
 def _stage_step(sim, ev, stream):
-    """One step as its three kernels with an event between launches (flags as in a step)."""
+    """One step as its three kernels (the ones biofvm_step launches) with an event between
+    launches."""
     ev[0].record(stream)
-    sim.run_stage(8)
+    sim.run_stage(9)
     ev[1].record(stream)
-    sim.run_stage(2)
+    sim.run_stage(10)
     ev[2].record(stream)
-    sim.run_stage(3)
+    sim.run_stage(11)
     ev[3].record(stream)
 
 
@@ -334,6 +335,8 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-envs", type=int, default=256)
     ap.add_argument("--batch-steps", type=int, default=50)
+    ap.add_argument("--batch-only", action="store_true",
+                    help="run only the batched leg (profiling only; not a bench line)")
     ap.add_argument("--shape", type=int, nargs=3, metavar=("NX", "NY", "NZ"),
                     help="smaller grid of the same recipe (profiling only; not a bench line)")
     ap.add_argument("--only", nargs="+", choices=["fp64", "fp32"],
@@ -348,7 +351,7 @@ def main():
     rank, world, res = run_gpu(args)
     if rank != 0:
         return 0
-    if args.only or args.shape:  # profiling run: per-precision numbers only
+    if args.only or args.shape or args.batch_only:  # profiling run: numbers only
         print(json.dumps({"profiling_run": True, "shape": SHAPE, "results": res}), flush=True)
         return 0
     peaks, src = measured_peaks()

@@ -127,8 +127,12 @@ biofvm_status biofvm_set_params(biofvm_t *h, const double *D,
  * stage 0 = Src then B, 1 = X^-1 then B, 2 = Y^-1 then B, 3 = Z^-1 then B,
  * 4 = the source update alone (no Dirichlet), 5 = X^-1 alone, 6 = Y^-1
  * alone, 7 = Z^-1 alone, 8 = Src, B, X^-1, B in one launch (the first kernel
- * of a step; with stages 2 and 3 it makes one whole step).  Async.
- * Errors: ARG, CUDA. */
+ * of a step; with stages 2 and 3 it makes one whole step).  Stages 9, 10, 11
+ * are the three kernels of biofvm_step itself, launched one by one (for
+ * timing each): in FP64 the step's x- and y-sweeps leave the field divided
+ * by a per-substrate constant that the z-sweep takes out again, so only the
+ * sequence 9, 10, 11 as a whole is a step (equal to stages 8, 2, 3 up to
+ * rounding).  Async.  Errors: ARG, CUDA. */
 biofvm_status biofvm_run_stage(biofvm_t *h, int stage);
 
 /* One time step, like biofvm_step(h, 1), that also writes the forward states

@@ -78,6 +78,9 @@ struct PipePlan {
   CUtensorMap map[2]{};  // y/z: [0] the field, [1] the adjoint field
   int have_map[2]{};
 };
+struct StreamPlan {
+  int use = 0, pf = 1, grid = 0;
+};
 struct XPlan {
   int T = 1, m = 1, maxm = 8, rows_per_warp = 1, warps = 1, rows_per_cta = 1, use_bulk = 0;
   size_t smem = 0;
@@ -98,12 +101,20 @@ struct biofvm {
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;
   size_t nel = 0;
-  DevBuf rho, tab[3], dir_on_d, dir_val_d, status;
+  DevBuf rho, tab[3], tabT[3], dir_on_d, dir_val_d, status;
+  // streaming sweep (FP64): [3][n][S] inv, mul, q per axis; Dirichlet values
+  // in the units of each sweep's scaled output [3][S]; omega [S]; k0 per axis
+  DevBuf tabS[3], dir_scaled_d, omega_d, stream_const_d;
+  int stream_k0[3] = {0, 0, 0};
   XPlan xp;
   ColPlan cp[3];  // [1] = y, [2] = z
   PipePlan pp[3];
+  StreamPlan sp[3];
   int num_sms = 0;
   int pipe_enabled = 1;
+  int stream_enabled = 1;
+  int stream_ctas_per_sm = 3;
+  int stream_pf = 1;
   int forced = 0;  // chunk lengths fixed by the caller (batched environments)
   unsigned generation = 0;  // bumped when kernel arguments change (sources, constants)
   // sources
@@ -348,9 +359,10 @@ void plan_pipe(biofvm *h, int axis) {
   const int64_t nx = h->g.nx, ny = h->g.ny, nz = h->g.nz, S = h->g.n_sub;
   const size_t esz = h->esz;
   const int n = axis_len(h, axis);
+  if (esz != 4) return;  // FP64 streams whole lines instead
   ColPlan cp;
-  if (!plan_col(n, esz == 8, cp)) return;
-  if ((cp.T + 1) * 32 > pipe_max_threads(cp.maxm, esz)) return;
+  if (!plan_col(n, false, cp)) return;
+  if ((cp.T + 1) * 32 > pipe_max_threads_f32(cp.maxm)) return;
   p.T = cp.T;
   p.m = cp.m;
   p.maxm = cp.maxm;
@@ -379,27 +391,52 @@ void plan_pipe(biofvm *h, int axis) {
     p.ntiles = (int64_t)nplanes * ((C + 31) / 32);
   }
   const size_t stage = (size_t)p.stage_elems * esz;
-  const size_t tab = (size_t)pipe_tab_elems_host(n, (int)S, p.T) * esz;  // staged in shared memory
+  const size_t tab = (size_t)pipe_tab_elems_host(n, (int)S) * esz;
   const size_t scratch = 2 * (size_t)p.T * 32 * esz + 16 + 2 * 8 * 8;
+  // constants staged in shared memory whenever two stages leave room for them
+  // (read through L1 they cost more than a deeper ring gains), else via L1
   for (int ns = 4; ns >= 2 && !p.stages; ns--)
-    if (ns * stage + tab + scratch <= kMaxDynamicSmem) p.stages = ns;
+    if (ns * stage + tab + scratch <= kMaxDynamicSmem) {
+      p.stages = ns;
+      p.tab_in_smem = 1;
+    }
+  for (int ns = 4; ns >= 2 && !p.stages; ns--)
+    if (ns * stage + scratch <= kMaxDynamicSmem) p.stages = ns;
   if (!p.stages) return;
-  p.tab_in_smem = 1;
-  p.smem = p.stages * stage + tab + scratch;
+  p.smem = p.stages * stage + (p.tab_in_smem ? tab : 0) + scratch;
   if (axis != 0 && !encode_pipe_map(h, axis, 0, h->rho.p)) return;
   // the attribute is per kernel, shared by every handle: always the opt-in maximum
-  const cudaError_t e = esz == 8 ? allow_pipe_smem_f64(p.maxm, kMaxDynamicSmem)
-                                 : allow_pipe_smem_f32(p.maxm, kMaxDynamicSmem);
+  const cudaError_t e = allow_pipe_smem_f32(p.maxm, kMaxDynamicSmem);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return;
   }
   const int threads = (p.T + 1) * 32;
-  const int regs = p.maxm * (int)esz / 4 + 96;
+  const int regs = p.maxm + 96;
   int per_sm = (int)std::min<size_t>({kMaxDynamicSmem / p.smem, (size_t)(2048 / threads),
                                       (size_t)(65536 / (threads * regs))});
   per_sm = std::max(per_sm, 1);
   p.grid = (int)std::min<int64_t>(p.ntiles, (int64_t)h->num_sms * per_sm);
+  p.use = 1;
+}
+
+// Plan the streaming sweep of an axis (FP64 only): a persistent grid of
+// stream_ctas_per_sm 128-thread CTAs per SM, prefetch variant stream_pf.  Each
+// warp keeps its 32 lines' intermediates (32 n elements) in L2 between the two
+// passes, so the warps in flight bound the L2 footprint (12 warps per SM at
+// n = 400: about 93 MB on average).
+void plan_stream(biofvm *h, int axis) {
+  StreamPlan &p = h->sp[axis];
+  p = StreamPlan{};
+  if (h->prec != BIOFVM_FP64 || !h->stream_enabled) return;
+  const int S = h->g.n_sub;
+  if (axis == 0 && S > 32) return;
+  p.pf = (h->stream_pf == 4 || h->stream_pf == 8 || h->stream_pf == 16) ? h->stream_pf : 1;
+  if (allow_stream_smem_f64(p.pf) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  p.grid = h->num_sms * std::max(1, h->stream_ctas_per_sm);
   p.use = 1;
 }
 
@@ -441,6 +478,51 @@ void axis_partition(const biofvm *h, int axis, int &T, int &m) {
   }
 }
 
+// Tables of the streaming sweep of one axis, position-major [3][n][S]:
+// inv_i, mul_i (App. A) and q_i = inv_i / sigma, sigma being the interior limit
+// of inv_i: 1/denom_inf with denom_inf = (b + sqrt(b^2 - 4 r^2)) / 2 the fixed
+// point of denom = b - r^2 / denom, b = 1 + 2r + lam3 (inv_0 when n < 3).
+// k0 = 1 + the last position below n-1 where some substrate's inv_i differs
+// from sigma, or mul_i from r sigma, by more than 4e-16 relative; on
+// [k0, n-1) the tables hold exactly inv = sigma, mul = r sigma, q = 1 (a
+// rounding-level change of single terms), so the kernels use per-substrate
+// constants there instead of loading them.  mulinf[S] = r sigma.
+void stream_tables(const biofvm *h, int axis, std::vector<double> &tt, double *sigma,
+                   double *mulinf, int &k0) {
+  const int n = axis_len(h, axis), S = h->g.n_sub;
+  tt.assign((size_t)3 * n * S, 0.0);
+  std::vector<double> inv(n), mul(n);
+  std::vector<double> rr(S);
+  k0 = 0;
+  for (int s = 0; s < S; s++) {
+    const double r = h->D[s] * h->dt / (h->dx * h->dx);
+    const double lam3 = h->lam[s] * h->dt / 3.0;
+    axis_constants(n, r, lam3, inv.data(), mul.data());
+    double sg = inv[0];
+    if (n >= 3) {
+      const double b = 1.0 + 2.0 * r + lam3;
+      sg = 2.0 / (b + std::sqrt((1.0 + lam3) * (1.0 + 4.0 * r + lam3)));
+    }
+    sigma[s] = sg;
+    mulinf[s] = r * sg;
+    rr[s] = r;
+    for (int i = 0; i < n; i++) {
+      tt[(size_t)i * S + s] = inv[i];
+      tt[((size_t)n + i) * S + s] = mul[i];
+      tt[((size_t)2 * n + i) * S + s] = inv[i] / sg;
+      const bool same = std::fabs(inv[i] / sg - 1.0) <= 4e-16 &&
+                        (mulinf[s] == 0.0 || std::fabs(mul[i] / mulinf[s] - 1.0) <= 4e-16);
+      if (!same && i < n - 1) k0 = std::max(k0, i + 1);
+    }
+  }
+  for (int i = k0; i < n - 1; i++)
+    for (int s = 0; s < S; s++) {
+      tt[(size_t)i * S + s] = sigma[s];
+      tt[((size_t)n + i) * S + s] = mulinf[s];
+      tt[((size_t)2 * n + i) * S + s] = 1.0;
+    }
+}
+
 biofvm_status upload_constants(biofvm *h) {
   std::vector<double> t;
   for (int axis = 0; axis < 3; axis++) {
@@ -448,6 +530,49 @@ biofvm_status upload_constants(biofvm *h) {
     axis_partition(h, axis, T, m);
     axis_tables(h, axis, T, m, h->prec == BIOFVM_FP32, t);
     biofvm_status st = upload_doubles(h, h->tab[axis], t);
+    if (st) return st;
+    // the same inv, mul, pf, pb substrate-major [4][S][npad] for the pipelined kernel
+    const int n = axis_len(h, axis), S = h->g.n_sub, npad = pipe_npad_host(n);
+    std::vector<double> tt((size_t)4 * S * npad, 0.0);
+    for (int w = 0; w < 4; w++)
+      for (int i = 0; i < n; i++)
+        for (int s = 0; s < S; s++)
+          tt[((size_t)w * S + s) * npad + i] = t[(size_t)w * n * S + (size_t)i * S + s];
+    st = upload_doubles(h, h->tabT[axis], tt);
+    if (st) return st;
+  }
+  if (h->prec == BIOFVM_FP64) {
+    const int S = h->g.n_sub;
+    std::vector<double> sigma((size_t)3 * S), minf((size_t)3 * S), tt;
+    for (int axis = 0; axis < 3; axis++) {
+      stream_tables(h, axis, tt, &sigma[(size_t)axis * S], &minf[(size_t)axis * S],
+                    h->stream_k0[axis]);
+      biofvm_status st = upload_doubles(h, h->tabS[axis], tt);
+      if (st) return st;
+    }
+    {
+      // per-axis constants [3][2][S]: sigma, r sigma (the interior inv and mul)
+      std::vector<double> c((size_t)6 * S);
+      for (int axis = 0; axis < 3; axis++)
+        for (int s = 0; s < S; s++) {
+          c[((size_t)axis * 2) * S + s] = sigma[(size_t)axis * S + s];
+          c[((size_t)axis * 2 + 1) * S + s] = minf[(size_t)axis * S + s];
+        }
+      biofvm_status st = upload_doubles(h, h->stream_const_d, c);
+      if (st) return st;
+    }
+    // Dirichlet values in stored units: dval / sigma_x after x, dval / (sigma_x sigma_y)
+    // after y, dval after z (the z-sweep stores the true field)
+    std::vector<double> dsc((size_t)3 * S), om(S);
+    for (int s = 0; s < S; s++) {
+      const double sx = sigma[s], sy = sigma[S + s], sz = sigma[2 * S + s];
+      dsc[s] = h->dir_val[s] / sx;
+      dsc[S + s] = h->dir_val[s] / (sx * sy);
+      dsc[2 * S + s] = h->dir_val[s];
+      om[s] = sx * sy * sz;
+    }
+    biofvm_status st = upload_doubles(h, h->dir_scaled_d, dsc);
+    if (!st) st = upload_doubles(h, h->omega_d, om);
     if (st) return st;
   }
   if (h->graph) {
@@ -474,6 +599,7 @@ AxisTab axis_tab(const biofvm *h, int axis) {
   axis_partition(h, axis, T, m);
   t.cfix = base + 4 * blk + (size_t)T * S * h->esz;
   t.cw = base + 4 * blk + ((size_t)T * S + 2 * (size_t)S) * h->esz;
+  t.tabT = h->tabT[axis].p;
   t.n = n;
   t.T = T;
   t.m = m;
@@ -522,8 +648,54 @@ cudaError_t launch_pipe(const biofvm *h, int axis, int flags, cudaStream_t st, v
   b.dir_val = h->dir_val_d.p;
   b.status = static_cast<int *>(h->status.p);
   const CUtensorMap &map = p.map[axis == 0 ? 0 : buf];
-  return h->prec == BIOFVM_FP64 ? launch_pipe_f64(map, b, p.maxm, p.grid, p.smem, st)
-                                : launch_pipe_f32(map, b, p.maxm, p.grid, p.smem, st);
+  return launch_pipe_f32(map, b, p.maxm, p.grid, p.smem, st);
+}
+
+bool stream_ok(const biofvm *h, int axis, int flags) {
+  return h->sp[axis].use && (flags & kSolve);
+}
+
+cudaError_t launch_stream(const biofvm *h, int axis, int flags, cudaStream_t st, void *field) {
+  const StreamPlan &p = h->sp[axis];
+  const int64_t nx = h->g.nx, ny = h->g.ny, nz = h->g.nz, S = h->g.n_sub;
+  StreamArgs a{};
+  a.rho = field;
+  a.n = axis_len(h, axis);
+  a.S = (int)S;
+  a.mode = axis;
+  a.nx = (int)nx;
+  a.ny = (int)ny;
+  a.nz = (int)nz;
+  if (axis == 0) {
+    a.stride = S;
+    a.C = nx * S;
+    a.rows_per_warp = (int)(32 / S);
+    a.ngroups = (ny * nz + a.rows_per_warp - 1) / a.rows_per_warp;
+  } else {
+    a.C = axis == 1 ? nx * S : nx * ny * S;
+    a.stride = a.C;
+    a.plane_stride = axis == 1 ? nx * ny * S : 0;
+    a.colgroups = (a.C + 31) / 32;
+    a.ngroups = a.colgroups * (axis == 1 ? nz : 1);
+  }
+  a.tab = h->tabS[axis].p;
+  a.flags = flags;
+  if (!h->any_dir) a.flags &= ~(kDirBefore | kDirAfter);
+  a.out = (flags & kScaled) ? (axis == 2 ? 2 : 1) : 0;
+  a.k0 = h->stream_k0[axis];
+  a.omega = h->omega_d.p;
+  a.interior = static_cast<const char *>(h->stream_const_d.p) + (size_t)axis * 2 * S * h->esz;
+  a.src_row_off = static_cast<const int64_t *>(h->src_row_off.p);
+  a.src_elem = static_cast<const int64_t *>(h->src_elem.p);
+  a.src_alpha = h->src_alpha.p;
+  a.src_scale = h->src_scale.p;
+  a.has_src = h->n_entries > 0;
+  a.dir_on = static_cast<const uint8_t *>(h->dir_on_d.p);
+  const char *dsc = static_cast<const char *>(h->dir_scaled_d.p);
+  a.dir_val = a.out ? dsc + (size_t)axis * S * h->esz : h->dir_val_d.p;
+  a.dir_val_in = (a.out && axis > 0) ? dsc + (size_t)(axis - 1) * S * h->esz : h->dir_val_d.p;
+  const int grid = (int)std::min<int64_t>(p.grid, (a.ngroups + 3) / 4);
+  return launch_stream_f64(a, p.pf, grid, st);
 }
 
 bool pipe_ok(const biofvm *h, int axis, int flags, int buf) {
@@ -532,6 +704,7 @@ bool pipe_ok(const biofvm *h, int axis, int flags, int buf) {
 }
 
 cudaError_t launch_x(const biofvm *h, int flags, cudaStream_t st, void *field = nullptr) {
+  if (stream_ok(h, 0, flags)) return launch_stream(h, 0, flags, st, field ? field : h->rho.p);
   if (pipe_ok(h, 0, flags, 0)) return launch_pipe(h, 0, flags, st, field ? field : h->rho.p, 0);
   XLaunch a{};
   a.rho = field ? field : h->rho.p;
@@ -586,14 +759,21 @@ cudaError_t launch_col(const biofvm *h, int axis, int flags, cudaStream_t st, in
   if (!h->any_dir) a.flags &= ~kDirAfter;
   a.dir_on = static_cast<const uint8_t *>(h->dir_on_d.p);
   a.dir_val = h->dir_val_d.p;
+  if (stream_ok(h, axis, flags)) return launch_stream(h, axis, flags, st, a.rho);
   if (pipe_ok(h, axis, flags, buf)) return launch_pipe(h, axis, flags, st, a.rho, buf);
   return h->prec == BIOFVM_FP64 ? launch_col_f64(a, st) : launch_col_f32(a, st);
 }
 
+// Scaled intermediates (stream.cuh) only when all three sweeps of a step stream.
+int step_scaled(const biofvm *h) {
+  return (h->sp[0].use && h->sp[1].use && h->sp[2].use) ? kScaled : 0;
+}
+
 biofvm_status launch_step(const biofvm *h, cudaStream_t st) {
-  CK(launch_x(h, kSrc | kDirBefore | kSolve | kDirAfter, st));
-  CK(launch_col(h, 1, kSolve | kDirAfter, st));
-  CK(launch_col(h, 2, kSolve | kDirAfter, st));
+  const int sc = step_scaled(h);
+  CK(launch_x(h, kSrc | kDirBefore | kSolve | kDirAfter | sc, st));
+  CK(launch_col(h, 1, kSolve | kDirAfter | sc, st));
+  CK(launch_col(h, 2, kSolve | kDirAfter | sc, st));
   return BIOFVM_OK;
 }
 
@@ -621,7 +801,9 @@ void destroy_impl(biofvm *h) {
   if (h->stream || h->rho.p) cudaStreamSynchronize(h->stream);
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   if (h->graph) cudaGraphDestroy(h->graph);
-  for (DevBuf *b : {&h->rho, &h->tab[0], &h->tab[1], &h->tab[2], &h->dir_on_d, &h->dir_val_d,
+  for (DevBuf *b : {&h->rho, &h->tab[0], &h->tab[1], &h->tab[2], &h->tabT[0], &h->tabT[1],
+                    &h->tabT[2], &h->tabS[0], &h->tabS[1], &h->tabS[2], &h->dir_scaled_d,
+                    &h->omega_d, &h->stream_const_d, &h->dir_on_d, &h->dir_val_d,
                     &h->status, &h->src_row_off, &h->src_elem, &h->src_alpha, &h->src_scale,
                     &h->adj, &h->partial, &h->ag_elem, &h->ag_entry, &h->ag_weight,
                     &h->ag_target})
@@ -768,6 +950,11 @@ biofvm_status create_impl(const biofvm_grid *grid, double dx, double dt, const d
   if (const char *env = getenv("BIOFVM_PIPELINE")) h->pipe_enabled = atoi(env) != 0;
   if (h->pipe_enabled && !h->forced)
     for (int axis = 0; axis < 3; axis++) plan_pipe(h, axis);
+  if (const char *env = getenv("BIOFVM_STREAM")) h->stream_enabled = atoi(env) != 0;
+  if (const char *env = getenv("BIOFVM_STREAM_CTAS")) h->stream_ctas_per_sm = atoi(env);
+  if (const char *env = getenv("BIOFVM_STREAM_PF")) h->stream_pf = atoi(env);
+  if (!h->forced)
+    for (int axis = 0; axis < 3; axis++) plan_stream(h, axis);
   if ((st = upload_doubles(h, h->dir_val_d, h->dir_val)) != BIOFVM_OK ||
       (st = upload_constants(h)) != BIOFVM_OK) {
     std::string msg = g_last_error;
@@ -963,7 +1150,11 @@ biofvm_status biofvm_run_stage(biofvm_t *h, int stage) {
     case 6: CK(launch_col(h, 1, kSolve, h->stream)); break;
     case 7: CK(launch_col(h, 2, kSolve, h->stream)); break;
     case 8: CK(launch_x(h, kSrc | kDirBefore | kSolve | kDirAfter, h->stream)); break;
-    default: return fail(BIOFVM_ERR_ARG, "stage must be in [0, 8] (got %d)", stage);
+    case 9: CK(launch_x(h, kSrc | kDirBefore | kSolve | kDirAfter | step_scaled(h), h->stream));
+      break;
+    case 10: CK(launch_col(h, 1, kSolve | kDirAfter | step_scaled(h), h->stream)); break;
+    case 11: CK(launch_col(h, 2, kSolve | kDirAfter | step_scaled(h), h->stream)); break;
+    default: return fail(BIOFVM_ERR_ARG, "stage must be in [0, 11] (got %d)", stage);
   }
   return BIOFVM_OK;
 }
@@ -1149,12 +1340,16 @@ biofvm_status batch_upload(biofvm_batch *b) {
     x.tiles[0] = (nrows + x.rows_per_tile - 1) / x.rows_per_tile;
     x.tiles[1] = (int64_t)x.nz * ((rowlen + 31) / 32);
     x.tiles[2] = (rowlen * x.ny + 31) / 32;
+    for (int ph = 0; ph < 3; ph++) {
+      x.group[ph] = std::max(1, kBatchWarps / x.T[ph]);
+      x.items[ph] = (x.tiles[ph] + x.group[ph] - 1) / x.group[ph];
+    }
     x.src_row_off = static_cast<const int64_t *>(h->src_row_off.p);
     x.src_elem = static_cast<const int64_t *>(h->src_elem.p);
     x.src_alpha = h->src_alpha.p;
     x.src_scale = h->src_scale.p;
     x.has_src = h->n_entries > 0;
-    for (int ph = 0; ph < 3; ph++) off[ph * (ne + 1) + e + 1] = off[ph * (ne + 1) + e] + x.tiles[ph];
+    for (int ph = 0; ph < 3; ph++) off[ph * (ne + 1) + e + 1] = off[ph * (ne + 1) + e] + x.items[ph];
     b->env_gen[e] = h->generation;
   }
   b->per_step = off[0 * (ne + 1) + ne] + off[1 * (ne + 1) + ne] + off[2 * (ne + 1) + ne];
@@ -1286,6 +1481,7 @@ biofvm_status biofvm_batch_step(biofvm_batch_t *b, int n_steps) {
     a.abort_flag = static_cast<int *>(b->flags_d.p);
     a.status = static_cast<int *>(b->flags_d.p) + 1;
     a.stall_test = b->stall_test;
+    a.maxm = b->maxm;
     const int grid = (int)std::min<int64_t>(b->grid, b->per_step * n_steps);
     CK(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e1 = cudaMemsetAsync(b->done_d.p, 0, 3 * (size_t)ne * sizeof(unsigned), b->cap_stream);

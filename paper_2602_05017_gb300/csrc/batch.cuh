@@ -2,9 +2,11 @@
 // substrate count advanced by ONE persistent launch (all environments, all
 // steps).
 //
-// Work items are tiles of 32 independent lines of one sweep of one
-// environment, in the order (step, phase x/y/z, environment, tile).  CTA b
-// takes items b, b + G, b + 2G, ... (G = gridDim.x, every CTA resident).
+// Work items are groups of tiles (32 independent lines each) of one sweep of
+// one environment, in the order (step, phase x/y/z, environment, item): a
+// line cut into T chunks takes T warps, so the 8 warps of a CTA solve
+// floor(8/T) tiles at once.  CTA b takes items b, b + G, b + 2G, ...
+// (G = gridDim.x, every CTA resident).
 // Before an item, its dependency on the previous phase of the same
 // environment is checked on a per-(phase, environment) completion counter:
 //     x of step k   needs all z tiles of step k-1 (k > 0)
@@ -40,11 +42,19 @@ __device__ __forceinline__ int ld_relaxed_int(const int *p) {
   return v;
 }
 
-template <typename E, int MAXM>
+// Chunks live in shared memory ([warp][position][lane], lane fastest: every
+// access of a warp is one conflict-free row) and every loop runs exactly the
+// chunk's length: one launch serves environments whose chunk lengths differ,
+// so a register array unrolled for the longest chunk would waste the issue
+// slots of every shorter one.
+template <typename E>
 __global__ void __launch_bounds__(kBatchWarps * 32) batch_kernel(const BatchArgs a) {
-  __shared__ E s_end[kBatchWarps * 32], s_beg[kBatchWarps * 32];
+  extern __shared__ __align__(16) unsigned char batch_smem[];
+  E *const s_chunk = reinterpret_cast<E *>(batch_smem);  // [8][maxm][32]
+  E *const s_end = s_chunk + kBatchWarps * a.maxm * 32;  // [8][32]
+  E *const s_beg = s_end + kBatchWarps * 32;             // [8][32]
   __shared__ int s_go;
-  const int lane = threadIdx.x & 31, t = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   const int64_t total = a.per_step * a.n_steps;
   int last_env = -1, last_phase = -1, last_step = -1;  // last dependency known satisfied
   for (int64_t g = blockIdx.x; g < total; g += gridDim.x) {
@@ -62,7 +72,7 @@ __global__ void __launch_bounds__(kBatchWarps * 32) batch_kernel(const BatchArgs
       if (off[mid] <= r) lo_e = mid; else hi_e = mid - 1;
     }
     const int ei = lo_e;
-    const int64_t tile = r - off[ei];
+    const int64_t item = r - off[ei];
     const BatchEnv &E_ = a.env[ei];
 
     // ---- dependency on the previous phase of this environment ----
@@ -73,8 +83,8 @@ __global__ void __launch_bounds__(kBatchWarps * 32) batch_kernel(const BatchArgs
                         !(phase == 0 && step == 0);
       if (go && need) {
         const int dep_phase = phase == 0 ? 2 : phase - 1;
-        unsigned want = (unsigned)(E_.tiles[dep_phase] * (phase == 0 ? step : step + 1));
-        if (a.stall_test && phase == 1 && step == 0 && ei == 0 && tile == 0) want = 0xffffffffu;
+        unsigned want = (unsigned)(E_.items[dep_phase] * (phase == 0 ? step : step + 1));
+        if (a.stall_test && phase == 1 && step == 0 && ei == 0 && item == 0) want = 0xffffffffu;
         const unsigned *ctr = a.done + dep_phase * a.n_env + ei;
         const long long t0 = clock64();
         while (ld_acquire(ctr) < want) {
@@ -99,30 +109,35 @@ __global__ void __launch_bounds__(kBatchWarps * 32) batch_kernel(const BatchArgs
     last_phase = phase;
     last_step = step;
 
-    // ---- geometry of the 32 lines of this tile ----
+    // ---- geometry: warp w solves chunk w % T of tile (item*group + w / T) ----
     const int S = E_.S, nx = E_.nx, ny = E_.ny;
     const int n = phase == 0 ? nx : phase == 1 ? ny : E_.nz;
     const int T = E_.T[phase], m = E_.m[phase];
+    const int grp = wp / T, t = wp - grp * T;  // warp group (tile) and chunk
+    const int64_t tile = item * E_.group[phase] + grp;
+    const bool tile_ok = grp < E_.group[phase] && tile < E_.tiles[phase];
     E *const field = static_cast<E *>(E_.field);
     const int64_t rowlen = (int64_t)nx * S;
     long long base = 0, pstride;
     bool active;
     int s;
     if (phase == 0) {
-      const int64_t r0 = tile * E_.rows_per_tile;
       const int64_t nrows = (int64_t)ny * E_.nz;
-      const int rows = (int)min((int64_t)E_.rows_per_tile, nrows - r0);
-      // Src on this tile's rows (only this CTA touches them in this phase)
+      // Src on this item's rows (only this CTA touches them in this phase)
       if (E_.has_src) {
-        const int64_t e0 = E_.src_row_off[r0], e1 = E_.src_row_off[r0 + rows];
+        const int64_t ra = item * E_.group[0] * E_.rows_per_tile;
+        const int64_t rb = min(nrows, ra + (int64_t)E_.group[0] * E_.rows_per_tile);
+        const int64_t e0 = E_.src_row_off[ra], e1 = E_.src_row_off[rb];
         for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
           const int64_t el = E_.src_elem[e];
           field[el] = (field[el] + ldg<E>(E_.src_alpha, e)) * ldg<E>(E_.src_scale, e);
         }
         __syncthreads();
       }
+      const int64_t r0 = tile * E_.rows_per_tile;
+      const int rows = tile_ok ? (int)min((int64_t)E_.rows_per_tile, nrows - r0) : 0;
       s = lane % S;
-      active = lane < E_.rows_per_tile * S && lane / S < rows;
+      active = tile_ok && lane < E_.rows_per_tile * S && lane / S < rows;
       base = (r0 + lane / S) * rowlen + s;
       pstride = S;
     } else {
@@ -130,81 +145,75 @@ __global__ void __launch_bounds__(kBatchWarps * 32) batch_kernel(const BatchArgs
       const int64_t tpp = (C + 31) / 32;
       const int64_t plane = tile / tpp;
       const int64_t c = (tile - plane * tpp) * 32 + lane;
-      active = c < C;
+      active = tile_ok && c < C;
       s = (int)(c % S);
       base = plane * C * n + c;
       pstride = C;
     }
     const int lo = t * m;
-    const int len = (active && t < T) ? min(m, n - lo) : 0;
-    E *col = field + (active ? base : 0);
+    const int len = active ? min(m, n - lo) : 0;
+    E *col = field + (active ? base : 0) + (long long)lo * pstride;
+    E *vs = s_chunk + (wp * a.maxm) * 32 + lane;  // position i at vs[i * 32]
     const E *tb = static_cast<const E *>(E_.tab[phase]);
     const E *T_inv = tb, *T_mul = tb + n * S, *T_pf = T_mul + n * S, *T_pb = T_pf + n * S;
     const E *T_pc = T_pb + n * S, *T_cfix = T_pc + T * S;
+    const E *T_cw = T_cfix + 2 * S;  // [T][T][S]
+    const int q0 = lo * S + s;       // table index of position 0 of the chunk
 
-    E v[MAXM];
-#pragma unroll
-    for (int i = 0; i < MAXM; i++)
-      if (i < len) v[i] = col[(lo + i) * pstride];
+    for (int i = 0; i < len; i++) vs[i * 32] = col[(long long)i * pstride];
     if constexpr (kDefect<E>) {
-      E prev = (len > 0 && lo > 0) ? col[(lo - 1) * pstride] : E(0);
-      const E after = (len > 0 && lo + len < n) ? col[(lo + len) * pstride] : E(0);
-#pragma unroll
-      for (int i = 0; i < MAXM; i++)
-        if (i < len) {
-          const E cur = v[i];
-          const E nxt = (i + 1 < MAXM && i + 1 < len) ? v[i + 1] : after;
-          v[i] = second_difference(cur, prev, nxt, lo + i, n);
+      // e = L_N d; the zero-flux ends use mirrored halos (d_{-1} = d_0, d_n = d_{n-1})
+      if (len > 0) {
+        E prev = lo > 0 ? col[-pstride] : vs[0];
+        const E after = lo + len < n ? col[(long long)len * pstride] : vs[(len - 1) * 32];
+        for (int i = 0; i < len; i++) {
+          const E cur = vs[i * 32];
+          const E nxt = i + 1 < len ? vs[(i + 1) * 32] : after;
+          vs[i * 32] = (cur - prev) + (cur - nxt);
           prev = cur;
         }
+      }
     }
     E gcar = E(0);
-#pragma unroll
-    for (int i = 0; i < MAXM; i++)
-      if (i < len) {
-        const int q = (lo + i) * S + s;
-        gcar = fma(__ldg(T_mul + q), gcar, v[i] * __ldg(T_inv + q));
-        v[i] = gcar;
-      }
-    s_end[t * 32 + lane] = gcar;
-    __syncthreads();
-    const E *T_cw = T_cfix + 2 * S;  // [T][T][S]
-    E carry = E(0);
-    if (t < T)
-      for (int u = t - 1; u >= 0; u--)
-        carry = fma(__ldg(T_cw + (u * T + t) * S + s), s_end[u * 32 + lane], carry);
-#pragma unroll
-    for (int i = 0; i < MAXM; i++)
-      if (i < len) v[i] = fma(__ldg(T_pf + (lo + i) * S + s), carry, v[i]);
-    E xcar = E(0);
-#pragma unroll
-    for (int i = MAXM - 1; i >= 0; i--)
-      if (i < len) {
-        xcar = fma(__ldg(T_mul + (lo + i) * S + s), xcar, v[i]);
-        v[i] = xcar;
-      }
-    s_beg[t * 32 + lane] = xcar;
-    __syncthreads();
-    carry = E(0);
-    if (t < T)
-      for (int u = t + 1; u < T; u++)
-        carry = fma(__ldg(T_cw + (u * T + t) * S + s), s_beg[u * 32 + lane], carry);
-#pragma unroll
-    for (int i = 0; i < MAXM; i++)
-      if (i < len) v[i] = fma(__ldg(T_pb + (lo + i) * S + s), carry, v[i]);
-    if constexpr (kDefect<E>) {
-      const E chi = __ldg(T_cfix + s), clo = __ldg(T_cfix + S + s);
-#pragma unroll
-      for (int i = 0; i < MAXM; i++)
-        if (i < len) {
-          const E d = col[(lo + i) * pstride];
-          v[i] = fma(chi, d, fma(clo, d, v[i]));
-        }
+#pragma unroll 4
+    for (int i = 0; i < len; i++) {
+      const int q = q0 + i * S;
+      gcar = fma(__ldg(T_mul + q), gcar, vs[i * 32] * __ldg(T_inv + q));
+      vs[i * 32] = gcar;
     }
-    __syncthreads();  // every halo read of the tile precedes every write
-#pragma unroll
-    for (int i = 0; i < MAXM; i++)
-      if (i < len) col[(lo + i) * pstride] = v[i];
+    s_end[wp * 32 + lane] = gcar;
+    __syncthreads();
+    if (grp < E_.group[phase] && t > 0) {  // chunk 0 enters with a zero carry
+      E carry = E(0);
+      for (int u = t - 1; u >= 0; u--)
+        carry = fma(__ldg(T_cw + (u * T + t) * S + s), s_end[(grp * T + u) * 32 + lane], carry);
+#pragma unroll 4
+      for (int i = 0; i < len; i++) vs[i * 32] = fma(__ldg(T_pf + q0 + i * S), carry, vs[i * 32]);
+    }
+    E xcar = E(0);
+#pragma unroll 4
+    for (int i = len - 1; i >= 0; i--) {
+      xcar = fma(__ldg(T_mul + q0 + i * S), xcar, vs[i * 32]);
+      vs[i * 32] = xcar;
+    }
+    s_beg[wp * 32 + lane] = xcar;
+    __syncthreads();
+    if (grp < E_.group[phase] && t + 1 < T) {  // the last chunk enters with a zero carry
+      E carry = E(0);
+      for (int u = t + 1; u < T; u++)
+        carry = fma(__ldg(T_cw + (u * T + t) * S + s), s_beg[(grp * T + u) * 32 + lane], carry);
+#pragma unroll 4
+      for (int i = 0; i < len; i++) vs[i * 32] = fma(__ldg(T_pb + q0 + i * S), carry, vs[i * 32]);
+    }
+    if constexpr (kDefect<E>) {  // x = c_hi d + (c_lo d + y), d re-read from the field (L2)
+      const E chi = __ldg(T_cfix + s), clo = __ldg(T_cfix + S + s);
+      for (int i = 0; i < len; i++) {
+        const E d = col[(long long)i * pstride];
+        vs[i * 32] = fma(chi, d, fma(clo, d, vs[i * 32]));
+      }
+    }
+    __syncthreads();  // every halo read of the item precedes every write
+    for (int i = 0; i < len; i++) col[(long long)i * pstride] = vs[i * 32];
     __syncthreads();
     if (threadIdx.x == 0) {
       __threadfence();
@@ -213,15 +222,24 @@ __global__ void __launch_bounds__(kBatchWarps * 32) batch_kernel(const BatchArgs
   }
 }
 
-template <typename E, int MAXM>
+inline size_t batch_smem_bytes(int maxm, size_t esz) {
+  return ((size_t)kBatchWarps * maxm * 32 + 2 * (size_t)kBatchWarps * 32) * esz;
+}
+
+template <typename E>
 cudaError_t launch_batch_one(const BatchArgs &a, int grid, cudaStream_t st) {
-  batch_kernel<E, MAXM><<<grid, kBatchWarps * 32, 0, st>>>(a);
+  batch_kernel<E><<<grid, kBatchWarps * 32, batch_smem_bytes(a.maxm, sizeof(E)), st>>>(a);
   return cudaGetLastError();
 }
 
-template <typename E, int MAXM>
-cudaError_t batch_blocks_per_sm(int *out) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, batch_kernel<E, MAXM>, kBatchWarps * 32, 0);
+template <typename E>
+cudaError_t batch_blocks_per_sm(int maxm, int *out) {
+  const size_t smem = batch_smem_bytes(maxm, sizeof(E));
+  cudaError_t e = cudaFuncSetAttribute(batch_kernel<E>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, batch_kernel<E>, kBatchWarps * 32,
+                                                       smem);
 }
 
 }  // namespace bfv

@@ -15,6 +15,8 @@ struct BatchEnv {
   int T[3], m[3];
   int rows_per_tile;    // x tiles: floor(32/S) rows of S lines each
   int64_t tiles[3];     // tiles per phase
+  int group[3];         // tiles solved together by one work item: floor(8 / T) warp groups
+  int64_t items[3];     // work items per phase = ceil(tiles / group)
   const int64_t *src_row_off, *src_elem;
   const void *src_alpha, *src_scale;
   int has_src;
@@ -23,9 +25,10 @@ struct BatchEnv {
 struct BatchArgs {
   const BatchEnv *env;
   int n_env, n_steps;
-  const int64_t *tile_off;  // [3][n_env + 1] prefix sums of tiles per phase
-  int64_t per_step;         // tiles of one step
-  unsigned int *done;       // [3][n_env] completed tiles (cumulative over steps)
+  int maxm;                 // longest chunk of any environment (shared-memory chunk rows)
+  const int64_t *tile_off;  // [3][n_env + 1] prefix sums of work items per phase
+  int64_t per_step;         // work items of one step
+  unsigned int *done;       // [3][n_env] completed work items (cumulative over steps)
   int *abort_flag, *status;
   int stall_test;           // test hook: the first y tile of environment 0 waits for a count
                             // that never comes, so its bounded wait expires

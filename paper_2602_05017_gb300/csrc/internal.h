@@ -16,6 +16,7 @@ enum : int {
   kSolve = 4,      // Thomas solve along the axis
   kDirAfter = 8,   // Dirichlet application after the solve
   kMaskZero = 16,  // Dirichlet applications write 0 (the adjoint of B: dB/du = mask)
+  kScaled = 32,    // streaming sweeps of a whole step: scaled intermediate output
 };
 
 // Status word values written by kernels (mirror biofvm_status).
@@ -40,8 +41,12 @@ enum : int { kStatusOk = 0, kStatusTimeout = 4 };
 // cw [T][T][S]: the carry entering chunk t from chunk u is cw[u][t] times the
 // end (forward) or start (backward) value of chunk u, cw[u][t] being the
 // product of pc over the chunks strictly between u and t.
+//
+// tabT: inv, mul, pf, pb again, substrate-major [4][S][n_pad] with
+// n_pad = 32*ceil(n/32) + 1 (the layout the pipelined kernel reads; staged
+// into shared memory when it fits, read through L1 otherwise).
 struct AxisTab {
-  const void *inv, *mul, *pf, *pb, *pc, *cfix, *cw;
+  const void *inv, *mul, *pf, *pb, *pc, *cfix, *cw, *tabT;
   int n, T, m;
 };
 
@@ -78,6 +83,33 @@ struct ColLaunch {
   int flags;  // kSolve | kDirAfter
   const uint8_t *dir_on;
   const void *dir_val;
+};
+
+// Streaming sweep (stream.cuh): one lane per whole line, persistent grid of
+// 128-thread CTAs, warps striding over groups of 32 lines.
+struct StreamArgs {
+  void *rho;
+  int n, S;
+  int mode;               // 0 = x (lanes: rows x substrates), 1 = y, 2 = z (lanes: columns)
+  int nx, ny, nz;
+  long long stride;       // elements between consecutive positions of a line
+  long long C;            // x: row length nx*S; y/z: columns per plane
+  long long plane_stride; // y: elements per z-plane; z: 0
+  long long colgroups;    // y/z: 32-column groups per plane
+  long long ngroups;      // 32-line groups in all
+  int rows_per_warp;      // x: 32/S
+  const void *tab;        // inv, mul, q position-major [3][n][S]
+  int out;                // 0: x; 1: y = x / sigma; 2: omega y (stream.cuh)
+  int k0;                 // inv_i = sigma, mul_i = r sigma, q_i = 1 for k0 <= i < n-1
+  const void *omega;      // [S] sigma_x sigma_y sigma_z (out 2)
+  const void *interior;   // [2][S] inv and mul on [k0, n-1): sigma, r sigma
+  int flags;
+  const int64_t *src_row_off, *src_elem;
+  const void *src_alpha, *src_scale;
+  int has_src;
+  const uint8_t *dir_on;
+  const void *dir_val;     // Dirichlet value written after the solve (output units)
+  const void *dir_val_in;  // ... and before it (input units)
 };
 
 // Persistent TMA-pipelined sweep (pipe.cuh): tiles of 32 lines x n positions
@@ -131,12 +163,16 @@ cudaError_t launch_x_f64(const XLaunch &a, cudaStream_t st);
 cudaError_t launch_x_f32(const XLaunch &a, cudaStream_t st);
 cudaError_t launch_col_f64(const ColLaunch &a, cudaStream_t st);
 cudaError_t launch_col_f32(const ColLaunch &a, cudaStream_t st);
-cudaError_t allow_pipe_smem_f64(int maxm, size_t bytes);
+// The pipelined sweep is FP32 only (FP64 streams whole lines, stream.cuh).
 cudaError_t allow_pipe_smem_f32(int maxm, size_t bytes);
-cudaError_t launch_pipe_f64(const CUtensorMap &map, const PipeArgs &a, int maxm, int grid,
-                            size_t smem, cudaStream_t st);
 cudaError_t launch_pipe_f32(const CUtensorMap &map, const PipeArgs &a, int maxm, int grid,
                             size_t smem, cudaStream_t st);
+// Streaming sweep, prefetch variant pf (1: registers; 4, 8, 16: cp.async ring
+// of that many groups); FP64
+// only (the FP32 kernels solve in defect-correction form, which needs d again
+// after the solve).
+cudaError_t allow_stream_smem_f64(int pf);
+cudaError_t launch_stream_f64(const StreamArgs &a, int pf, int grid, cudaStream_t st);
 // Sets the thread-local message biofvm_last_error() returns.
 void set_error_message(const char *msg);
 
@@ -148,12 +184,10 @@ cudaError_t launch_batch_f64(const BatchArgs &a, int maxm, int grid, cudaStream_
 cudaError_t launch_batch_f32(const BatchArgs &a, int maxm, int grid, cudaStream_t st);
 cudaError_t batch_occupancy_f64(int maxm, int *out);
 cudaError_t batch_occupancy_f32(int maxm, int *out);
-// Largest CTA the pipelined sweep with chunk capacity maxm may use.
-int pipe_max_threads(int maxm, size_t esz);
-// Shared-memory constants of the pipelined sweep (elements): [4][S][npad] + pc + cfix.
-inline int pipe_tab_elems_host(int n, int S, int T) {
-  const int npad = (n + 31) / 32 * 32 + 1;
-  return 4 * S * npad + T * S + 2 * S;
-}
+// Largest CTA the FP32 pipelined sweep with chunk capacity maxm may use.
+int pipe_max_threads_f32(int maxm);
+// Substrate-major constants of the pipelined sweep (elements): [4][S][npad].
+inline int pipe_npad_host(int n) { return (n + 31) / 32 * 32 + 1; }
+inline int pipe_tab_elems_host(int n, int S) { return 4 * S * pipe_npad_host(n); }
 
 }  // namespace bfv

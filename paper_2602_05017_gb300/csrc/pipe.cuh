@@ -82,14 +82,11 @@ struct PipeBound {  // chunk registers + about 96 for addressing, carries, const
   static constexpr int threads = (raw >= 1024 ? 1024 : raw) / 32 * 32;
 };
 
-// Shared-memory constants of the pipelined kernel: inv, mul, pf, pb stored
-// substrate-major [S][n_pad] (n_pad = 1 mod 32, so lanes of different
-// substrates read different banks and each thread walks its own row with
-// compile-time offsets), then pc [T][S] and cfix [2][S] as in global memory.
+// Constants of the pipelined kernel: inv, mul, pf, pb substrate-major
+// [S][n_pad] (n_pad = 1 mod 32, so lanes of different substrates read
+// different banks and each thread walks its own row with compile-time
+// offsets) -- AxisTab::tabT, copied into shared memory when it fits.
 __host__ __device__ inline int pipe_npad(int n) { return (n + 31) / 32 * 32 + 1; }
-__host__ __device__ inline int pipe_tab_elems(int n, int S, int T) {
-  return 4 * S * pipe_npad(n) + T * S + 2 * S;
-}
 
 // One chunk of one column: e = L_N d (FP32), forward elimination, carry in,
 // back substitution, carry in, c d + y (FP32), Dirichlet, write-back.
@@ -189,10 +186,8 @@ __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
   const int64_t stage_elems = a.stage_elems;
   const int npad = pipe_npad(n);
   E *stage0 = reinterpret_cast<E *>(smem_raw);
-  E *tab = stage0 + NS * stage_elems;
-  E *s_inv = tab, *s_mul = tab + S * npad, *s_pf = s_mul + S * npad, *s_pb = s_pf + S * npad;
-  E *s_pc = s_pb + S * npad, *s_cfix = s_pc + T * S;
-  E *s_end = s_cfix + 2 * S;
+  E *tab = stage0 + NS * stage_elems;  // [4][S][npad] when staged
+  E *s_end = tab + (a.tab_in_smem ? 4 * S * npad : 0);
   E *s_beg = s_end + T * 32;
   uint64_t *full = reinterpret_cast<uint64_t *>(
       (reinterpret_cast<uintptr_t>(s_beg + T * 32) + 15) & ~uintptr_t(15));
@@ -212,16 +207,14 @@ __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
     fence_mbar_init();
     fence_proxy_async_smem();
   }
-  {  // constants: global [n][S] -> shared [S][npad] (transposed), then pc and cfix
-    const E *g = static_cast<const E *>(a.tab.inv);
-    const int nS = n * S;
-    for (int q = threadIdx.x; q < 4 * nS; q += blockDim.x) {
-      const int which = q / nS, r = q - which * nS, i = r / S, ss = r - i * S;
-      tab[which * S * npad + ss * npad + i] = __ldg(g + q);
-    }
-    for (int q = threadIdx.x; q < T * S + 2 * S; q += blockDim.x) s_pc[q] = __ldg(g + 4 * nS + q);
-  }
+  const E *gT = static_cast<const E *>(a.tab.tabT);
+  if (a.tab_in_smem)
+    for (int q = threadIdx.x; q < 4 * S * npad; q += blockDim.x) tab[q] = __ldg(gT + q);
   __syncthreads();
+  const E *ctab = a.tab_in_smem ? tab : gT;
+  const E *s_inv = ctab, *s_mul = ctab + S * npad, *s_pf = s_mul + S * npad,
+          *s_pb = s_pf + S * npad;
+  const E *g_cfix = static_cast<const E *>(a.tab.cfix);
 
   if (warp == 0) {  // ------------------------------------------------ producer
     if (lane != 0) return;
@@ -364,7 +357,7 @@ __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
     const int rowoff = s * npad + lo;
     const bool dir = dir_after && a.dir_on[s];
     const E dval = dir ? dir_value<E>(a.flags, a.dir_val, s) : E(0);
-    const E chi = s_cfix[s], clo = s_cfix[S + s];
+    const E chi = __ldg(g_cfix + s), clo = __ldg(g_cfix + S + s);
     // the unguarded path only when every lane of the warp has a full chunk:
     // the choice is warp-uniform, so a warp never splits across the paths
     if (__all_sync(0xffffffffu, len == MAXM))

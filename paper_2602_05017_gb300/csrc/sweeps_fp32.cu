@@ -80,6 +80,12 @@ cudaError_t launch_pipe_f32(const CUtensorMap &map, const PipeArgs &a, int maxm,
   return cudaErrorInvalidValue;
 }
 
+int pipe_max_threads_f32(int maxm) {  // mirrors PipeBound<float, maxm>
+  const int regs = maxm * 4 / 4 + 96;
+  const int raw = 65536 / regs;
+  return (raw >= 1024 ? 1024 : raw) / 32 * 32;
+}
+
 
 cudaError_t launch_adj_reduce_f32(const ReduceLaunch &a, cudaStream_t st) {
   adj_reduce_kernel<float><<<a.nblocks, kReduceThreads, 0, st>>>(
@@ -103,26 +109,10 @@ cudaError_t launch_src_adjoint_f32(const SrcAdjLaunch &a, cudaStream_t st) {
 }
 
 
-cudaError_t launch_batch_f32(const BatchArgs &a, int maxm, int grid, cudaStream_t st) {
-  switch (maxm) {
-    case 8: return launch_batch_one<float, 8>(a, grid, st);
-    case 16: return launch_batch_one<float, 16>(a, grid, st);
-    case 24: return launch_batch_one<float, 24>(a, grid, st);
-    case 32: return launch_batch_one<float, 32>(a, grid, st);
-    case 48: return launch_batch_one<float, 48>(a, grid, st);
-  }
-  return cudaErrorInvalidValue;
+cudaError_t launch_batch_f32(const BatchArgs &a, int, int grid, cudaStream_t st) {
+  return launch_batch_one<float>(a, grid, st);
 }
 
-cudaError_t batch_occupancy_f32(int maxm, int *out) {
-  switch (maxm) {
-    case 8: return batch_blocks_per_sm<float, 8>(out);
-    case 16: return batch_blocks_per_sm<float, 16>(out);
-    case 24: return batch_blocks_per_sm<float, 24>(out);
-    case 32: return batch_blocks_per_sm<float, 32>(out);
-    case 48: return batch_blocks_per_sm<float, 48>(out);
-  }
-  return cudaErrorInvalidValue;
-}
+cudaError_t batch_occupancy_f32(int maxm, int *out) { return batch_blocks_per_sm<float>(maxm, out); }
 
 }  // namespace bfv

@@ -1,7 +1,7 @@
 // FP64 instantiations of the sweep kernels (element type double).
 #include "adjoint.cuh"
 #include "batch.cuh"
-#include "pipe.cuh"
+#include "stream.cuh"
 #include "sweeps.cuh"
 
 namespace bfv {
@@ -44,38 +44,6 @@ cudaError_t allow_x_smem_f64(int maxm, size_t bytes) {
 }
 
 
-cudaError_t allow_pipe_smem_f64(int maxm, size_t bytes) {
-  switch (maxm) {
-    case 8: return allow_pipe_smem<double, 8>(bytes);
-    case 16: return allow_pipe_smem<double, 16>(bytes);
-    case 24: return allow_pipe_smem<double, 24>(bytes);
-    case 32: return allow_pipe_smem<double, 32>(bytes);
-    case 48: return allow_pipe_smem<double, 48>(bytes);
-    case 64: return allow_pipe_smem<double, 64>(bytes);
-  }
-  return cudaErrorInvalidValue;
-}
-
-cudaError_t launch_pipe_f64(const CUtensorMap &map, const PipeArgs &a, int maxm, int grid,
-                            size_t smem, cudaStream_t st) {
-  switch (maxm) {
-    case 8: return launch_pipe_one<double, 8>(map, a, grid, smem, st);
-    case 16: return launch_pipe_one<double, 16>(map, a, grid, smem, st);
-    case 24: return launch_pipe_one<double, 24>(map, a, grid, smem, st);
-    case 32: return launch_pipe_one<double, 32>(map, a, grid, smem, st);
-    case 48: return launch_pipe_one<double, 48>(map, a, grid, smem, st);
-    case 64: return launch_pipe_one<double, 64>(map, a, grid, smem, st);
-  }
-  return cudaErrorInvalidValue;
-}
-
-int pipe_max_threads(int maxm, size_t esz) {  // mirrors PipeBound
-  const int regs = maxm * (int)esz / 4 + 96;
-  const int raw = 65536 / regs;
-  return (raw >= 1024 ? 1024 : raw) / 32 * 32;
-}
-
-
 cudaError_t launch_adj_reduce_f64(const ReduceLaunch &a, cudaStream_t st) {
   adj_reduce_kernel<double><<<a.nblocks, kReduceThreads, 0, st>>>(
       static_cast<const double *>(a.mu), static_cast<const double *>(a.u), a.nel, a.S, a.stride,
@@ -98,24 +66,28 @@ cudaError_t launch_src_adjoint_f64(const SrcAdjLaunch &a, cudaStream_t st) {
 }
 
 
-cudaError_t launch_batch_f64(const BatchArgs &a, int maxm, int grid, cudaStream_t st) {
-  switch (maxm) {
-    case 8: return launch_batch_one<double, 8>(a, grid, st);
-    case 16: return launch_batch_one<double, 16>(a, grid, st);
-    case 24: return launch_batch_one<double, 24>(a, grid, st);
-    case 32: return launch_batch_one<double, 32>(a, grid, st);
-    case 48: return launch_batch_one<double, 48>(a, grid, st);
+cudaError_t launch_batch_f64(const BatchArgs &a, int, int grid, cudaStream_t st) {
+  return launch_batch_one<double>(a, grid, st);
+}
+
+cudaError_t batch_occupancy_f64(int maxm, int *out) { return batch_blocks_per_sm<double>(maxm, out); }
+
+cudaError_t allow_stream_smem_f64(int pf) {
+  switch (pf) {
+    case 1: return allow_stream_smem<double, 1>();
+    case 4: return allow_stream_smem<double, 4>();
+    case 8: return allow_stream_smem<double, 8>();
+    case 16: return allow_stream_smem<double, 16>();
   }
   return cudaErrorInvalidValue;
 }
 
-cudaError_t batch_occupancy_f64(int maxm, int *out) {
-  switch (maxm) {
-    case 8: return batch_blocks_per_sm<double, 8>(out);
-    case 16: return batch_blocks_per_sm<double, 16>(out);
-    case 24: return batch_blocks_per_sm<double, 24>(out);
-    case 32: return batch_blocks_per_sm<double, 32>(out);
-    case 48: return batch_blocks_per_sm<double, 48>(out);
+cudaError_t launch_stream_f64(const StreamArgs &a, int pf, int grid, cudaStream_t st) {
+  switch (pf) {
+    case 1: return launch_stream_one<double, 1>(a, grid, st);
+    case 4: return launch_stream_one<double, 4>(a, grid, st);
+    case 8: return launch_stream_one<double, 8>(a, grid, st);
+    case 16: return launch_stream_one<double, 16>(a, grid, st);
   }
   return cudaErrorInvalidValue;
 }

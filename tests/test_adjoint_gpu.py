@@ -78,8 +78,10 @@ def _problem(seed, shape=(13, 11, 9), ns=2, dirichlet=True, n_agents=40):
     return w, probes, targets
 
 
-def test_one_adjoint_step_matches_cpu_adjoint(torch):
+@pytest.mark.parametrize("stream", ["0", "1"])
+def test_one_adjoint_step_matches_cpu_adjoint(torch, monkeypatch, stream):
     from paper_2602_05017_gb300 import binding
+    monkeypatch.setenv("BIOFVM_STREAM", stream)
     w, _, _ = _problem(1)
     p = oracle.Problem(**w.oracle_kwargs())
     gout = np.random.default_rng(2).normal(size=w.shape)

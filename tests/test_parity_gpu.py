@@ -89,13 +89,38 @@ def test_each_stage_matches_oracle(binding, shape):
         assert rel_err(got, fn(w.rho0)) <= 1e-13, stage
 
 
-def test_graph_steps_equal_stage_sequence(binding):
+@pytest.mark.parametrize("stream", ["0", "1"])
+def test_graph_steps_equal_stage_sequence(binding, monkeypatch, stream):
+    """Graph-launched steps against the same stages launched one by one.  Without the
+    streaming sweep both run the same kernels: bit-identical.  With it, a whole step solves
+    for scaled intermediates (x / sigma) while single stages solve for x itself: the two
+    differ by rounding only."""
+    monkeypatch.setenv("BIOFVM_STREAM", stream)
     rng = np.random.default_rng(3)
     w = inputs.random_problem(rng, 21, 17, 13, 2, n_agents=30, dirichlet=True)
     a = gpu_run(binding, w, "fp64", 3)
     sim = binding.BioFVM.from_workload(w, precision="fp64")
     for _ in range(3):
         for stage in (0, 1, 2, 3):
+            sim.run_stage(stage)
+    b = sim.density()
+    sim.close()
+    if stream == "0":
+        assert np.array_equal(a, b)
+    else:
+        assert rel_err(a, b) <= 1e-14
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_step_kernels_one_by_one_equal_step(binding, prec):
+    """Stages 9, 10, 11 (the kernels of biofvm_step, launched one by one) make exactly one
+    graph-launched step, bit for bit."""
+    rng = np.random.default_rng(8)
+    w = inputs.random_problem(rng, 30, 26, 22, 3, n_agents=50, dirichlet=True)
+    a = gpu_run(binding, w, prec, 2)
+    sim = binding.BioFVM.from_workload(w, precision=prec)
+    for _ in range(2):
+        for stage in (9, 10, 11):
             sim.run_stage(stage)
     b = sim.density()
     sim.close()
@@ -245,14 +270,24 @@ def test_workload3_full_size_20_steps_fp32_properties(binding):
     assert err <= 1e-5
 
 
-@pytest.mark.parametrize("pipeline", ["0", "1"])
-@pytest.mark.parametrize("shape", [(40, 36, 28, 4), (64, 300, 9, 2), (8, 8, 520, 1), (16, 70, 70, 3)],
+PATHS = {"plain": ("0", "0"), "pipe": ("1", "0"), "stream": ("1", "1")}
+
+
+@pytest.mark.parametrize("path", list(PATHS))
+@pytest.mark.parametrize("shape", [(40, 36, 28, 4), (64, 300, 9, 2), (8, 8, 520, 1), (16, 70, 70, 3),
+                                   (33, 1, 47, 5), (1, 65, 2, 7), (100, 30, 20, 8)],
                          ids=lambda s: "x".join(map(str, s)) if isinstance(s, tuple) else s)
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_sweep_paths_match_oracle(binding, monkeypatch, shape, pipeline, prec):
-    """Both sweep implementations (plain kernels and the persistent TMA pipeline,
-    chosen at create through BIOFVM_PIPELINE) against the oracle, with Dirichlet faces."""
-    monkeypatch.setenv("BIOFVM_PIPELINE", pipeline)
+def test_sweep_paths_match_oracle(binding, monkeypatch, shape, path, prec):
+    """Every sweep implementation -- plain kernels, the persistent TMA pipeline and (FP64) the
+    streaming whole-line kernel, chosen at create through BIOFVM_PIPELINE / BIOFVM_STREAM --
+    against the oracle, with Dirichlet faces and sources."""
+    if prec == "fp32" and path == "stream":
+        pytest.skip("the streaming sweep is FP64 only")
+    if prec == "fp64" and path == "pipe":
+        pytest.skip("the pipelined sweep is FP32 only")
+    monkeypatch.setenv("BIOFVM_PIPELINE", PATHS[path][0])
+    monkeypatch.setenv("BIOFVM_STREAM", PATHS[path][1])
     nx, ny, nz, ns = shape
     rng = np.random.default_rng(17)
     w = inputs.random_problem(rng, nx, ny, nz, ns, n_agents=100, dirichlet=True)
