@@ -72,7 +72,7 @@ struct ColPlan {
 struct PipePlan {
   int use = 0, T = 1, m = 1, maxm = 8;
   int box_rows = 0, nbox = 0, rows_per_tile = 0, pitch = 0;
-  int stages = 0, tab_in_smem = 0, grid = 0;
+  int stages = 0, grid = 0;
   int64_t stage_elems = 0, ntiles = 0;
   size_t smem = 0;
   CUtensorMap map[2]{};  // y/z: [0] the field, [1] the adjoint field
@@ -393,17 +393,10 @@ void plan_pipe(biofvm *h, int axis) {
   const size_t stage = (size_t)p.stage_elems * esz;
   const size_t tab = (size_t)pipe_tab_elems_host(n, (int)S) * esz;
   const size_t scratch = 2 * (size_t)p.T * 32 * esz + 16 + 2 * 8 * 8;
-  // constants staged in shared memory whenever two stages leave room for them
-  // (read through L1 they cost more than a deeper ring gains), else via L1
-  for (int ns = 4; ns >= 2 && !p.stages; ns--)
-    if (ns * stage + tab + scratch <= kMaxDynamicSmem) {
-      p.stages = ns;
-      p.tab_in_smem = 1;
-    }
-  for (int ns = 4; ns >= 2 && !p.stages; ns--)
-    if (ns * stage + scratch <= kMaxDynamicSmem) p.stages = ns;
+  for (int ns = 4; ns >= 2 && !p.stages; ns--)  // the constants always staged
+    if (ns * stage + tab + scratch <= kMaxDynamicSmem) p.stages = ns;
   if (!p.stages) return;
-  p.smem = p.stages * stage + (p.tab_in_smem ? tab : 0) + scratch;
+  p.smem = p.stages * stage + tab + scratch;
   if (axis != 0 && !encode_pipe_map(h, axis, 0, h->rho.p)) return;
   // the attribute is per kernel, shared by every handle: always the opt-in maximum
   const cudaError_t e = allow_pipe_smem_f32(p.maxm, kMaxDynamicSmem);
@@ -632,7 +625,6 @@ cudaError_t launch_pipe(const biofvm *h, int axis, int flags, cudaStream_t st, v
   b.nrows = (int64_t)h->g.ny * h->g.nz;
   b.field = field;
   b.stages = p.stages;
-  b.tab_in_smem = p.tab_in_smem;
   b.stage_elems = p.stage_elems;
   b.tab = axis_tab(h, axis);
   b.tab.T = p.T;

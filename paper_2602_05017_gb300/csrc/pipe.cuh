@@ -85,7 +85,8 @@ struct PipeBound {  // chunk registers + about 96 for addressing, carries, const
 // Constants of the pipelined kernel: inv, mul, pf, pb substrate-major
 // [S][n_pad] (n_pad = 1 mod 32, so lanes of different substrates read
 // different banks and each thread walks its own row with compile-time
-// offsets) -- AxisTab::tabT, copied into shared memory when it fits.
+// offsets) -- AxisTab::tabT, copied into shared memory (the planner only
+// takes this kernel when they fit).
 __host__ __device__ inline int pipe_npad(int n) { return (n + 31) / 32 * 32 + 1; }
 
 // One chunk of one column: e = L_N d (FP32), forward elimination, carry in,
@@ -186,8 +187,8 @@ __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
   const int64_t stage_elems = a.stage_elems;
   const int npad = pipe_npad(n);
   E *stage0 = reinterpret_cast<E *>(smem_raw);
-  E *tab = stage0 + NS * stage_elems;  // [4][S][npad] when staged
-  E *s_end = tab + (a.tab_in_smem ? 4 * S * npad : 0);
+  E *tab = stage0 + NS * stage_elems;  // [4][S][npad]
+  E *s_end = tab + 4 * S * npad;
   E *s_beg = s_end + T * 32;
   uint64_t *full = reinterpret_cast<uint64_t *>(
       (reinterpret_cast<uintptr_t>(s_beg + T * 32) + 15) & ~uintptr_t(15));
@@ -207,13 +208,12 @@ __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
     fence_mbar_init();
     fence_proxy_async_smem();
   }
-  const E *gT = static_cast<const E *>(a.tab.tabT);
-  if (a.tab_in_smem)
+  {
+    const E *gT = static_cast<const E *>(a.tab.tabT);
     for (int q = threadIdx.x; q < 4 * S * npad; q += blockDim.x) tab[q] = __ldg(gT + q);
+  }
   __syncthreads();
-  const E *ctab = a.tab_in_smem ? tab : gT;
-  const E *s_inv = ctab, *s_mul = ctab + S * npad, *s_pf = s_mul + S * npad,
-          *s_pb = s_pf + S * npad;
+  const E *s_inv = tab, *s_mul = tab + S * npad, *s_pf = s_mul + S * npad, *s_pb = s_pf + S * npad;
   const E *g_cfix = static_cast<const E *>(a.tab.cfix);
 
   if (warp == 0) {  // ------------------------------------------------ producer

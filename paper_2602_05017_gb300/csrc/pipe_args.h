@@ -31,7 +31,7 @@ struct PipeArgs {
   int64_t nrows;
   void *field;
   // ring of stages
-  int stages, tab_in_smem;
+  int stages;
   int64_t stage_elems;
   AxisTab tab;
   int flags;
