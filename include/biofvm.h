@@ -181,10 +181,13 @@ typedef struct biofvm_batch biofvm_batch_t;
 
 /* Create n_env >= 1 environments: grids[e] (host), dx[e], dt[e], and
  * D_flat / lambda_flat holding the n_sub of environment 0, then of
- * environment 1, ... (host).  tile_m: NULL or [n_env][3] chunk lengths of the
- * partitioned solve along x, y, z per environment (<= 0 picks a default; each
- * axis must give at most 8 chunks of at most 48 positions) -- the tile shapes
- * an autotuner chooses.  All environments share `prec` and the stream.
+ * environment 1, ... (host).  tile_m: NULL or [n_env][3] tile shapes along
+ * x, y, z per environment -- the shapes an autotuner chooses: a value >= the
+ * axis length solves whole lines (one warp streams 32 lines, no chunks; FP32
+ * then allocates a field-sized scratch for the environment); a smaller value
+ * is the chunk length of the partitioned solve (at most 8 chunks of at most
+ * 48 positions); <= 0 picks a default (whole lines, except chunks along x
+ * when n_sub <= 2).  All environments share `prec` and the stream.
  * Errors: ARG, OOM, CUDA (with the failing environment in the message). */
 biofvm_status biofvm_batch_create(int n_env, const biofvm_grid *grids, const double *dx,
                                   const double *dt, const double *D_flat,
@@ -206,10 +209,10 @@ biofvm_status biofvm_batch_step(biofvm_batch_t *b, int n_steps);
  * TIMEOUT. */
 biofvm_status biofvm_batch_sync(biofvm_batch_t *b);
 
-/* Change the tile shapes (chunk lengths, same rules as tile_m of
- * biofvm_batch_create) of every environment without touching the fields or
- * agents: re-partitions the App. A constants.  Used by the autotuner.  Waits
- * for the stream.  Errors: ARG (nothing changed), CUDA. */
+/* Change the tile shapes (same rules as tile_m of biofvm_batch_create) of
+ * every environment without touching the fields or agents: re-partitions the
+ * App. A constants.  Used by the autotuner.  Waits for the stream.  Errors:
+ * ARG (nothing changed), OOM (scratch), CUDA. */
 biofvm_status biofvm_batch_set_tiles(biofvm_batch_t *b, const int *tile_m);
 
 /* CTAs of the persistent batched launch (resident at once). */

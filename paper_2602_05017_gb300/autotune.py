@@ -1,12 +1,14 @@
 """Autotuner for the tile shapes of the batched persistent step.
 
-The tunable shape of an environment is the chunk length of the partitioned Thomas solve along
-each axis (a line of n voxels is cut into ceil(n/m) chunks, one warp each, at most 8): it sets
-the registers per thread, the warps per tile and the length of the serial recurrences.  For each
-class (edge-length bucket, substrate count) the tuner builds a batch of identical environments
-large enough to fill the GPU, times the candidates with CUDA events (y/z chunk first, then x),
-and records the fastest in a JSON cache.  ``tile_shapes`` maps any list of environments to
-per-environment chunk lengths from that cache.
+The tunable shape of an environment is, per axis, either the chunk length m of the
+partitioned Thomas solve (a line of n voxels cut into ceil(n/m) chunks, one warp each, at most
+8, chunks of at most 48 in shared memory, carries across the CTA's warps) or the whole line
+(m >= n: each warp streams 32 whole lines, no carries, the forward intermediate through L2).
+It sets the warps per tile, the length of the serial recurrences and the memory traffic pattern.
+For each class (edge-length bucket, substrate count) the tuner builds a batch of identical
+environments large enough to fill the GPU, times the candidates with CUDA events (y/z first,
+then x), and records the fastest in a JSON cache (WHOLE = -1 for whole lines).
+``tile_shapes`` maps any list of environments to per-environment tile shapes from that cache.
 """
 from __future__ import annotations
 
@@ -21,17 +23,19 @@ from . import inputs
 
 N_BUCKETS = (32, 64, 96, 128, 160, 192)
 MAX_CHUNKS = 8     # warps of the batched CTA
-MAX_CHUNK = 48     # largest register chunk compiled for the batched kernel
+MAX_CHUNK = 48     # longest chunk the batched kernel keeps in shared memory
+WHOLE = -1         # cache marker: whole lines
 
 
 def candidates(n, S=None):
-    """Valid chunk lengths for an axis of n voxels (at most MAX_CHUNKS chunks; for the x axis,
-    given S, also at most 32/S chunks so that a row's lines fit one warp)."""
+    """Tile shapes for an axis of n voxels: valid chunk lengths m < n (at most MAX_CHUNKS chunks
+    of at most MAX_CHUNK; for the x axis, given S, also at most 32/S chunks so that a row's
+    lines fit one warp), then n itself (whole lines)."""
     lo = max(4, math.ceil(n / MAX_CHUNKS))
     if S is not None:
         lo = max(lo, math.ceil(n / max(1, 32 // S)))
-    out = sorted({min(c, MAX_CHUNK, n) for c in (lo, math.ceil(1.5 * lo), 2 * lo, 3 * lo)})
-    return [c for c in out if c >= lo] or [min(MAX_CHUNK, n)]
+    out = sorted({min(c, MAX_CHUNK) for c in (lo, math.ceil(1.5 * lo), 2 * lo, 3 * lo)})
+    return [c for c in out if lo <= c < n] + [n]
 
 
 def _bucket(n):
@@ -89,10 +93,10 @@ def tune(precision="fp32", n_buckets=N_BUCKETS, subs=range(1, 9), target_vs=1.2e
                         best_x, best_rate = mx, rate
             finally:
                 b.close()
-            cache["classes"][f"{n},{S}"] = {"m": [best_x, best_yz, best_yz],
-                                            "vs_per_s": best_rate, "envs": k}
+            m = [WHOLE if c >= n else c for c in (best_x, best_yz, best_yz)]
+            cache["classes"][f"{n},{S}"] = {"m": m, "vs_per_s": best_rate, "envs": k}
             if log:
-                log(f"tune n={n} S={S}: m={[best_x, best_yz, best_yz]} {best_rate:.3e} vs/s")
+                log(f"tune n={n} S={S}: m={m} {best_rate:.3e} vs/s")
     if path:
         with open(path, "w") as f:
             json.dump(cache, f, indent=1)
@@ -105,13 +109,18 @@ def load(path):
 
 
 def tile_shapes(envs, cache):
-    """Per-environment [m_x, m_y, m_z] from a cache (nearest class), kept valid for each axis."""
+    """Per-environment [m_x, m_y, m_z] from a cache (nearest class), kept valid for each axis:
+    WHOLE becomes the environment's own axis length, a chunk length is raised to the fewest
+    chunks allowed and lowered to MAX_CHUNK (0: library default)."""
     out = []
     for w in envs:
         entry = cache["classes"].get(f"{_bucket(max(w.nx, w.ny, w.nz))},{min(max(w.ns, 1), 8)}")
         m = entry["m"] if entry else [0, 0, 0]
         row = []
         for a, (mm, n) in enumerate(zip(m, (w.nx, w.ny, w.nz))):
+            if mm == WHOLE:
+                row.append(int(n))
+                continue
             lo = math.ceil(n / MAX_CHUNKS)
             if a == 0:
                 lo = max(lo, math.ceil(n / max(1, 32 // w.ns)))

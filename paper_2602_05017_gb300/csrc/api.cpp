@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -79,7 +80,7 @@ struct PipePlan {
   int have_map[2]{};
 };
 struct StreamPlan {
-  int use = 0, pf = 1, grid = 0;
+  int use = 0, grid = 0;
 };
 struct XPlan {
   int T = 1, m = 1, maxm = 8, rows_per_warp = 1, warps = 1, rows_per_cta = 1, use_bulk = 0;
@@ -114,7 +115,8 @@ struct biofvm {
   int pipe_enabled = 1;
   int stream_enabled = 1;
   int stream_ctas_per_sm = 3;
-  int stream_pf = 1;
+  int stream32_enabled = 0;  // FP32 streaming sweeps instead of the pipelined ones
+  DevBuf scratch;            // FP32 streaming: forward intermediate, field-sized
   int forced = 0;  // chunk lengths fixed by the caller (batched environments)
   unsigned generation = 0;  // bumped when kernel arguments change (sources, constants)
   // sources
@@ -413,22 +415,26 @@ void plan_pipe(biofvm *h, int axis) {
   p.use = 1;
 }
 
-// Plan the streaming sweep of an axis (FP64 only): a persistent grid of
-// stream_ctas_per_sm 128-thread CTAs per SM, prefetch variant stream_pf.  Each
-// warp keeps its 32 lines' intermediates (32 n elements) in L2 between the two
-// passes, so the warps in flight bound the L2 footprint (12 warps per SM at
-// n = 400: about 93 MB on average).
+// Plan the streaming sweep of an axis: a persistent grid of
+// stream_ctas_per_sm 128-thread CTAs per SM.  Each warp keeps its 32 lines'
+// intermediates (32 n elements; FP32: and the field values the backward pass
+// re-reads) in L2 between the two passes, so the warps in flight bound the L2
+// footprint (12 warps per SM at n = 400: about 93 MB on average).  FP64 always
+// (the FP64 step is bound by FP64 operations); FP32 when stream32_enabled,
+// with a field-sized scratch buffer.
 void plan_stream(biofvm *h, int axis) {
   StreamPlan &p = h->sp[axis];
   p = StreamPlan{};
-  if (h->prec != BIOFVM_FP64 || !h->stream_enabled) return;
+  if (!h->stream_enabled) return;
+  if (h->prec == BIOFVM_FP32) {
+    if (!h->stream32_enabled) return;
+    if (!h->scratch.p && dev_alloc(h->scratch, h->nel * h->esz) != cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
+  }
   const int S = h->g.n_sub;
   if (axis == 0 && S > 32) return;
-  p.pf = (h->stream_pf == 4 || h->stream_pf == 8 || h->stream_pf == 16) ? h->stream_pf : 1;
-  if (allow_stream_smem_f64(p.pf) != cudaSuccess) {
-    cudaGetLastError();
-    return;
-  }
   p.grid = h->num_sms * std::max(1, h->stream_ctas_per_sm);
   p.use = 1;
 }
@@ -516,14 +522,42 @@ void stream_tables(const biofvm *h, int axis, std::vector<double> &tt, double *s
     }
 }
 
+// FP32 streaming constants of one axis from its (defect-form) tables t:
+// the float-rounded interior limits inv'_inf = (-c r) sigma and mul_inf =
+// r sigma into c[0][S], c[1][S], and k0 = 1 + the last position below n-1
+// whose float-rounded entry differs from them (the entries from k0 to n-2
+// then equal the constants bit for bit; n < 3 has no interior: k0 = n).
+void stream_consts_f32(const biofvm *h, int axis, const std::vector<double> &t, double *c,
+                       int &k0) {
+  const int n = axis_len(h, axis), S = h->g.n_sub;
+  k0 = n < 3 ? n : 0;
+  for (int s = 0; s < S; s++) {
+    const double r = h->D[s] * h->dt / (h->dx * h->dx);
+    const double lam3 = h->lam[s] * h->dt / 3.0;
+    const double b = 1.0 + 2.0 * r + lam3;
+    const double den = 0.5 * (b + std::sqrt((1.0 + lam3) * (1.0 + 4.0 * r + lam3)));
+    const double cc = 1.0 / (1.0 + lam3), scale = -cc * r;  // as the tables form them
+    const float iv = (float)(scale * (1.0 / den)), mu = (float)(r / den);
+    c[s] = iv;
+    c[S + s] = mu;
+    if (n < 3) continue;
+    for (int i = 0; i < n - 1; i++)
+      if ((float)t[(size_t)i * S + s] != iv || (float)t[((size_t)n + i) * S + s] != mu)
+        k0 = std::max(k0, i + 1);
+  }
+}
+
 biofvm_status upload_constants(biofvm *h) {
   std::vector<double> t;
+  std::vector<double> c32((size_t)6 * h->g.n_sub);
   for (int axis = 0; axis < 3; axis++) {
     int T, m;
     axis_partition(h, axis, T, m);
     axis_tables(h, axis, T, m, h->prec == BIOFVM_FP32, t);
     biofvm_status st = upload_doubles(h, h->tab[axis], t);
     if (st) return st;
+    if (h->prec == BIOFVM_FP32)
+      stream_consts_f32(h, axis, t, &c32[(size_t)axis * 2 * h->g.n_sub], h->stream_k0[axis]);
     // the same inv, mul, pf, pb substrate-major [4][S][npad] for the pipelined kernel
     const int n = axis_len(h, axis), S = h->g.n_sub, npad = pipe_npad_host(n);
     std::vector<double> tt((size_t)4 * S * npad, 0.0);
@@ -532,6 +566,10 @@ biofvm_status upload_constants(biofvm *h) {
         for (int s = 0; s < S; s++)
           tt[((size_t)w * S + s) * npad + i] = t[(size_t)w * n * S + (size_t)i * S + s];
     st = upload_doubles(h, h->tabT[axis], tt);
+    if (st) return st;
+  }
+  if (h->prec == BIOFVM_FP32) {
+    biofvm_status st = upload_doubles(h, h->stream_const_d, c32);
     if (st) return st;
   }
   if (h->prec == BIOFVM_FP64) {
@@ -660,20 +698,20 @@ cudaError_t launch_stream(const biofvm *h, int axis, int flags, cudaStream_t st,
   a.nz = (int)nz;
   if (axis == 0) {
     a.stride = S;
-    a.C = nx * S;
     a.rows_per_warp = (int)(32 / S);
     a.ngroups = (ny * nz + a.rows_per_warp - 1) / a.rows_per_warp;
   } else {
-    a.C = axis == 1 ? nx * S : nx * ny * S;
-    a.stride = a.C;
-    a.plane_stride = axis == 1 ? nx * ny * S : 0;
-    a.colgroups = (a.C + 31) / 32;
-    a.ngroups = a.colgroups * (axis == 1 ? nz : 1);
+    const int64_t C = axis == 1 ? nx * S : nx * ny * S;
+    a.stride = C;
+    a.ngroups = (C + 31) / 32 * (axis == 1 ? nz : 1);
   }
-  a.tab = h->tabS[axis].p;
+  const bool fp64 = h->prec == BIOFVM_FP64;
+  a.tab = fp64 ? h->tabS[axis].p : h->tab[axis].p;  // FP32: inv, mul lead the axis table
+  a.cfix = fp64 ? nullptr : axis_tab(h, axis).cfix;
+  a.scratch = h->scratch.p;
   a.flags = flags;
   if (!h->any_dir) a.flags &= ~(kDirBefore | kDirAfter);
-  a.out = (flags & kScaled) ? (axis == 2 ? 2 : 1) : 0;
+  a.out = (fp64 && (flags & kScaled)) ? (axis == 2 ? 2 : 1) : 0;
   a.k0 = h->stream_k0[axis];
   a.omega = h->omega_d.p;
   a.interior = static_cast<const char *>(h->stream_const_d.p) + (size_t)axis * 2 * S * h->esz;
@@ -687,7 +725,7 @@ cudaError_t launch_stream(const biofvm *h, int axis, int flags, cudaStream_t st,
   a.dir_val = a.out ? dsc + (size_t)axis * S * h->esz : h->dir_val_d.p;
   a.dir_val_in = (a.out && axis > 0) ? dsc + (size_t)(axis - 1) * S * h->esz : h->dir_val_d.p;
   const int grid = (int)std::min<int64_t>(p.grid, (a.ngroups + 3) / 4);
-  return launch_stream_f64(a, p.pf, grid, st);
+  return fp64 ? launch_stream_f64(a, grid, st) : launch_stream_f32(a, grid, st);
 }
 
 bool pipe_ok(const biofvm *h, int axis, int flags, int buf) {
@@ -756,9 +794,9 @@ cudaError_t launch_col(const biofvm *h, int axis, int flags, cudaStream_t st, in
   return h->prec == BIOFVM_FP64 ? launch_col_f64(a, st) : launch_col_f32(a, st);
 }
 
-// Scaled intermediates (stream.cuh) only when all three sweeps of a step stream.
+// Scaled intermediates (FP64, stream.cuh) only when all three sweeps of a step stream.
 int step_scaled(const biofvm *h) {
-  return (h->sp[0].use && h->sp[1].use && h->sp[2].use) ? kScaled : 0;
+  return (h->prec == BIOFVM_FP64 && h->sp[0].use && h->sp[1].use && h->sp[2].use) ? kScaled : 0;
 }
 
 biofvm_status launch_step(const biofvm *h, cudaStream_t st) {
@@ -795,7 +833,7 @@ void destroy_impl(biofvm *h) {
   if (h->graph) cudaGraphDestroy(h->graph);
   for (DevBuf *b : {&h->rho, &h->tab[0], &h->tab[1], &h->tab[2], &h->tabT[0], &h->tabT[1],
                     &h->tabT[2], &h->tabS[0], &h->tabS[1], &h->tabS[2], &h->dir_scaled_d,
-                    &h->omega_d, &h->stream_const_d, &h->dir_on_d, &h->dir_val_d,
+                    &h->omega_d, &h->stream_const_d, &h->scratch, &h->dir_on_d, &h->dir_val_d,
                     &h->status, &h->src_row_off, &h->src_elem, &h->src_alpha, &h->src_scale,
                     &h->adj, &h->partial, &h->ag_elem, &h->ag_entry, &h->ag_weight,
                     &h->ag_target})
@@ -944,7 +982,7 @@ biofvm_status create_impl(const biofvm_grid *grid, double dx, double dt, const d
     for (int axis = 0; axis < 3; axis++) plan_pipe(h, axis);
   if (const char *env = getenv("BIOFVM_STREAM")) h->stream_enabled = atoi(env) != 0;
   if (const char *env = getenv("BIOFVM_STREAM_CTAS")) h->stream_ctas_per_sm = atoi(env);
-  if (const char *env = getenv("BIOFVM_STREAM_PF")) h->stream_pf = atoi(env);
+  if (const char *env = getenv("BIOFVM_STREAM32")) h->stream32_enabled = atoi(env) != 0;
   if (!h->forced)
     for (int axis = 0; axis < 3; axis++) plan_stream(h, axis);
   if ((st = upload_doubles(h, h->dir_val_d, h->dir_val)) != BIOFVM_OK ||
@@ -1275,6 +1313,7 @@ void biofvm_destroy(biofvm_t *h) { destroy_impl(h); }
 struct biofvm_batch {
   std::vector<biofvm *> env;
   std::vector<unsigned> env_gen;
+  std::vector<std::array<int, 3>> whole;  // per environment and axis: whole-line tiles
   biofvm_precision prec = BIOFVM_FP32;
   cudaStream_t stream = nullptr, cap_stream = nullptr;
   int device = 0, maxm = 8, grid = 0;
@@ -1287,6 +1326,39 @@ struct biofvm_batch {
 };
 
 namespace {
+
+// Tile shape of one batched axis of n voxels.  want >= n: whole lines
+// (streaming solve, chunk_m = 0 lets the environment's own handle plan its
+// chunks); otherwise chunks of want positions -- at most kBatchWarps chunks of
+// at most 48 positions, and along x a row's S lines in one warp (T*S <= 32);
+// want <= 0 picks a default.  Returns false (message set) if not allowed.
+bool batch_axis_shape(int e, int axis, int n, int S, int want, int &chunk_m, int &whole) {
+  whole = 0;
+  chunk_m = 0;
+  // default: whole lines, except along x with one or two substrates (a warp
+  // would then read 16 or 32 rows at once), where chunks measured faster
+  if (want <= 0 && (axis > 0 || S >= 3)) want = n;
+  if (want >= n && n >= 1) {
+    whole = 1;
+    return true;
+  }
+  if (want <= 0) want = std::max(8, (n + kBatchWarps - 1) / kBatchWarps);
+  if (axis == 0 && S >= 1 && S <= 32)
+    want = std::max(want, (n + 32 / S - 1) / (32 / S));
+  const int m = std::min(want, std::max(n, 1));
+  if (m >= n) {  // the default reached the whole line
+    whole = 1;
+    return true;
+  }
+  if ((n + m - 1) / m > kBatchWarps || m > 48) {
+    fail(BIOFVM_ERR_ARG,
+         "environment %d axis %d: chunk length %d gives more than %d chunks or exceeds 48 "
+         "(use >= %d for whole lines)", e, axis, m, kBatchWarps, n);
+    return false;
+  }
+  chunk_m = m;
+  return true;
+}
 
 void batch_drop_graph(biofvm_batch *b) {
   if (b->gexec) cudaGraphExecDestroy(b->gexec);
@@ -1332,10 +1404,17 @@ biofvm_status batch_upload(biofvm_batch *b) {
     x.tiles[0] = (nrows + x.rows_per_tile - 1) / x.rows_per_tile;
     x.tiles[1] = (int64_t)x.nz * ((rowlen + 31) / 32);
     x.tiles[2] = (rowlen * x.ny + 31) / 32;
+    const bool fp64 = h->prec == BIOFVM_FP64;
     for (int ph = 0; ph < 3; ph++) {
-      x.group[ph] = std::max(1, kBatchWarps / x.T[ph]);
+      x.whole[ph] = b->whole[e][ph];
+      x.group[ph] = x.whole[ph] ? kBatchWarps : std::max(1, kBatchWarps / x.T[ph]);
       x.items[ph] = (x.tiles[ph] + x.group[ph] - 1) / x.group[ph];
+      x.stab[ph] = fp64 ? h->tabS[ph].p : h->tab[ph].p;
+      x.sint[ph] = static_cast<const char *>(h->stream_const_d.p) + (size_t)ph * 2 * x.S * h->esz;
+      x.cfix[ph] = axis_tab(h, ph).cfix;
+      x.k0[ph] = h->stream_k0[ph];
     }
+    x.scratch = h->scratch.p;
     x.src_row_off = static_cast<const int64_t *>(h->src_row_off.p);
     x.src_elem = static_cast<const int64_t *>(h->src_elem.p);
     x.src_alpha = h->src_alpha.p;
@@ -1372,25 +1451,19 @@ biofvm_status biofvm_batch_create(int n_env, const biofvm_grid *grids, const dou
   int64_t off = 0;
   for (int e = 0; e < n_env; e++) {
     const biofvm_grid &g = grids[e];
-    int m[3];
+    int m[3], whole[3];
     const int ns[3] = {g.nx, g.ny, g.nz};
-    for (int a = 0; a < 3; a++) {
-      int want = tile_m ? tile_m[3 * e + a] : 0;
-      if (want <= 0) want = std::max(8, (ns[a] + kBatchWarps - 1) / kBatchWarps);  // default
-      if (a == 0 && g.n_sub >= 1 && g.n_sub <= 32)  // a row's lines in one warp: T*S <= 32
-        want = std::max(want, (ns[0] + 32 / g.n_sub - 1) / (32 / g.n_sub));
-      m[a] = std::min(want, std::max(ns[a], 1));
-      if ((ns[a] + m[a] - 1) / m[a] > kBatchWarps || m[a] > 48) {
-        batch_destroy_impl(b);
-        return fail(BIOFVM_ERR_ARG,
-                    "environment %d axis %d: chunk length %d gives more than %d chunks or "
-                    "exceeds 48", e, a, m[a], kBatchWarps);
-      }
-    }
     if (g.n_sub < 1 || g.n_sub > 32) {
       batch_destroy_impl(b);
       return fail(BIOFVM_ERR_ARG, "environment %d: n_sub must be in [1, 32]", e);
     }
+    for (int a = 0; a < 3; a++)
+      if (!batch_axis_shape(e, a, ns[a], g.n_sub, tile_m ? tile_m[3 * e + a] : 0, m[a],
+                            whole[a])) {
+        const biofvm_status st = BIOFVM_ERR_ARG;
+        batch_destroy_impl(b);
+        return st;
+      }
     biofvm *h = nullptr;
     biofvm_status st = create_impl(&g, dx[e], dt[e], D_flat + off, lambda_flat + off, nullptr,
                                    prec, cuda_stream, m, &h);
@@ -1401,7 +1474,13 @@ biofvm_status biofvm_batch_create(int n_env, const biofvm_grid *grids, const dou
     }
     b->env.push_back(h);
     b->env_gen.push_back(0);
+    b->whole.push_back({whole[0], whole[1], whole[2]});
     for (int a = 0; a < 3; a++) b->maxm = std::max(b->maxm, m[a]);
+    if ((whole[0] || whole[1] || whole[2]) && prec == BIOFVM_FP32 && !h->scratch.p &&
+        dev_alloc(h->scratch, h->nel * h->esz) != cudaSuccess) {
+      batch_destroy_impl(b);
+      return fail(BIOFVM_ERR_OOM, "environment %d: scratch field allocation failed", e);
+    }
     off += g.n_sub;
   }
   for (int c : kBatchMaxm)
@@ -1522,20 +1601,25 @@ biofvm_status biofvm_batch_set_tiles(biofvm_batch_t *b, const int *tile_m) {
   std::vector<XPlan> xp(b->env.size());
   std::vector<ColPlan> cy(b->env.size()), cz(b->env.size());
   int maxm = 8;
+  std::vector<std::array<int, 3>> whole(b->env.size());
   for (size_t e = 0; e < b->env.size(); e++) {  // validate everything before changing anything
     const biofvm *h = b->env[e];
     const int ns[3] = {h->g.nx, h->g.ny, h->g.nz};
     int m[3];
     for (int a = 0; a < 3; a++) {
-      m[a] = std::min(tile_m[3 * e + a] > 0 ? tile_m[3 * e + a] : 8, ns[a]);
-      if ((ns[a] + m[a] - 1) / m[a] > kBatchWarps || m[a] > 48)
-        return fail(BIOFVM_ERR_ARG, "environment %zu axis %d: chunk length %d not allowed", e, a,
-                    m[a]);
+      if (!batch_axis_shape((int)e, a, ns[a], h->g.n_sub, tile_m[3 * e + a], m[a], whole[e][a]))
+        return BIOFVM_ERR_ARG;
       maxm = std::max(maxm, m[a]);
     }
     if (!plan_x(h->g.nx, h->g.n_sub, fp64, xp[e], m[0]) || !plan_col(h->g.ny, fp64, cy[e], m[1]) ||
         !plan_col(h->g.nz, fp64, cz[e], m[2]))
       return fail(BIOFVM_ERR_ARG, "environment %zu: tile shapes do not fit the kernels", e);
+  }
+  for (size_t e = 0; e < b->env.size(); e++) {  // scratch fields for FP32 whole-line axes
+    biofvm *h = b->env[e];
+    if ((whole[e][0] || whole[e][1] || whole[e][2]) && !fp64 && !h->scratch.p &&
+        dev_alloc(h->scratch, h->nel * h->esz) != cudaSuccess)
+      return fail(BIOFVM_ERR_OOM, "environment %zu: scratch field allocation failed", e);
   }
   for (int c : kBatchMaxm)
     if (c >= maxm) {
@@ -1553,6 +1637,7 @@ biofvm_status biofvm_batch_set_tiles(biofvm_batch_t *b, const int *tile_m) {
     if (st) return st;
   }
   b->maxm = maxm;
+  b->whole = whole;
   b->grid = std::max(per_sm, 1) * b->env[0]->num_sms;
   return batch_upload(b);
 }

@@ -17,16 +17,19 @@
 // wait is bounded (about two seconds); on a timeout the status word is set
 // and an abort flag makes every CTA stop at its next item.
 //
-// Tiles read and write the field directly (lines in registers, chunk carries
-// through shared memory), with the arithmetic of the single-grid kernels:
-// partitioned Thomas on the App. A system, FP32 in defect-correction form,
-// the source update applied to an x tile's rows before its solve.  Zero-flux
+// A tile is solved either cut into chunks (chunk lengths m < n: chunks in
+// shared memory, carries across the CTA's warps) or whole (m >= n: each
+// warp streams its 32 lines as the single-grid streaming kernels do, no
+// carries; an item is then 8 tiles, one per warp), with the arithmetic of the
+// single-grid kernels: App. A system, FP32 in defect-correction form, the
+// source update applied to an x item's rows before its solve.  Zero-flux
 // boundaries (the batched microenvironments have no Dirichlet faces).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "batch_args.h"
+#include "stream.cuh"
 #include "sweeps.cuh"
 
 namespace bfv {
@@ -46,13 +49,26 @@ __device__ __forceinline__ int ld_relaxed_int(const int *p) {
 // access of a warp is one conflict-free row) and every loop runs exactly the
 // chunk's length: one launch serves environments whose chunk lengths differ,
 // so a register array unrolled for the longest chunk would waste the issue
-// slots of every shorter one.
+// slots of every shorter one.  A chunk and its two halo values arrive by
+// cp.async (every element of the chunk in flight at once, no register round
+// trip); FP32 keeps d beside the working array for the final x = c d + y.
+__device__ __forceinline__ void cp_async_elem(void *smem, const void *gmem, int bytes) {
+  if (bytes == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(smem)), "l"(gmem)
+                 : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(smem)), "l"(gmem)
+                 : "memory");
+}
+
 template <typename E>
 __global__ void __launch_bounds__(kBatchWarps * 32) batch_kernel(const BatchArgs a) {
   extern __shared__ __align__(16) unsigned char batch_smem[];
-  E *const s_chunk = reinterpret_cast<E *>(batch_smem);  // [8][maxm][32]
-  E *const s_end = s_chunk + kBatchWarps * a.maxm * 32;  // [8][32]
-  E *const s_beg = s_end + kBatchWarps * 32;             // [8][32]
+  constexpr int NB = kDefect<E> ? 2 : 1;                         // d (+ working array)
+  E *const s_chunk = reinterpret_cast<E *>(batch_smem);          // [NB][8][maxm][32]
+  E *const s_halo = s_chunk + NB * kBatchWarps * a.maxm * 32;    // [8][2][32]
+  E *const s_end = s_halo + kBatchWarps * 64;                    // [8][32]
+  E *const s_beg = s_end + kBatchWarps * 32;                     // [8][32]
   __shared__ int s_go;
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   const int64_t total = a.per_step * a.n_steps;
@@ -109,31 +125,69 @@ __global__ void __launch_bounds__(kBatchWarps * 32) batch_kernel(const BatchArgs
     last_phase = phase;
     last_step = step;
 
-    // ---- geometry: warp w solves chunk w % T of tile (item*group + w / T) ----
     const int S = E_.S, nx = E_.nx, ny = E_.ny;
     const int n = phase == 0 ? nx : phase == 1 ? ny : E_.nz;
+    E *const field = static_cast<E *>(E_.field);
+    const int64_t rowlen = (int64_t)nx * S;
+    // Src on this item's rows (only this CTA touches them in this phase)
+    if (phase == 0 && E_.has_src) {
+      const int64_t nrows = (int64_t)ny * E_.nz;
+      const int64_t ra = item * E_.group[0] * E_.rows_per_tile;
+      const int64_t rb = min(nrows, ra + (int64_t)E_.group[0] * E_.rows_per_tile);
+      const int64_t e0 = E_.src_row_off[ra], e1 = E_.src_row_off[rb];
+      for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+        const int64_t el = E_.src_elem[e];
+        field[el] = (field[el] + ldg<E>(E_.src_alpha, e)) * ldg<E>(E_.src_scale, e);
+      }
+      __syncthreads();
+    }
+    if (E_.whole[phase]) {  // ---- whole lines: warp w streams tile item*8 + w ----
+      const int64_t tile = item * kBatchWarps + wp;
+      if (tile < E_.tiles[phase]) {
+        const LaneLine L = lane_line(phase, tile, lane, S, nx, ny, E_.nz, rowlen, E_.rows_per_tile);
+        const long long st = phase == 0 ? S : phase == 1 ? rowlen : rowlen * ny;
+        const E *tb = static_cast<const E *>(E_.stab[phase]);
+        LineCoef<E> cf;
+        cf.S = S;
+        cf.k0 = E_.k0[phase];
+        cf.inv = tb + L.s;
+        cf.mul = tb + (size_t)n * S + L.s;
+        cf.q = tb + 2 * (size_t)n * S + L.s;
+        cf.c0 = ldg<E>(E_.sint[phase], L.s);
+        cf.c1 = ldg<E>(E_.sint[phase], S + L.s);
+        LineDir dr;
+        dr.before = dr.after = false;
+        dr.face = L.face;
+        E *line = field + (L.active ? L.base : 0);
+        if constexpr (sizeof(E) == 8) {
+          cf.om = E(1);
+          cf.clo = E(0);
+          solve_lines_f64<0, 8>(line, n, st, L.active, cf, dr, E(0), E(0));
+        } else {
+          cf.om = ldg<E>(E_.cfix[phase], L.s);
+          cf.clo = ldg<E>(E_.cfix[phase], S + L.s);
+          E *sline = static_cast<E *>(E_.scratch) + (L.active ? L.base : 0);
+          solve_lines_f32<8>(line, sline, n, st, L.active, cf, dr, E(0), E(0));
+        }
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(a.done + phase * a.n_env + ei, 1u);
+      }
+      continue;
+    }
+
+    // ---- chunks: warp w solves chunk w % T of tile (item*group + w / T) ----
     const int T = E_.T[phase], m = E_.m[phase];
     const int grp = wp / T, t = wp - grp * T;  // warp group (tile) and chunk
     const int64_t tile = item * E_.group[phase] + grp;
     const bool tile_ok = grp < E_.group[phase] && tile < E_.tiles[phase];
-    E *const field = static_cast<E *>(E_.field);
-    const int64_t rowlen = (int64_t)nx * S;
     long long base = 0, pstride;
     bool active;
     int s;
     if (phase == 0) {
       const int64_t nrows = (int64_t)ny * E_.nz;
-      // Src on this item's rows (only this CTA touches them in this phase)
-      if (E_.has_src) {
-        const int64_t ra = item * E_.group[0] * E_.rows_per_tile;
-        const int64_t rb = min(nrows, ra + (int64_t)E_.group[0] * E_.rows_per_tile);
-        const int64_t e0 = E_.src_row_off[ra], e1 = E_.src_row_off[rb];
-        for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-          const int64_t el = E_.src_elem[e];
-          field[el] = (field[el] + ldg<E>(E_.src_alpha, e)) * ldg<E>(E_.src_scale, e);
-        }
-        __syncthreads();
-      }
       const int64_t r0 = tile * E_.rows_per_tile;
       const int rows = tile_ok ? (int)min((int64_t)E_.rows_per_tile, nrows - r0) : 0;
       s = lane % S;
@@ -153,22 +207,35 @@ __global__ void __launch_bounds__(kBatchWarps * 32) batch_kernel(const BatchArgs
     const int lo = t * m;
     const int len = active ? min(m, n - lo) : 0;
     E *col = field + (active ? base : 0) + (long long)lo * pstride;
-    E *vs = s_chunk + (wp * a.maxm) * 32 + lane;  // position i at vs[i * 32]
+    E *vd = s_chunk + (wp * a.maxm) * 32 + lane;  // d at position i: vd[i * 32]
+    E *vs = kDefect<E> ? vd + kBatchWarps * a.maxm * 32 : vd;  // working array
+    E *hl = s_halo + wp * 64 + lane;              // halos d_{lo-1}, d_{lo+len}
     const E *tb = static_cast<const E *>(E_.tab[phase]);
     const E *T_inv = tb, *T_mul = tb + n * S, *T_pf = T_mul + n * S, *T_pb = T_pf + n * S;
     const E *T_pc = T_pb + n * S, *T_cfix = T_pc + T * S;
     const E *T_cw = T_cfix + 2 * S;  // [T][T][S]
     const int q0 = lo * S + s;       // table index of position 0 of the chunk
 
-    for (int i = 0; i < len; i++) vs[i * 32] = col[(long long)i * pstride];
+    {
+      const E *src = col;
+      for (int i = 0; i < len; i++) {
+        cp_async_elem(vd + i * 32, src, (int)sizeof(E));
+        src += pstride;
+      }
+      if (kDefect<E> && len > 0) {
+        if (lo > 0) cp_async_elem(hl, col - pstride, (int)sizeof(E));
+        if (lo + len < n) cp_async_elem(hl + 32, col + (long long)len * pstride, (int)sizeof(E));
+      }
+      asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+    }
     if constexpr (kDefect<E>) {
       // e = L_N d; the zero-flux ends use mirrored halos (d_{-1} = d_0, d_n = d_{n-1})
       if (len > 0) {
-        E prev = lo > 0 ? col[-pstride] : vs[0];
-        const E after = lo + len < n ? col[(long long)len * pstride] : vs[(len - 1) * 32];
+        E prev = lo > 0 ? hl[0] : vd[0];
+        const E after = lo + len < n ? hl[32] : vd[(len - 1) * 32];
         for (int i = 0; i < len; i++) {
-          const E cur = vs[i * 32];
-          const E nxt = i + 1 < len ? vs[(i + 1) * 32] : after;
+          const E cur = vd[i * 32];
+          const E nxt = i + 1 < len ? vd[(i + 1) * 32] : after;
           vs[i * 32] = (cur - prev) + (cur - nxt);
           prev = cur;
         }
@@ -205,15 +272,19 @@ __global__ void __launch_bounds__(kBatchWarps * 32) batch_kernel(const BatchArgs
 #pragma unroll 4
       for (int i = 0; i < len; i++) vs[i * 32] = fma(__ldg(T_pb + q0 + i * S), carry, vs[i * 32]);
     }
-    if constexpr (kDefect<E>) {  // x = c_hi d + (c_lo d + y), d re-read from the field (L2)
+    // every halo of the item arrived before the carry barriers above, so the
+    // chunks can be written back now
+    if constexpr (kDefect<E>) {  // x = c_hi d + (c_lo d + y), one final rounding
       const E chi = __ldg(T_cfix + s), clo = __ldg(T_cfix + S + s);
+#pragma unroll 4
       for (int i = 0; i < len; i++) {
-        const E d = col[(long long)i * pstride];
-        vs[i * 32] = fma(chi, d, fma(clo, d, vs[i * 32]));
+        const E d = vd[i * 32];
+        col[(long long)i * pstride] = fma(chi, d, fma(clo, d, vs[i * 32]));
       }
+    } else {
+#pragma unroll 4
+      for (int i = 0; i < len; i++) col[(long long)i * pstride] = vs[i * 32];
     }
-    __syncthreads();  // every halo read of the item precedes every write
-    for (int i = 0; i < len; i++) col[(long long)i * pstride] = vs[i * 32];
     __syncthreads();
     if (threadIdx.x == 0) {
       __threadfence();
@@ -223,7 +294,8 @@ __global__ void __launch_bounds__(kBatchWarps * 32) batch_kernel(const BatchArgs
 }
 
 inline size_t batch_smem_bytes(int maxm, size_t esz) {
-  return ((size_t)kBatchWarps * maxm * 32 + 2 * (size_t)kBatchWarps * 32) * esz;
+  const size_t nb = esz == 4 ? 2 : 1;  // FP32 keeps d beside the working array
+  return (nb * kBatchWarps * maxm * 32 + 4 * (size_t)kBatchWarps * 32) * esz;
 }
 
 template <typename E>

@@ -20,6 +20,14 @@ struct BatchEnv {
   const int64_t *src_row_off, *src_elem;
   const void *src_alpha, *src_scale;
   int has_src;
+  // whole-line axes (tile shape m >= n): streaming solve, one warp per tile
+  // (stream.cuh), coefficients position-major [n][S] (FP64: inv, mul, q;
+  // FP32: inv', mul of the defect form), interior constants [2][S] from
+  // position k0 on, FP32 c_hi/c_lo and a field-sized scratch
+  int whole[3];
+  const void *stab[3], *sint[3], *cfix[3];
+  int k0[3];
+  void *scratch;
 };
 
 struct BatchArgs {

@@ -93,16 +93,15 @@ struct StreamArgs {
   int mode;               // 0 = x (lanes: rows x substrates), 1 = y, 2 = z (lanes: columns)
   int nx, ny, nz;
   long long stride;       // elements between consecutive positions of a line
-  long long C;            // x: row length nx*S; y/z: columns per plane
-  long long plane_stride; // y: elements per z-plane; z: 0
-  long long colgroups;    // y/z: 32-column groups per plane
   long long ngroups;      // 32-line groups in all
   int rows_per_warp;      // x: 32/S
-  const void *tab;        // inv, mul, q position-major [3][n][S]
-  int out;                // 0: x; 1: y = x / sigma; 2: omega y (stream.cuh)
-  int k0;                 // inv_i = sigma, mul_i = r sigma, q_i = 1 for k0 <= i < n-1
-  const void *omega;      // [S] sigma_x sigma_y sigma_z (out 2)
-  const void *interior;   // [2][S] inv and mul on [k0, n-1): sigma, r sigma
+  const void *tab;        // position-major [n][S] blocks: inv, mul (FP64: and q)
+  int out;                // FP64: 0: x; 1: y = x / sigma; 2: omega y (stream.cuh)
+  int k0;                 // interior (one value per substrate) from k0 to n-2
+  const void *interior;   // [2][S] the interior inv and mul (FP64: sigma, r sigma)
+  const void *omega;      // FP64 [S] sigma_x sigma_y sigma_z (out 2)
+  const void *cfix;       // FP32 [2][S] c_hi, c_lo (defect form)
+  void *scratch;          // FP32: field-sized scratch for the forward intermediate
   int flags;
   const int64_t *src_row_off, *src_elem;
   const void *src_alpha, *src_scale;
@@ -167,12 +166,9 @@ cudaError_t launch_col_f32(const ColLaunch &a, cudaStream_t st);
 cudaError_t allow_pipe_smem_f32(int maxm, size_t bytes);
 cudaError_t launch_pipe_f32(const CUtensorMap &map, const PipeArgs &a, int maxm, int grid,
                             size_t smem, cudaStream_t st);
-// Streaming sweep, prefetch variant pf (1: registers; 4, 8, 16: cp.async ring
-// of that many groups); FP64
-// only (the FP32 kernels solve in defect-correction form, which needs d again
-// after the solve).
-cudaError_t allow_stream_smem_f64(int pf);
-cudaError_t launch_stream_f64(const StreamArgs &a, int pf, int grid, cudaStream_t st);
+// Streaming sweeps (stream.cuh).
+cudaError_t launch_stream_f64(const StreamArgs &a, int grid, cudaStream_t st);
+cudaError_t launch_stream_f32(const StreamArgs &a, int grid, cudaStream_t st);
 // Sets the thread-local message biofvm_last_error() returns.
 void set_error_message(const char *msg);
 

@@ -1,297 +1,360 @@
-// Streaming line sweep: one lane owns one whole grid line.
+// Streaming line sweeps: one lane owns one whole grid line.
 //
-// The FP64 pipe of a GB300 SM retires two FMAs per clock, so the FP64 step is
-// bound by its FP64 operations, not by HBM.  Cutting a line into chunks (the
-// partitioned solve of the other kernels) costs carry corrections on top of
-// the three operations per element that the Thomas algorithm (App. A) needs;
-// this kernel does not cut lines at all.  Written in the scaled form
+// A warp owns 32 lines and runs the Thomas recurrences (App. A) along them
+// without cutting them into chunks, so no carry corrections and no barriers
+// are needed.  The forward pass writes its intermediate back to memory; the
+// backward pass follows at once and reads it in reverse order, so it is
+// mostly still in L2.  Loads run one register block of R positions ahead.
 //
+// FP64 (solve_lines_f64).  The FP64 pipe of a GB300 SM retires two FMAs per
+// clock, so the FP64 step is bound by its FP64 operations, not by HBM.
+// Scaled form:
 //   forward   h_0 = d_0,  h_i = d_i + mul_{i-1} h_{i-1}    (h_i = d'_i / inv_i)
 //   backward  x_{n-1} = inv_{n-1} h_{n-1},  x_i = inv_i h_i + mul_i x_{i+1}
-//
-// (mul_i = r inv_i = -c'_i), each recurrence carries one FMA per element
-// along its dependency chain; the product inv_i h_i is off the chain.
-//
-// Scaled output (OUT 1, 2; the three sweeps of a whole step).  Away from the
-// first few positions inv_i equals its interior limit sigma to the last bit,
-// so the solve is run for y = x / sigma:
+// (mul_i = r inv_i = -c'_i): one FMA per element along each dependency
+// chain, the product inv_i h_i off the chain; h is written back in place.
+// Scaled output (OUT 1, 2; the three sweeps of a whole step): from position
+// k0 on, inv_i equals its interior limit sigma to the last bit, so the
+// solve is run for y = x / sigma:
 //   y_{n-1} = q_{n-1} h_{n-1},  y_i = q_i h_i + mul_i y_{i+1},  q_i = inv_i / sigma,
-// with q_i = 1 (no multiply) from position k0 on.  The next sweep is linear,
-// so the factor passes through it untouched; the x- and y-sweeps store y
-// (OUT 1) and the z-sweep stores omega y with omega = sigma_x sigma_y sigma_z
-// (OUT 2), the true field.  A step then costs about 7 FP64 operations per
-// element instead of 9.  Dirichlet values are passed in the same units.
+// with q_i = 1 (no multiply) past k0.  The next sweep is linear, so the
+// factor passes through it; the x- and y-sweeps store y (OUT 1), the z-sweep
+// stores omega y with omega = sigma_x sigma_y sigma_z (OUT 2), the true
+// field.  A step then costs about 7 FP64 operations per element instead of
+// 9.  Dirichlet values come in the same units.
 //
-// Interior constants.  On [k0, n-1) the tables hold exactly inv = sigma and
-// mul = r sigma (q = 1), so a group of positions inside that range runs on
-// two per-substrate registers and loads no table entry.
+// FP32 (solve_lines_f32), defect-correction form: x = c d + y with
+// y = (-c r) A^-1 (L_N d); e = L_N d is formed on the fly (one position
+// behind the loads, mirrored ends), the forward intermediate g goes to a
+// scratch field (d stays in place for the final c d), and the backward
+// pass reads g and d and writes x = c_hi d + (c_lo d + y).
 //
-// Memory.  The forward pass writes h back in place; the backward pass follows
-// at once and reads it in reverse order, so h mostly stays in L2 between the
-// two passes.  Two ways of keeping loads in flight (PF):
-//   PF = G > 1  each lane prefetches its own line through a private ring of G
-//         groups of 8 positions in shared memory (cp.async, 8 bytes per lane
-//         and position): few registers, 8 (G-1) positions in flight per lane;
-//   PF = 1  two register blocks of 16 positions (the next block loads while
-//         the current one is solved): 16 to 32 positions in flight, many
-//         registers.
+// Interior constants.  On [k0, n-1) the coefficient tables hold one value
+// per substrate (FP64: the tables are set to exactly sigma and r sigma; FP32:
+// the float-rounded entries already equal the float-rounded limits), so a
+// group of positions inside that range runs on two per-substrate registers
+// and loads no table entry.
 //
 // Lanes:  x-sweep  lane = (row, substrate), rows of nx*S elements, 32/S rows
 //                  per warp; the warp owns whole rows, so it also applies the
 //                  source update of those rows before its solve;
 //         y/z      lane = one of 32 consecutive columns of a plane (a row of a
-//                  warp is one 32-element coalesced access).
-// Tables: inv, mul, q position-major [3][n][S], read through L1 (the S values
-// a warp reads at one position share a cache line).
+//                  warp is one coalesced access).
+// Tables: inv, mul (and q) position-major [n][S], read through L1.
 #pragma once
 #include "sweeps.cuh"
 
 namespace bfv {
 
 constexpr int kStreamThreads = 128;
-// PF 0 (cp.async ring of PF groups of 8 positions) or 1 (register blocks)
-template <int PF>
-struct StreamCfg {
-  static constexpr int R = PF == 1 ? 16 : 8;   // positions per group
-  static constexpr int G = PF == 1 ? 1 : PF;   // ring groups
-  static constexpr int ctas = PF == 1 ? 3 : 8; // CTAs per SM the registers must allow
+constexpr int kStreamR = 16;  // positions per register block
+
+// One lane's line within the warp's group of 32 lines.
+struct LaneLine {
+  long long base;  // element offset of position 0
+  int s;           // substrate
+  bool active;     // the lane has a line
+  bool face;       // the line lies on a face of the two other axes
 };
 
-__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(smem)), "l"(gmem)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-  asm volatile("cp.async.commit_group;" ::: "memory");
-}
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-
-template <typename E, int PF, int OUT>
-__global__ void __launch_bounds__(kStreamThreads, StreamCfg<PF>::ctas)
-    stream_sweep_kernel(const StreamArgs a) {
-  constexpr int R = StreamCfg<PF>::R, G = StreamCfg<PF>::G;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int S = a.S, n = a.n, flags = a.flags, k0 = a.k0;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  // PF 0: this lane's ring, [G][R] slots 32 elements apart (conflict-free)
-  E *ring = reinterpret_cast<E *>(smem_raw) + (size_t)warp * G * R * 32 + lane;
-  const E *tinv = static_cast<const E *>(a.tab);
-  const E *tmul = tinv + (size_t)n * S, *tq = tmul + (size_t)n * S;
-  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  const long long nrows = (long long)a.ny * a.nz;
-  E *const rho = static_cast<E *>(a.rho);
-  const long long st = a.stride;
-  const int ngrp = (n + R - 1) / R;
-
-  for (long long grp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; grp < a.ngroups;
-       grp += nwarps) {
-    bool active, face;
-    int s;
-    long long base;
-    if (a.mode == 0) {
-      const int RW = a.rows_per_warp;
-      const int lr = lane / S;
-      s = lane - lr * S;
-      const long long row = grp * RW + lr;
-      active = lr < RW && row < nrows;
-      const int y = (int)(row % a.ny), z = (int)(row / a.ny);
-      face = y == 0 || y == a.ny - 1 || z == 0 || z == a.nz - 1;
-      base = row * a.C + s;
-      if ((flags & kSrc) && a.has_src) {  // Src on this warp's rows, then visible to the warp
-        const long long r0 = grp * RW, r1 = min(r0 + RW, nrows);
-        const long long e0 = a.src_row_off[r0], e1 = a.src_row_off[r1];
-        for (long long e = e0 + lane; e < e1; e += 32) {
-          const long long k = a.src_elem[e];
-          rho[k] = (rho[k] + ldg<E>(a.src_alpha, e)) * ldg<E>(a.src_scale, e);
-        }
-        __syncwarp();
-      }
+// mode 0: x (grp = group of rows_per_warp rows); 1: y (grp = plane z x column
+// group); 2: z (grp = column group of the whole xy plane).
+__device__ __forceinline__ LaneLine lane_line(int mode, long long grp, int lane, int S, int nx,
+                                              int ny, int nz, long long rowlen, int rows_per_warp) {
+  LaneLine L;
+  if (mode == 0) {
+    const int lr = lane / S;
+    L.s = lane - lr * S;
+    const long long row = grp * rows_per_warp + lr;
+    L.active = lr < rows_per_warp && row < (long long)ny * nz;
+    const int y = (int)(row % ny), z = (int)(row / ny);
+    L.face = y == 0 || y == ny - 1 || z == 0 || z == nz - 1;
+    L.base = row * rowlen + L.s;
+  } else {
+    const long long C = mode == 1 ? rowlen : rowlen * ny;
+    const long long colgroups = (C + 31) / 32;
+    const long long p = grp / colgroups;
+    const long long c = (grp - p * colgroups) * 32 + lane;
+    L.active = c < C;
+    L.s = (int)(c % S);
+    const long long xy = c / S;
+    if (mode == 1) {
+      L.face = xy == 0 || xy == nx - 1 || p == 0 || p == nz - 1;
+      L.base = p * rowlen * ny + c;
     } else {
-      const long long p = grp / a.colgroups;
-      const long long c = (grp - p * a.colgroups) * 32 + lane;
-      active = c < a.C;
-      s = (int)(c % S);
-      const long long xy = c / S;
-      if (a.mode == 1) {  // column -> x, plane -> z
-        face = xy == 0 || xy == a.nx - 1 || p == 0 || p == a.nz - 1;
-      } else {            // column -> (x, y)
-        const int x = (int)(xy % a.nx), y = (int)(xy / a.nx);
-        face = x == 0 || x == a.nx - 1 || y == 0 || y == a.ny - 1;
-      }
-      base = p * a.plane_stride + c;
+      const int x = (int)(xy % nx), y = (int)(xy / nx);
+      L.face = x == 0 || x == nx - 1 || y == 0 || y == ny - 1;
+      L.base = c;
     }
-    if (!(flags & kSolve)) continue;
-    const bool dirl = active && (flags & (kDirBefore | kDirAfter)) && a.dir_on[s];
-    const bool dB = dirl && (flags & kDirBefore), dA = dirl && (flags & kDirAfter);
-    const bool dBf = dB && face, dAf = dA && face;
-    const E dval = dirl ? dir_value<E>(flags, a.dir_val, s) : E(0);
-    const E dval_in = dirl ? dir_value<E>(flags, a.dir_val_in, s) : E(0);
-    E *line = rho + (active ? base : 0);
-    const E om = (OUT == 2 && active) ? ldg<E>(a.omega, s) : E(1);
-    const E sig = active ? ldg<E>(a.interior, s) : E(0);
-    const E minf = active ? ldg<E>(a.interior, S + s) : E(0);
+  }
+  return L;
+}
 
-    // ---------------------------------------------------------------- forward
-    E h = E(0), mp = E(0);
-    auto fwd_group = [&](int g, auto get) {
-      if (!active) return;
-      const int i0 = g * R;
-      E *q = line + (long long)i0 * st;
-      if (i0 - 1 >= k0 && i0 + R < n) {  // interior: mul_{i-1} = r sigma (warp-uniform)
-#pragma unroll
-        for (int k = 0; k < R; k++) {
-          const E d = dBf ? dval_in : get(k);
-          h = fma(minf, h, d);
-          *q = h;
-          q += st;
-        }
-        mp = minf;
-      } else {
-#pragma unroll
-        for (int k = 0; k < R; k++) {
-          const int i = i0 + k;
-          if (i < n) {
-            E d = get(k);
-            if (dB && (face || i == 0 || i == n - 1)) d = dval_in;
-            h = fma(mp, h, d);
-            *q = (OUT != 0 && i == n - 1) ? __ldg(tq + (size_t)i * S + s) * h : h;
-            mp = __ldg(tmul + (size_t)i * S + s);
-          }
-          q += st;
-        }
-      }
-    };
-    // ---------------------------------------------------------------- backward
-    // group g holds positions n-1-g*R down to n-R-g*R
-    E x = E(0);
-    auto bwd_group = [&](int g, auto get) {
-      if (!active) return;
-      const int i1 = n - 1 - g * R;
-      E *q = line + (long long)i1 * st;
-      // interior: inv = sigma, mul = r sigma, q = 1; with scaled output the
-      // first position n-1 also qualifies (y_{n-1} was stored pre-scaled and
-      // mul_{n-1} multiplies zero); position 0 never does (its Dirichlet end)
-      if (i1 - R + 1 >= max(k0, 1) && (OUT != 0 || i1 < n - 1)) {
-#pragma unroll
-        for (int k = 0; k < R; k++) {
-          const E hv = get(k);
-          x = fma(minf, x, OUT == 0 ? sig * hv : hv);
-          *q = dAf ? dval : (OUT == 2 ? om * x : x);
-          q -= st;
-        }
-        if (dA && i1 == n - 1) line[(long long)(n - 1) * st] = dval;
-      } else {
-#pragma unroll
-        for (int k = 0; k < R; k++) {
-          const int i = i1 - k;
-          if (i >= 0) {
-            const E hv = get(k);
-            const E t = OUT == 0 ? __ldg(tinv + (size_t)i * S + s) * hv
-                                 : (i == n - 1 ? hv : __ldg(tq + (size_t)i * S + s) * hv);
-            x = fma(__ldg(tmul + (size_t)i * S + s), x, t);
-            *q = (dA && (face || i == 0 || i == n - 1)) ? dval : (OUT == 2 ? om * x : x);
-          }
-          q -= st;
-        }
-      }
-    };
+// Coefficients of one lane's line.
+template <typename E>
+struct LineCoef {
+  const E *inv, *mul, *q;  // this substrate's entries: position i at [i * S]
+  int S, k0;
+  E c0, c1;                // interior constants (FP64: sigma, r sigma; FP32: inv', mul)
+  E om;                    // FP64 OUT 2: omega; FP32: c_hi
+  E clo;                   // FP32: c_lo
+};
 
-    if constexpr (PF != 1) {
-      auto issue = [&](int g, bool fwd) {
-        E *slot = ring + (g % G) * R * 32;
-        const int i0 = fwd ? g * R : n - 1 - g * R;
-        const E *q = line + (long long)i0 * st;
-        const long long step = fwd ? st : -st;
+struct LineDir {
+  bool before, after;  // Dirichlet applications on this line
+  bool face;
+};
+
+// Load R positions starting at i0 and walking by +st (fwd) or -st.
+template <typename E, int R>
+__device__ __forceinline__ void load_block(E (&buf)[R], const E *line, long long st, int i0,
+                                           bool fwd, int n, bool active) {
+  const E *q = line + (long long)i0 * st;
+  const long long step = fwd ? st : -st;
 #pragma unroll
-        for (int k = 0; k < R; k++) {
-          const int i = fwd ? i0 + k : i0 - k;
-          if (active && i >= 0 && i < n) cp_async8(slot + k * 32, q);
-          q += step;
-        }
-        cp_async_commit();  // possibly empty: keeps the group count uniform
-      };
-      for (int pass = 0; pass < 2; pass++) {
-        const bool fwd = pass == 0;
+  for (int k = 0; k < R; k++) {
+    const int i = fwd ? i0 + k : i0 - k;
+    buf[k] = (active && i >= 0 && i < n) ? *q : E(0);
+    q += step;
+  }
+}
+
+// FP64 solve of a warp's lines (see the header).  OUT 0: x itself; 1: x/sigma;
+// 2: omega x/sigma.
+template <int OUT, int R = kStreamR>
+__device__ __forceinline__ void solve_lines_f64(double *line, int n, long long st, bool active,
+                                                const LineCoef<double> &cf, const LineDir &dr,
+                                                double dval_in, double dval) {
+  const int S = cf.S, k0 = cf.k0, ngrp = (n + R - 1) / R;
+  const bool dBf = dr.before && dr.face, dAf = dr.after && dr.face;
+  double h = 0.0, mp = 0.0;
+  auto fwd_group = [&](int g, const double(&buf)[R]) {
+    if (!active) return;
+    const int i0 = g * R;
+    double *q = line + (long long)i0 * st;
+    if (i0 - 1 >= k0 && i0 + R < n) {  // interior: mul_{i-1} = r sigma (warp-uniform)
 #pragma unroll
-        for (int g = 0; g < G - 1; g++) issue(g, fwd);
-        for (int g = 0; g < ngrp; g++) {
-          issue(g + G - 1, fwd);
-          cp_async_wait<G - 1>();
-          const E *slot = ring + (g % G) * R * 32;
-          auto get = [&](int k) { return slot[k * 32]; };
-          if (fwd)
-            fwd_group(g, get);
-          else
-            bwd_group(g, get);
-        }
-        cp_async_wait<0>();
+      for (int k = 0; k < R; k++) {
+        h = fma(cf.c1, h, dBf ? dval_in : buf[k]);
+        *q = h;
+        q += st;
       }
+      mp = cf.c1;
     } else {
-      E A[R], B[R];
-      auto load = [&](E(&buf)[R], int g, bool fwd) {
-        const int i0 = fwd ? g * R : n - 1 - g * R;
-        const E *q = line + (long long)i0 * st;
-        const long long step = fwd ? st : -st;
 #pragma unroll
-        for (int k = 0; k < R; k++) {
-          const int i = fwd ? i0 + k : i0 - k;
-          buf[k] = (active && i >= 0 && i < n) ? *q : E(0);
-          q += step;
+      for (int k = 0; k < R; k++) {
+        const int i = i0 + k;
+        if (i < n) {
+          double d = buf[k];
+          if (dr.before && (dr.face || i == 0 || i == n - 1)) d = dval_in;
+          h = fma(mp, h, d);
+          *q = (OUT != 0 && i == n - 1) ? __ldg(cf.q + (size_t)i * S) * h : h;
+          mp = __ldg(cf.mul + (size_t)i * S);
         }
-      };
-      for (int pass = 0; pass < 2; pass++) {
-        const bool fwd = pass == 0;
-        load(A, 0, fwd);
-        for (int g = 0; g < ngrp; g += 2) {
-          load(B, g + 1, fwd);
-          if (fwd)
-            fwd_group(g, [&](int k) { return A[k]; });
-          else
-            bwd_group(g, [&](int k) { return A[k]; });
-          load(A, g + 2, fwd);
-          if (g + 1 < ngrp) {
-            if (fwd)
-              fwd_group(g + 1, [&](int k) { return B[k]; });
-            else
-              bwd_group(g + 1, [&](int k) { return B[k]; });
-          }
+        q += st;
+      }
+    }
+  };
+  double x = 0.0;
+  auto bwd_group = [&](int g, const double(&buf)[R]) {
+    if (!active) return;
+    const int i1 = n - 1 - g * R;
+    double *q = line + (long long)i1 * st;
+    // interior: inv = sigma, mul = r sigma, q = 1; with scaled output the first
+    // position n-1 also qualifies (y_{n-1} was stored pre-scaled and mul_{n-1}
+    // multiplies zero); position 0 never does (its Dirichlet end)
+    if (i1 - R + 1 >= max(k0, 1) && (OUT != 0 || i1 < n - 1)) {
+#pragma unroll
+      for (int k = 0; k < R; k++) {
+        x = fma(cf.c1, x, OUT == 0 ? cf.c0 * buf[k] : buf[k]);
+        *q = dAf ? dval : (OUT == 2 ? cf.om * x : x);
+        q -= st;
+      }
+      if (dr.after && i1 == n - 1) line[(long long)(n - 1) * st] = dval;
+    } else {
+#pragma unroll
+      for (int k = 0; k < R; k++) {
+        const int i = i1 - k;
+        if (i >= 0) {
+          const double hv = buf[k];
+          const double t = OUT == 0 ? __ldg(cf.inv + (size_t)i * S) * hv
+                                    : (i == n - 1 ? hv : __ldg(cf.q + (size_t)i * S) * hv);
+          x = fma(__ldg(cf.mul + (size_t)i * S), x, t);
+          *q = (dr.after && (dr.face || i == 0 || i == n - 1)) ? dval
+                                                                : (OUT == 2 ? cf.om * x : x);
         }
+        q -= st;
+      }
+    }
+  };
+  double A[R], B[R];
+  for (int pass = 0; pass < 2; pass++) {
+    const bool fwd = pass == 0;
+    auto first = [&](int g) { return fwd ? g * R : n - 1 - g * R; };
+    load_block<double, R>(A, line, st, first(0), fwd, n, active);
+    for (int g = 0; g < ngrp; g += 2) {
+      load_block<double, R>(B, line, st, first(g + 1), fwd, n, active);
+      if (fwd) fwd_group(g, A); else bwd_group(g, A);
+      load_block<double, R>(A, line, st, first(g + 2), fwd, n, active);
+      if (g + 1 < ngrp) {
+        if (fwd) fwd_group(g + 1, B); else bwd_group(g + 1, B);
       }
     }
   }
 }
 
-// Dynamic shared memory of one CTA: the warps' rings (PF != 1).
-template <typename E, int PF>
-constexpr size_t stream_smem_bytes() {
-  return PF != 1 ? (size_t)(kStreamThreads / 32) * StreamCfg<PF>::G * StreamCfg<PF>::R * 32 *
-                       sizeof(E)
-                 : 0;
+// FP32 defect-correction solve of a warp's lines (see the header); sline is
+// the scratch field at the same offset as line.
+template <int R = kStreamR>
+__device__ __forceinline__ void solve_lines_f32(float *line, float *sline, int n, long long st,
+                                                bool active, const LineCoef<float> &cf,
+                                                const LineDir &dr, float dval_in, float dval) {
+  const int S = cf.S, k0 = cf.k0, ngrp = (n + R - 1) / R;
+  auto dmod = [&](float v, int i) {
+    return (dr.before && (dr.face || i == 0 || i == n - 1)) ? dval_in : v;
+  };
+  // ---- forward: d_i arrives, position p = i - 1 is eliminated
+  float g = 0.f, dm1 = 0.f, dm2 = 0.f;
+  auto emit = [&](int p, float e, bool interior, float *sq) {
+    const float iv = interior ? cf.c0 : __ldg(cf.inv + (size_t)p * S);
+    const float mu = interior ? cf.c1 : __ldg(cf.mul + (size_t)p * S);
+    g = fmaf(mu, g, e * iv);
+    *sq = g;
+  };
+  auto fwd_group = [&](int gi, const float(&buf)[R]) {
+    if (!active) return;
+    const int i0 = gi * R;
+    const bool interior = i0 - 1 >= k0 && i0 + R - 2 < n - 1;
+    float *sq = sline + (long long)(i0 - 1) * st;  // position i - 1
+#pragma unroll
+    for (int k = 0; k < R; k++) {
+      const int i = i0 + k;
+      if (i < n) {
+        const float d = dmod(buf[k], i);
+        if (i == 0) {
+          dm1 = d;
+          dm2 = d;  // mirrored start: d_{-1} = d_0
+        } else {
+          emit(i - 1, (dm1 - dm2) + (dm1 - d), interior, sq);
+          dm2 = dm1;
+          dm1 = d;
+        }
+      }
+      sq += st;
+    }
+  };
+  // ---- backward: y_i = g_i + mul_i y_{i+1}, x_i = c_hi d_i + (c_lo d_i + y_i)
+  float y = 0.f;
+  auto bwd_group = [&](int gi, const float(&gb)[R], const float(&db)[R]) {
+    if (!active) return;
+    const int i1 = n - 1 - gi * R;
+    const bool interior = i1 < n - 1 && i1 - R + 1 >= k0;
+    float *q = line + (long long)i1 * st;
+#pragma unroll
+    for (int k = 0; k < R; k++) {
+      const int i = i1 - k;
+      if (i >= 0) {
+        const float mu = interior ? cf.c1 : __ldg(cf.mul + (size_t)i * S);
+        y = fmaf(mu, y, gb[k]);
+        const float d = dmod(db[k], i);
+        const float xv = fmaf(cf.om, d, fmaf(cf.clo, d, y));
+        *q = (dr.after && (dr.face || i == 0 || i == n - 1)) ? dval : xv;
+      }
+      q -= st;
+    }
+  };
+  {
+    float A[R], B[R];
+    load_block<float, R>(A, line, st, 0, true, n, active);
+    for (int gi = 0; gi < ngrp; gi += 2) {
+      load_block<float, R>(B, line, st, (gi + 1) * R, true, n, active);
+      fwd_group(gi, A);
+      load_block<float, R>(A, line, st, (gi + 2) * R, true, n, active);
+      if (gi + 1 < ngrp) fwd_group(gi + 1, B);
+    }
+    if (active && n > 0) emit(n - 1, dm1 - dm2, false, sline + (long long)(n - 1) * st);
+  }
+  {
+    float GA[R], DA[R], GB[R], DB[R];
+    load_block<float, R>(GA, sline, st, n - 1, false, n, active);
+    load_block<float, R>(DA, line, st, n - 1, false, n, active);
+    for (int gi = 0; gi < ngrp; gi += 2) {
+      load_block<float, R>(GB, sline, st, n - 1 - (gi + 1) * R, false, n, active);
+      load_block<float, R>(DB, line, st, n - 1 - (gi + 1) * R, false, n, active);
+      bwd_group(gi, GA, DA);
+      load_block<float, R>(GA, sline, st, n - 1 - (gi + 2) * R, false, n, active);
+      load_block<float, R>(DA, line, st, n - 1 - (gi + 2) * R, false, n, active);
+      if (gi + 1 < ngrp) bwd_group(gi + 1, GB, DB);
+    }
+  }
 }
 
-template <typename E, int PF>
-cudaError_t allow_stream_smem() {
-  cudaError_t e = cudaSuccess;
-  for (auto f : {stream_sweep_kernel<E, PF, 0>, stream_sweep_kernel<E, PF, 1>,
-                 stream_sweep_kernel<E, PF, 2>})
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)stream_smem_bytes<E, PF>());
-  return e;
+// Source update of a warp's rows (x-sweep), then visible to the whole warp.
+template <typename E>
+__device__ __forceinline__ void warp_rows_src(E *rho, long long r0, long long r1,
+                                              const int64_t *row_off, const int64_t *elem,
+                                              const void *alpha, const void *scale, int lane) {
+  const long long e0 = row_off[r0], e1 = row_off[r1];
+  for (long long e = e0 + lane; e < e1; e += 32) {
+    const long long k = elem[e];
+    rho[k] = (rho[k] + ldg<E>(alpha, e)) * ldg<E>(scale, e);
+  }
+  __syncwarp();
 }
 
-template <typename E, int PF>
+// Single-grid streaming sweep, persistent grid of 128-thread CTAs; E = double
+// (OUT as above) or float (defect form, OUT 0, scratch field a.scratch).
+template <typename E, int OUT>
+__global__ void __launch_bounds__(kStreamThreads, sizeof(E) == 8 ? 3 : 4)
+    stream_sweep_kernel(const StreamArgs a) {
+  const int S = a.S, n = a.n, flags = a.flags;
+  const int lane = threadIdx.x & 31;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  const long long nrows = (long long)a.ny * a.nz;
+  E *const rho = static_cast<E *>(a.rho);
+  const long long rowlen = (long long)a.nx * S;
+  const E *tinv = static_cast<const E *>(a.tab);
+  for (long long grp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; grp < a.ngroups;
+       grp += nwarps) {
+    const LaneLine L = lane_line(a.mode, grp, lane, S, a.nx, a.ny, a.nz, rowlen, a.rows_per_warp);
+    if (a.mode == 0 && (flags & kSrc) && a.has_src) {
+      const long long r0 = grp * a.rows_per_warp;
+      warp_rows_src<E>(rho, r0, min(r0 + a.rows_per_warp, nrows), a.src_row_off, a.src_elem,
+                       a.src_alpha, a.src_scale, lane);
+    }
+    if (!(flags & kSolve)) continue;
+    const bool dirl = L.active && (flags & (kDirBefore | kDirAfter)) && a.dir_on[L.s];
+    LineDir dr;
+    dr.before = dirl && (flags & kDirBefore);
+    dr.after = dirl && (flags & kDirAfter);
+    dr.face = L.face;
+    const E dval = dirl ? dir_value<E>(flags, a.dir_val, L.s) : E(0);
+    const E dval_in = dirl ? dir_value<E>(flags, a.dir_val_in, L.s) : E(0);
+    LineCoef<E> cf;
+    cf.S = S;
+    cf.k0 = a.k0;
+    cf.inv = tinv + L.s;
+    cf.mul = tinv + (size_t)n * S + L.s;
+    cf.q = tinv + 2 * (size_t)n * S + L.s;
+    cf.c0 = L.active ? ldg<E>(a.interior, L.s) : E(0);
+    cf.c1 = L.active ? ldg<E>(a.interior, S + L.s) : E(0);
+    cf.clo = E(0);
+    E *line = rho + (L.active ? L.base : 0);
+    if constexpr (sizeof(E) == 8) {
+      cf.om = (OUT == 2 && L.active) ? ldg<E>(a.omega, L.s) : E(1);
+      solve_lines_f64<OUT>(line, n, a.stride, L.active, cf, dr, dval_in, dval);
+    } else {
+      cf.om = L.active ? ldg<E>(a.cfix, L.s) : E(0);
+      cf.clo = L.active ? ldg<E>(a.cfix, S + L.s) : E(0);
+      E *sline = static_cast<E *>(a.scratch) + (L.active ? L.base : 0);
+      solve_lines_f32(line, sline, n, a.stride, L.active, cf, dr, dval_in, dval);
+    }
+  }
+}
+
+template <typename E, int OUT>
 cudaError_t launch_stream_one(const StreamArgs &a, int grid, cudaStream_t st) {
-  const size_t smem = stream_smem_bytes<E, PF>();
-  if (a.out == 1)
-    stream_sweep_kernel<E, PF, 1><<<grid, kStreamThreads, smem, st>>>(a);
-  else if (a.out == 2)
-    stream_sweep_kernel<E, PF, 2><<<grid, kStreamThreads, smem, st>>>(a);
-  else
-    stream_sweep_kernel<E, PF, 0><<<grid, kStreamThreads, smem, st>>>(a);
+  stream_sweep_kernel<E, OUT><<<grid, kStreamThreads, 0, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -3,6 +3,7 @@
 #include "adjoint.cuh"
 #include "batch.cuh"
 #include "pipe.cuh"
+#include "stream.cuh"
 #include "sweeps.cuh"
 
 namespace bfv {
@@ -114,5 +115,9 @@ cudaError_t launch_batch_f32(const BatchArgs &a, int, int grid, cudaStream_t st)
 }
 
 cudaError_t batch_occupancy_f32(int maxm, int *out) { return batch_blocks_per_sm<float>(maxm, out); }
+
+cudaError_t launch_stream_f32(const StreamArgs &a, int grid, cudaStream_t st) {
+  return launch_stream_one<float, 0>(a, grid, st);
+}
 
 }  // namespace bfv

@@ -72,24 +72,12 @@ cudaError_t launch_batch_f64(const BatchArgs &a, int, int grid, cudaStream_t st)
 
 cudaError_t batch_occupancy_f64(int maxm, int *out) { return batch_blocks_per_sm<double>(maxm, out); }
 
-cudaError_t allow_stream_smem_f64(int pf) {
-  switch (pf) {
-    case 1: return allow_stream_smem<double, 1>();
-    case 4: return allow_stream_smem<double, 4>();
-    case 8: return allow_stream_smem<double, 8>();
-    case 16: return allow_stream_smem<double, 16>();
-  }
-  return cudaErrorInvalidValue;
-}
-
-cudaError_t launch_stream_f64(const StreamArgs &a, int pf, int grid, cudaStream_t st) {
-  switch (pf) {
+cudaError_t launch_stream_f64(const StreamArgs &a, int grid, cudaStream_t st) {
+  switch (a.out) {
     case 1: return launch_stream_one<double, 1>(a, grid, st);
-    case 4: return launch_stream_one<double, 4>(a, grid, st);
-    case 8: return launch_stream_one<double, 8>(a, grid, st);
-    case 16: return launch_stream_one<double, 16>(a, grid, st);
+    case 2: return launch_stream_one<double, 2>(a, grid, st);
   }
-  return cudaErrorInvalidValue;
+  return launch_stream_one<double, 0>(a, grid, st);
 }
 
 }  // namespace bfv

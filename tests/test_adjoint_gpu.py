@@ -164,7 +164,9 @@ def test_gradients_match_central_fd_on_the_gpu(torch):
         check(g0.reshape(-1)[e], "rho0", e)
 
 
-def test_fp32_adjoint_tracks_fp64(torch):
+@pytest.mark.parametrize("stream32", ["0", "1"])
+def test_fp32_adjoint_tracks_fp64(torch, monkeypatch, stream32):
+    monkeypatch.setenv("BIOFVM_STREAM32", stream32)
     w, probes, targets = _problem(7, shape=(20, 16, 14))
     _, gc, dDc, dlc, dsc = cpu_loss_and_grads(w, 6, probes, targets)
     _, gg, dDg, dlg, dsg = gpu_loss_and_grads(torch, w, 6, probes, targets, prec="fp32")

@@ -51,6 +51,44 @@ def test_batch_matches_oracle_per_environment(binding, prec):
     b.close()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_batch_whole_lines_match_oracle(binding, prec):
+    """Whole-line tiles (m >= n on every axis: one warp streams 32 whole lines) against the
+    oracle, environment by environment, with sources."""
+    envs = _envs(11, SHAPES)
+    b = binding.BioFVMBatch(envs, precision=prec, tile_m=[[w.nx, w.ny, w.nz] for w in envs])
+    for sim, w in zip(b.envs, envs):
+        sim.set_density(w.rho0)
+        sim.set_sources(w.voxel, w.secretion, w.target, w.uptake, w.weight)
+    b.step(4)
+    b.sync()
+    for sim, w in zip(b.envs, envs):
+        ref = oracle.Problem(**w.oracle_kwargs()).step(w.rho0, 4)
+        assert rel(sim.density(), ref) <= TOL[prec], w.name
+    b.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_batch_mixed_whole_and_chunked_axes_and_retiling(binding, prec):
+    """Whole lines on some axes and chunks on others in one launch, then re-tiled the other
+    way round (biofvm_batch_set_tiles) with the field carried over."""
+    envs = _envs(12, [(64, 40, 36, 3), (150, 20, 90, 2), (33, 96, 17, 5)])
+    first = [[w.nx, 16, w.nz] for w in envs]
+    second = [[0, w.ny, 24] for w in envs]
+    b = binding.BioFVMBatch(envs, precision=prec, tile_m=first)
+    for sim, w in zip(b.envs, envs):
+        sim.set_density(w.rho0)
+        sim.set_sources(w.voxel, w.secretion, w.target, w.uptake, w.weight)
+    b.step(2)
+    b.set_tiles(second)
+    b.step(3)
+    b.sync()
+    for sim, w in zip(b.envs, envs):
+        ref = oracle.Problem(**w.oracle_kwargs()).step(w.rho0, 5)
+        assert rel(sim.density(), ref) <= TOL[prec], w.name
+    b.close()
+
+
 def test_batch_with_explicit_tile_shapes_and_repeated_calls(binding):
     envs = _envs(2, [(48, 40, 36, 2), (25, 31, 19, 4), (64, 64, 8, 1)])
     shapes = [[m, m, m] for m in (8, 12, 16)]
@@ -88,6 +126,8 @@ def test_batch_rejects_invalid_tile_shapes(binding):
     envs = _envs(4, [(100, 10, 10, 1)])
     with pytest.raises(binding.BioFVMError):
         binding.BioFVMBatch(envs, tile_m=[[8, 8, 8]])  # 100/8 -> 13 chunks > 8
+    with pytest.raises(binding.BioFVMError):
+        binding.BioFVMBatch(envs, tile_m=[[60, 8, 8]])  # chunks of more than 48 (not whole)
 
 
 def test_batched_workload_recipe_reduced(binding):

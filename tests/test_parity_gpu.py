@@ -270,7 +270,7 @@ def test_workload3_full_size_20_steps_fp32_properties(binding):
     assert err <= 1e-5
 
 
-PATHS = {"plain": ("0", "0"), "pipe": ("1", "0"), "stream": ("1", "1")}
+PATHS = {"plain": ("0", "0", "0"), "pipe": ("1", "0", "0"), "stream": ("1", "1", "1")}
 
 
 @pytest.mark.parametrize("path", list(PATHS))
@@ -279,15 +279,14 @@ PATHS = {"plain": ("0", "0"), "pipe": ("1", "0"), "stream": ("1", "1")}
                          ids=lambda s: "x".join(map(str, s)) if isinstance(s, tuple) else s)
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_sweep_paths_match_oracle(binding, monkeypatch, shape, path, prec):
-    """Every sweep implementation -- plain kernels, the persistent TMA pipeline and (FP64) the
-    streaming whole-line kernel, chosen at create through BIOFVM_PIPELINE / BIOFVM_STREAM --
-    against the oracle, with Dirichlet faces and sources."""
-    if prec == "fp32" and path == "stream":
-        pytest.skip("the streaming sweep is FP64 only")
+    """Every sweep implementation -- plain kernels, the persistent TMA pipeline (FP32) and the
+    streaming whole-line kernels, chosen at create through BIOFVM_PIPELINE / BIOFVM_STREAM /
+    BIOFVM_STREAM32 -- against the oracle, with Dirichlet faces and sources."""
     if prec == "fp64" and path == "pipe":
         pytest.skip("the pipelined sweep is FP32 only")
     monkeypatch.setenv("BIOFVM_PIPELINE", PATHS[path][0])
     monkeypatch.setenv("BIOFVM_STREAM", PATHS[path][1])
+    monkeypatch.setenv("BIOFVM_STREAM32", PATHS[path][2])
     nx, ny, nz, ns = shape
     rng = np.random.default_rng(17)
     w = inputs.random_problem(rng, nx, ny, nz, ns, n_agents=100, dirichlet=True)
