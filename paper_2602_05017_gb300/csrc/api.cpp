@@ -121,7 +121,7 @@ struct biofvm {
   unsigned generation = 0;  // bumped when kernel arguments change (sources, constants)
   // sources
   int64_t n_entries = 0;
-  DevBuf src_row_off, src_elem, src_alpha, src_scale;
+  DevBuf src_row_off, src_elem, src_rowcol, src_alpha, src_scale;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
   // adjoint: the adjoint field, reduction partials, agents on the device
@@ -671,6 +671,7 @@ cudaError_t launch_pipe(const biofvm *h, int axis, int flags, cudaStream_t st, v
   if (!h->any_dir) b.flags &= ~(kDirBefore | kDirAfter);
   b.src_row_off = static_cast<const int64_t *>(h->src_row_off.p);
   b.src_elem = static_cast<const int64_t *>(h->src_elem.p);
+  b.src_rowcol = static_cast<const int2 *>(h->src_rowcol.p);
   b.src_alpha = h->src_alpha.p;
   b.src_scale = h->src_scale.p;
   b.has_src = h->n_entries > 0;
@@ -834,7 +835,7 @@ void destroy_impl(biofvm *h) {
   for (DevBuf *b : {&h->rho, &h->tab[0], &h->tab[1], &h->tab[2], &h->tabT[0], &h->tabT[1],
                     &h->tabT[2], &h->tabS[0], &h->tabS[1], &h->tabS[2], &h->dir_scaled_d,
                     &h->omega_d, &h->stream_const_d, &h->scratch, &h->dir_on_d, &h->dir_val_d,
-                    &h->status, &h->src_row_off, &h->src_elem, &h->src_alpha, &h->src_scale,
+                    &h->status, &h->src_row_off, &h->src_elem, &h->src_rowcol, &h->src_alpha, &h->src_scale,
                     &h->adj, &h->partial, &h->ag_elem, &h->ag_entry, &h->ag_weight,
                     &h->ag_target})
     b->release();
@@ -1099,10 +1100,13 @@ biofvm_status biofvm_set_sources(biofvm_t *h, int64_t n, const int64_t *voxel,
   const int64_t rowlen = (int64_t)h->g.nx * S;
   const int64_t nrows = (int64_t)h->g.ny * h->g.nz;
   std::vector<int64_t> off(nrows + 1, 0), elem(u);
+  std::vector<int32_t> rowcol(2 * u);  // (row, position in the row) of each entry
   std::vector<double> alpha(u), scale(u);
   for (size_t i = 0; i < u; i++) {
     off[ent[i].e / rowlen + 1]++;
     elem[i] = ent[i].e;
+    rowcol[2 * i] = (int32_t)(ent[i].e / rowlen);
+    rowcol[2 * i + 1] = (int32_t)(ent[i].e % rowlen);
     alpha[i] = ent[i].alpha;
     scale[i] = 1.0 / (1.0 + ent[i].beta);
   }
@@ -1116,6 +1120,9 @@ biofvm_status biofvm_set_sources(biofvm_t *h, int64_t n, const int64_t *voxel,
     if (dev_alloc(h->src_elem, u * 8) != cudaSuccess)
       return fail(BIOFVM_ERR_OOM, "device allocation for %zu source entries failed", u);
     CK(cudaMemcpy(h->src_elem.p, elem.data(), u * 8, cudaMemcpyHostToDevice));
+    if (dev_alloc(h->src_rowcol, u * 8) != cudaSuccess)
+      return fail(BIOFVM_ERR_OOM, "device allocation for %zu source entries failed", u);
+    CK(cudaMemcpy(h->src_rowcol.p, rowcol.data(), u * 8, cudaMemcpyHostToDevice));
     biofvm_status st = upload_doubles(h, h->src_alpha, alpha);
     if (st) return st;
     st = upload_doubles(h, h->src_scale, scale);

@@ -286,6 +286,35 @@ __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
   const int ps_rt = MODE == 0 ? S : 32;
   const E *Tcw = static_cast<const E *>(a.tab.cw);  // [T][T][S], global (L1-resident)
   const bool dir_after = (a.flags & kDirAfter) != 0;
+  // x tiles: the source entries flow ahead of the tiles -- the offsets of
+  // tile k+2 and this thread's first entry of tile k+1 are loaded while tile
+  // k is solved, so no tile waits on global loads for its sources.
+  const bool srcs = MODE == 0 && (a.flags & kSrc) && a.has_src;
+  auto src_range = [&](long long kk, long long &e0, long long &e1) {
+    e0 = e1 = 0;
+    if (!srcs || kk >= count) return;
+    const long long r0 = (first + kk * gridDim.x) * a.rows_per_tile;
+    e0 = __ldg(a.src_row_off + r0);
+    e1 = __ldg(a.src_row_off + min(r0 + (long long)a.rows_per_tile, (long long)a.nrows));
+  };
+  long long n0 = 0, n1 = 0, f0 = 0, f1 = 0;  // ranges of the next tile and the one after
+  int2 prc = make_int2(0, 0);
+  E pal = E(0), psc = E(0);
+  bool pv = false;  // this thread's prefetched entry of the next tile
+  auto src_fetch = [&](long long e0, long long e1) {
+    const long long e = e0 + ctid;
+    pv = e < e1;
+    if (pv) {
+      prc = __ldg(a.src_rowcol + e);
+      pal = ldg<E>(a.src_alpha, e);
+      psc = ldg<E>(a.src_scale, e);
+    }
+  };
+  if (srcs) {
+    src_range(0, n0, n1);
+    src_fetch(n0, n1);
+    src_range(1, f0, f1);
+  }
   for (long long k = 0; k < count; k++) {
     const int st = (int)(k % NS);
     bool ok = mbar_wait_bounded(&full[st], (uint32_t)((k / NS) & 1), a.status);
@@ -305,14 +334,22 @@ __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
         face = y == 0 || y == a.ny - 1 || z == 0 || z == a.nz - 1;
       }
       // Src then B on the staged rows, before any solve
-      if ((a.flags & kSrc) && a.has_src) {
-        const long long e0 = a.src_row_off[r0], e1 = a.src_row_off[r0 + rows];
-        for (long long e = e0 + ctid; e < e1; e += ncons) {
-          const long long el = a.src_elem[e];
-          const long long rr = el / a.rowlen;
-          E *q = stg + (rr - r0) * a.pitch + (el - rr * a.rowlen);
+      if (srcs) {
+        if (pv) {  // the prefetched entry, then (rarely) the thread's further ones
+          E *q = stg + (prc.x - r0) * a.pitch + prc.y;
+          *q = (*q + pal) * psc;
+        }
+        for (long long e = n0 + ctid + ncons; e < n1; e += ncons) {
+          const int2 rc = __ldg(a.src_rowcol + e);
+          E *q = stg + (rc.x - r0) * a.pitch + rc.y;
           *q = (*q + ldg<E>(a.src_alpha, e)) * ldg<E>(a.src_scale, e);
         }
+        // next tile's first entries (offsets loaded one tile ago), and the
+        // offsets of the tile after it
+        n0 = f0;
+        n1 = f1;
+        src_fetch(n0, n1);
+        src_range(k + 2, f0, f1);
       }
       // B must see the source update of every element (a source can sit on a face)
       if ((a.flags & kSrc) && a.has_src && (a.flags & kDirBefore)) consumers_sync(ncons);

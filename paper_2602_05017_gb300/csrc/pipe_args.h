@@ -37,6 +37,7 @@ struct PipeArgs {
   int flags;
   // mode 0: sources (CSR over rows) and the Dirichlet application before the solve
   const int64_t *src_row_off, *src_elem;
+  const int2 *src_rowcol;  // (row, position in the row) of each entry
   const void *src_alpha, *src_scale;
   int has_src;
   const uint8_t *dir_on;
