@@ -39,6 +39,13 @@ GB300_SMS = 152
 # Floating-point operations of the Thomas algorithm per element and sweep (Sect. 2.1, Eq. 2:
 # forward axpy + division, backward negated axpy).
 FLOPS_PER_ELEMENT_SWEEP = 5
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the kernel each
+# roofline names, from one ncu capture of this bench's 400^3 x 4 workload; valid only for the
+# kernel version they were taken on (re-measure whenever that kernel changes).
+MEASURED_TRAFFIC = {
+    ("f64", "z-sweep"): 3003365120 + 3133865472,   # stream_sweep_kernel<double, 2>
+    ("f32", "x-sweep"): 1090899968 + 963519488,    # sweep_pipe_kernel<float, 32, 0>
+}
 
 
 def measured_peaks():
@@ -386,13 +393,17 @@ def main():
     return 0
 
 
-def roofline(r, w, peaks, src, traffic=None):
+def roofline(r, w, peaks, src):
     """Roofline of the dominant (longest) sweep kernel.  FP32: HBM-bound, algorithmic bytes =
-    one read + one write of the field.  FP64: bound by the FP64 pipe (its HBM time is half its
-    FP64-ALU time at the measured rates), algorithmic flops = Eq. 2's 5 per element."""
+    one read + one write of the field.  FP64: bound by the FP64 pipe (its DRAM time, measured
+    traffic included, stays below its FP64-ALU time), algorithmic flops = Eq. 2's 5 per
+    element.  traffic: measured DRAM bytes per launch (full workload only)."""
     kms = r["kernel_ms"]
     i = int(np.argmax(kms))
     name = ("x", "y", "z")[i]
+    traffic = None if SHAPE else MEASURED_TRAFFIC.get(("f64" if r["esz"] == 8 else "f32",
+                                                       f"{name}-sweep"))
+    dram = None if traffic is None else traffic / (kms[i] * 1e-3) / 1e9
     if r["esz"] == 8:
         clk = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
         peak = 2.0 * FP64_FMA_PER_CLK_PER_SM * GB300_SMS * clk / 1e12
@@ -400,13 +411,15 @@ def roofline(r, w, peaks, src, traffic=None):
         return {"bound": "alu", "kernel": f"{name}-sweep", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                 "peak_source": "FP64 FMA rate 2/clk/SM (measured probe) x 152 SMs x sm_max_mhz",
-                "hbm_GBps": 2 * r["esz"] * w.n_vs / (kms[i] * 1e-3) / 1e9}
+                "hbm_GBps": 2 * r["esz"] * w.n_vs / (kms[i] * 1e-3) / 1e9,
+                "dram_GBps_measured_traffic": dram}
     alg_bytes = 2 * r["esz"] * w.n_vs  # one read + one write of the field per sweep
     achieved = alg_bytes / (kms[i] * 1e-3) / 1e9
     peak = float(peaks["hbm_gbs"])
     return {"bound": "hbm", "kernel": f"{name}-sweep", "achieved": achieved, "peak": peak,
             "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-            "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({src})"}
+            "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({src})",
+            "dram_GBps_measured_traffic": dram}
 
 
 if __name__ == "__main__":

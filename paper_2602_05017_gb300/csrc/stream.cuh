@@ -105,6 +105,28 @@ struct LineDir {
   bool face;
 };
 
+// L2 eviction priorities.  The forward intermediate must survive in L2 until
+// the backward pass reads it back (stored evict_last); the final values are
+// not read again by this kernel (stored evict_first), so they leave L2 first.
+struct L2Pol {
+  unsigned long long keep, drop;
+};
+__device__ __forceinline__ L2Pol make_l2pol() {
+  L2Pol p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p.keep));
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p.drop));
+  return p;
+}
+__device__ __forceinline__ void st_hint(double *p, double v, unsigned long long pol) {
+  asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(p), "d"(v), "l"(pol));
+}
+__device__ __forceinline__ void st_hint(float *p, float v, unsigned long long pol) {
+  asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(pol));
+}
+// Compiler barrier between the passes: the hinted stores are asm statements,
+// so the backward pass's ordinary loads must not move above them.
+__device__ __forceinline__ void pass_barrier() { asm volatile("" ::: "memory"); }
+
 // Load R positions starting at i0 and walking by +st (fwd) or -st.
 template <typename E, int R>
 __device__ __forceinline__ void load_block(E (&buf)[R], const E *line, long long st, int i0,
@@ -126,6 +148,7 @@ __device__ __forceinline__ void solve_lines_f64(double *line, int n, long long s
                                                 const LineCoef<double> &cf, const LineDir &dr,
                                                 double dval_in, double dval) {
   const int S = cf.S, k0 = cf.k0, ngrp = (n + R - 1) / R;
+  const L2Pol pol = make_l2pol();
   const bool dBf = dr.before && dr.face, dAf = dr.after && dr.face;
   double h = 0.0, mp = 0.0;
   auto fwd_group = [&](int g, const double(&buf)[R]) {
@@ -136,7 +159,7 @@ __device__ __forceinline__ void solve_lines_f64(double *line, int n, long long s
 #pragma unroll
       for (int k = 0; k < R; k++) {
         h = fma(cf.c1, h, dBf ? dval_in : buf[k]);
-        *q = h;
+        st_hint(q, h, pol.keep);
         q += st;
       }
       mp = cf.c1;
@@ -148,7 +171,7 @@ __device__ __forceinline__ void solve_lines_f64(double *line, int n, long long s
           double d = buf[k];
           if (dr.before && (dr.face || i == 0 || i == n - 1)) d = dval_in;
           h = fma(mp, h, d);
-          *q = (OUT != 0 && i == n - 1) ? __ldg(cf.q + (size_t)i * S) * h : h;
+          st_hint(q, (OUT != 0 && i == n - 1) ? __ldg(cf.q + (size_t)i * S) * h : h, pol.keep);
           mp = __ldg(cf.mul + (size_t)i * S);
         }
         q += st;
@@ -167,10 +190,10 @@ __device__ __forceinline__ void solve_lines_f64(double *line, int n, long long s
 #pragma unroll
       for (int k = 0; k < R; k++) {
         x = fma(cf.c1, x, OUT == 0 ? cf.c0 * buf[k] : buf[k]);
-        *q = dAf ? dval : (OUT == 2 ? cf.om * x : x);
+        st_hint(q, dAf ? dval : (OUT == 2 ? cf.om * x : x), pol.drop);
         q -= st;
       }
-      if (dr.after && i1 == n - 1) line[(long long)(n - 1) * st] = dval;
+      if (dr.after && i1 == n - 1) st_hint(line + (long long)(n - 1) * st, dval, pol.drop);
     } else {
 #pragma unroll
       for (int k = 0; k < R; k++) {
@@ -180,8 +203,9 @@ __device__ __forceinline__ void solve_lines_f64(double *line, int n, long long s
           const double t = OUT == 0 ? __ldg(cf.inv + (size_t)i * S) * hv
                                     : (i == n - 1 ? hv : __ldg(cf.q + (size_t)i * S) * hv);
           x = fma(__ldg(cf.mul + (size_t)i * S), x, t);
-          *q = (dr.after && (dr.face || i == 0 || i == n - 1)) ? dval
-                                                                : (OUT == 2 ? cf.om * x : x);
+          st_hint(q, (dr.after && (dr.face || i == 0 || i == n - 1)) ? dval
+                                                                     : (OUT == 2 ? cf.om * x : x),
+                  pol.drop);
         }
         q -= st;
       }
@@ -190,6 +214,7 @@ __device__ __forceinline__ void solve_lines_f64(double *line, int n, long long s
   double A[R], B[R];
   for (int pass = 0; pass < 2; pass++) {
     const bool fwd = pass == 0;
+    pass_barrier();
     auto first = [&](int g) { return fwd ? g * R : n - 1 - g * R; };
     load_block<double, R>(A, line, st, first(0), fwd, n, active);
     for (int g = 0; g < ngrp; g += 2) {
@@ -210,6 +235,7 @@ __device__ __forceinline__ void solve_lines_f32(float *line, float *sline, int n
                                                 bool active, const LineCoef<float> &cf,
                                                 const LineDir &dr, float dval_in, float dval) {
   const int S = cf.S, k0 = cf.k0, ngrp = (n + R - 1) / R;
+  const L2Pol pol = make_l2pol();
   auto dmod = [&](float v, int i) {
     return (dr.before && (dr.face || i == 0 || i == n - 1)) ? dval_in : v;
   };
@@ -219,7 +245,7 @@ __device__ __forceinline__ void solve_lines_f32(float *line, float *sline, int n
     const float iv = interior ? cf.c0 : __ldg(cf.inv + (size_t)p * S);
     const float mu = interior ? cf.c1 : __ldg(cf.mul + (size_t)p * S);
     g = fmaf(mu, g, e * iv);
-    *sq = g;
+    st_hint(sq, g, pol.keep);
   };
   auto fwd_group = [&](int gi, const float(&buf)[R]) {
     if (!active) return;
@@ -258,7 +284,7 @@ __device__ __forceinline__ void solve_lines_f32(float *line, float *sline, int n
         y = fmaf(mu, y, gb[k]);
         const float d = dmod(db[k], i);
         const float xv = fmaf(cf.om, d, fmaf(cf.clo, d, y));
-        *q = (dr.after && (dr.face || i == 0 || i == n - 1)) ? dval : xv;
+        st_hint(q, (dr.after && (dr.face || i == 0 || i == n - 1)) ? dval : xv, pol.drop);
       }
       q -= st;
     }
@@ -274,6 +300,7 @@ __device__ __forceinline__ void solve_lines_f32(float *line, float *sline, int n
     }
     if (active && n > 0) emit(n - 1, dm1 - dm2, false, sline + (long long)(n - 1) * st);
   }
+  pass_barrier();
   {
     float GA[R], DA[R], GB[R], DB[R];
     load_block<float, R>(GA, sline, st, n - 1, false, n, active);
