@@ -435,6 +435,10 @@ void plan_stream(biofvm *h, int axis) {
   }
   const int S = h->g.n_sub;
   if (axis == 0 && S > 32) return;
+  if (h->prec == BIOFVM_FP64 && allow_stream_smem_f64() != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
   p.grid = h->num_sms * std::max(1, h->stream_ctas_per_sm);
   p.use = 1;
 }

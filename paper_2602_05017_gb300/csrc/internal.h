@@ -167,6 +167,7 @@ cudaError_t allow_pipe_smem_f32(int maxm, size_t bytes);
 cudaError_t launch_pipe_f32(const CUtensorMap &map, const PipeArgs &a, int maxm, int grid,
                             size_t smem, cudaStream_t st);
 // Streaming sweeps (stream.cuh).
+cudaError_t allow_stream_smem_f64();
 cudaError_t launch_stream_f64(const StreamArgs &a, int grid, cudaStream_t st);
 cudaError_t launch_stream_f32(const StreamArgs &a, int grid, cudaStream_t st);
 // Sets the thread-local message biofvm_last_error() returns.

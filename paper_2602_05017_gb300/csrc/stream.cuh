@@ -142,13 +142,21 @@ __device__ __forceinline__ void load_block(E (&buf)[R], const E *line, long long
 }
 
 // FP64 solve of a warp's lines (see the header).  OUT 0: x itself; 1: x/sigma;
-// 2: omega x/sigma.
-template <int OUT, int R = kStreamR>
+// 2: omega x/sigma.  KS > 0: the intermediate of positions below KS (a
+// multiple of R) stays in shared memory (hsm: this lane's slab, position i at
+// hsm[i * 32]) -- the first positions of a line live longest between the two
+// passes, so they weigh most on the L2 footprint.
+template <int OUT, int R = kStreamR, int KS = 0>
 __device__ __forceinline__ void solve_lines_f64(double *line, int n, long long st, bool active,
                                                 const LineCoef<double> &cf, const LineDir &dr,
-                                                double dval_in, double dval) {
+                                                double dval_in, double dval,
+                                                double *hsm = nullptr) {
   const int S = cf.S, k0 = cf.k0, ngrp = (n + R - 1) / R;
   const L2Pol pol = make_l2pol();
+  // forward groups start at multiples of R, so a group is wholly below KS or not
+  auto put_h = [&](double *q, int i, double v) {
+    if (KS > 0 && i < KS) hsm[i * 32] = v; else st_hint(q, v, pol.keep);
+  };
   const bool dBf = dr.before && dr.face, dAf = dr.after && dr.face;
   double h = 0.0, mp = 0.0;
   auto fwd_group = [&](int g, const double(&buf)[R]) {
@@ -159,7 +167,7 @@ __device__ __forceinline__ void solve_lines_f64(double *line, int n, long long s
 #pragma unroll
       for (int k = 0; k < R; k++) {
         h = fma(cf.c1, h, dBf ? dval_in : buf[k]);
-        st_hint(q, h, pol.keep);
+        put_h(q, i0 + k, h);
         q += st;
       }
       mp = cf.c1;
@@ -171,7 +179,7 @@ __device__ __forceinline__ void solve_lines_f64(double *line, int n, long long s
           double d = buf[k];
           if (dr.before && (dr.face || i == 0 || i == n - 1)) d = dval_in;
           h = fma(mp, h, d);
-          st_hint(q, (OUT != 0 && i == n - 1) ? __ldg(cf.q + (size_t)i * S) * h : h, pol.keep);
+          put_h(q, i, (OUT != 0 && i == n - 1) ? __ldg(cf.q + (size_t)i * S) * h : h);
           mp = __ldg(cf.mul + (size_t)i * S);
         }
         q += st;
@@ -212,15 +220,29 @@ __device__ __forceinline__ void solve_lines_f64(double *line, int n, long long s
     }
   };
   double A[R], B[R];
+  // backward blocks come from shared memory below KS, from the field above
+  auto load = [&](double(&buf)[R], int i0, bool fwd) {
+    if (KS == 0 || fwd || i0 - R + 1 >= KS) {
+      load_block<double, R>(buf, line, st, i0, fwd, n, active);
+    } else {
+      const double *q = line + (long long)i0 * st;
+#pragma unroll
+      for (int k = 0; k < R; k++) {
+        const int i = i0 - k;
+        buf[k] = !(active && i >= 0 && i < n) ? 0.0 : (i < KS ? hsm[i * 32] : *q);
+        q -= st;
+      }
+    }
+  };
   for (int pass = 0; pass < 2; pass++) {
     const bool fwd = pass == 0;
     pass_barrier();
     auto first = [&](int g) { return fwd ? g * R : n - 1 - g * R; };
-    load_block<double, R>(A, line, st, first(0), fwd, n, active);
+    load(A, first(0), fwd);
     for (int g = 0; g < ngrp; g += 2) {
-      load_block<double, R>(B, line, st, first(g + 1), fwd, n, active);
+      load(B, first(g + 1), fwd);
       if (fwd) fwd_group(g, A); else bwd_group(g, A);
-      load_block<double, R>(A, line, st, first(g + 2), fwd, n, active);
+      load(A, first(g + 2), fwd);
       if (g + 1 < ngrp) {
         if (fwd) fwd_group(g + 1, B); else bwd_group(g + 1, B);
       }
@@ -331,9 +353,14 @@ __device__ __forceinline__ void warp_rows_src(E *rho, long long r0, long long r1
 
 // Single-grid streaming sweep, persistent grid of 128-thread CTAs; E = double
 // (OUT as above) or float (defect form, OUT 0, scratch field a.scratch).
+// Positions of a line whose FP64 intermediate stays in shared memory
+// (4 warps x 64 x 32 doubles = 64 KB per CTA, 3 CTAs per SM).
+constexpr int kStreamKS = 64;
+
 template <typename E, int OUT>
 __global__ void __launch_bounds__(kStreamThreads, sizeof(E) == 8 ? 3 : 4)
     stream_sweep_kernel(const StreamArgs a) {
+  extern __shared__ __align__(16) unsigned char stream_smem[];
   const int S = a.S, n = a.n, flags = a.flags;
   const int lane = threadIdx.x & 31;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -369,7 +396,10 @@ __global__ void __launch_bounds__(kStreamThreads, sizeof(E) == 8 ? 3 : 4)
     E *line = rho + (L.active ? L.base : 0);
     if constexpr (sizeof(E) == 8) {
       cf.om = (OUT == 2 && L.active) ? ldg<E>(a.omega, L.s) : E(1);
-      solve_lines_f64<OUT>(line, n, a.stride, L.active, cf, dr, dval_in, dval);
+      double *hsm = reinterpret_cast<double *>(stream_smem) +
+                    (size_t)(threadIdx.x >> 5) * kStreamKS * 32 + lane;
+      solve_lines_f64<OUT, kStreamR, kStreamKS>(line, n, a.stride, L.active, cf, dr, dval_in,
+                                                dval, hsm);
     } else {
       cf.om = L.active ? ldg<E>(a.cfix, L.s) : E(0);
       cf.clo = L.active ? ldg<E>(a.cfix, S + L.s) : E(0);
@@ -379,9 +409,26 @@ __global__ void __launch_bounds__(kStreamThreads, sizeof(E) == 8 ? 3 : 4)
   }
 }
 
+template <typename E>
+constexpr size_t stream_smem_bytes() {
+  return sizeof(E) == 8 ? (size_t)(kStreamThreads / 32) * kStreamKS * 32 * sizeof(double) : 0;
+}
+
+// Raise the dynamic shared-memory limit of the FP64 instantiations (once per
+// handle, outside any graph capture).
+template <typename E>
+cudaError_t allow_stream_smem() {
+  cudaError_t e = cudaSuccess;
+  for (auto f : {stream_sweep_kernel<E, 0>, stream_sweep_kernel<E, 1>, stream_sweep_kernel<E, 2>})
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)stream_smem_bytes<E>());
+  return e;
+}
+
 template <typename E, int OUT>
 cudaError_t launch_stream_one(const StreamArgs &a, int grid, cudaStream_t st) {
-  stream_sweep_kernel<E, OUT><<<grid, kStreamThreads, 0, st>>>(a);
+  stream_sweep_kernel<E, OUT><<<grid, kStreamThreads, stream_smem_bytes<E>(), st>>>(a);
   return cudaGetLastError();
 }
 

@@ -72,6 +72,8 @@ cudaError_t launch_batch_f64(const BatchArgs &a, int, int grid, cudaStream_t st)
 
 cudaError_t batch_occupancy_f64(int maxm, int *out) { return batch_blocks_per_sm<double>(maxm, out); }
 
+cudaError_t allow_stream_smem_f64() { return allow_stream_smem<double>(); }
+
 cudaError_t launch_stream_f64(const StreamArgs &a, int grid, cudaStream_t st) {
   switch (a.out) {
     case 1: return launch_stream_one<double, 1>(a, grid, st);
