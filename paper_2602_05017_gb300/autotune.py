@@ -23,7 +23,7 @@ from . import inputs
 
 N_BUCKETS = (32, 64, 96, 128, 160, 192)
 MAX_CHUNKS = 8     # warps of the batched CTA
-MAX_CHUNK = 48     # longest chunk the batched kernel keeps in shared memory
+MAX_CHUNK = 32     # longest chunk offered (the batched kernel allows 48; 32 keeps 3 CTAs per SM)
 WHOLE = -1         # cache marker: whole lines
 
 

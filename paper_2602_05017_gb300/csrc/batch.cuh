@@ -61,8 +61,15 @@ __device__ __forceinline__ void cp_async_elem(void *smem, const void *gmem, int 
                  : "memory");
 }
 
+// FP32 whole-line tiles keep the first kBatchKS positions of g and d in shared
+// memory (64 KB per CTA).
+constexpr int kBatchKS = 32;
+
+// Three 256-thread CTAs per SM (80 registers): the kernel is latency-bound, so
+// resident warps matter more than registers (64 KB of shared memory per CTA
+// with chunks of at most 32 positions).
 template <typename E>
-__global__ void __launch_bounds__(kBatchWarps * 32) batch_kernel(const BatchArgs a) {
+__global__ void __launch_bounds__(kBatchWarps * 32, 3) batch_kernel(const BatchArgs a) {
   extern __shared__ __align__(16) unsigned char batch_smem[];
   constexpr int NB = kDefect<E> ? 2 : 1;                         // d (+ working array)
   E *const s_chunk = reinterpret_cast<E *>(batch_smem);          // [NB][8][maxm][32]
@@ -167,7 +174,9 @@ __global__ void __launch_bounds__(kBatchWarps * 32) batch_kernel(const BatchArgs
           cf.om = ldg<E>(E_.cfix[phase], L.s);
           cf.clo = ldg<E>(E_.cfix[phase], S + L.s);
           E *sline = static_cast<E *>(E_.scratch) + (L.active ? L.base : 0);
-          solve_lines_f32<8>(line, sline, n, st, L.active, cf, dr, E(0), E(0));
+          float *gsm = reinterpret_cast<float *>(batch_smem) + (size_t)wp * 2 * kBatchKS * 32 + lane;
+          solve_lines_f32<8, kBatchKS>(line, sline, n, st, L.active, cf, dr, E(0), E(0), gsm,
+                                       gsm + kBatchKS * 32);
         }
       }
       __syncthreads();
@@ -295,7 +304,10 @@ __global__ void __launch_bounds__(kBatchWarps * 32) batch_kernel(const BatchArgs
 
 inline size_t batch_smem_bytes(int maxm, size_t esz) {
   const size_t nb = esz == 4 ? 2 : 1;  // FP32 keeps d beside the working array
-  return (nb * kBatchWarps * maxm * 32 + 4 * (size_t)kBatchWarps * 32) * esz;
+  const size_t chunks = (nb * kBatchWarps * maxm * 32 + 4 * (size_t)kBatchWarps * 32) * esz;
+  // FP32 whole-line tiles: g and d of the first kBatchKS positions per warp
+  const size_t lines = esz == 4 ? (size_t)kBatchWarps * 2 * kBatchKS * 32 * 4 : 0;
+  return chunks > lines ? chunks : lines;
 }
 
 template <typename E>

@@ -251,11 +251,15 @@ __device__ __forceinline__ void solve_lines_f64(double *line, int n, long long s
 }
 
 // FP32 defect-correction solve of a warp's lines (see the header); sline is
-// the scratch field at the same offset as line.
-template <int R = kStreamR>
+// the scratch field at the same offset as line.  KS > 0: for positions below
+// KS (a multiple of R) both g and d stay in shared memory (gsm, dsm: this
+// lane's slabs, position i at [i * 32]), since they live longest between the
+// two passes.
+template <int R = kStreamR, int KS = 0>
 __device__ __forceinline__ void solve_lines_f32(float *line, float *sline, int n, long long st,
                                                 bool active, const LineCoef<float> &cf,
-                                                const LineDir &dr, float dval_in, float dval) {
+                                                const LineDir &dr, float dval_in, float dval,
+                                                float *gsm = nullptr, float *dsm = nullptr) {
   const int S = cf.S, k0 = cf.k0, ngrp = (n + R - 1) / R;
   const L2Pol pol = make_l2pol();
   auto dmod = [&](float v, int i) {
@@ -267,7 +271,7 @@ __device__ __forceinline__ void solve_lines_f32(float *line, float *sline, int n
     const float iv = interior ? cf.c0 : __ldg(cf.inv + (size_t)p * S);
     const float mu = interior ? cf.c1 : __ldg(cf.mul + (size_t)p * S);
     g = fmaf(mu, g, e * iv);
-    st_hint(sq, g, pol.keep);
+    if (KS > 0 && p < KS) gsm[p * 32] = g; else st_hint(sq, g, pol.keep);
   };
   auto fwd_group = [&](int gi, const float(&buf)[R]) {
     if (!active) return;
@@ -278,6 +282,7 @@ __device__ __forceinline__ void solve_lines_f32(float *line, float *sline, int n
     for (int k = 0; k < R; k++) {
       const int i = i0 + k;
       if (i < n) {
+        if (KS > 0 && i < KS) dsm[i * 32] = buf[k];
         const float d = dmod(buf[k], i);
         if (i == 0) {
           dm1 = d;
@@ -324,15 +329,30 @@ __device__ __forceinline__ void solve_lines_f32(float *line, float *sline, int n
   }
   pass_barrier();
   {
+    // backward blocks: shared memory below KS, global above
+    auto load2 = [&](float(&gb)[R], float(&db)[R], int i1) {
+      if (KS == 0 || i1 - R + 1 >= KS) {
+        load_block<float, R>(gb, sline, st, i1, false, n, active);
+        load_block<float, R>(db, line, st, i1, false, n, active);
+      } else {
+        const float *qs = sline + (long long)i1 * st, *qd = line + (long long)i1 * st;
+#pragma unroll
+        for (int k = 0; k < R; k++) {
+          const int i = i1 - k;
+          const bool ok = active && i >= 0 && i < n;
+          gb[k] = !ok ? 0.f : (i < KS ? gsm[i * 32] : *qs);
+          db[k] = !ok ? 0.f : (i < KS ? dsm[i * 32] : *qd);
+          qs -= st;
+          qd -= st;
+        }
+      }
+    };
     float GA[R], DA[R], GB[R], DB[R];
-    load_block<float, R>(GA, sline, st, n - 1, false, n, active);
-    load_block<float, R>(DA, line, st, n - 1, false, n, active);
+    load2(GA, DA, n - 1);
     for (int gi = 0; gi < ngrp; gi += 2) {
-      load_block<float, R>(GB, sline, st, n - 1 - (gi + 1) * R, false, n, active);
-      load_block<float, R>(DB, line, st, n - 1 - (gi + 1) * R, false, n, active);
+      load2(GB, DB, n - 1 - (gi + 1) * R);
       bwd_group(gi, GA, DA);
-      load_block<float, R>(GA, sline, st, n - 1 - (gi + 2) * R, false, n, active);
-      load_block<float, R>(DA, line, st, n - 1 - (gi + 2) * R, false, n, active);
+      load2(GA, DA, n - 1 - (gi + 2) * R);
       if (gi + 1 < ngrp) bwd_group(gi + 1, GB, DB);
     }
   }
