@@ -107,10 +107,12 @@ biofvm_status biofvm_set_sources(biofvm_t *h, int64_t n, const int64_t *voxel,
                                  const double *secretion, const double *target,
                                  const double *uptake, const double *weight);
 
-/* Advance n_steps >= 0 time steps (async).  The first call after create or
- * after a parameter change captures one step into a CUDA graph; every step is
- * then one graph launch on the handle's stream.  Errors: ARG, CUDA,
- * TIMEOUT (reported by the next synchronising call). */
+/* Advance n_steps >= 0 time steps (async).  Steps run as CUDA graphs captured
+ * on first use (after create or a parameter change): a block of K steps
+ * (K = 1; with the FP64 streaming sweeps up to 16, the steps between which the
+ * field may stay divided by a per-substrate constant) and shorter tails; the
+ * field is the true one whenever the call's steps are done.  Errors: ARG,
+ * CUDA, TIMEOUT (reported by the next synchronising call). */
 biofvm_status biofvm_step(biofvm_t *h, int n_steps);
 
 /* Copy the field out into dst (host pointer if dst_on_device = 0, device
@@ -132,7 +134,11 @@ biofvm_status biofvm_set_params(biofvm_t *h, const double *D,
  * timing each): in FP64 the step's x- and y-sweeps leave the field divided
  * by a per-substrate constant that the z-sweep takes out again, so only the
  * sequence 9, 10, 11 as a whole is a step (equal to stages 8, 2, 3 up to
- * rounding).  Async.  Errors: ARG, CUDA. */
+ * rounding).  Stage 12 is the z-sweep as it runs inside a block of FP64
+ * steps: it leaves the field divided by that constant (biofvm_step brings
+ * the field back every 16 steps or fewer, and always before it returns);
+ * without the FP64 streaming sweeps it equals stage 11.  Async.  Errors: ARG,
+ * CUDA. */
 biofvm_status biofvm_run_stage(biofvm_t *h, int stage);
 
 /* One time step, like biofvm_step(h, 1), that also writes the forward states

@@ -79,6 +79,8 @@ struct PipePlan {
   CUtensorMap map[2]{};  // y/z: [0] the field, [1] the adjoint field
   int have_map[2]{};
 };
+constexpr int kMaxRenorm = 16;  // steps between renormalisations of the scaled FP64 field
+
 struct StreamPlan {
   int use = 0, grid = 0;
 };
@@ -105,7 +107,7 @@ struct biofvm {
   DevBuf rho, tab[3], tabT[3], dir_on_d, dir_val_d, status;
   // streaming sweep (FP64): [3][n][S] inv, mul, q per axis; Dirichlet values
   // in the units of each sweep's scaled output [3][S]; omega [S]; k0 per axis
-  DevBuf tabS[3], dir_scaled_d, omega_d, stream_const_d;
+  DevBuf tabS[3], stream_const_d;
   int stream_k0[3] = {0, 0, 0};
   XPlan xp;
   ColPlan cp[3];  // [1] = y, [2] = z
@@ -115,6 +117,7 @@ struct biofvm {
   int pipe_enabled = 1;
   int stream_enabled = 1;
   int stream_ctas_per_sm = 3;
+  int stream_ks = 64;        // FP64: positions of each line's intermediate kept in shared memory
   int stream32_enabled = 0;  // FP32 streaming sweeps instead of the pipelined ones
   DevBuf scratch;            // FP32 streaming: forward intermediate, field-sized
   int forced = 0;  // chunk lengths fixed by the caller (batched environments)
@@ -122,8 +125,15 @@ struct biofvm {
   // sources
   int64_t n_entries = 0;
   DevBuf src_row_off, src_elem, src_rowcol, src_alpha, src_scale;
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t gexec = nullptr;
+  // step graphs: [0] a block of renorm_k steps, [r] a tail of r < renorm_k steps
+  cudaGraph_t graph[kMaxRenorm + 1] = {};
+  cudaGraphExec_t gexec[kMaxRenorm + 1] = {};
+  // FP64 streaming step: the field stays scaled by omega^-m for m < renorm_k
+  // steps (no multiply by omega in the z-sweep) and is brought back every
+  // renorm_k steps and at the end of every biofvm_step call; renorm_d holds the
+  // per-step constants [renorm_k][6][S] (see launch_step)
+  int renorm_k = 1;
+  DevBuf renorm_d;
   // adjoint: the adjoint field, reduction partials, agents on the device
   DevBuf adj, partial, ag_elem, ag_entry, ag_weight, ag_target;
   int reduce_blocks = 0;
@@ -136,6 +146,15 @@ namespace {
 
 int axis_len(const biofvm *h, int axis) {
   return axis == 0 ? h->g.nx : axis == 1 ? h->g.ny : h->g.nz;
+}
+
+void drop_graphs(biofvm *h) {
+  for (int r = 0; r <= kMaxRenorm; r++) {
+    if (h->gexec[r]) cudaGraphExecDestroy(h->gexec[r]);
+    if (h->graph[r]) cudaGraphDestroy(h->graph[r]);
+    h->gexec[r] = nullptr;
+    h->graph[r] = nullptr;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -596,26 +615,39 @@ biofvm_status upload_constants(biofvm *h) {
       biofvm_status st = upload_doubles(h, h->stream_const_d, c);
       if (st) return st;
     }
-    // Dirichlet values in stored units: dval / sigma_x after x, dval / (sigma_x sigma_y)
-    // after y, dval after z (the z-sweep stores the true field)
-    std::vector<double> dsc((size_t)3 * S), om(S);
+    // Per-step constants of the scaled step.  Step m of a block reads a field
+    // stored as true / omega^m (omega = sigma_x sigma_y sigma_z); its rows:
+    //   [0] omega^-m                  source alpha factor
+    //   [1] dval omega^-m             Dirichlet before the x-solve
+    //   [2] dval / (omega^m sigma_x)  after x      [3] ... / (sigma_x sigma_y)  after y
+    //   [4] dval / omega^(m+1)        after z, field left scaled
+    //   [5] omega^(m+1)               z multiplier of the renormalising step (then dval after z)
+    // renorm_k: the longest block (<= kMaxRenorm) whose omega^k stays above 1e-150.
+    std::vector<double> om(S);
+    double om_min = 1.0;
     for (int s = 0; s < S; s++) {
-      const double sx = sigma[s], sy = sigma[S + s], sz = sigma[2 * S + s];
-      dsc[s] = h->dir_val[s] / sx;
-      dsc[S + s] = h->dir_val[s] / (sx * sy);
-      dsc[2 * S + s] = h->dir_val[s];
-      om[s] = sx * sy * sz;
+      om[s] = sigma[s] * sigma[S + s] * sigma[2 * S + s];
+      om_min = std::min(om_min, om[s]);
     }
-    biofvm_status st = upload_doubles(h, h->dir_scaled_d, dsc);
-    if (!st) st = upload_doubles(h, h->omega_d, om);
+    int K = 1;
+    while (K < kMaxRenorm && std::pow(om_min, K + 1) >= 1e-150) K++;
+    h->renorm_k = K;
+    std::vector<double> tb((size_t)K * 6 * S);
+    for (int m = 0; m < K; m++)
+      for (int s = 0; s < S; s++) {
+        const double dv = h->dir_val[s], wm = std::pow(om[s], m);
+        double *r = &tb[(size_t)m * 6 * S];
+        r[s] = 1.0 / wm;
+        r[S + s] = dv / wm;
+        r[2 * S + s] = dv / (wm * sigma[s]);
+        r[3 * S + s] = dv / (wm * sigma[s] * sigma[S + s]);
+        r[4 * S + s] = dv / (wm * om[s]);
+        r[5 * S + s] = wm * om[s];
+      }
+    biofvm_status st = upload_doubles(h, h->renorm_d, tb);
     if (st) return st;
   }
-  if (h->graph) {
-    cudaGraphExecDestroy(h->gexec);
-    cudaGraphDestroy(h->graph);
-    h->graph = nullptr;
-    h->gexec = nullptr;
-  }
+  drop_graphs(h);
   h->generation++;
   return BIOFVM_OK;
 }
@@ -714,11 +746,12 @@ cudaError_t launch_stream(const biofvm *h, int axis, int flags, cudaStream_t st,
   a.tab = fp64 ? h->tabS[axis].p : h->tab[axis].p;  // FP32: inv, mul lead the axis table
   a.cfix = fp64 ? nullptr : axis_tab(h, axis).cfix;
   a.scratch = h->scratch.p;
+  a.ks = std::max(0, std::min(h->stream_ks, 208));  // 4 warps x ks x 256 B <= 208 KB
   a.flags = flags;
   if (!h->any_dir) a.flags &= ~(kDirBefore | kDirAfter);
-  a.out = (fp64 && (flags & kScaled)) ? (axis == 2 ? 2 : 1) : 0;
+  const bool scaled = fp64 && (flags & kScaled);
+  a.out = !scaled ? 0 : (axis == 2 && !(flags & kKeepScale)) ? 2 : 1;
   a.k0 = h->stream_k0[axis];
-  a.omega = h->omega_d.p;
   a.interior = static_cast<const char *>(h->stream_const_d.p) + (size_t)axis * 2 * S * h->esz;
   a.src_row_off = static_cast<const int64_t *>(h->src_row_off.p);
   a.src_elem = static_cast<const int64_t *>(h->src_elem.p);
@@ -726,9 +759,23 @@ cudaError_t launch_stream(const biofvm *h, int axis, int flags, cudaStream_t st,
   a.src_scale = h->src_scale.p;
   a.has_src = h->n_entries > 0;
   a.dir_on = static_cast<const uint8_t *>(h->dir_on_d.p);
-  const char *dsc = static_cast<const char *>(h->dir_scaled_d.p);
-  a.dir_val = a.out ? dsc + (size_t)axis * S * h->esz : h->dir_val_d.p;
-  a.dir_val_in = (a.out && axis > 0) ? dsc + (size_t)(axis - 1) * S * h->esz : h->dir_val_d.p;
+  a.dir_val = a.dir_val_in = h->dir_val_d.p;
+  if (scaled) {  // the step's row of the renormalisation table (upload_constants)
+    const int m = (flags >> 8) & 0xff;
+    const char *row = static_cast<const char *>(h->renorm_d.p) + (size_t)m * 6 * S * h->esz;
+    auto at = [&](int k) { return static_cast<const void *>(row + (size_t)k * S * h->esz); };
+    if (axis == 0) {
+      a.src_fac = m > 0 ? at(0) : nullptr;
+      a.dir_val_in = at(1);
+      a.dir_val = at(2);
+    } else if (axis == 1) {
+      a.dir_val = at(3);
+    } else if (flags & kKeepScale) {
+      a.dir_val = at(4);
+    } else {
+      a.omega = at(5);  // renormalising: omega^(m+1), the true field, dval itself
+    }
+  }
   const int grid = (int)std::min<int64_t>(p.grid, (a.ngroups + 3) / 4);
   return fp64 ? launch_stream_f64(a, grid, st) : launch_stream_f32(a, grid, st);
 }
@@ -804,11 +851,15 @@ int step_scaled(const biofvm *h) {
   return (h->prec == BIOFVM_FP64 && h->sp[0].use && h->sp[1].use && h->sp[2].use) ? kScaled : 0;
 }
 
-biofvm_status launch_step(const biofvm *h, cudaStream_t st) {
+// One step.  Scaled (FP64 streaming): step m of a renormalisation block reads a
+// field stored as true / omega^m and, unless `renorm`, leaves it as
+// true / omega^(m+1); a renormalising step stores the true field.
+biofvm_status launch_step(const biofvm *h, cudaStream_t st, int m = 0, bool renorm = true) {
   const int sc = step_scaled(h);
-  CK(launch_x(h, kSrc | kDirBefore | kSolve | kDirAfter | sc, st));
-  CK(launch_col(h, 1, kSolve | kDirAfter | sc, st));
-  CK(launch_col(h, 2, kSolve | kDirAfter | sc, st));
+  const int mf = sc ? (m << 8) : 0;
+  CK(launch_x(h, kSrc | kDirBefore | kSolve | kDirAfter | sc | mf, st));
+  CK(launch_col(h, 1, kSolve | kDirAfter | sc | mf, st));
+  CK(launch_col(h, 2, kSolve | kDirAfter | sc | mf | (sc && !renorm ? kKeepScale : 0), st));
   return BIOFVM_OK;
 }
 
@@ -834,11 +885,10 @@ void destroy_impl(biofvm *h) {
   if (!h) return;
   cudaSetDevice(h->device);
   if (h->stream || h->rho.p) cudaStreamSynchronize(h->stream);
-  if (h->gexec) cudaGraphExecDestroy(h->gexec);
-  if (h->graph) cudaGraphDestroy(h->graph);
+  drop_graphs(h);
   for (DevBuf *b : {&h->rho, &h->tab[0], &h->tab[1], &h->tab[2], &h->tabT[0], &h->tabT[1],
-                    &h->tabT[2], &h->tabS[0], &h->tabS[1], &h->tabS[2], &h->dir_scaled_d,
-                    &h->omega_d, &h->stream_const_d, &h->scratch, &h->dir_on_d, &h->dir_val_d,
+                    &h->tabT[2], &h->tabS[0], &h->tabS[1], &h->tabS[2], &h->renorm_d,
+                    &h->stream_const_d, &h->scratch, &h->dir_on_d, &h->dir_val_d,
                     &h->status, &h->src_row_off, &h->src_elem, &h->src_rowcol, &h->src_alpha, &h->src_scale,
                     &h->adj, &h->partial, &h->ag_elem, &h->ag_entry, &h->ag_weight,
                     &h->ag_target})
@@ -988,6 +1038,7 @@ biofvm_status create_impl(const biofvm_grid *grid, double dx, double dt, const d
   if (const char *env = getenv("BIOFVM_STREAM")) h->stream_enabled = atoi(env) != 0;
   if (const char *env = getenv("BIOFVM_STREAM_CTAS")) h->stream_ctas_per_sm = atoi(env);
   if (const char *env = getenv("BIOFVM_STREAM32")) h->stream32_enabled = atoi(env) != 0;
+  if (const char *env = getenv("BIOFVM_STREAM_KS")) h->stream_ks = atoi(env) / 16 * 16;
   if (!h->forced)
     for (int axis = 0; axis < 3; axis++) plan_stream(h, axis);
   if ((st = upload_doubles(h, h->dir_val_d, h->dir_val)) != BIOFVM_OK ||
@@ -1142,11 +1193,8 @@ biofvm_status biofvm_set_sources(biofvm_t *h, int64_t n, const int64_t *voxel,
   h->h_src_elem = elem;
   h->agents_on_device = false;
   h->generation++;
-  if (h->graph) {  // kernel arguments changed
-    cudaGraphExecDestroy(h->gexec);
-    cudaGraphDestroy(h->graph);
-    h->graph = nullptr;
-    h->gexec = nullptr;
+  {  // kernel arguments changed
+    drop_graphs(h);
   }
   return BIOFVM_OK;
 }
@@ -1156,9 +1204,15 @@ biofvm_status biofvm_step(biofvm_t *h, int n_steps) {
   if (n_steps < 0) return fail(BIOFVM_ERR_ARG, "n_steps must be >= 0");
   if (n_steps == 0) return BIOFVM_OK;
   CK(cudaSetDevice(h->device));
-  if (!h->gexec) {
+  // graphs of K steps (a renormalisation block) and of a shorter tail, each
+  // ending with the true field; K = 1 unless the FP64 streaming step applies
+  const int K = step_scaled(h) ? h->renorm_k : 1;
+  auto ensure = [&](int r) -> biofvm_status {  // graph slot 0: K steps; slot r: r < K steps
+    const int slot = r == K ? 0 : r;
+    if (h->gexec[slot]) return BIOFVM_OK;
     CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-    biofvm_status st = launch_step(h, h->cap_stream);
+    biofvm_status st = BIOFVM_OK;
+    for (int m = 0; m < r && st == BIOFVM_OK; m++) st = launch_step(h, h->cap_stream, m, m == r - 1);
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(h->cap_stream, &graph);
     if (st != BIOFVM_OK) {
@@ -1167,14 +1221,20 @@ biofvm_status biofvm_step(biofvm_t *h, int n_steps) {
     }
     if (e != cudaSuccess)
       return fail(BIOFVM_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
-    e = cudaGraphInstantiate(&h->gexec, graph, 0);
+    e = cudaGraphInstantiate(&h->gexec[slot], graph, 0);
     if (e != cudaSuccess) {
       cudaGraphDestroy(graph);
       return fail(BIOFVM_ERR_CUDA, "cudaGraphInstantiate failed: %s", cudaGetErrorString(e));
     }
-    h->graph = graph;
-  }
-  for (int k = 0; k < n_steps; k++) CK(cudaGraphLaunch(h->gexec, h->stream));
+    h->graph[slot] = graph;
+    return BIOFVM_OK;
+  };
+  const int blocks = n_steps / K, tail = n_steps % K;
+  biofvm_status st;
+  if (blocks > 0 && (st = ensure(K)) != BIOFVM_OK) return st;
+  if (tail > 0 && (st = ensure(tail)) != BIOFVM_OK) return st;
+  for (int b = 0; b < blocks; b++) CK(cudaGraphLaunch(h->gexec[0], h->stream));
+  if (tail > 0) CK(cudaGraphLaunch(h->gexec[tail], h->stream));
   return BIOFVM_OK;
 }
 
@@ -1195,7 +1255,11 @@ biofvm_status biofvm_run_stage(biofvm_t *h, int stage) {
       break;
     case 10: CK(launch_col(h, 1, kSolve | kDirAfter | step_scaled(h), h->stream)); break;
     case 11: CK(launch_col(h, 2, kSolve | kDirAfter | step_scaled(h), h->stream)); break;
-    default: return fail(BIOFVM_ERR_ARG, "stage must be in [0, 11] (got %d)", stage);
+    case 12:
+      CK(launch_col(h, 2, kSolve | kDirAfter | step_scaled(h) | (step_scaled(h) ? kKeepScale : 0),
+                    h->stream));
+      break;
+    default: return fail(BIOFVM_ERR_ARG, "stage must be in [0, 12] (got %d)", stage);
   }
   return BIOFVM_OK;
 }

@@ -17,6 +17,8 @@ enum : int {
   kDirAfter = 8,   // Dirichlet application after the solve
   kMaskZero = 16,  // Dirichlet applications write 0 (the adjoint of B: dB/du = mask)
   kScaled = 32,    // streaming sweeps of a whole step: scaled intermediate output
+  kKeepScale = 64, // z-sweep of a scaled step that leaves the field scaled (no omega)
+  // bits 8..15: the step's index m within its renormalisation block (host only)
 };
 
 // Status word values written by kernels (mirror biofvm_status).
@@ -99,9 +101,11 @@ struct StreamArgs {
   int out;                // FP64: 0: x; 1: y = x / sigma; 2: omega y (stream.cuh)
   int k0;                 // interior (one value per substrate) from k0 to n-2
   const void *interior;   // [2][S] the interior inv and mul (FP64: sigma, r sigma)
-  const void *omega;      // FP64 [S] sigma_x sigma_y sigma_z (out 2)
+  const void *omega;      // FP64 [S] z multiplier of a renormalising step (out 2)
+  const void *src_fac;    // FP64 [S] factor on the source alpha (field stored scaled), or NULL
   const void *cfix;       // FP32 [2][S] c_hi, c_lo (defect form)
   void *scratch;          // FP32: field-sized scratch for the forward intermediate
+  int ks;                 // FP64: positions whose intermediate stays in shared memory
   int flags;
   const int64_t *src_row_off, *src_elem;
   const void *src_alpha, *src_scale;

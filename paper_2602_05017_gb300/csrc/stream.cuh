@@ -143,14 +143,14 @@ __device__ __forceinline__ void load_block(E (&buf)[R], const E *line, long long
 
 // FP64 solve of a warp's lines (see the header).  OUT 0: x itself; 1: x/sigma;
 // 2: omega x/sigma.  KS > 0: the intermediate of positions below KS (a
-// multiple of R) stays in shared memory (hsm: this lane's slab, position i at
+// multiple of R, warp-uniform) stays in shared memory (hsm: this lane's slab, position i at
 // hsm[i * 32]) -- the first positions of a line live longest between the two
 // passes, so they weigh most on the L2 footprint.
-template <int OUT, int R = kStreamR, int KS = 0>
+template <int OUT, int R = kStreamR>
 __device__ __forceinline__ void solve_lines_f64(double *line, int n, long long st, bool active,
                                                 const LineCoef<double> &cf, const LineDir &dr,
                                                 double dval_in, double dval,
-                                                double *hsm = nullptr) {
+                                                double *hsm = nullptr, int KS = 0) {
   const int S = cf.S, k0 = cf.k0, ngrp = (n + R - 1) / R;
   const L2Pol pol = make_l2pol();
   // forward groups start at multiples of R, so a group is wholly below KS or not
@@ -359,23 +359,24 @@ __device__ __forceinline__ void solve_lines_f32(float *line, float *sline, int n
 }
 
 // Source update of a warp's rows (x-sweep), then visible to the whole warp.
+// fac (or NULL): per-substrate factor on alpha when the field is stored scaled.
 template <typename E>
 __device__ __forceinline__ void warp_rows_src(E *rho, long long r0, long long r1,
                                               const int64_t *row_off, const int64_t *elem,
-                                              const void *alpha, const void *scale, int lane) {
+                                              const void *alpha, const void *scale, int lane,
+                                              const void *fac = nullptr, int S = 1) {
   const long long e0 = row_off[r0], e1 = row_off[r1];
   for (long long e = e0 + lane; e < e1; e += 32) {
     const long long k = elem[e];
-    rho[k] = (rho[k] + ldg<E>(alpha, e)) * ldg<E>(scale, e);
+    E al = ldg<E>(alpha, e);
+    if (fac) al *= ldg<E>(fac, (int)(k % S));
+    rho[k] = (rho[k] + al) * ldg<E>(scale, e);
   }
   __syncwarp();
 }
 
 // Single-grid streaming sweep, persistent grid of 128-thread CTAs; E = double
 // (OUT as above) or float (defect form, OUT 0, scratch field a.scratch).
-// Positions of a line whose FP64 intermediate stays in shared memory
-// (4 warps x 64 x 32 doubles = 64 KB per CTA, 3 CTAs per SM).
-constexpr int kStreamKS = 64;
 
 template <typename E, int OUT>
 __global__ void __launch_bounds__(kStreamThreads, sizeof(E) == 8 ? 3 : 4)
@@ -394,7 +395,7 @@ __global__ void __launch_bounds__(kStreamThreads, sizeof(E) == 8 ? 3 : 4)
     if (a.mode == 0 && (flags & kSrc) && a.has_src) {
       const long long r0 = grp * a.rows_per_warp;
       warp_rows_src<E>(rho, r0, min(r0 + a.rows_per_warp, nrows), a.src_row_off, a.src_elem,
-                       a.src_alpha, a.src_scale, lane);
+                       a.src_alpha, a.src_scale, lane, a.src_fac, S);
     }
     if (!(flags & kSolve)) continue;
     const bool dirl = L.active && (flags & (kDirBefore | kDirAfter)) && a.dir_on[L.s];
@@ -417,9 +418,9 @@ __global__ void __launch_bounds__(kStreamThreads, sizeof(E) == 8 ? 3 : 4)
     if constexpr (sizeof(E) == 8) {
       cf.om = (OUT == 2 && L.active) ? ldg<E>(a.omega, L.s) : E(1);
       double *hsm = reinterpret_cast<double *>(stream_smem) +
-                    (size_t)(threadIdx.x >> 5) * kStreamKS * 32 + lane;
-      solve_lines_f64<OUT, kStreamR, kStreamKS>(line, n, a.stride, L.active, cf, dr, dval_in,
-                                                dval, hsm);
+                    (size_t)(threadIdx.x >> 5) * a.ks * 32 + lane;
+      solve_lines_f64<OUT, kStreamR>(line, n, a.stride, L.active, cf, dr, dval_in, dval, hsm,
+                                     a.ks);
     } else {
       cf.om = L.active ? ldg<E>(a.cfix, L.s) : E(0);
       cf.clo = L.active ? ldg<E>(a.cfix, S + L.s) : E(0);
@@ -429,9 +430,9 @@ __global__ void __launch_bounds__(kStreamThreads, sizeof(E) == 8 ? 3 : 4)
   }
 }
 
-template <typename E>
-constexpr size_t stream_smem_bytes() {
-  return sizeof(E) == 8 ? (size_t)(kStreamThreads / 32) * kStreamKS * 32 * sizeof(double) : 0;
+// Shared memory of one CTA: the warps' slabs of ks positions (FP64).
+inline size_t stream_smem_bytes(int ks, size_t esz) {
+  return esz == 8 ? (size_t)(kStreamThreads / 32) * ks * 32 * sizeof(double) : 0;
 }
 
 // Raise the dynamic shared-memory limit of the FP64 instantiations (once per
@@ -442,13 +443,13 @@ cudaError_t allow_stream_smem() {
   for (auto f : {stream_sweep_kernel<E, 0>, stream_sweep_kernel<E, 1>, stream_sweep_kernel<E, 2>})
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)stream_smem_bytes<E>());
+                               (int)kMaxDynamicSmem);
   return e;
 }
 
 template <typename E, int OUT>
 cudaError_t launch_stream_one(const StreamArgs &a, int grid, cudaStream_t st) {
-  stream_sweep_kernel<E, OUT><<<grid, kStreamThreads, stream_smem_bytes<E>(), st>>>(a);
+  stream_sweep_kernel<E, OUT><<<grid, kStreamThreads, stream_smem_bytes(a.ks, sizeof(E)), st>>>(a);
   return cudaGetLastError();
 }
 

@@ -114,17 +114,44 @@ def test_graph_steps_equal_stage_sequence(binding, monkeypatch, stream):
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_step_kernels_one_by_one_equal_step(binding, prec):
     """Stages 9, 10, 11 (the kernels of biofvm_step, launched one by one) make exactly one
-    graph-launched step, bit for bit."""
+    graph-launched step, bit for bit.  Over several steps the FP64 graph leaves the field scaled
+    between steps of a renormalisation block (stage 12: the z-sweep without the multiply), so
+    there the sequences agree up to rounding."""
     rng = np.random.default_rng(8)
     w = inputs.random_problem(rng, 30, 26, 22, 3, n_agents=50, dirichlet=True)
-    a = gpu_run(binding, w, prec, 2)
-    sim = binding.BioFVM.from_workload(w, precision=prec)
-    for _ in range(2):
-        for stage in (9, 10, 11):
-            sim.run_stage(stage)
-    b = sim.density()
-    sim.close()
-    assert np.array_equal(a, b)
+    for n in (1, 3):
+        a = gpu_run(binding, w, prec, n)
+        sim = binding.BioFVM.from_workload(w, precision=prec)
+        for _ in range(n):
+            for stage in (9, 10, 11):
+                sim.run_stage(stage)
+        b = sim.density()
+        sim.close()
+        if n == 1 or prec == "fp32":
+            assert np.array_equal(a, b), n
+        else:
+            assert rel_err(a, b) <= 1e-14, n
+
+
+def test_renormalisation_blocks_and_tails_match_oracle(binding):
+    """FP64 steps in renormalisation blocks: 1, 15, 16, 17 and 35 steps (tails, one block, a
+    block and a tail, two blocks and a tail) against the oracle, with Dirichlet faces and
+    sources, and two calls in a row (each call ends with the true field)."""
+    rng = np.random.default_rng(9)
+    w = inputs.random_problem(rng, 24, 21, 19, 3, n_agents=80, dirichlet=True)
+    w.D = np.array([1e5, 1e3, 1e2])
+    w.lam = np.array([0.1, 0.01, 1e-3])
+    p = orc(w)
+    for n in (1, 15, 16, 17, 35):
+        sim = binding.BioFVM.from_workload(w, precision="fp64")
+        sim.step(n)
+        got = sim.density()
+        sim.step(2)
+        got2 = sim.density()
+        sim.close()
+        ref = p.step(w.rho0, n)
+        assert rel_err(got, ref) <= 1e-12, n
+        assert rel_err(got2, p.step(ref, 2)) <= 1e-12, n
 
 
 def test_sources_can_be_replaced_and_cleared(binding):
