@@ -43,7 +43,7 @@ FLOPS_PER_ELEMENT_SWEEP = 5
 # roofline names, from one ncu capture of this bench's 400^3 x 4 workload; valid only for the
 # kernel version they were taken on (re-measure whenever that kernel changes).
 MEASURED_TRAFFIC = {
-    ("f64", "z-sweep"): 2707706624 + 2822000640,   # stream_sweep_kernel<double, 2>
+    ("f64", "x-sweep"): 2831562240 + 2815582464,   # stream_sweep_kernel<double, 1>, with Src
     ("f32", "x-sweep"): 1090899968 + 963519488,    # sweep_pipe_kernel<float, 32, 0>
 }
 
