@@ -114,7 +114,7 @@ def gaussian_blobs(rng, nx, ny, nz, ns, dx, n_blobs=64, sigma=(100.0, 400.0), am
 
 
 # --------------------------------------------------------------------------------------------
-# The five workloads.  `shape` overrides the grid (parity tests at reduced size keep every
+# The workloads.  `shape` overrides the grid (parity tests at reduced size keep every
 # other recipe); `with_field=False` skips the initial field for callers that draw their own.
 # --------------------------------------------------------------------------------------------
 
@@ -171,7 +171,32 @@ def workload(k: int, shape=None, n_agents=None, with_field=True, field_dtype=np.
         w.extra["probe_target"] = rng.uniform(0.0, 38.0, n_probe)
         w.extra["checkpoint_every"] = 20
         return w
+    if k == 6:
+        # End-to-end run of Sect. 5.3: a 5 mm cube (250^3 voxels of 20 um), one substrate,
+        # 1000 basic agents -- 500 bulk sources, 500 uptake sinks -- at seeded voxels, 500 steps
+        # (5 min), a Gaussian initial profile (centred, sigma 1 mm, peak 38).
+        nx, ny, nz = shape or (250, 250, 250)
+        w = Workload("e2e_5mm_s1", nx, ny, nz, 1, 20.0, 0.01, np.array([1e5]), np.array([0.1]),
+                     500)
+        if with_field:
+            w.rho0 = gaussian_profile(nx, ny, nz, w.dx, 1000.0, TARGET_DENSITY, field_dtype)
+        na = 1000 if n_agents is None else n_agents
+        w.voxel = rng.integers(0, nx * ny * nz, size=na, dtype=np.int64)
+        src = np.arange(na) < na // 2
+        w.secretion = np.where(src, 10.0, 0.0)[:, None]
+        w.target = np.full((na, 1), TARGET_DENSITY)
+        w.uptake = np.where(src, 0.0, 1.0)[:, None]
+        return w
     raise ValueError(f"unknown workload {k}")
+
+
+def gaussian_profile(nx, ny, nz, dx, sigma, peak, dtype=np.float64):
+    """A Gaussian centred in the box, voxel centres at (i + 1/2) dx: [nz, ny, nx, 1]."""
+    def axis(n):
+        c = (np.arange(n) + 0.5) * dx - 0.5 * n * dx
+        return np.exp(-0.5 * (c / sigma) ** 2)
+    gx, gy, gz = axis(nx), axis(ny), axis(nz)
+    return (peak * gz[:, None, None] * gy[None, :, None] * gx[None, None, :])[..., None].astype(dtype)
 
 
 def batched_workloads(n_env=256, edge=(32, 192), ns=(1, 8), seed=None, n_steps=50,

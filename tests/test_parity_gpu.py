@@ -133,6 +133,31 @@ def test_step_kernels_one_by_one_equal_step(binding, prec):
             assert rel_err(a, b) <= 1e-14, n
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_paper_e2e_workload_reduced(binding, prec):
+    """The Sect. 5.3 end-to-end recipe (Gaussian profile, 500 sources and 500 sinks) at 48^3,
+    60 steps, against the oracle."""
+    w = inputs.workload(6, shape=(48, 48, 48))
+    ref = orc(w).step(w.rho0, 60)
+    got = gpu_run(binding, w, prec, 60)
+    assert rel_err(got, ref) <= TOL[prec]
+
+
+@pytest.mark.slow
+def test_paper_e2e_workload_full_size_first_steps(binding):
+    """The full 5 mm cube (250^3), FP64, 5 steps against the oracle (7.8e7 element updates on
+    the CPU), then 500 steps: finite, within the source-free bounds [0, 38]."""
+    w = inputs.workload(6)
+    ref = orc(w).step(w.rho0, 5)
+    sim = binding.BioFVM.from_workload(w, precision="fp64")
+    sim.step(5)
+    assert rel_err(sim.density(), ref) <= 1e-12
+    sim.step(495)
+    out = sim.density()
+    sim.close()
+    assert np.isfinite(out).all() and out.min() >= 0.0 and out.max() <= 38.0 * (1 + 1e-12)
+
+
 def test_renormalisation_blocks_and_tails_match_oracle(binding):
     """FP64 steps in renormalisation blocks: 1, 15, 16, 17 and 35 steps (tails, one block, a
     block and a tail, two blocks and a tail) against the oracle, with Dirichlet faces and
