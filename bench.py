@@ -223,6 +223,9 @@ def run_gpu(args):
     if rank == 0 and not args.no_paper_e2e and not args.shape and not args.only \
             and not args.batch_only:
         results["paper_e2e"] = {p: run_paper_e2e(p, stream, dev) for p in ("fp64", "fp32")}
+    if rank == 0 and not args.no_adjoint and not args.shape and not args.only \
+            and not args.batch_only:
+        results["adjoint"] = {p: run_adjoint(p, dev) for p in ("fp64", "fp32")}
     if world > 1:
         dist.destroy_process_group()
     return rank, world, results
@@ -317,6 +320,49 @@ def run_paper_e2e(prec, stream, dev):
                         "1000 agents (500 sources, 500 sinks), 500 steps, Gaussian profile"}
 
 
+def run_adjoint(prec, dev):
+    """Workload 5 (128^3 x 2, 200 steps, checkpoints every 20): the forward run alone, then the
+    forward run plus the gradients of a probe loss with respect to the initial field, the
+    per-voxel secretion rates, D and lambda (LODSteps: checkpoints, recomputation with
+    biofvm_step_save, biofvm_adjoint_step), timed on the host with the device synchronised."""
+    import torch
+
+    from paper_2602_05017_gb300 import binding, inputs
+    from paper_2602_05017_gb300.adjoint import lod_steps
+    w = inputs.workload(5)
+    n, K = w.n_steps, w.extra["checkpoint_every"]
+    fdt = torch.float64 if prec == "fp64" else torch.float32
+    sim = binding.BioFVM(w.nx, w.ny, w.nz, w.ns, w.dx, w.dt, w.D, w.lam, precision=prec)
+    agents = dict(voxel=w.voxel, target=w.target, uptake=w.uptake, weight=w.weight)
+    pr = torch.as_tensor(w.extra["probe_index"], device=dev)
+    tg = torch.as_tensor(w.extra["probe_target"], device=dev)
+
+    def run(steps, backward):
+        rho0 = torch.tensor(w.rho0, dtype=torch.float64, device=dev, requires_grad=True)
+        sec = torch.tensor(w.secretion, dtype=torch.float64, device=dev, requires_grad=True)
+        D = torch.tensor(w.D, dtype=torch.float64, device=dev, requires_grad=True)
+        lam = torch.tensor(w.lam, dtype=torch.float64, device=dev, requires_grad=True)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        out = lod_steps(rho0.to(fdt), sec, D, lam, sim, agents, steps, K)
+        loss = ((out.reshape(-1).double()[pr] - tg) ** 2).sum()
+        if backward:
+            loss.backward()
+        torch.cuda.synchronize(dev)
+        return time.perf_counter() - t0
+
+    run(K, True)  # warm-up: graphs, buffers
+    t_fwd = min(run(n, False) for _ in range(2))
+    t_all = min(run(n, True) for _ in range(2))
+    sim.close()
+    return {"seconds_forward": t_fwd, "seconds_forward_and_gradients": t_all,
+            "forward_vs_per_s": w.n_vs * n / t_fwd,
+            "gradient_vs_per_s": w.n_vs * n / (t_all - t_fwd),
+            "dtype": prec.replace("fp", "f"),
+            "workload": "128^3 x 2, 200 steps, checkpoints every 20, 4096-probe loss; gradients "
+                        "w.r.t. initial field, secretion rates, D, lambda"}
+
+
 def _stage_step(sim, ev, stream, renorm):
     """One step as the three kernels biofvm_step launches, with an event between launches: the
     z-sweep of a step inside a renormalisation block (stage 12, FP64 leaves the field scaled)
@@ -397,6 +443,8 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-paper-e2e", action="store_true",
                     help="skip the Sect. 5.3 end-to-end run (time to solution)")
+    ap.add_argument("--no-adjoint", action="store_true",
+                    help="skip the adjoint run (workload 5: forward and gradients)")
     ap.add_argument("--batch-envs", type=int, default=256)
     ap.add_argument("--batch-steps", type=int, default=50)
     ap.add_argument("--batch-only", action="store_true",
@@ -446,6 +494,8 @@ def main():
                          "fp32": dict(zip(("x", "y", "z"), res["fp32"]["kernel_ms"]))}
     if "paper_e2e" in res:
         line["paper_e2e"] = res["paper_e2e"]
+    if "adjoint" in res:
+        line["adjoint"] = res["adjoint"]
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(args)
     print(json.dumps(line), flush=True)
