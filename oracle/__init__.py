@@ -60,9 +60,9 @@ def _get():
         lib.oracle_sweep.argtypes = [i, i, i, i, i, d, d, _dp, _dp, _dp]
         lib.oracle_dirichlet.argtypes = [i, i, i, i, _u8p, _dp, _dp]
         lib.oracle_sources.argtypes = [i, i, i, i, d, L, _i64p, _dp, _dp, _dp, _dp, _dp]
-        lib.oracle_step.argtypes = [i, i, i, i, d, d, _dp, _dp, _u8p, _dp, L, _i64p, _dp, _dp,
+        lib.oracle_step.argtypes = [i, i, i, i, _dp, d, _dp, _dp, _u8p, _dp, L, _i64p, _dp, _dp,
                                     _dp, _dp, i, _dp]
-        lib.oracle_adjoint_step.argtypes = [i, i, i, i, d, d, _dp, _dp, _u8p, _dp, L, _i64p, _dp,
+        lib.oracle_adjoint_step.argtypes = [i, i, i, i, _dp, d, _dp, _dp, _u8p, _dp, L, _i64p, _dp,
                                             _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
         for f in (lib.oracle_axis_coefficients, lib.oracle_thomas, lib.oracle_sweep,
                   lib.oracle_dirichlet, lib.oracle_sources, lib.oracle_step,
@@ -92,12 +92,15 @@ class Problem:
     """Grid, parameters, boundary and agents of one microenvironment (all FP64, host).
 
     Field layout is ``rho[z, y, x, s]`` (substrates interleaved per voxel, x fastest of the axes).
+    dx: the voxel spacing, or three spacings (x, y, z) for an anisotropic grid.
     """
 
     def __init__(self, nx, ny, nz, ns, dx, dt, D, lam, dirichlet_on=None, dirichlet_value=None,
                  voxel=None, secretion=None, target=None, uptake=None, weight=None):
         self.nx, self.ny, self.nz, self.ns = int(nx), int(ny), int(nz), int(ns)
-        self.dx, self.dt = float(dx), float(dt)
+        self.h3 = np.ascontiguousarray(np.broadcast_to(np.asarray(dx, dtype=np.float64),
+                                                       (3,)).copy())
+        self.dx, self.dt = float(self.h3[0]), float(dt)
         self.D = _f64(D, self.ns)
         self.lam = _f64(lam, self.ns)
         if dirichlet_on is not None:
@@ -136,7 +139,8 @@ class Problem:
 
     def sweep(self, axis, rho):
         out = self._field(rho)
-        _check(_get().oracle_sweep(axis, self.nx, self.ny, self.nz, self.ns, self.dx, self.dt,
+        _check(_get().oracle_sweep(axis, self.nx, self.ny, self.nz, self.ns,
+                                   float(self.h3[axis]), self.dt,
                                    _ptr(self.D), _ptr(self.lam), _ptr(out)), "sweep")
         return out
 
@@ -154,7 +158,7 @@ class Problem:
 
     def step(self, rho, n_steps=1):
         out = self._field(rho)
-        _check(_get().oracle_step(self.nx, self.ny, self.nz, self.ns, self.dx, self.dt,
+        _check(_get().oracle_step(self.nx, self.ny, self.nz, self.ns, _ptr(self.h3), self.dt,
                                   _ptr(self.D), _ptr(self.lam), _ptr(self.on, _u8p),
                                   _ptr(self.val), *self._agents(), int(n_steps), _ptr(out)), "step")
         return out
@@ -170,7 +174,7 @@ class Problem:
         dsec = np.zeros(na * self.ns)
         dupt = np.zeros(na * self.ns)
         _check(_get().oracle_adjoint_step(
-            self.nx, self.ny, self.nz, self.ns, self.dx, self.dt, _ptr(self.D), _ptr(self.lam),
+            self.nx, self.ny, self.nz, self.ns, _ptr(self.h3), self.dt, _ptr(self.D), _ptr(self.lam),
             _ptr(self.on, _u8p), _ptr(self.val), *self._agents(), _ptr(rho_in), _ptr(gout),
             _ptr(gin), _ptr(dD), _ptr(dl), _ptr(dsec) if na else None,
             _ptr(dupt) if na else None), "adjoint_step")

@@ -251,13 +251,15 @@ int oracle_sources(int nx, int ny, int nz, int ns, double dt, i64 n_agents,
   return 0;
 }
 
-/* n_steps full time steps, in place on rho. */
-int oracle_step(int nx, int ny, int nz, int ns, double dx, double dt,
+/* n_steps full time steps, in place on rho.  h3: the voxel spacing along x, y
+ * and z (the paper's grids are isotropic, h3[0] = h3[1] = h3[2]; each axis's
+ * App. A system takes r = D dt / h^2 with its own h). */
+int oracle_step(int nx, int ny, int nz, int ns, const double *h3, double dt,
                 const double *D, const double *lambda, const unsigned char *on,
                 const double *value, i64 n_agents, const i64 *voxel,
                 const double *sec, const double *tgt, const double *upt,
                 const double *w, int n_steps, double *rho) {
-  if (n_steps < 0) return -1;
+  if (n_steps < 0 || !h3) return -1;
   for (int k = 0; k < n_steps; k++) {
     int rc = oracle_sources(nx, ny, nz, ns, dt, n_agents, voxel, sec, tgt, upt,
                             w, rho);
@@ -265,7 +267,7 @@ int oracle_step(int nx, int ny, int nz, int ns, double dx, double dt,
     for (int axis = 0; axis < 3; axis++) {
       rc = oracle_dirichlet(nx, ny, nz, ns, on, value, rho);
       if (rc) return rc;
-      rc = oracle_sweep(axis, nx, ny, nz, ns, dx, dt, D, lambda, rho);
+      rc = oracle_sweep(axis, nx, ny, nz, ns, h3[axis], dt, D, lambda, rho);
       if (rc) return rc;
     }
     rc = oracle_dirichlet(nx, ny, nz, ns, on, value, rho);
@@ -325,7 +327,7 @@ static void sweep_param_grad(int axis, int nx, int ny, int nz, int ns,
  * uptake rates dsec[n_agents*ns], dupt[n_agents*ns] (either may be NULL).
  * Each 1D matrix is symmetric, so A^-T = A^-1 and the adjoint sweeps are the
  * forward sweeps run in reverse stage order. */
-int oracle_adjoint_step(int nx, int ny, int nz, int ns, double dx, double dt,
+int oracle_adjoint_step(int nx, int ny, int nz, int ns, const double *h3, double dt,
                         const double *D, const double *lambda,
                         const unsigned char *on, const double *value,
                         i64 n_agents, const i64 *voxel, const double *sec,
@@ -333,7 +335,7 @@ int oracle_adjoint_step(int nx, int ny, int nz, int ns, double dx, double dt,
                         const double *rho_in, const double *gbar_out,
                         double *gbar_in, double *dD, double *dlambda,
                         double *dsec, double *dupt) {
-  if (!check_grid(nx, ny, nz, ns) || !rho_in || !gbar_out || !gbar_in ||
+  if (!check_grid(nx, ny, nz, ns) || !h3 || !rho_in || !gbar_out || !gbar_in ||
       !dD || !dlambda || n_agents < 0)
     return -1;
   i64 nel = (i64)nx * ny * nz * ns;
@@ -354,26 +356,26 @@ int oracle_adjoint_step(int nx, int ny, int nz, int ns, double dx, double dt,
                        u1);
   memcpy(u3, u1, bytes);
   rc |= oracle_dirichlet(nx, ny, nz, ns, on, value, u3);
-  rc |= oracle_sweep(0, nx, ny, nz, ns, dx, dt, D, lambda, u3);
+  rc |= oracle_sweep(0, nx, ny, nz, ns, h3[0], dt, D, lambda, u3);
   memcpy(u5, u3, bytes);
   rc |= oracle_dirichlet(nx, ny, nz, ns, on, value, u5);
-  rc |= oracle_sweep(1, nx, ny, nz, ns, dx, dt, D, lambda, u5);
+  rc |= oracle_sweep(1, nx, ny, nz, ns, h3[1], dt, D, lambda, u5);
   memcpy(u7, u5, bytes);
   rc |= oracle_dirichlet(nx, ny, nz, ns, on, value, u7);
-  rc |= oracle_sweep(2, nx, ny, nz, ns, dx, dt, D, lambda, u7);
+  rc |= oracle_sweep(2, nx, ny, nz, ns, h3[2], dt, D, lambda, u7);
   if (rc) goto done;
 
   /* reverse: gbar_in walks back through B, Z^-1, B, Y^-1, B, X^-1, B, Src */
   memcpy(gbar_in, gbar_out, bytes);
   dirichlet_mask(nx, ny, nz, ns, on, gbar_in);
-  rc |= oracle_sweep(2, nx, ny, nz, ns, dx, dt, D, lambda, gbar_in);
-  sweep_param_grad(2, nx, ny, nz, ns, dx, dt, gbar_in, u7, dD, dlambda);
+  rc |= oracle_sweep(2, nx, ny, nz, ns, h3[2], dt, D, lambda, gbar_in);
+  sweep_param_grad(2, nx, ny, nz, ns, h3[2], dt, gbar_in, u7, dD, dlambda);
   dirichlet_mask(nx, ny, nz, ns, on, gbar_in);
-  rc |= oracle_sweep(1, nx, ny, nz, ns, dx, dt, D, lambda, gbar_in);
-  sweep_param_grad(1, nx, ny, nz, ns, dx, dt, gbar_in, u5, dD, dlambda);
+  rc |= oracle_sweep(1, nx, ny, nz, ns, h3[1], dt, D, lambda, gbar_in);
+  sweep_param_grad(1, nx, ny, nz, ns, h3[1], dt, gbar_in, u5, dD, dlambda);
   dirichlet_mask(nx, ny, nz, ns, on, gbar_in);
-  rc |= oracle_sweep(0, nx, ny, nz, ns, dx, dt, D, lambda, gbar_in);
-  sweep_param_grad(0, nx, ny, nz, ns, dx, dt, gbar_in, u3, dD, dlambda);
+  rc |= oracle_sweep(0, nx, ny, nz, ns, h3[0], dt, D, lambda, gbar_in);
+  sweep_param_grad(0, nx, ny, nz, ns, h3[0], dt, gbar_in, u3, dD, dlambda);
   dirichlet_mask(nx, ny, nz, ns, on, gbar_in);
   if (rc) goto done;
 

@@ -42,6 +42,7 @@ class Workload:
     target: Optional[np.ndarray] = None           # [n_agents, ns]
     uptake: Optional[np.ndarray] = None           # [n_agents, ns]
     weight: Optional[np.ndarray] = None           # [n_agents] or None (=> 1)
+    spacing: Optional[tuple] = None               # (dx, dy, dz) of an anisotropic grid, or None
     extra: dict = field(default_factory=dict)
 
     @property
@@ -58,7 +59,8 @@ class Workload:
         return 0 if self.voxel is None else int(self.voxel.size)
 
     def oracle_kwargs(self):
-        return dict(nx=self.nx, ny=self.ny, nz=self.nz, ns=self.ns, dx=self.dx, dt=self.dt,
+        return dict(nx=self.nx, ny=self.ny, nz=self.nz, ns=self.ns,
+                    dx=self.dx if self.spacing is None else self.spacing, dt=self.dt,
                     D=self.D, lam=self.lam, dirichlet_on=self.dirichlet_on,
                     dirichlet_value=self.dirichlet_value, voxel=self.voxel,
                     secretion=self.secretion, target=self.target, uptake=self.uptake,

@@ -84,8 +84,9 @@ def dense_step(w, rho):
         return u
 
     rho = B(rho)
+    h3 = (w.dx,) * 3 if w.spacing is None else w.spacing
     for axis in range(3):
-        rho = B(dense_sweep(axis, rho, w.D, w.lam, w.dt, w.dx))
+        rho = B(dense_sweep(axis, rho, w.D, w.lam, w.dt, h3[axis]))
     return rho
 
 
@@ -229,6 +230,61 @@ def test_cosine_modes_decay_by_closed_form(k):
         f = mode_factor((nx, ny, nz), k, D[s], lam[s], w.dt, w.dx) ** 3
         # rounding scales with the amplitude before the steps (1), not with the decayed one
         np.testing.assert_allclose(out[..., s], f * base, rtol=1e-12, atol=1e-14)
+
+
+# ---------------------------------------------------------------------------------------------
+# Anisotropic spacing (dx, dy, dz): each axis's App. A system takes r = D dt / h^2 with its own h.
+# ---------------------------------------------------------------------------------------------
+
+def test_isotropic_spacing_triple_equals_scalar():
+    w = inputs.random_problem(RNG, 7, 6, 5, 2, n_agents=8, dirichlet=True)
+    a = P(w).step(w.rho0, 2)
+    w.spacing = (w.dx, w.dx, w.dx)
+    assert np.array_equal(P(w).step(w.rho0, 2), a)
+
+
+@pytest.mark.parametrize("dirichlet", [False, True])
+def test_anisotropic_step_matches_dense_composition(dirichlet):
+    w = inputs.random_problem(RNG, 5, 4, 6, 2, n_agents=7, dirichlet=dirichlet)
+    w.spacing = (10.0, 25.0, 40.0)
+    np.testing.assert_allclose(P(w).step(w.rho0, 1), dense_step(w, w.rho0), rtol=1e-12,
+                               atol=1e-12)
+
+
+@pytest.mark.parametrize("k", [(1, 0, 0), (0, 2, 0), (0, 0, 3), (2, 1, 4)])
+def test_anisotropic_cosine_modes_decay_by_closed_form(k):
+    """prod_d 1 / (1 + lambda dt/3 + 2 (D dt / h_d^2) (1 - cos(k_d pi / n_d)))."""
+    nx, ny, nz = 9, 8, 10
+    h3 = (12.0, 20.0, 31.0)
+    D, lam, dt = 2e4, 0.3, 0.01
+    w = inputs.Workload("cos", nx, ny, nz, 1, h3[0], dt, np.array([D]), np.array([lam]), 1)
+    w.spacing = h3
+    base = cosine_mode(nx, ny, nz, k)
+    out = P(w).step(base[..., None], 2)[..., 0]
+    f = 1.0
+    for nd, kd, hd in zip((nx, ny, nz), k, h3):
+        f /= 1.0 + lam * dt / 3.0 + 2.0 * (D * dt / hd ** 2) * (1.0 - math.cos(kd * math.pi / nd))
+    np.testing.assert_allclose(out, f ** 2 * base, rtol=1e-12, atol=1e-14)
+
+
+def test_anisotropic_adjoint_D_matches_finite_differences():
+    w = inputs.random_problem(RNG, 6, 5, 4, 2, n_agents=5, dirichlet=True)
+    w.spacing = (15.0, 22.0, 30.0)
+    probes = RNG.choice(w.rho0.size, 20, replace=False)
+    targets = RNG.uniform(0, 38, 20)
+    L0, _, dD, dl, _ = _loss_and_grads(w, 2, probes, targets)
+    import copy
+    for s in range(2):
+        h = 1e-6 * max(1.0, abs(w.D[s]))
+        up, dn = copy.deepcopy(w), copy.deepcopy(w)
+        up.D = w.D.copy()
+        dn.D = w.D.copy()
+        up.D[s] += h
+        dn.D[s] -= h
+        fd = (_loss_and_grads(up, 2, probes, targets)[0] -
+              _loss_and_grads(dn, 2, probes, targets)[0]) / (2 * h)
+        noise = 8 * np.finfo(float).eps * abs(L0) / h
+        assert dD[s] == pytest.approx(fd, rel=1e-6, abs=noise), s
 
 
 def test_zero_diffusion_is_pointwise_division():
