@@ -125,6 +125,13 @@ biofvm_status biofvm_density(biofvm_t *h, void *dst, int dst_on_device);
 biofvm_status biofvm_set_params(biofvm_t *h, const double *D,
                                 const double *lambda);
 
+/* Anisotropic grid: set the voxel spacing along x, y and z (um) and recompute
+ * the App. A constants, each axis taking r = D dt / h^2 with its own h.  The
+ * paper's grids are isotropic (biofvm_create's dx on all three axes); this is
+ * an extension.  The adjoint's D gradient follows (per-axis dt / h^2).
+ * Errors: ARG (a spacing not finite and > 0; nothing changed), CUDA. */
+biofvm_status biofvm_set_spacing(biofvm_t *h, double dx, double dy, double dz);
+
 /* Run exactly one stage of the step in place, for stage-by-stage checks:
  * stage 0 = Src then B, 1 = X^-1 then B, 2 = Y^-1 then B, 3 = Z^-1 then B,
  * 4 = the source update alone (no Dirichlet), 5 = X^-1 alone, 6 = Y^-1

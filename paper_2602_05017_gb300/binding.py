@@ -70,6 +70,7 @@ def load():
         "biofvm_density": (st, [vp, vp, ctypes.c_int]),
         "biofvm_set_params": (st, [vp, dp, dp]),
         "biofvm_run_stage": (st, [vp, ctypes.c_int]),
+        "biofvm_set_spacing": (st, [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
         "biofvm_sync": (st, [vp]),
         "biofvm_density_ptr": (st, [vp, ctypes.POINTER(vp)]),
         "biofvm_launches_per_step": (ctypes.c_int, [vp]),
@@ -262,6 +263,10 @@ class BioFVM:
             None if dsec is None else self._dev(dsec, dsec.numel(), torch.float64),
             self._dev(saved, 4 * self.n_elem, fd)), self.lib)
 
+    def set_spacing(self, dx, dy, dz):
+        """Anisotropic grid: voxel spacing along x, y, z (recomputes the constants)."""
+        _check(self.lib.biofvm_set_spacing(self.h, float(dx), float(dy), float(dz)), self.lib)
+
     def run_stage(self, stage):
         _check(self.lib.biofvm_run_stage(self.h, int(stage)), self.lib)
 
@@ -288,6 +293,8 @@ class BioFVM:
         """Create, upload the initial field and the agents of an ``inputs.Workload``."""
         sim = cls(w.nx, w.ny, w.nz, w.ns, w.dx, w.dt, w.D, w.lam, w.dirichlet_on,
                   w.dirichlet_value, precision=precision, stream=stream)
+        if w.spacing is not None:
+            sim.set_spacing(*w.spacing)
         if w.rho0 is not None:
             sim.set_density(w.rho0)
         if w.n_agents:

@@ -94,6 +94,7 @@ struct XPlan {
 struct biofvm {
   biofvm_grid g{};
   double dx = 0, dt = 0;
+  double h3[3] = {0, 0, 0};  // voxel spacing along x, y, z (all dx unless set apart)
   std::vector<double> D, lam;
   std::vector<uint8_t> dir_on;
   std::vector<double> dir_val;
@@ -119,6 +120,7 @@ struct biofvm {
   int stream_ctas_per_sm = 3;
   int stream_ks = 64;        // FP64: positions of each line's intermediate kept in shared memory
   int stream32_enabled = 0;  // FP32 streaming sweeps instead of the pipelined ones
+  int pipe_chunk = 0;        // FP32 pipelined sweeps: chunk length (0: the planner's)
   DevBuf scratch;            // FP32 streaming: forward intermediate, field-sized
   int forced = 0;  // chunk lengths fixed by the caller (batched environments)
   unsigned generation = 0;  // bumped when kernel arguments change (sources, constants)
@@ -186,7 +188,7 @@ void axis_tables(const biofvm *h, int axis, int T, int m, bool defect, std::vect
          *cw = cfix + 2 * (size_t)S;
   std::vector<double> ci(n), cm(n);
   for (int s = 0; s < S; s++) {
-    const double r = h->D[s] * h->dt / (h->dx * h->dx);
+    const double r = h->D[s] * h->dt / (h->h3[axis] * h->h3[axis]);
     const double lam3 = h->lam[s] * h->dt / 3.0;
     const double c = 1.0 / (1.0 + lam3);
     const double scale = defect ? -c * r : 1.0;
@@ -382,7 +384,11 @@ void plan_pipe(biofvm *h, int axis) {
   const int n = axis_len(h, axis);
   if (esz != 4) return;  // FP64 streams whole lines instead
   ColPlan cp;
-  if (!plan_col(n, false, cp)) return;
+  if (h->pipe_chunk > 0) {  // chunk length chosen by the caller (tuning)
+    if (!plan_col(n, false, cp, std::min(h->pipe_chunk, n))) return;
+  } else if (!plan_col(n, false, cp)) {
+    return;
+  }
   if ((cp.T + 1) * 32 > pipe_max_threads_f32(cp.maxm)) return;
   p.T = cp.T;
   p.m = cp.m;
@@ -517,7 +523,7 @@ void stream_tables(const biofvm *h, int axis, std::vector<double> &tt, double *s
   std::vector<double> rr(S);
   k0 = 0;
   for (int s = 0; s < S; s++) {
-    const double r = h->D[s] * h->dt / (h->dx * h->dx);
+    const double r = h->D[s] * h->dt / (h->h3[axis] * h->h3[axis]);
     const double lam3 = h->lam[s] * h->dt / 3.0;
     axis_constants(n, r, lam3, inv.data(), mul.data());
     double sg = inv[0];
@@ -555,7 +561,7 @@ void stream_consts_f32(const biofvm *h, int axis, const std::vector<double> &t, 
   const int n = axis_len(h, axis), S = h->g.n_sub;
   k0 = n < 3 ? n : 0;
   for (int s = 0; s < S; s++) {
-    const double r = h->D[s] * h->dt / (h->dx * h->dx);
+    const double r = h->D[s] * h->dt / (h->h3[axis] * h->h3[axis]);
     const double lam3 = h->lam[s] * h->dt / 3.0;
     const double b = 1.0 + 2.0 * r + lam3;
     const double den = 0.5 * (b + std::sqrt((1.0 + lam3) * (1.0 + 4.0 * r + lam3)));
@@ -952,6 +958,7 @@ biofvm_status create_impl(const biofvm_grid *grid, double dx, double dt, const d
   if (!h) return fail(BIOFVM_ERR_OOM, "host allocation failed");
   h->g = g;
   h->dx = dx;
+  h->h3[0] = h->h3[1] = h->h3[2] = dx;
   h->dt = dt;
   h->D.assign(D, D + g.n_sub);
   h->lam.assign(lambda, lambda + g.n_sub);
@@ -1032,13 +1039,15 @@ biofvm_status create_impl(const biofvm_grid *grid, double dx, double dt, const d
                 cudaGetErrorString(e));
   }
   h->num_sms = prop.multiProcessorCount;
+  // sweep selection and tuning knobs (environment, read once per handle)
   if (const char *env = getenv("BIOFVM_PIPELINE")) h->pipe_enabled = atoi(env) != 0;
-  if (h->pipe_enabled && !h->forced)
-    for (int axis = 0; axis < 3; axis++) plan_pipe(h, axis);
+  if (const char *env = getenv("BIOFVM_PIPE_CHUNK")) h->pipe_chunk = atoi(env);
   if (const char *env = getenv("BIOFVM_STREAM")) h->stream_enabled = atoi(env) != 0;
   if (const char *env = getenv("BIOFVM_STREAM_CTAS")) h->stream_ctas_per_sm = atoi(env);
   if (const char *env = getenv("BIOFVM_STREAM32")) h->stream32_enabled = atoi(env) != 0;
   if (const char *env = getenv("BIOFVM_STREAM_KS")) h->stream_ks = atoi(env) / 16 * 16;
+  if (h->pipe_enabled && !h->forced)
+    for (int axis = 0; axis < 3; axis++) plan_pipe(h, axis);
   if (!h->forced)
     for (int axis = 0; axis < 3; axis++) plan_stream(h, axis);
   if ((st = upload_doubles(h, h->dir_val_d, h->dir_val)) != BIOFVM_OK ||
@@ -1097,6 +1106,17 @@ biofvm_status biofvm_set_params(biofvm_t *h, const double *D, const double *lamb
   CK(cudaSetDevice(h->device));
   h->D.assign(D, D + h->g.n_sub);
   h->lam.assign(lambda, lambda + h->g.n_sub);
+  return upload_constants(h);
+}
+
+biofvm_status biofvm_set_spacing(biofvm_t *h, double dx, double dy, double dz) {
+  if (!h) return fail(BIOFVM_ERR_ARG, "NULL handle");
+  if (!(dx > 0 && dy > 0 && dz > 0 && std::isfinite(dx) && std::isfinite(dy) && std::isfinite(dz)))
+    return fail(BIOFVM_ERR_ARG, "spacings must be finite and > 0");
+  CK(cudaSetDevice(h->device));
+  h->h3[0] = dx;
+  h->h3[1] = dy;
+  h->h3[2] = dz;
   return upload_constants(h);
 }
 
@@ -1343,7 +1363,7 @@ biofvm_status biofvm_adjoint_step(biofvm_t *h, const void *grad_out, void *grad_
     r.used = (long long)r.nblocks * kReduceThreads / S * S;
     r.partial = static_cast<double *>(h->partial.p);
     r.scale_lambda = -h->dt / 3.0;
-    r.scale_D = -h->dt / (h->dx * h->dx);
+    r.scale_D = -h->dt / (h->h3[axis] * h->h3[axis]);
     r.dlambda = dlambda;
     r.dD = dD;
     return h->prec == BIOFVM_FP64 ? launch_adj_reduce_f64(r, st) : launch_adj_reduce_f32(r, st);

@@ -104,6 +104,30 @@ def test_one_adjoint_step_matches_cpu_adjoint(torch, monkeypatch, stream):
     assert rel(ds.cpu().numpy(), ds_c.reshape(-1)) <= 1e-10
 
 
+def test_anisotropic_adjoint_matches_cpu_adjoint(torch):
+    """dx != dy != dz: one adjoint step (D gradient scaled per axis) against the CPU adjoint."""
+    from paper_2602_05017_gb300 import binding
+    w, _, _ = _problem(11, shape=(14, 12, 10))
+    w.spacing = (11.0, 19.0, 27.0)
+    p = oracle.Problem(**w.oracle_kwargs())
+    gout = np.random.default_rng(12).normal(size=w.shape)
+    gin_c, dD_c, dl_c, ds_c, _ = p.adjoint_step(w.rho0, gout)
+    sim = binding.BioFVM.from_workload(w, precision="fp64")
+    saved = torch.empty(4 * sim.n_elem, dtype=torch.float64, device="cuda")
+    sim.step_save(saved)
+    g = torch.tensor(gout, device="cuda")
+    dD = torch.zeros(w.ns, dtype=torch.float64, device="cuda")
+    dl = torch.zeros_like(dD)
+    ds = torch.zeros(w.n_agents * w.ns, dtype=torch.float64, device="cuda")
+    sim.adjoint_step(g, g, dD, dl, ds, saved)
+    sim.sync()
+    sim.close()
+    assert rel(g.cpu().numpy(), gin_c) <= 1e-10
+    assert rel(dD.cpu().numpy(), dD_c) <= 1e-10
+    assert rel(dl.cpu().numpy(), dl_c) <= 1e-10
+    assert rel(ds.cpu().numpy(), ds_c.reshape(-1)) <= 1e-10
+
+
 @pytest.mark.parametrize("dirichlet", [False, True])
 def test_multi_step_gradients_match_cpu_adjoint(torch, dirichlet):
     w, probes, targets = _problem(3, shape=(17, 14, 12), dirichlet=dirichlet)

@@ -18,6 +18,8 @@ from paper_2602_05017_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 TOL = {"fp64": 1e-12, "fp32": 1e-5}
+# sweep implementations selected at create: BIOFVM_PIPELINE, BIOFVM_STREAM, BIOFVM_STREAM32
+PATHS = {"plain": ("0", "0", "0"), "pipe": ("1", "0", "0"), "stream": ("1", "1", "1")}
 
 
 @pytest.fixture(scope="module")
@@ -156,6 +158,37 @@ def test_paper_e2e_workload_full_size_first_steps(binding):
     out = sim.density()
     sim.close()
     assert np.isfinite(out).all() and out.min() >= 0.0 and out.max() <= 38.0 * (1 + 1e-12)
+
+
+@pytest.mark.parametrize("path", list(PATHS))
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_anisotropic_spacing_matches_oracle(binding, monkeypatch, path, prec):
+    """dx != dy != dz (biofvm_set_spacing) on every sweep implementation, with Dirichlet faces
+    and sources, over 20 steps (FP64: a renormalisation block and a tail)."""
+    if prec == "fp64" and path == "pipe":
+        pytest.skip("the pipelined sweep is FP32 only")
+    monkeypatch.setenv("BIOFVM_PIPELINE", PATHS[path][0])
+    monkeypatch.setenv("BIOFVM_STREAM", PATHS[path][1])
+    monkeypatch.setenv("BIOFVM_STREAM32", PATHS[path][2])
+    rng = np.random.default_rng(21)
+    w = inputs.random_problem(rng, 45, 38, 33, 3, n_agents=90, dirichlet=True)
+    w.spacing = (12.0, 20.0, 33.0)
+    ref = orc(w).step(w.rho0, 20)
+    got = gpu_run(binding, w, prec, 20)
+    assert rel_err(got, ref) <= TOL[prec]
+
+
+def test_set_spacing_rejects_bad_values_and_changes_nothing(binding):
+    rng = np.random.default_rng(22)
+    w = inputs.random_problem(rng, 10, 9, 8, 2)
+    sim = binding.BioFVM.from_workload(w, precision="fp64")
+    for bad in ((0.0, 1.0, 1.0), (1.0, -2.0, 1.0), (1.0, 1.0, float("nan"))):
+        with pytest.raises(binding.BioFVMError):
+            sim.set_spacing(*bad)
+    sim.step(2)
+    got = sim.density()
+    sim.close()
+    assert rel_err(got, orc(w).step(w.rho0, 2)) <= 1e-12
 
 
 def test_renormalisation_blocks_and_tails_match_oracle(binding):
@@ -320,9 +353,6 @@ def test_workload3_full_size_20_steps_fp32_properties(binding):
     err = float((f[..., 1].double() - expect.double()).abs().max()) / 38.0
     sim.close()
     assert err <= 1e-5
-
-
-PATHS = {"plain": ("0", "0", "0"), "pipe": ("1", "0", "0"), "stream": ("1", "1", "1")}
 
 
 @pytest.mark.parametrize("path", list(PATHS))
