@@ -259,10 +259,11 @@ bool plan_col(int n, bool fp64, ColPlan &p, int forced_m = 0) {
     return true;
   }
   for (int target = 32; target <= 128; target *= 2) {
+    // chunks of exactly `target` positions (the last one shorter): every full
+    // chunk then matches its compiled capacity and takes the unguarded path
     int T = (n + target - 1) / target;
     if (T < 1) T = 1;
-    int m = (n + T - 1) / T;
-    T = (n + m - 1) / m;  // every chunk non-empty
+    const int m = T == 1 ? n : target;
     const int maxm = pick_maxm(m, fp64);
     if (maxm == 0) return false;
     if (T * 32 <= col_bound_threads(maxm, esz)) {
