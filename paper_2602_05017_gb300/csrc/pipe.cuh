@@ -171,7 +171,9 @@ __device__ __forceinline__ void pipe_chunk(E *p, const int ps_rt, const int len,
     for (int i = 0; i < MAXM; i++)
       if ((FULL || i < len) && (face || lo + i == 0 || lo + i == n - 1)) v[i] = dval;
   }
-  consumers_sync(ncons);  // every halo read of this tile is done before any write-back
+  // No barrier before the write-back: the only reads of other chunks' positions
+  // (the halos of e = L_N d) happen before the first barrier above, and the
+  // carry arrays are rewritten only after barriers every warp has passed.
 #pragma unroll
   for (int i = 0; i < MAXM; i++)
     if (FULL || i < len) p[i * ps] = v[i];
