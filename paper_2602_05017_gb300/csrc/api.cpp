@@ -1,11 +1,12 @@
 // Host half of libbiofvm: the C ABI of include/biofvm.h.
 //
 // Owns the handle, validates arguments, computes the Thomas constants of
-// Appendix A in double (the paper's "first solver iteration ... stores the
-// constant coefficients"), chooses the launch plan of each sweep, aggregates
-// agents into per-element source terms, captures one step into a CUDA graph,
-// and maps CUDA failures to status codes.  All compute runs in the kernels of
-// sweeps_fp64.cu / sweeps_fp32.cu.
+// Appendix A in double (computed once and kept, as the paper's solver keeps
+// them after its first iteration), chooses the launch plan of each sweep
+// (FP64: streaming whole lines; FP32: the TMA pipeline; plain kernels as the
+// fallback), aggregates agents into per-element source terms, captures blocks
+// of steps into CUDA graphs, and maps CUDA failures to status codes.  All
+// compute runs in the kernels of sweeps_fp64.cu / sweeps_fp32.cu / noalloc.cu.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -68,8 +69,9 @@ cudaError_t dev_alloc(DevBuf &b, size_t bytes) {
 struct ColPlan {
   int T = 1, m = 1, maxm = 8;
 };
-// Persistent TMA pipeline of one sweep (used when rows are 16-byte aligned and
-// a ring of >= 2 stages fits in shared memory; otherwise the plain kernels).
+// Persistent TMA pipeline of one FP32 sweep (used when rows are 16-byte aligned
+// and a ring of >= 2 stages with the constants fits in shared memory; otherwise
+// the plain kernels).
 struct PipePlan {
   int use = 0, T = 1, m = 1, maxm = 8;
   int box_rows = 0, nbox = 0, rows_per_tile = 0, pitch = 0;

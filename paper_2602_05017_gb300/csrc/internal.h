@@ -8,8 +8,8 @@
 
 namespace bfv {
 
-// Stage flags of the x-sweep kernel (the kernel that also owns Src and the
-// first two Dirichlet applications of a step).
+// Stage flags of the sweep kernels (the x-sweep also owns Src and the first
+// two Dirichlet applications of a step).
 enum : int {
   kSrc = 1,        // rho <- (rho + alpha) * scale on the listed elements
   kDirBefore = 2,  // Dirichlet application before the solve
@@ -45,8 +45,8 @@ enum : int { kStatusOk = 0, kStatusTimeout = 4 };
 // product of pc over the chunks strictly between u and t.
 //
 // tabT: inv, mul, pf, pb again, substrate-major [4][S][n_pad] with
-// n_pad = 32*ceil(n/32) + 1 (the layout the pipelined kernel reads; staged
-// into shared memory when it fits, read through L1 otherwise).
+// n_pad = 32*ceil(n/32) + 1 (the layout the pipelined kernel stages into
+// shared memory; the planner takes that kernel only when they fit).
 struct AxisTab {
   const void *inv, *mul, *pf, *pb, *pc, *cfix, *cw, *tabT;
   int n, T, m;
