@@ -7,8 +7,9 @@
  * the CUDA library: it restates the method from the paper in the plainest
  * form, one line at a time, in double precision, single-threaded.
  *
- * What one step computes (paper Sect. 2, "the solver operates in 7 stages",
- * with the cell source/uptake update of the end-to-end run, Sect. 5.3):
+ * What one step computes (paper Sect. 2: seven stages, four Dirichlet
+ * applications around the three axis solves; preceded by the cell
+ * source/uptake update of the end-to-end run, Sect. 5.3):
  *
  *     rho+ = B . Z^-1 . B . Y^-1 . B . X^-1 . B . Src (rho)
  *
