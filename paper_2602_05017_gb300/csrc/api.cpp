@@ -410,6 +410,7 @@ void plan_pipe(biofvm *h, int axis) {
       }
     }
     p.stage_elems = (int64_t)p.rows_per_tile * p.pitch;
+    if (ny * nz > (int64_t)0x7fffffff) return;  // the kernel tracks rows in 32 bits
     p.ntiles = (ny * nz + p.rows_per_tile - 1) / p.rows_per_tile;
   } else {
     const int64_t C = axis == 1 ? nx * S : nx * ny * S;
@@ -419,6 +420,7 @@ void plan_pipe(biofvm *h, int axis) {
     p.box_rows = (n + p.nbox - 1) / p.nbox;
     p.stage_elems = (int64_t)p.nbox * p.box_rows * 32;
     p.ntiles = (int64_t)nplanes * ((C + 31) / 32);
+    if (p.ntiles > (int64_t)0x7fffffff) return;  // tiles are indexed in 32 bits
   }
   const size_t stage = (size_t)p.stage_elems * esz;
   const size_t tab = (size_t)pipe_tab_elems_host(n, (int)S) * esz;

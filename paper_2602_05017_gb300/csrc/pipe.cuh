@@ -94,12 +94,13 @@ __host__ __device__ inline int pipe_npad(int n) { return (n + 31) / 32 * 32 + 1;
 // FULL: the chunk has exactly MAXM positions (no per-position guards).
 // PS > 0: compile-time stride between positions in the staged tile.
 template <typename E, int MAXM, bool FULL, int PS>
-__device__ __forceinline__ void pipe_chunk(E *p, const int ps_rt, const int len, const int lo,
+__device__ __forceinline__ bool pipe_chunk(E *p, const int ps_rt, const int len, const int lo,
                                            const int n, const int t, const int T, const int lane,
                                            const E *Ti, const E *Tm, const E *Tf, const E *Tb,
                                            const E *Tcw, const int S, const int s, const E chi,
                                            const E clo, E *s_end, E *s_beg, const int ncons,
-                                           const bool dir, const bool face, const E dval) {
+                                           const bool dir, const bool face, const E dval,
+                                           const bool ok) {
   const int ps = PS > 0 ? PS : ps_rt;
   E v[MAXM];
 #pragma unroll
@@ -134,7 +135,10 @@ __device__ __forceinline__ void pipe_chunk(E *p, const int ps_rt, const int len,
       v[i] = g;
     }
   s_end[t * 32 + lane] = g;
-  consumers_sync(ncons);
+  // The first carry barrier also ANDs the outcome of every consumer's wait
+  // for the tile: on a timeout all consumers leave together, before any
+  // write-back (what they computed from the unfinished stage stays local).
+  if (!consumers_all(ok, ncons)) return false;
   if (t > 0) {  // chunk 0 enters with a zero carry
     E carry = E(0);
     for (int u = t - 1; u >= 0; u--) carry = fma(Tcw[(u * T + t) * S + s], s_end[u * 32 + lane], carry);
@@ -177,6 +181,7 @@ __device__ __forceinline__ void pipe_chunk(E *p, const int ps_rt, const int len,
 #pragma unroll
   for (int i = 0; i < MAXM; i++)
     if (FULL || i < len) p[i * ps] = v[i];
+  return true;
 }
 
 // MODE 0: x tiles (per-row bulk copies, Src and B before the solve);
@@ -235,8 +240,8 @@ __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
           bulk_g2s(dst + (size_t)r * a.pitch, field + (tile * a.rows_per_tile + r) * a.rowlen, rb,
                    &full[s]);
       } else {
-        const int plane = (int)(tile / a.tiles_per_plane);
-        const int c0 = (int)(tile % a.tiles_per_plane) * 32;
+        const int plane = (int)((uint32_t)tile / (uint32_t)a.tiles_per_plane);
+        const int c0 = (int)((uint32_t)tile % (uint32_t)a.tiles_per_plane) * 32;
         mbar_arrive_expect_tx(&full[s], (uint32_t)(stage_elems * sizeof(E)));
         for (int b = 0; b < a.nbox; b++)
           tma_load_3d(dst + (size_t)b * a.box_rows * 32, &map, c0, b * a.box_rows, plane, &full[s]);
@@ -251,8 +256,8 @@ __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
         for (int r = 0; r < rows; r++)
           bulk_s2g(field + (tile * a.rows_per_tile + r) * a.rowlen, src + (size_t)r * a.pitch, rb);
       } else {
-        const int plane = (int)(tile / a.tiles_per_plane);
-        const int c0 = (int)(tile % a.tiles_per_plane) * 32;
+        const int plane = (int)((uint32_t)tile / (uint32_t)a.tiles_per_plane);
+        const int c0 = (int)((uint32_t)tile % (uint32_t)a.tiles_per_plane) * 32;
         for (int b = 0; b < a.nbox; b++)
           tma_store_3d(&map, c0, b * a.box_rows, plane, src + (size_t)b * a.box_rows * 32);
       }
@@ -288,6 +293,9 @@ __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
   const int ps_rt = MODE == 0 ? S : 32;
   const E *Tcw = static_cast<const E *>(a.tab.cw);  // [T][T][S], global (L1-resident)
   const bool dir_after = (a.flags & kDirAfter) != 0;
+  // The planner keeps tile, row and column counts below 2^31, so the per-tile
+  // index arithmetic below runs in 32 bits (a 64-bit division is a long
+  // software sequence, and every consumer thread repeats it per tile).
   // x tiles: the source entries flow ahead of the tiles -- the offsets of
   // tile k+2 and this thread's first entry of tile k+1 are loaded while tile
   // k is solved, so no tile waits on global loads for its sources.
@@ -319,8 +327,9 @@ __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
   }
   for (long long k = 0; k < count; k++) {
     const int st = (int)(k % NS);
-    bool ok = mbar_wait_bounded(&full[st], (uint32_t)((k / NS) & 1), a.status);
-    if (!consumers_all(ok, ncons)) break;
+    // (a timed-out wait is acted on at the first carry barrier of the chunk
+    // solve; the steps before it only touch this stage and registers)
+    const bool ok = mbar_wait_bounded(&full[st], (uint32_t)((k / NS) & 1), a.status);
     const long long tile = first + k * gridDim.x;
     E *const stg = stage0 + st * stage_elems;
     int s;
@@ -329,9 +338,9 @@ __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
       const long long r0 = tile * a.rows_per_tile;
       const int rows = (int)min((long long)a.rows_per_tile, a.nrows - r0);
       s = lane % S;
-      const long long row = r0 + lane / S;
       active = lane < a.rows_per_tile * S && lane / S < rows;
       {
+        const long long row = r0 + lane / S;
         const int y = (int)(row % a.ny), z = (int)(row / a.ny);
         face = y == 0 || y == a.ny - 1 || z == 0 || z == a.nz - 1;
       }
@@ -357,36 +366,37 @@ __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
       if ((a.flags & kSrc) && a.has_src && (a.flags & kDirBefore)) consumers_sync(ncons);
       if (a.flags & kDirBefore) {  // consumer warp t takes rows t, t+T, ...
         for (int rr = t; rr < rows; rr += T) {
-          const long long gr = r0 + rr;
-          const int y = (int)(gr % a.ny), z = (int)(gr / a.ny);
-          E *tr = stg + (size_t)rr * a.pitch;
+          const uint32_t row = (uint32_t)r0 + (uint32_t)rr;
+          const int z = (int)(row / (uint32_t)a.ny), y = (int)row - z * a.ny;
+          E *trow = stg + (size_t)rr * a.pitch;
           if (y == 0 || y == a.ny - 1 || z == 0 || z == a.nz - 1) {
             for (int kk = lane; kk < a.rowlen; kk += 32) {
               const int ss = kk % S;
-              if (a.dir_on[ss]) tr[kk] = dir_value<E>(a.flags, a.dir_val, ss);
+              if (a.dir_on[ss]) trow[kk] = dir_value<E>(a.flags, a.dir_val, ss);
             }
           } else {
             for (int kk = lane; kk < 2 * S; kk += 32) {
               const int ss = kk % S;
               if (a.dir_on[ss])
-                tr[kk < S ? ss : (a.nx - 1) * S + ss] = dir_value<E>(a.flags, a.dir_val, ss);
+                trow[kk < S ? ss : (a.nx - 1) * S + ss] = dir_value<E>(a.flags, a.dir_val, ss);
             }
           }
         }
       }
       if ((a.flags & (kSrc | kDirBefore)) != 0) consumers_sync(ncons);
     } else {
-      const int plane = (int)(tile / a.tiles_per_plane);
-      const long long c = (tile % a.tiles_per_plane) * 32 + lane;
-      active = c < a.C;
-      s = (int)(c % S);
+      const int plane = (int)((uint32_t)tile / (uint32_t)a.tiles_per_plane);
+      const uint32_t c = ((uint32_t)tile - (uint32_t)plane * (uint32_t)a.tiles_per_plane) * 32u +
+                         (uint32_t)lane;
+      active = c < (uint32_t)a.C;
+      s = (int)(c % (uint32_t)S);
       if (dir_after) {
         if (a.mode == 1) {
-          const int x0 = (int)(c / S);
+          const int x0 = (int)(c / (uint32_t)S);
           face = (x0 == 0 || x0 == a.nx - 1 || plane == 0 || plane == a.nz - 1);
         } else {
-          const long long vox = c / S;
-          const int x0 = (int)(vox % a.nx), y = (int)(vox / a.nx);
+          const uint32_t vox = c / (uint32_t)S;
+          const int x0 = (int)(vox % (uint32_t)a.nx), y = (int)(vox / (uint32_t)a.nx);
           face = (x0 == 0 || x0 == a.nx - 1 || y == 0 || y == a.ny - 1);
         }
       }
@@ -399,16 +409,16 @@ __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
     const E chi = __ldg(g_cfix + s), clo = __ldg(g_cfix + S + s);
     // the unguarded path only when every lane of the warp has a full chunk:
     // the choice is warp-uniform, so a warp never splits across the paths
+    bool solved;
     if (__all_sync(0xffffffffu, len == MAXM))
-      pipe_chunk<E, MAXM, true, MODE == 0 ? 0 : 32>(p, ps_rt, len, lo, n, t, T, lane,
-                                                    s_inv + rowoff, s_mul + rowoff, s_pf + rowoff,
-                                                    s_pb + rowoff, Tcw, S, s, chi, clo, s_end,
-                                                    s_beg, ncons, dir, face, dval);
+      solved = pipe_chunk<E, MAXM, true, MODE == 0 ? 0 : 32>(
+          p, ps_rt, len, lo, n, t, T, lane, s_inv + rowoff, s_mul + rowoff, s_pf + rowoff,
+          s_pb + rowoff, Tcw, S, s, chi, clo, s_end, s_beg, ncons, dir, face, dval, ok);
     else
-      pipe_chunk<E, MAXM, false, MODE == 0 ? 0 : 32>(p, ps_rt, len, lo, n, t, T, lane,
-                                                     s_inv + rowoff, s_mul + rowoff, s_pf + rowoff,
-                                                     s_pb + rowoff, Tcw, S, s, chi, clo, s_end,
-                                                     s_beg, ncons, dir, face, dval);
+      solved = pipe_chunk<E, MAXM, false, MODE == 0 ? 0 : 32>(
+          p, ps_rt, len, lo, n, t, T, lane, s_inv + rowoff, s_mul + rowoff, s_pf + rowoff,
+          s_pb + rowoff, Tcw, S, s, chi, clo, s_end, s_beg, ncons, dir, face, dval, ok);
+    if (!solved) break;
     fence_proxy_async_smem();  // generic-proxy writes -> visible to the bulk store
     mbar_arrive(&done[st]);
   }
