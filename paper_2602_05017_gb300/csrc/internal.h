@@ -1,5 +1,5 @@
 // Internal interface between the host half of libbiofvm (api.cpp) and the
-// sweep kernels (sweeps_fp64.cu, sweeps_fp32.cu).  Not installed; the public
+// sweep kernels (sweeps_fp64.cu, sweeps_fp32.cu, pipe_fp32.cu).  Not installed; the public
 // C ABI is include/biofvm.h.
 #pragma once
 #include <cuda.h>  // CUtensorMap (type only; the encoder is fetched at run time)

@@ -185,8 +185,10 @@ __device__ __forceinline__ bool pipe_chunk(E *p, const int ps_rt, const int len,
 }
 
 // MODE 0: x tiles (per-row bulk copies, Src and B before the solve);
-// MODE 1: y/z tiles (tensor boxes).
-template <typename E, int MAXM, int MODE>
+// MODE 1: y/z tiles (tensor boxes).  PSX > 0 (x tiles only): the substrate
+// count S, known at compile time, so the staged positions (S apart) need no
+// per-access address arithmetic; 0: S read at run time.
+template <typename E, int MAXM, int MODE, int PSX = 0>
 __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
     sweep_pipe_kernel(const __grid_constant__ CUtensorMap map, const PipeArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -339,9 +341,9 @@ __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
       const int rows = (int)min((long long)a.rows_per_tile, a.nrows - r0);
       s = lane % S;
       active = lane < a.rows_per_tile * S && lane / S < rows;
-      {
-        const long long row = r0 + lane / S;
-        const int y = (int)(row % a.ny), z = (int)(row / a.ny);
+      if (dir_after) {  // (only the Dirichlet application after the solve needs the face)
+        const uint32_t row = (uint32_t)r0 + (uint32_t)(lane / S);
+        const int z = (int)(row / (uint32_t)a.ny), y = (int)row - z * a.ny;
         face = y == 0 || y == a.ny - 1 || z == 0 || z == a.nz - 1;
       }
       // Src then B on the staged rows, before any solve
@@ -409,38 +411,66 @@ __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
     const E chi = __ldg(g_cfix + s), clo = __ldg(g_cfix + S + s);
     // the unguarded path only when every lane of the warp has a full chunk:
     // the choice is warp-uniform, so a warp never splits across the paths
+    constexpr int PS = MODE == 0 ? PSX : 32;
     bool solved;
     if (__all_sync(0xffffffffu, len == MAXM))
-      solved = pipe_chunk<E, MAXM, true, MODE == 0 ? 0 : 32>(
-          p, ps_rt, len, lo, n, t, T, lane, s_inv + rowoff, s_mul + rowoff, s_pf + rowoff,
-          s_pb + rowoff, Tcw, S, s, chi, clo, s_end, s_beg, ncons, dir, face, dval, ok);
+      solved = pipe_chunk<E, MAXM, true, PS>(p, ps_rt, len, lo, n, t, T, lane, s_inv + rowoff,
+                                             s_mul + rowoff, s_pf + rowoff, s_pb + rowoff, Tcw, S,
+                                             s, chi, clo, s_end, s_beg, ncons, dir, face, dval, ok);
     else
-      solved = pipe_chunk<E, MAXM, false, MODE == 0 ? 0 : 32>(
-          p, ps_rt, len, lo, n, t, T, lane, s_inv + rowoff, s_mul + rowoff, s_pf + rowoff,
-          s_pb + rowoff, Tcw, S, s, chi, clo, s_end, s_beg, ncons, dir, face, dval, ok);
+      solved = pipe_chunk<E, MAXM, false, PS>(p, ps_rt, len, lo, n, t, T, lane, s_inv + rowoff,
+                                              s_mul + rowoff, s_pf + rowoff, s_pb + rowoff, Tcw, S,
+                                              s, chi, clo, s_end, s_beg, ncons, dir, face, dval, ok);
     if (!solved) break;
     fence_proxy_async_smem();  // generic-proxy writes -> visible to the bulk store
     mbar_arrive(&done[st]);
   }
 }
 
+// x tiles with a compile-time substrate count: the default chunk length only
+// (each specialisation is a full copy of the kernel).
+template <int MAXM>
+constexpr bool pipe_x_specialised() {
+  return MAXM == 32;
+}
+
 template <typename E, int MAXM>
 cudaError_t allow_pipe_smem(size_t bytes) {
-  cudaError_t e = cudaFuncSetAttribute(sweep_pipe_kernel<E, MAXM, 0>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(sweep_pipe_kernel<E, MAXM, 1>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  cudaError_t e = cudaSuccess;
+  auto set = [&](const void *f) {
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  };
+  set((const void *)sweep_pipe_kernel<E, MAXM, 0>);
+  set((const void *)sweep_pipe_kernel<E, MAXM, 1>);
+  if constexpr (pipe_x_specialised<MAXM>()) {
+    set((const void *)sweep_pipe_kernel<E, MAXM, 0, 1>);
+    set((const void *)sweep_pipe_kernel<E, MAXM, 0, 2>);
+    set((const void *)sweep_pipe_kernel<E, MAXM, 0, 4>);
+    set((const void *)sweep_pipe_kernel<E, MAXM, 0, 8>);
+  }
+  return e;
 }
 
 template <typename E, int MAXM>
 cudaError_t launch_pipe_one(const CUtensorMap &map, const PipeArgs &a, int grid, size_t smem,
                             cudaStream_t st) {
   if ((a.tab.T + 1) * 32 > PipeBound<E, MAXM>::threads) return cudaErrorInvalidConfiguration;
-  if (a.mode == 0)
-    sweep_pipe_kernel<E, MAXM, 0><<<grid, (a.tab.T + 1) * 32, smem, st>>>(map, a);
-  else
-    sweep_pipe_kernel<E, MAXM, 1><<<grid, (a.tab.T + 1) * 32, smem, st>>>(map, a);
+  const int threads = (a.tab.T + 1) * 32;
+  if (a.mode != 0) {
+    sweep_pipe_kernel<E, MAXM, 1><<<grid, threads, smem, st>>>(map, a);
+    return cudaGetLastError();
+  }
+  if constexpr (pipe_x_specialised<MAXM>()) {
+    switch (a.S) {
+      case 1: sweep_pipe_kernel<E, MAXM, 0, 1><<<grid, threads, smem, st>>>(map, a); return cudaGetLastError();
+      case 2: sweep_pipe_kernel<E, MAXM, 0, 2><<<grid, threads, smem, st>>>(map, a); return cudaGetLastError();
+      case 4: sweep_pipe_kernel<E, MAXM, 0, 4><<<grid, threads, smem, st>>>(map, a); return cudaGetLastError();
+      case 8: sweep_pipe_kernel<E, MAXM, 0, 8><<<grid, threads, smem, st>>>(map, a); return cudaGetLastError();
+      default: break;
+    }
+  }
+  sweep_pipe_kernel<E, MAXM, 0><<<grid, threads, smem, st>>>(map, a);
   return cudaGetLastError();
 }
 

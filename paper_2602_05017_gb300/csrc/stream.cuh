@@ -360,17 +360,34 @@ __device__ __forceinline__ void solve_lines_f32(float *line, float *sline, int n
 
 // Source update of a warp's rows (x-sweep), then visible to the whole warp.
 // fac (or NULL): per-substrate factor on alpha when the field is stored scaled.
+// The entries are unique elements (aggregated and sorted on the host), so a
+// lane issues the loads of U entries before any of their read-modify-writes:
+// two rounds of memory latency per U entries instead of two per entry.
 template <typename E>
 __device__ __forceinline__ void warp_rows_src(E *rho, long long r0, long long r1,
                                               const int64_t *row_off, const int64_t *elem,
                                               const void *alpha, const void *scale, int lane,
                                               const void *fac = nullptr, int S = 1) {
+  constexpr int U = 4;
   const long long e0 = row_off[r0], e1 = row_off[r1];
-  for (long long e = e0 + lane; e < e1; e += 32) {
-    const long long k = elem[e];
-    E al = ldg<E>(alpha, e);
-    if (fac) al *= ldg<E>(fac, (int)(k % S));
-    rho[k] = (rho[k] + al) * ldg<E>(scale, e);
+  for (long long eb = e0 + lane; eb < e1; eb += 32 * U) {
+    long long k[U];
+    E al[U], sc[U], v[U];
+#pragma unroll
+    for (int j = 0; j < U; j++) {
+      const long long e = eb + 32 * j;
+      k[j] = e < e1 ? __ldg(elem + e) : -1;
+      al[j] = e < e1 ? ldg<E>(alpha, e) : E(0);
+      sc[j] = e < e1 ? ldg<E>(scale, e) : E(0);
+    }
+#pragma unroll
+    for (int j = 0; j < U; j++) {
+      v[j] = k[j] >= 0 ? rho[k[j]] : E(0);
+      if (fac && k[j] >= 0) al[j] *= ldg<E>(fac, (int)(k[j] % S));
+    }
+#pragma unroll
+    for (int j = 0; j < U; j++)
+      if (k[j] >= 0) rho[k[j]] = (v[j] + al[j]) * sc[j];
   }
   __syncwarp();
 }
