@@ -9,7 +9,8 @@ Every function follows one passage of the paper (arXiv 2602.05017):
     a_i = c_i = -D dt/dx^2 and b = 1 + lambda dt/3 on a one-voxel axis;
   * ``thomas``            -- the TDMA of Sect. 2.1 (forward: divide, backward: negated axpy);
   * ``sweep``             -- Algorithm 1 for one dimension over every line and substrate;
-  * ``dirichlet``         -- one of the four Dirichlet applications of the 7-stage solver (Sect. 2);
+  * ``dirichlet``         -- one of the four Dirichlet applications of the 7-stage solver (Sect. 2):
+    the flagged faces, then the Dirichlet nodes (listed voxels, in list order);
   * ``sources``           -- the cell source/uptake update of the end-to-end run (Sect. 5.3),
     in the implicit form of the cited BioFVM, agents sharing a voxel aggregated;
   * ``step``              -- Src, B, X^-1, B, Y^-1, B, Z^-1, B, repeated n_steps times;
@@ -59,14 +60,16 @@ def _get():
         lib.oracle_thomas.argtypes = [i, _dp, _dp, _dp, _dp]
         lib.oracle_sweep.argtypes = [i, i, i, i, i, d, d, _dp, _dp, _dp]
         lib.oracle_dirichlet.argtypes = [i, i, i, i, _u8p, _dp, _dp]
+        lib.oracle_dirichlet_nodes.argtypes = [i, i, i, i, L, _i64p, _dp, _dp]
         lib.oracle_sources.argtypes = [i, i, i, i, d, L, _i64p, _dp, _dp, _dp, _dp, _dp]
-        lib.oracle_step.argtypes = [i, i, i, i, _dp, d, _dp, _dp, _u8p, _dp, L, _i64p, _dp, _dp,
-                                    _dp, _dp, i, _dp]
-        lib.oracle_adjoint_step.argtypes = [i, i, i, i, _dp, d, _dp, _dp, _u8p, _dp, L, _i64p, _dp,
-                                            _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
+        lib.oracle_step.argtypes = [i, i, i, i, _dp, d, _dp, _dp, _u8p, _dp, L, _i64p, _dp,
+                                    L, _i64p, _dp, _dp, _dp, _dp, i, _dp]
+        lib.oracle_adjoint_step.argtypes = [i, i, i, i, _dp, d, _dp, _dp, _u8p, _dp, L, _i64p,
+                                            _dp, L, _i64p, _dp, _dp, _dp, _dp, _dp, _dp, _dp,
+                                            _dp, _dp, _dp, _dp]
         for f in (lib.oracle_axis_coefficients, lib.oracle_thomas, lib.oracle_sweep,
-                  lib.oracle_dirichlet, lib.oracle_sources, lib.oracle_step,
-                  lib.oracle_adjoint_step):
+                  lib.oracle_dirichlet, lib.oracle_dirichlet_nodes, lib.oracle_sources,
+                  lib.oracle_step, lib.oracle_adjoint_step):
             f.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -93,10 +96,14 @@ class Problem:
 
     Field layout is ``rho[z, y, x, s]`` (substrates interleaved per voxel, x fastest of the axes).
     dx: the voxel spacing, or three spacings (x, y, z) for an anisotropic grid.
+    dirichlet_nodes: None or (voxel, substrate, value) arrays of Dirichlet nodes, overwritten at
+    each Dirichlet application after the flagged faces (a repeated (voxel, substrate) takes its
+    last value).
     """
 
     def __init__(self, nx, ny, nz, ns, dx, dt, D, lam, dirichlet_on=None, dirichlet_value=None,
-                 voxel=None, secretion=None, target=None, uptake=None, weight=None):
+                 voxel=None, secretion=None, target=None, uptake=None, weight=None,
+                 dirichlet_nodes=None):
         self.nx, self.ny, self.nz, self.ns = int(nx), int(ny), int(nz), int(ns)
         self.h3 = np.ascontiguousarray(np.broadcast_to(np.asarray(dx, dtype=np.float64),
                                                        (3,)).copy())
@@ -108,6 +115,15 @@ class Problem:
             self.val = _f64(dirichlet_value, self.ns)
         else:
             self.on, self.val = None, None
+        if dirichlet_nodes is not None and len(dirichlet_nodes[0]) > 0:
+            nv, ns_, val = (np.asarray(a).reshape(-1) for a in dirichlet_nodes)
+            if not (nv.size == ns_.size == val.size):
+                raise ValueError("node voxel, substrate and value arrays differ in length")
+            self.node_elem = np.ascontiguousarray(nv.astype(np.int64) * self.ns
+                                                  + ns_.astype(np.int64))
+            self.node_val = _f64(val)
+        else:
+            self.node_elem, self.node_val = None, None
         if voxel is not None and len(voxel) > 0:
             self.voxel = np.ascontiguousarray(np.asarray(voxel, dtype=np.int64).reshape(-1))
             na = self.voxel.size
@@ -133,6 +149,10 @@ class Problem:
             raise ValueError("field has the wrong size")
         return a.reshape(self.shape)
 
+    def _nodes(self):
+        n = 0 if self.node_elem is None else int(self.node_elem.size)
+        return (n, _ptr(self.node_elem, _i64p), _ptr(self.node_val))
+
     def _agents(self):
         return (self.n_agents, _ptr(self.voxel, _i64p), _ptr(self.sec), _ptr(self.tgt),
                 _ptr(self.upt), _ptr(self.w))
@@ -148,6 +168,8 @@ class Problem:
         out = self._field(rho)
         _check(_get().oracle_dirichlet(self.nx, self.ny, self.nz, self.ns, _ptr(self.on, _u8p),
                                        _ptr(self.val), _ptr(out)), "dirichlet")
+        _check(_get().oracle_dirichlet_nodes(self.nx, self.ny, self.nz, self.ns, *self._nodes(),
+                                             _ptr(out)), "dirichlet nodes")
         return out
 
     def sources(self, rho):
@@ -160,7 +182,8 @@ class Problem:
         out = self._field(rho)
         _check(_get().oracle_step(self.nx, self.ny, self.nz, self.ns, _ptr(self.h3), self.dt,
                                   _ptr(self.D), _ptr(self.lam), _ptr(self.on, _u8p),
-                                  _ptr(self.val), *self._agents(), int(n_steps), _ptr(out)), "step")
+                                  _ptr(self.val), *self._nodes(), *self._agents(), int(n_steps),
+                                  _ptr(out)), "step")
         return out
 
     def adjoint_step(self, rho_in, gbar_out):
@@ -175,7 +198,8 @@ class Problem:
         dupt = np.zeros(na * self.ns)
         _check(_get().oracle_adjoint_step(
             self.nx, self.ny, self.nz, self.ns, _ptr(self.h3), self.dt, _ptr(self.D), _ptr(self.lam),
-            _ptr(self.on, _u8p), _ptr(self.val), *self._agents(), _ptr(rho_in), _ptr(gout),
+            _ptr(self.on, _u8p), _ptr(self.val), *self._nodes(), *self._agents(), _ptr(rho_in),
+            _ptr(gout),
             _ptr(gin), _ptr(dD), _ptr(dl), _ptr(dsec) if na else None,
             _ptr(dupt) if na else None), "adjoint_step")
         return gin, dD, dl, dsec.reshape(na, self.ns), dupt.reshape(na, self.ns)

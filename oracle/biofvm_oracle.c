@@ -31,6 +31,10 @@
  *   - Stage order of the 7 stages: B, X^-1, B, Y^-1, B, Z^-1, B.
  *   - Dirichlet application overwrites the voxels of the six faces; the
  *     matrices keep their zero-flux end rows.
+ *   - Dirichlet nodes (BioFVM's Dirichlet voxels anywhere in the grid, and
+ *     face values that differ per face): a list of (element, value) pairs
+ *     overwritten at each of the same four applications, after the faces;
+ *     an element listed twice takes its last value.
  *   - Source/uptake (not printed in this paper; the implicit update of the
  *     cited BioFVM): rho <- (rho + alpha) / (1 + beta) with, summed over the
  *     agents in the voxel, alpha = sum dt*w*S*rho_target and
@@ -199,6 +203,29 @@ int oracle_dirichlet(int nx, int ny, int nz, int ns, const unsigned char *on,
   return 0;
 }
 
+/* The node part of B: rho[elem[k]] = val[k] in list order. */
+int oracle_dirichlet_nodes(int nx, int ny, int nz, int ns, i64 n_nodes,
+                           const i64 *elem, const double *val, double *rho) {
+  if (!check_grid(nx, ny, nz, ns) || !rho || n_nodes < 0) return -1;
+  if (n_nodes == 0) return 0;
+  if (!elem || !val) return -1;
+  i64 nel = (i64)nx * ny * nz * ns;
+  for (i64 k = 0; k < n_nodes; k++)
+    if (elem[k] < 0 || elem[k] >= nel) return -1;
+  for (i64 k = 0; k < n_nodes; k++) rho[elem[k]] = val[k];
+  return 0;
+}
+
+/* One full Dirichlet application: the faces, then the nodes. */
+static int apply_b(int nx, int ny, int nz, int ns, const unsigned char *on,
+                   const double *value, i64 n_nodes, const i64 *node_elem,
+                   const double *node_val, double *rho) {
+  int rc = oracle_dirichlet(nx, ny, nz, ns, on, value, rho);
+  if (rc) return rc;
+  return oracle_dirichlet_nodes(nx, ny, nz, ns, n_nodes, node_elem, node_val,
+                                rho);
+}
+
 /* Dense per-element alpha and beta aggregated from an agent list. */
 static int aggregate_sources(i64 nvox, int ns, double dt, i64 n_agents,
                              const i64 *voxel, const double *sec,
@@ -257,7 +284,8 @@ int oracle_sources(int nx, int ny, int nz, int ns, double dt, i64 n_agents,
  * App. A system takes r = D dt / h^2 with its own h). */
 int oracle_step(int nx, int ny, int nz, int ns, const double *h3, double dt,
                 const double *D, const double *lambda, const unsigned char *on,
-                const double *value, i64 n_agents, const i64 *voxel,
+                const double *value, i64 n_nodes, const i64 *node_elem,
+                const double *node_val, i64 n_agents, const i64 *voxel,
                 const double *sec, const double *tgt, const double *upt,
                 const double *w, int n_steps, double *rho) {
   if (n_steps < 0 || !h3) return -1;
@@ -266,12 +294,12 @@ int oracle_step(int nx, int ny, int nz, int ns, const double *h3, double dt,
                             w, rho);
     if (rc) return rc;
     for (int axis = 0; axis < 3; axis++) {
-      rc = oracle_dirichlet(nx, ny, nz, ns, on, value, rho);
+      rc = apply_b(nx, ny, nz, ns, on, value, n_nodes, node_elem, node_val, rho);
       if (rc) return rc;
       rc = oracle_sweep(axis, nx, ny, nz, ns, h3[axis], dt, D, lambda, rho);
       if (rc) return rc;
     }
-    rc = oracle_dirichlet(nx, ny, nz, ns, on, value, rho);
+    rc = apply_b(nx, ny, nz, ns, on, value, n_nodes, node_elem, node_val, rho);
     if (rc) return rc;
   }
   return 0;
@@ -281,9 +309,12 @@ int oracle_step(int nx, int ny, int nz, int ns, const double *h3, double dt,
 /* Adjoint of one step (reverse mode), derived from the stages above.        */
 /* ------------------------------------------------------------------------ */
 
-/* Zero the adjoint where B overwrote the forward value (dB/du = mask). */
+/* Zero the adjoint where B overwrote the forward value (dB/du = mask): the
+ * flagged faces and the nodes. */
 static void dirichlet_mask(int nx, int ny, int nz, int ns,
-                           const unsigned char *on, double *g) {
+                           const unsigned char *on, i64 n_nodes,
+                           const i64 *node_elem, double *g) {
+  for (i64 k = 0; k < n_nodes; k++) g[node_elem[k]] = 0.0;
   if (!on) return;
   for (int z = 0; z < nz; z++)
     for (int y = 0; y < ny; y++)
@@ -331,14 +362,18 @@ static void sweep_param_grad(int axis, int nx, int ny, int nz, int ns,
 int oracle_adjoint_step(int nx, int ny, int nz, int ns, const double *h3, double dt,
                         const double *D, const double *lambda,
                         const unsigned char *on, const double *value,
-                        i64 n_agents, const i64 *voxel, const double *sec,
-                        const double *tgt, const double *upt, const double *w,
-                        const double *rho_in, const double *gbar_out,
-                        double *gbar_in, double *dD, double *dlambda,
-                        double *dsec, double *dupt) {
+                        i64 n_nodes, const i64 *node_elem,
+                        const double *node_val, i64 n_agents, const i64 *voxel,
+                        const double *sec, const double *tgt, const double *upt,
+                        const double *w, const double *rho_in,
+                        const double *gbar_out, double *gbar_in, double *dD,
+                        double *dlambda, double *dsec, double *dupt) {
   if (!check_grid(nx, ny, nz, ns) || !h3 || !rho_in || !gbar_out || !gbar_in ||
-      !dD || !dlambda || n_agents < 0)
+      !dD || !dlambda || n_agents < 0 || n_nodes < 0 ||
+      (n_nodes > 0 && (!node_elem || !node_val)))
     return -1;
+  for (i64 k = 0; k < n_nodes; k++)
+    if (node_elem[k] < 0 || node_elem[k] >= (i64)nx * ny * nz * ns) return -1;
   i64 nel = (i64)nx * ny * nz * ns;
   size_t bytes = sizeof(double) * (size_t)nel;
   /* forward intermediates: u1 = Src(rho), u3 = X^-1 B u1, u5, u7 */
@@ -356,28 +391,28 @@ int oracle_adjoint_step(int nx, int ny, int nz, int ns, const double *h3, double
   rc |= oracle_sources(nx, ny, nz, ns, dt, n_agents, voxel, sec, tgt, upt, w,
                        u1);
   memcpy(u3, u1, bytes);
-  rc |= oracle_dirichlet(nx, ny, nz, ns, on, value, u3);
+  rc |= apply_b(nx, ny, nz, ns, on, value, n_nodes, node_elem, node_val, u3);
   rc |= oracle_sweep(0, nx, ny, nz, ns, h3[0], dt, D, lambda, u3);
   memcpy(u5, u3, bytes);
-  rc |= oracle_dirichlet(nx, ny, nz, ns, on, value, u5);
+  rc |= apply_b(nx, ny, nz, ns, on, value, n_nodes, node_elem, node_val, u5);
   rc |= oracle_sweep(1, nx, ny, nz, ns, h3[1], dt, D, lambda, u5);
   memcpy(u7, u5, bytes);
-  rc |= oracle_dirichlet(nx, ny, nz, ns, on, value, u7);
+  rc |= apply_b(nx, ny, nz, ns, on, value, n_nodes, node_elem, node_val, u7);
   rc |= oracle_sweep(2, nx, ny, nz, ns, h3[2], dt, D, lambda, u7);
   if (rc) goto done;
 
   /* reverse: gbar_in walks back through B, Z^-1, B, Y^-1, B, X^-1, B, Src */
   memcpy(gbar_in, gbar_out, bytes);
-  dirichlet_mask(nx, ny, nz, ns, on, gbar_in);
+  dirichlet_mask(nx, ny, nz, ns, on, n_nodes, node_elem, gbar_in);
   rc |= oracle_sweep(2, nx, ny, nz, ns, h3[2], dt, D, lambda, gbar_in);
   sweep_param_grad(2, nx, ny, nz, ns, h3[2], dt, gbar_in, u7, dD, dlambda);
-  dirichlet_mask(nx, ny, nz, ns, on, gbar_in);
+  dirichlet_mask(nx, ny, nz, ns, on, n_nodes, node_elem, gbar_in);
   rc |= oracle_sweep(1, nx, ny, nz, ns, h3[1], dt, D, lambda, gbar_in);
   sweep_param_grad(1, nx, ny, nz, ns, h3[1], dt, gbar_in, u5, dD, dlambda);
-  dirichlet_mask(nx, ny, nz, ns, on, gbar_in);
+  dirichlet_mask(nx, ny, nz, ns, on, n_nodes, node_elem, gbar_in);
   rc |= oracle_sweep(0, nx, ny, nz, ns, h3[0], dt, D, lambda, gbar_in);
   sweep_param_grad(0, nx, ny, nz, ns, h3[0], dt, gbar_in, u3, dD, dlambda);
-  dirichlet_mask(nx, ny, nz, ns, on, gbar_in);
+  dirichlet_mask(nx, ny, nz, ns, on, n_nodes, node_elem, gbar_in);
   if (rc) goto done;
 
   /* Src: u1 = (u0 + alpha)/(1 + beta).  du1/du0 = 1/(1+beta);

@@ -43,6 +43,7 @@ class Workload:
     uptake: Optional[np.ndarray] = None           # [n_agents, ns]
     weight: Optional[np.ndarray] = None           # [n_agents] or None (=> 1)
     spacing: Optional[tuple] = None               # (dx, dy, dz) of an anisotropic grid, or None
+    dirichlet_nodes: Optional[tuple] = None       # (voxel, substrate, value) arrays, or None
     extra: dict = field(default_factory=dict)
 
     @property
@@ -64,7 +65,7 @@ class Workload:
                     D=self.D, lam=self.lam, dirichlet_on=self.dirichlet_on,
                     dirichlet_value=self.dirichlet_value, voxel=self.voxel,
                     secretion=self.secretion, target=self.target, uptake=self.uptake,
-                    weight=self.weight)
+                    weight=self.weight, dirichlet_nodes=self.dirichlet_nodes)
 
 
 def _loguniform(rng, lo, hi, size):
@@ -220,9 +221,47 @@ def batched_workloads(n_env=256, edge=(32, 192), ns=(1, 8), seed=None, n_steps=5
     return envs
 
 
+def random_nodes(rng, nvox, ns, n, repeat=True):
+    """Dirichlet nodes: n (voxel, substrate, value) triples at seeded random voxels (interior or
+    on faces), values uniform in [0, 38]; with ``repeat`` a few (voxel, substrate) pairs occur
+    twice with different values."""
+    voxel = rng.integers(0, nvox, size=n, dtype=np.int64)
+    sub = rng.integers(0, ns, size=n).astype(np.int32)
+    val = rng.uniform(0.0, 38.0, n)
+    if repeat and n >= 4:
+        k = max(1, n // 8)
+        voxel[-k:], sub[-k:] = voxel[:k], sub[:k]
+    return voxel, sub, val
+
+
+def face_value_nodes(nx, ny, nz, values):
+    """Per-face Dirichlet values as nodes.  values[f, s] (NaN: no condition) for the faces
+    f = x-, x+, y-, y+, z-, z+; listed in that order, so where faces meet (edges, corners) the
+    later face's value is the one that stays."""
+    values = np.asarray(values, dtype=np.float64)
+    ns = values.shape[1]
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    vox = ((z * ny + y) * nx + x).reshape(-1)
+    on = [x.reshape(-1) == 0, x.reshape(-1) == nx - 1, y.reshape(-1) == 0, y.reshape(-1) == ny - 1,
+          z.reshape(-1) == 0, z.reshape(-1) == nz - 1]
+    vs, ss, vals = [], [], []
+    for f in range(6):
+        for s in range(ns):
+            if np.isnan(values[f, s]):
+                continue
+            sel = vox[on[f]]
+            vs.append(sel)
+            ss.append(np.full(sel.size, s, dtype=np.int32))
+            vals.append(np.full(sel.size, values[f, s]))
+    if not vs:
+        return (np.zeros(0, np.int64), np.zeros(0, np.int32), np.zeros(0))
+    return np.concatenate(vs).astype(np.int64), np.concatenate(ss), np.concatenate(vals)
+
+
 def random_problem(rng, nx, ny, nz, ns, n_agents=0, dirichlet=False, dx=20.0, dt=0.01,
-                   D_range=(1e2, 1e5), lam_range=(1e-3, 1.0)) -> Workload:
-    """A small random problem for edge-case parity tests (any shape, optional Dirichlet)."""
+                   D_range=(1e2, 1e5), lam_range=(1e-3, 1.0), n_nodes=0) -> Workload:
+    """A small random problem for edge-case parity tests (any shape, optional Dirichlet faces
+    and Dirichlet nodes)."""
     D = _loguniform(rng, D_range[0], D_range[1], ns)
     lam = _loguniform(rng, lam_range[0], lam_range[1], ns)
     w = Workload(f"rand_{nx}x{ny}x{nz}_s{ns}", nx, ny, nz, ns, dx, dt, D, lam, 1)
@@ -234,4 +273,6 @@ def random_problem(rng, nx, ny, nz, ns, n_agents=0, dirichlet=False, dx=20.0, dt
     if n_agents:
         w.voxel, w.secretion, w.target, w.uptake = random_agents(rng, nx * ny * nz, ns, n_agents)
         w.weight = rng.uniform(0.5, 1.5, n_agents)
+    if n_nodes:
+        w.dirichlet_nodes = random_nodes(rng, nx * ny * nz, ns, n_nodes)
     return w

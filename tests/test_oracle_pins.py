@@ -75,12 +75,15 @@ def dense_step(w, rho):
     fm = face_mask(nz, ny, nx)
 
     def B(u):
-        if w.dirichlet_on is None:
-            return u
         u = u.copy()
-        for s in range(ns):
-            if w.dirichlet_on[s]:
-                u[..., s][fm] = w.dirichlet_value[s]
+        if w.dirichlet_on is not None:
+            for s in range(ns):
+                if w.dirichlet_on[s]:
+                    u[..., s][fm] = w.dirichlet_value[s]
+        if w.dirichlet_nodes is not None:  # after the faces, in list order
+            flat = u.reshape(-1)
+            for v, s, val in zip(*w.dirichlet_nodes):
+                flat[int(v) * ns + int(s)] = val
         return u
 
     rho = B(rho)
@@ -142,9 +145,10 @@ def test_sweep_matches_dense_kronecker_solve(shape, axis):
 
 @pytest.mark.parametrize("shape", [(6, 5, 4), (3, 2, 5), (1, 4, 3), (4, 4, 1)])
 @pytest.mark.parametrize("dirichlet", [False, True])
-def test_step_matches_dense_composition(shape, dirichlet):
+@pytest.mark.parametrize("nodes", [0, 9])
+def test_step_matches_dense_composition(shape, dirichlet, nodes):
     nx, ny, nz = shape
-    w = inputs.random_problem(RNG, nx, ny, nz, 3, n_agents=7, dirichlet=dirichlet)
+    w = inputs.random_problem(RNG, nx, ny, nz, 3, n_agents=7, dirichlet=dirichlet, n_nodes=nodes)
     got = P(w).step(w.rho0, 1)
     ref = dense_step(w, w.rho0)
     np.testing.assert_allclose(got, ref, rtol=1e-13, atol=1e-12)
@@ -398,12 +402,49 @@ def test_dirichlet_steady_state_and_faces():
         assert np.all(out[..., s][fm] == c[s])
 
 
+def test_dirichlet_nodes_steady_state_and_values():
+    """Nodes holding the value of a uniform field keep it exactly without decay (the field is
+    then a fixed point of every stage); from a random start each listed element holds its last
+    listed value after every step, and an element listed twice takes the later value."""
+    w = inputs.random_problem(RNG, 6, 5, 7, 2, n_nodes=12)
+    w.lam = np.zeros(2)
+    c = 11.0
+    voxel, sub, _ = w.dirichlet_nodes
+    w.dirichlet_nodes = (voxel, sub, np.full(voxel.size, c))
+    rho = np.full(w.shape, c)
+    np.testing.assert_allclose(P(w).step(rho, 3), rho, rtol=1e-14)
+    w = inputs.random_problem(RNG, 6, 5, 7, 2, n_agents=10, n_nodes=12)
+    voxel, sub, val = w.dirichlet_nodes
+    assert (voxel[0], sub[0]) == (voxel[-1], sub[-1]) and val[0] != val[-1]
+    out = P(w).step(w.rho0, 2).reshape(-1)
+    last = {}
+    for v, s_, x in zip(voxel, sub, val):
+        last[int(v) * 2 + int(s_)] = x
+    for e, x in last.items():
+        assert out[e] == x
+
+
+def test_face_value_nodes_equal_face_dirichlet():
+    """The same value on all six faces, given as per-face nodes, is the face Dirichlet
+    condition: identical steps."""
+    w = inputs.random_problem(RNG, 5, 6, 4, 3, n_agents=9, dirichlet=True)
+    faces = np.full((6, 3), np.nan)
+    for s in range(3):
+        if w.dirichlet_on[s]:
+            faces[:, s] = w.dirichlet_value[s]
+    ref = P(w).step(w.rho0, 2)
+    w.dirichlet_nodes = inputs.face_value_nodes(5, 6, 4, faces)
+    w.dirichlet_on, w.dirichlet_value = None, None
+    np.testing.assert_array_equal(P(w).step(w.rho0, 2), ref)
+
+
 # ---------------------------------------------------------------------------------------------
 # Adjoint.
 # ---------------------------------------------------------------------------------------------
 
-def test_adjoint_dot_product_identity():
-    w = inputs.random_problem(RNG, 6, 5, 4, 2, n_agents=9, dirichlet=True)
+@pytest.mark.parametrize("nodes", [0, 10])
+def test_adjoint_dot_product_identity(nodes):
+    w = inputs.random_problem(RNG, 6, 5, 4, 2, n_agents=9, dirichlet=True, n_nodes=nodes)
     p = P(w)
     u = RNG.normal(size=w.shape)
     v = RNG.normal(size=w.shape)
@@ -435,11 +476,17 @@ def _loss_and_grads(w, n_steps, probes, targets):
     return loss, g, dD, dl, ds
 
 
-def test_adjoint_matches_central_finite_differences():
+@pytest.mark.parametrize("nodes", [0, 8])
+def test_adjoint_matches_central_finite_differences(nodes):
     """Central differences with step h carry a rounding error of about eps*|L|/h on top of the
-    O(h^2) truncation; the tolerance is 1e-6 relative plus that bound."""
-    w = inputs.random_problem(RNG, 6, 5, 4, 2, n_agents=6, dirichlet=True)
+    O(h^2) truncation; the tolerance is 1e-6 relative plus that bound.  With Dirichlet nodes,
+    some of them sit on agents' voxels (their secretion then has no effect)."""
+    w = inputs.random_problem(RNG, 6, 5, 4, 2, n_agents=6, dirichlet=True, n_nodes=nodes)
     w.dirichlet_on = np.array([1, 0], dtype=np.uint8)
+    if nodes:
+        voxel, sub, val = w.dirichlet_nodes
+        voxel[:2], sub[:2] = w.voxel[:2], 1
+        w.dirichlet_nodes = (voxel, sub, val)
     nsteps = 3
     probes = RNG.choice(w.rho0.size, 25, replace=False)
     targets = RNG.uniform(0, 38, 25)
