@@ -132,6 +132,21 @@ biofvm_status biofvm_set_params(biofvm_t *h, const double *D,
  * Errors: ARG (a spacing not finite and > 0; nothing changed), CUDA. */
 biofvm_status biofvm_set_spacing(biofvm_t *h, double dx, double dy, double dz);
 
+/* Dirichlet nodes: voxels anywhere in the grid held at a value, and faces
+ * whose values differ (give the face voxels as nodes).  Each of the four
+ * Dirichlet applications of a step (Sect. 2: before the x-solve and after each
+ * solve) overwrites the flagged faces of biofvm_boundary and then every node
+ * (voxel[k], substrate[k]) with value[k]; a (voxel, substrate) listed more
+ * than once takes its last value, and a node wins over a flagged face.  n >= 0
+ * nodes (0 removes them); voxel[k] in [0, nx*ny*nz), substrate[k] in
+ * [0, n_sub), value[k] finite; host arrays, copied.  The agents' source
+ * entries on node elements are dropped (the node overwrites them anyway), and
+ * the adjoint zeroes its gradient at the nodes at each application.  Not
+ * supported in batched environments (biofvm_batch_step then fails with ARG).
+ * Errors: ARG (nothing changed), OOM, CUDA. */
+biofvm_status biofvm_set_dirichlet_nodes(biofvm_t *h, int64_t n, const int64_t *voxel,
+                                         const int32_t *substrate, const double *value);
+
 /* Run exactly one stage of the step in place, for stage-by-stage checks:
  * stage 0 = Src then B, 1 = X^-1 then B, 2 = Y^-1 then B, 3 = Z^-1 then B,
  * 4 = the source update alone (no Dirichlet), 5 = X^-1 alone, 6 = Y^-1

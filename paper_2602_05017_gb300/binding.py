@@ -71,6 +71,8 @@ def load():
         "biofvm_set_params": (st, [vp, dp, dp]),
         "biofvm_run_stage": (st, [vp, ctypes.c_int]),
         "biofvm_set_spacing": (st, [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
+        "biofvm_set_dirichlet_nodes": (st, [vp, ctypes.c_int64, i64p,
+                                            ctypes.POINTER(ctypes.c_int32), dp]),
         "biofvm_sync": (st, [vp]),
         "biofvm_density_ptr": (st, [vp, ctypes.POINTER(vp)]),
         "biofvm_launches_per_step": (ctypes.c_int, [vp]),
@@ -226,6 +228,21 @@ class BioFVM:
             self.h, n, vox.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)) if n else None,
             *[_dptr(a) for a in arrs], _dptr(w)), self.lib)
 
+    def set_dirichlet_nodes(self, voxel, substrate, value):
+        """Dirichlet nodes (voxel, substrate, value), overwritten at every Dirichlet application
+        after the flagged faces; a repeated (voxel, substrate) keeps its last value.  Empty
+        arrays remove them."""
+        vox = np.ascontiguousarray(np.asarray(voxel, dtype=np.int64)).reshape(-1)
+        sub = np.ascontiguousarray(np.asarray(substrate, dtype=np.int32)).reshape(-1)
+        val = _f64(value, vox.size)
+        if sub.size != vox.size:
+            raise ValueError("voxel and substrate arrays differ in length")
+        n = vox.size
+        _check(self.lib.biofvm_set_dirichlet_nodes(
+            self.h, n, vox.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)) if n else None,
+            sub.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)) if n else None,
+            _dptr(val) if n else None), self.lib)
+
     def set_params(self, D, lam):
         ns = self.shape[3]
         _check(self.lib.biofvm_set_params(self.h, _dptr(_f64(D, ns)), _dptr(_f64(lam, ns))),
@@ -297,6 +314,8 @@ class BioFVM:
             sim.set_spacing(*w.spacing)
         if w.rho0 is not None:
             sim.set_density(w.rho0)
+        if w.dirichlet_nodes is not None:
+            sim.set_dirichlet_nodes(*w.dirichlet_nodes)
         if w.n_agents:
             sim.set_sources(w.voxel, w.secretion, w.target, w.uptake, w.weight)
         return sim

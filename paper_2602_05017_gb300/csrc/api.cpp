@@ -82,6 +82,7 @@ struct PipePlan {
   int have_map[2]{};
 };
 constexpr int kMaxRenorm = 16;  // steps between renormalisations of the scaled FP64 field
+constexpr int kRenormRows = 9;  // per-step constant rows of the scaled FP64 step
 
 struct StreamPlan {
   int use = 0, grid = 0;
@@ -135,7 +136,7 @@ struct biofvm {
   // FP64 streaming step: the field stays scaled by omega^-m for m < renorm_k
   // steps (no multiply by omega in the z-sweep) and is brought back every
   // renorm_k steps and at the end of every biofvm_step call; renorm_d holds the
-  // per-step constants [renorm_k][6][S] (see launch_step)
+  // per-step constants [renorm_k][kRenormRows][S] (see upload_constants)
   int renorm_k = 1;
   DevBuf renorm_d;
   // adjoint: the adjoint field, reduction partials, agents on the device
@@ -144,6 +145,18 @@ struct biofvm {
   bool agents_on_device = false;
   std::vector<int64_t> h_voxel, h_src_elem;
   std::vector<double> h_weight, h_target;
+  // the agents as last given (the source list is rebuilt when the nodes change)
+  std::vector<double> h_secretion, h_uptake;
+  // Dirichlet nodes (biofvm_set_dirichlet_nodes): the caller's list, sorted by
+  // element with the last value of a repeated element, and the list the
+  // kernels apply: those nodes plus, for a substrate whose flagged faces hold a
+  // node, its face voxels (the fused face application then skips that
+  // substrate: dir_on_k), so that nodes always win over faces
+  std::vector<int64_t> h_dn_elem, h_dn_kelem;
+  std::vector<double> h_dn_val;
+  std::vector<uint8_t> dir_on_k;  // face flags the kernels apply
+  int64_t n_dnode = 0;            // nodes the kernels apply
+  DevBuf dn_elem, dn_val;
 };
 
 namespace {
@@ -628,11 +641,12 @@ biofvm_status upload_constants(biofvm *h) {
     }
     // Per-step constants of the scaled step.  Step m of a block reads a field
     // stored as true / omega^m (omega = sigma_x sigma_y sigma_z); its rows:
-    //   [0] omega^-m                  source alpha factor
+    //   [0] omega^-m                  source alpha factor (and Dirichlet-node factor before x)
     //   [1] dval omega^-m             Dirichlet before the x-solve
     //   [2] dval / (omega^m sigma_x)  after x      [3] ... / (sigma_x sigma_y)  after y
     //   [4] dval / omega^(m+1)        after z, field left scaled
     //   [5] omega^(m+1)               z multiplier of the renormalising step (then dval after z)
+    //   [6] [7] [8]                   rows 2, 3, 4 as factors (dval = 1): Dirichlet nodes
     // renorm_k: the longest block (<= kMaxRenorm) whose omega^k stays above 1e-150.
     std::vector<double> om(S);
     double om_min = 1.0;
@@ -643,17 +657,20 @@ biofvm_status upload_constants(biofvm *h) {
     int K = 1;
     while (K < kMaxRenorm && std::pow(om_min, K + 1) >= 1e-150) K++;
     h->renorm_k = K;
-    std::vector<double> tb((size_t)K * 6 * S);
+    std::vector<double> tb((size_t)K * kRenormRows * S);
     for (int m = 0; m < K; m++)
       for (int s = 0; s < S; s++) {
         const double dv = h->dir_val[s], wm = std::pow(om[s], m);
-        double *r = &tb[(size_t)m * 6 * S];
+        double *r = &tb[(size_t)m * kRenormRows * S];
         r[s] = 1.0 / wm;
         r[S + s] = dv / wm;
         r[2 * S + s] = dv / (wm * sigma[s]);
         r[3 * S + s] = dv / (wm * sigma[s] * sigma[S + s]);
         r[4 * S + s] = dv / (wm * om[s]);
         r[5 * S + s] = wm * om[s];
+        r[6 * S + s] = 1.0 / (wm * sigma[s]);
+        r[7 * S + s] = 1.0 / (wm * sigma[s] * sigma[S + s]);
+        r[8 * S + s] = 1.0 / (wm * om[s]);
       }
     biofvm_status st = upload_doubles(h, h->renorm_d, tb);
     if (st) return st;
@@ -773,7 +790,7 @@ cudaError_t launch_stream(const biofvm *h, int axis, int flags, cudaStream_t st,
   a.dir_val = a.dir_val_in = h->dir_val_d.p;
   if (scaled) {  // the step's row of the renormalisation table (upload_constants)
     const int m = (flags >> 8) & 0xff;
-    const char *row = static_cast<const char *>(h->renorm_d.p) + (size_t)m * 6 * S * h->esz;
+    const char *row = static_cast<const char *>(h->renorm_d.p) + (size_t)m * kRenormRows * S * h->esz;
     auto at = [&](int k) { return static_cast<const void *>(row + (size_t)k * S * h->esz); };
     if (axis == 0) {
       a.src_fac = m > 0 ? at(0) : nullptr;
@@ -862,15 +879,118 @@ int step_scaled(const biofvm *h) {
   return (h->prec == BIOFVM_FP64 && h->sp[0].use && h->sp[1].use && h->sp[2].use) ? kScaled : 0;
 }
 
+// The Dirichlet nodes of one application on `field` (the handle's field when
+// NULL): their values times row `row` of step m of the renormalisation table
+// (row < 0: the values themselves), or zeros (the adjoint's mask).
+cudaError_t launch_nodes(const biofvm *h, cudaStream_t st, int m, int row, bool zero = false,
+                         void *field = nullptr) {
+  if (h->n_dnode <= 0) return cudaSuccess;
+  NodeLaunch a{};
+  a.rho = field ? field : h->rho.p;
+  a.elem = static_cast<const int64_t *>(h->dn_elem.p);
+  a.val = h->dn_val.p;
+  a.scale = row < 0 ? nullptr
+                    : static_cast<const char *>(h->renorm_d.p) +
+                          ((size_t)m * kRenormRows + row) * h->g.n_sub * h->esz;
+  a.n = h->n_dnode;
+  a.S = h->g.n_sub;
+  a.zero = zero ? 1 : 0;
+  a.grid = (int)std::max<int64_t>(1, std::min<int64_t>((a.n + 255) / 256, 4 * (int64_t)h->num_sms));
+  return h->prec == BIOFVM_FP64 ? launch_nodes_f64(a, st) : launch_nodes_f32(a, st);
+}
+
 // One step.  Scaled (FP64 streaming): step m of a renormalisation block reads a
 // field stored as true / omega^m and, unless `renorm`, leaves it as
-// true / omega^(m+1); a renormalising step stores the true field.
+// true / omega^(m+1); a renormalising step stores the true field.  Dirichlet
+// nodes, when set, take one launch around each sweep: the one before the
+// x-sweep stands for the node part of the application between Src and X^-1
+// (the source list holds no node element, and the fused face application
+// skips every substrate with a node on its faces, so the order holds).
 biofvm_status launch_step(const biofvm *h, cudaStream_t st, int m = 0, bool renorm = true) {
   const int sc = step_scaled(h);
   const int mf = sc ? (m << 8) : 0;
+  CK(launch_nodes(h, st, m, sc ? 0 : -1));
   CK(launch_x(h, kSrc | kDirBefore | kSolve | kDirAfter | sc | mf, st));
+  CK(launch_nodes(h, st, m, sc ? 6 : -1));
   CK(launch_col(h, 1, kSolve | kDirAfter | sc | mf, st));
+  CK(launch_nodes(h, st, m, sc ? 7 : -1));
   CK(launch_col(h, 2, kSolve | kDirAfter | sc | mf | (sc && !renorm ? kKeepScale : 0), st));
+  CK(launch_nodes(h, st, m, sc && !renorm ? 8 : -1));
+  return BIOFVM_OK;
+}
+
+// The device source lists from the agents as last given: (element, alpha,
+// beta) per agent and substrate, sorted by element and summed, without the
+// elements of Dirichlet nodes (a node's application overwrites whatever the
+// source update left there, so its entry would have no effect).
+biofvm_status build_sources(biofvm *h) {
+  const int S = h->g.n_sub;
+  const int64_t n = (int64_t)h->h_voxel.size();
+  struct Ent {
+    int64_t e;
+    double alpha, beta;
+  };
+  std::vector<Ent> ent;
+  ent.reserve((size_t)n * S);
+  for (int64_t k = 0; k < n; k++) {
+    const double w = h->h_weight.empty() ? 1.0 : h->h_weight[k];
+    for (int s = 0; s < S; s++) {
+      const double sv = h->h_secretion[k * S + s], uv = h->h_uptake[k * S + s];
+      const double tv = h->h_target[k * S + s];
+      const double alpha = h->dt * w * sv * tv, beta = h->dt * w * (sv + uv);
+      const int64_t e = h->h_voxel[k] * S + s;
+      if ((alpha != 0.0 || beta != 0.0) &&
+          !std::binary_search(h->h_dn_kelem.begin(), h->h_dn_kelem.end(), e))
+        ent.push_back({e, alpha, beta});
+    }
+  }
+  std::stable_sort(ent.begin(), ent.end(), [](const Ent &a, const Ent &b) { return a.e < b.e; });
+  size_t u = 0;
+  for (size_t i = 0; i < ent.size(); i++) {
+    if (u > 0 && ent[u - 1].e == ent[i].e) {
+      ent[u - 1].alpha += ent[i].alpha;
+      ent[u - 1].beta += ent[i].beta;
+    } else {
+      ent[u++] = ent[i];
+    }
+  }
+  ent.resize(u);
+  const int64_t rowlen = (int64_t)h->g.nx * S;
+  const int64_t nrows = (int64_t)h->g.ny * h->g.nz;
+  std::vector<int64_t> off(nrows + 1, 0), elem(u);
+  std::vector<int32_t> rowcol(2 * u);  // (row, position in the row) of each entry
+  std::vector<double> alpha(u), scale(u);
+  for (size_t i = 0; i < u; i++) {
+    off[ent[i].e / rowlen + 1]++;
+    elem[i] = ent[i].e;
+    rowcol[2 * i] = (int32_t)(ent[i].e / rowlen);
+    rowcol[2 * i + 1] = (int32_t)(ent[i].e % rowlen);
+    alpha[i] = ent[i].alpha;
+    scale[i] = 1.0 / (1.0 + ent[i].beta);
+  }
+  for (int64_t r = 0; r < nrows; r++) off[r + 1] += off[r];
+  CK(cudaStreamSynchronize(h->stream));  // the kernels may still read the old lists
+  h->n_entries = 0;
+  if (dev_alloc(h->src_row_off, off.size() * 8) != cudaSuccess)
+    return fail(BIOFVM_ERR_OOM, "device allocation for the source offsets failed");
+  CK(cudaMemcpy(h->src_row_off.p, off.data(), off.size() * 8, cudaMemcpyHostToDevice));
+  if (u > 0) {
+    if (dev_alloc(h->src_elem, u * 8) != cudaSuccess)
+      return fail(BIOFVM_ERR_OOM, "device allocation for %zu source entries failed", u);
+    CK(cudaMemcpy(h->src_elem.p, elem.data(), u * 8, cudaMemcpyHostToDevice));
+    if (dev_alloc(h->src_rowcol, u * 8) != cudaSuccess)
+      return fail(BIOFVM_ERR_OOM, "device allocation for %zu source entries failed", u);
+    CK(cudaMemcpy(h->src_rowcol.p, rowcol.data(), u * 8, cudaMemcpyHostToDevice));
+    biofvm_status st = upload_doubles(h, h->src_alpha, alpha);
+    if (st) return st;
+    st = upload_doubles(h, h->src_scale, scale);
+    if (st) return st;
+  }
+  h->n_entries = (int64_t)u;
+  h->h_src_elem = elem;
+  h->agents_on_device = false;  // the adjoint's agent-to-entry map follows the list
+  h->generation++;
+  drop_graphs(h);  // kernel arguments changed
   return BIOFVM_OK;
 }
 
@@ -902,7 +1022,7 @@ void destroy_impl(biofvm *h) {
                     &h->stream_const_d, &h->scratch, &h->dir_on_d, &h->dir_val_d,
                     &h->status, &h->src_row_off, &h->src_elem, &h->src_rowcol, &h->src_alpha, &h->src_scale,
                     &h->adj, &h->partial, &h->ag_elem, &h->ag_entry, &h->ag_weight,
-                    &h->ag_target})
+                    &h->ag_target, &h->dn_elem, &h->dn_val})
     b->release();
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   delete h;
@@ -986,6 +1106,7 @@ biofvm_status create_impl(const biofvm_grid *grid, double dx, double dt, const d
       }
     }
   }
+  h->dir_on_k = h->dir_on;
   h->prec = prec;
   h->esz = fp64 ? 8 : 4;
   h->nel = (size_t)g.nx * g.ny * g.nz * g.n_sub;
@@ -1030,7 +1151,7 @@ biofvm_status create_impl(const biofvm_grid *grid, double dx, double dt, const d
   }
   if ((e = cudaMemsetAsync(h->rho.p, 0, h->nel * h->esz, h->stream)) != cudaSuccess ||
       (e = cudaMemsetAsync(h->status.p, 0, sizeof(int), h->stream)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(h->dir_on_d.p, h->dir_on.data(), g.n_sub, cudaMemcpyHostToDevice,
+      (e = cudaMemcpyAsync(h->dir_on_d.p, h->dir_on_k.data(), g.n_sub, cudaMemcpyHostToDevice,
                            h->stream)) != cudaSuccess) {
     destroy_impl(h);
     return fail(BIOFVM_ERR_CUDA, "initialising device memory failed: %s", cudaGetErrorString(e));
@@ -1102,7 +1223,9 @@ biofvm_status biofvm_density_ptr(biofvm_t *h, void **dev_ptr) {
   return BIOFVM_OK;
 }
 
-int biofvm_launches_per_step(const biofvm_t *h) { return h ? 3 : 0; }
+int biofvm_launches_per_step(const biofvm_t *h) {
+  return h ? 3 + (h->n_dnode > 0 ? 4 : 0) : 0;  // the sweeps (+ the Dirichlet nodes)
+}
 
 biofvm_status biofvm_set_params(biofvm_t *h, const double *D, const double *lambda) {
   if (!h) return fail(BIOFVM_ERR_ARG, "NULL handle");
@@ -1123,6 +1246,97 @@ biofvm_status biofvm_set_spacing(biofvm_t *h, double dx, double dy, double dz) {
   h->h3[1] = dy;
   h->h3[2] = dz;
   return upload_constants(h);
+}
+
+biofvm_status biofvm_set_dirichlet_nodes(biofvm_t *h, int64_t n, const int64_t *voxel,
+                                         const int32_t *substrate, const double *value) {
+  if (!h) return fail(BIOFVM_ERR_ARG, "NULL handle");
+  if (n < 0) return fail(BIOFVM_ERR_ARG, "negative node count");
+  if (n > 0 && (!voxel || !substrate || !value))
+    return fail(BIOFVM_ERR_ARG, "voxel, substrate or value is NULL");
+  const int S = h->g.n_sub, nx = h->g.nx, ny = h->g.ny, nz = h->g.nz;
+  const int64_t nvox = (int64_t)nx * ny * nz;
+  for (int64_t k = 0; k < n; k++) {
+    if (voxel[k] < 0 || voxel[k] >= nvox)
+      return fail(BIOFVM_ERR_ARG, "node %lld: voxel %lld out of range [0, %lld)", (long long)k,
+                  (long long)voxel[k], (long long)nvox);
+    if (substrate[k] < 0 || substrate[k] >= S)
+      return fail(BIOFVM_ERR_ARG, "node %lld: substrate %d out of range [0, %d)", (long long)k,
+                  (int)substrate[k], S);
+    if (!std::isfinite(value[k]))
+      return fail(BIOFVM_ERR_ARG, "node %lld: value is not finite", (long long)k);
+  }
+  CK(cudaSetDevice(h->device));
+  // the caller's list: sorted by element, a repeated element keeps its last value
+  std::vector<std::pair<int64_t, double>> user((size_t)n);
+  for (int64_t k = 0; k < n; k++) user[k] = {voxel[k] * S + substrate[k], value[k]};
+  std::stable_sort(user.begin(), user.end(),
+                   [](const std::pair<int64_t, double> &a, const std::pair<int64_t, double> &b) {
+                     return a.first < b.first;
+                   });
+  size_t u = 0;
+  for (size_t i = 0; i < user.size(); i++) {
+    if (u > 0 && user[u - 1].first == user[i].first) user[u - 1] = user[i];
+    else user[u++] = user[i];
+  }
+  user.resize(u);
+  auto on_face = [&](int64_t v) {
+    const int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / ((int64_t)nx * ny));
+    return x == 0 || x == nx - 1 || y == 0 || y == ny - 1 || z == 0 || z == nz - 1;
+  };
+  // a substrate whose flagged faces hold a node has its faces applied as nodes
+  // too (the node values win there), the fused face application skipping it
+  std::vector<uint8_t> conv(S, 0);
+  for (const auto &p : user) {
+    const int s = (int)(p.first % S);
+    if (h->dir_on[s] && on_face(p.first / S)) conv[s] = 1;
+  }
+  std::vector<std::pair<int64_t, double>> kern = user;
+  for (int s = 0; s < S; s++) {
+    if (!conv[s]) continue;
+    for (int64_t v = 0; v < nvox; v++) {
+      if (!on_face(v)) continue;
+      const int64_t e = v * S + s;
+      auto it = std::lower_bound(
+          user.begin(), user.end(), e,
+          [](const std::pair<int64_t, double> &a, int64_t key) { return a.first < key; });
+      if (it == user.end() || it->first != e) kern.push_back({e, h->dir_val[s]});
+    }
+  }
+  std::sort(kern.begin(), kern.end(),
+            [](const std::pair<int64_t, double> &a, const std::pair<int64_t, double> &b) {
+              return a.first < b.first;
+            });
+  std::vector<int64_t> kel(kern.size());
+  std::vector<double> kval(kern.size());
+  for (size_t i = 0; i < kern.size(); i++) {
+    kel[i] = kern[i].first;
+    kval[i] = kern[i].second;
+  }
+  CK(cudaStreamSynchronize(h->stream));  // launches in flight may read the old lists
+  h->n_dnode = 0;
+  if (!kel.empty()) {
+    if (dev_alloc(h->dn_elem, kel.size() * 8) != cudaSuccess)
+      return fail(BIOFVM_ERR_OOM, "device allocation for %zu Dirichlet nodes failed", kel.size());
+    CK(cudaMemcpy(h->dn_elem.p, kel.data(), kel.size() * 8, cudaMemcpyHostToDevice));
+    biofvm_status st = upload_doubles(h, h->dn_val, kval);
+    if (st) return st;
+  }
+  h->n_dnode = (int64_t)kel.size();
+  h->h_dn_elem.resize(u);
+  h->h_dn_val.resize(u);
+  for (size_t i = 0; i < u; i++) {
+    h->h_dn_elem[i] = user[i].first;
+    h->h_dn_val[i] = user[i].second;
+  }
+  h->h_dn_kelem = kel;
+  h->any_dir = false;
+  for (int s = 0; s < S; s++) {
+    h->dir_on_k[s] = h->dir_on[s] && !conv[s];
+    h->any_dir = h->any_dir || h->dir_on_k[s];
+  }
+  CK(cudaMemcpy(h->dir_on_d.p, h->dir_on_k.data(), (size_t)S, cudaMemcpyHostToDevice));
+  return build_sources(h);  // no source entry on a node element; new graphs
 }
 
 biofvm_status biofvm_set_sources(biofvm_t *h, int64_t n, const int64_t *voxel,
@@ -1149,79 +1363,16 @@ biofvm_status biofvm_set_sources(biofvm_t *h, int64_t n, const int64_t *voxel,
     }
   }
   CK(cudaSetDevice(h->device));
-  // (element, alpha, beta) per agent and substrate, sorted by element and summed
-  struct Ent {
-    int64_t e;
-    double alpha, beta;
-  };
-  std::vector<Ent> ent;
-  ent.reserve((size_t)n * S);
-  for (int64_t k = 0; k < n; k++) {
-    const double w = weight ? weight[k] : 1.0;
-    for (int s = 0; s < S; s++) {
-      const double sv = secretion ? secretion[k * S + s] : 0.0;
-      const double uv = uptake ? uptake[k * S + s] : 0.0;
-      const double tv = target ? target[k * S + s] : 0.0;
-      const double alpha = h->dt * w * sv * tv, beta = h->dt * w * (sv + uv);
-      if (alpha != 0.0 || beta != 0.0) ent.push_back({voxel[k] * S + s, alpha, beta});
-    }
-  }
-  std::stable_sort(ent.begin(), ent.end(), [](const Ent &a, const Ent &b) { return a.e < b.e; });
-  size_t u = 0;
-  for (size_t i = 0; i < ent.size(); i++) {
-    if (u > 0 && ent[u - 1].e == ent[i].e) {
-      ent[u - 1].alpha += ent[i].alpha;
-      ent[u - 1].beta += ent[i].beta;
-    } else {
-      ent[u++] = ent[i];
-    }
-  }
-  ent.resize(u);
-  const int64_t rowlen = (int64_t)h->g.nx * S;
-  const int64_t nrows = (int64_t)h->g.ny * h->g.nz;
-  std::vector<int64_t> off(nrows + 1, 0), elem(u);
-  std::vector<int32_t> rowcol(2 * u);  // (row, position in the row) of each entry
-  std::vector<double> alpha(u), scale(u);
-  for (size_t i = 0; i < u; i++) {
-    off[ent[i].e / rowlen + 1]++;
-    elem[i] = ent[i].e;
-    rowcol[2 * i] = (int32_t)(ent[i].e / rowlen);
-    rowcol[2 * i + 1] = (int32_t)(ent[i].e % rowlen);
-    alpha[i] = ent[i].alpha;
-    scale[i] = 1.0 / (1.0 + ent[i].beta);
-  }
-  for (int64_t r = 0; r < nrows; r++) off[r + 1] += off[r];
-  CK(cudaStreamSynchronize(h->stream));  // the kernels may still read the old lists
-  h->n_entries = 0;
-  if (dev_alloc(h->src_row_off, off.size() * 8) != cudaSuccess)
-    return fail(BIOFVM_ERR_OOM, "device allocation for the source offsets failed");
-  CK(cudaMemcpy(h->src_row_off.p, off.data(), off.size() * 8, cudaMemcpyHostToDevice));
-  if (u > 0) {
-    if (dev_alloc(h->src_elem, u * 8) != cudaSuccess)
-      return fail(BIOFVM_ERR_OOM, "device allocation for %zu source entries failed", u);
-    CK(cudaMemcpy(h->src_elem.p, elem.data(), u * 8, cudaMemcpyHostToDevice));
-    if (dev_alloc(h->src_rowcol, u * 8) != cudaSuccess)
-      return fail(BIOFVM_ERR_OOM, "device allocation for %zu source entries failed", u);
-    CK(cudaMemcpy(h->src_rowcol.p, rowcol.data(), u * 8, cudaMemcpyHostToDevice));
-    biofvm_status st = upload_doubles(h, h->src_alpha, alpha);
-    if (st) return st;
-    st = upload_doubles(h, h->src_scale, scale);
-    if (st) return st;
-  }
-  h->n_entries = (int64_t)u;
-  // agents as the adjoint needs them (moved to the device on first use)
   h->h_voxel.assign(voxel, voxel + n);
   h->h_weight.clear();
   if (weight) h->h_weight.assign(weight, weight + n);
   h->h_target.assign((size_t)n * S, 0.0);
+  h->h_secretion.assign((size_t)n * S, 0.0);
+  h->h_uptake.assign((size_t)n * S, 0.0);
   if (target) std::copy(target, target + (size_t)n * S, h->h_target.begin());
-  h->h_src_elem = elem;
-  h->agents_on_device = false;
-  h->generation++;
-  {  // kernel arguments changed
-    drop_graphs(h);
-  }
-  return BIOFVM_OK;
+  if (secretion) std::copy(secretion, secretion + (size_t)n * S, h->h_secretion.begin());
+  if (uptake) std::copy(uptake, uptake + (size_t)n * S, h->h_uptake.begin());
+  return build_sources(h);
 }
 
 biofvm_status biofvm_step(biofvm_t *h, int n_steps) {
@@ -1266,25 +1417,42 @@ biofvm_status biofvm_step(biofvm_t *h, int n_steps) {
 biofvm_status biofvm_run_stage(biofvm_t *h, int stage) {
   if (!h) return fail(BIOFVM_ERR_ARG, "NULL handle");
   CK(cudaSetDevice(h->device));
+  if (stage < 0 || stage > 12) return fail(BIOFVM_ERR_ARG, "stage must be in [0, 12] (got %d)", stage);
+  cudaStream_t st = h->stream;
+  const int sc = step_scaled(h);
+  // Dirichlet nodes: after Src (stage 0), after each solve followed by B, and
+  // around the fused first kernel of a step (as launch_step does, step m = 0)
   switch (stage) {
-    case 0: CK(launch_x(h, kSrc | kDirBefore, h->stream)); break;
-    case 1: CK(launch_x(h, kSolve | kDirAfter, h->stream)); break;
-    case 2: CK(launch_col(h, 1, kSolve | kDirAfter, h->stream)); break;
-    case 3: CK(launch_col(h, 2, kSolve | kDirAfter, h->stream)); break;
-    case 4: CK(launch_x(h, kSrc, h->stream)); break;
-    case 5: CK(launch_x(h, kSolve, h->stream)); break;
-    case 6: CK(launch_col(h, 1, kSolve, h->stream)); break;
-    case 7: CK(launch_col(h, 2, kSolve, h->stream)); break;
-    case 8: CK(launch_x(h, kSrc | kDirBefore | kSolve | kDirAfter, h->stream)); break;
-    case 9: CK(launch_x(h, kSrc | kDirBefore | kSolve | kDirAfter | step_scaled(h), h->stream));
+    case 0: CK(launch_x(h, kSrc | kDirBefore, st)); CK(launch_nodes(h, st, 0, -1)); break;
+    case 1: CK(launch_x(h, kSolve | kDirAfter, st)); CK(launch_nodes(h, st, 0, -1)); break;
+    case 2: CK(launch_col(h, 1, kSolve | kDirAfter, st)); CK(launch_nodes(h, st, 0, -1)); break;
+    case 3: CK(launch_col(h, 2, kSolve | kDirAfter, st)); CK(launch_nodes(h, st, 0, -1)); break;
+    case 4: CK(launch_x(h, kSrc, st)); break;
+    case 5: CK(launch_x(h, kSolve, st)); break;
+    case 6: CK(launch_col(h, 1, kSolve, st)); break;
+    case 7: CK(launch_col(h, 2, kSolve, st)); break;
+    case 8:
+      CK(launch_nodes(h, st, 0, -1));
+      CK(launch_x(h, kSrc | kDirBefore | kSolve | kDirAfter, st));
+      CK(launch_nodes(h, st, 0, -1));
       break;
-    case 10: CK(launch_col(h, 1, kSolve | kDirAfter | step_scaled(h), h->stream)); break;
-    case 11: CK(launch_col(h, 2, kSolve | kDirAfter | step_scaled(h), h->stream)); break;
+    case 9:
+      CK(launch_nodes(h, st, 0, sc ? 0 : -1));
+      CK(launch_x(h, kSrc | kDirBefore | kSolve | kDirAfter | sc, st));
+      CK(launch_nodes(h, st, 0, sc ? 6 : -1));
+      break;
+    case 10:
+      CK(launch_col(h, 1, kSolve | kDirAfter | sc, st));
+      CK(launch_nodes(h, st, 0, sc ? 7 : -1));
+      break;
+    case 11:
+      CK(launch_col(h, 2, kSolve | kDirAfter | sc, st));
+      CK(launch_nodes(h, st, 0, -1));
+      break;
     case 12:
-      CK(launch_col(h, 2, kSolve | kDirAfter | step_scaled(h) | (step_scaled(h) ? kKeepScale : 0),
-                    h->stream));
+      CK(launch_col(h, 2, kSolve | kDirAfter | sc | (sc ? kKeepScale : 0), st));
+      CK(launch_nodes(h, st, 0, sc ? 8 : -1));
       break;
-    default: return fail(BIOFVM_ERR_ARG, "stage must be in [0, 12] (got %d)", stage);
   }
   return BIOFVM_OK;
 }
@@ -1295,18 +1463,25 @@ biofvm_status biofvm_step_save(biofvm_t *h, void *saved) {
   const size_t bytes = h->nel * h->esz;
   char *sv = static_cast<char *>(saved);
   cudaStream_t st = h->stream;
+  auto B = [&]() -> cudaError_t {  // faces, then nodes
+    if (h->any_dir) {
+      const cudaError_t e = launch_x(h, kDirAfter, st);
+      if (e != cudaSuccess) return e;
+    }
+    return launch_nodes(h, st, 0, -1);
+  };
   CK(launch_x(h, kSrc, st));
   CK(cudaMemcpyAsync(sv, h->rho.p, bytes, cudaMemcpyDeviceToDevice, st));
-  if (h->any_dir) CK(launch_x(h, kDirAfter, st));
+  CK(B());
   CK(launch_x(h, kSolve, st));
   CK(cudaMemcpyAsync(sv + bytes, h->rho.p, bytes, cudaMemcpyDeviceToDevice, st));
-  if (h->any_dir) CK(launch_x(h, kDirAfter, st));
+  CK(B());
   CK(launch_col(h, 1, kSolve, st));
   CK(cudaMemcpyAsync(sv + 2 * bytes, h->rho.p, bytes, cudaMemcpyDeviceToDevice, st));
-  if (h->any_dir) CK(launch_x(h, kDirAfter, st));
+  CK(B());
   CK(launch_col(h, 2, kSolve, st));
   CK(cudaMemcpyAsync(sv + 3 * bytes, h->rho.p, bytes, cudaMemcpyDeviceToDevice, st));
-  if (h->any_dir) CK(launch_x(h, kDirAfter, st));
+  CK(B());
   return BIOFVM_OK;
 }
 
@@ -1373,17 +1548,24 @@ biofvm_status biofvm_adjoint_step(biofvm_t *h, const void *grad_out, void *grad_
     r.dD = dD;
     return h->prec == BIOFVM_FP64 ? launch_adj_reduce_f64(r, st) : launch_adj_reduce_f32(r, st);
   };
+  auto Bt = [&]() -> cudaError_t {  // adjoint of B: zero at the faces and the nodes
+    if (h->any_dir) {
+      const cudaError_t e = launch_x(h, mask, st, h->adj.p);
+      if (e != cudaSuccess) return e;
+    }
+    return launch_nodes(h, st, 0, -1, true, h->adj.p);
+  };
   CK(cudaMemcpyAsync(h->adj.p, grad_out, bytes, cudaMemcpyDeviceToDevice, st));
-  if (h->any_dir) CK(launch_x(h, mask, st, h->adj.p));
+  CK(Bt());
   CK(launch_col(h, 2, kSolve, st, 1));
   CK(reduce(2, sv + 3 * bytes));
-  if (h->any_dir) CK(launch_x(h, mask, st, h->adj.p));
+  CK(Bt());
   CK(launch_col(h, 1, kSolve, st, 1));
   CK(reduce(1, sv + 2 * bytes));
-  if (h->any_dir) CK(launch_x(h, mask, st, h->adj.p));
+  CK(Bt());
   CK(launch_x(h, kSolve, st, h->adj.p));
   CK(reduce(0, sv + bytes));
-  if (h->any_dir) CK(launch_x(h, mask, st, h->adj.p));
+  CK(Bt());
   SrcAdjLaunch a{};
   a.gbar = h->adj.p;
   a.u1 = sv;
@@ -1487,6 +1669,8 @@ biofvm_status batch_upload(biofvm_batch *b) {
   std::vector<int64_t> off(3 * (size_t)(ne + 1), 0);
   for (int e = 0; e < ne; e++) {
     const biofvm *h = b->env[e];
+    if (h->n_dnode > 0)
+      return fail(BIOFVM_ERR_ARG, "environment %d: Dirichlet nodes are not supported in a batch", e);
     BatchEnv &x = d[e];
     x.field = h->rho.p;
     x.nx = h->g.nx;

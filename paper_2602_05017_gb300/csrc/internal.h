@@ -126,6 +126,16 @@ constexpr size_t kMaxDynamicSmem = 232448;
 constexpr int kReduceThreads = 256;
 
 // Adjoint parameter-gradient reduction of one sweep (adjoint.cuh).
+// Dirichlet nodes: rho[elem[k]] = val[k] * scale[elem[k] % S] (scale NULL: 1),
+// or 0 with `zero` (the adjoint's mask).  elem sorted and unique.
+struct NodeLaunch {
+  void *rho;
+  const int64_t *elem;
+  const void *val, *scale;
+  int64_t n;
+  int S, zero, grid;
+};
+
 struct ReduceLaunch {
   const void *mu, *u;           // adjoint after the sweep, forward sweep output
   long long nel, stride, used;  // elements; element stride along the axis; threads used
@@ -178,6 +188,8 @@ cudaError_t launch_stream_f32(const StreamArgs &a, int grid, cudaStream_t st);
 void set_error_message(const char *msg);
 
 cudaError_t launch_adj_reduce_f64(const ReduceLaunch &a, cudaStream_t st);
+cudaError_t launch_nodes_f64(const NodeLaunch &a, cudaStream_t st);
+cudaError_t launch_nodes_f32(const NodeLaunch &a, cudaStream_t st);
 cudaError_t launch_adj_reduce_f32(const ReduceLaunch &a, cudaStream_t st);
 cudaError_t launch_src_adjoint_f64(const SrcAdjLaunch &a, cudaStream_t st);
 cudaError_t launch_src_adjoint_f32(const SrcAdjLaunch &a, cudaStream_t st);

@@ -464,6 +464,28 @@ __global__ void __launch_bounds__(ColBound<E, MAXM>::threads) col_sweep_kernel(c
 }
 
 // ----------------------------------------------------------------------------
+// Dirichlet nodes (the listed part of every Dirichlet application): one thread
+// per node, grid-strided.  The elements are unique, so the writes never meet.
+// ----------------------------------------------------------------------------
+template <typename E>
+__global__ void __launch_bounds__(256) dirichlet_nodes_kernel(const NodeLaunch a) {
+  E *rho = static_cast<E *>(a.rho);
+  const E *val = static_cast<const E *>(a.val), *scale = static_cast<const E *>(a.scale);
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < a.n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = __ldg(a.elem + k);
+    rho[e] = a.zero ? E(0) : scale ? __ldg(val + k) * __ldg(scale + e % a.S) : __ldg(val + k);
+  }
+}
+
+template <typename E>
+cudaError_t launch_nodes_one(const NodeLaunch &a, cudaStream_t st) {
+  if (a.n <= 0) return cudaSuccess;
+  dirichlet_nodes_kernel<E><<<a.grid, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------
 // Dispatch on the register-chunk capacity.
 // ----------------------------------------------------------------------------
 template <typename E, int MAXM>

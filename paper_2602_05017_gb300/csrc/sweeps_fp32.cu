@@ -51,6 +51,10 @@ cudaError_t allow_x_smem_f32(int maxm, size_t bytes) {
 }
 
 
+cudaError_t launch_nodes_f32(const NodeLaunch &a, cudaStream_t st) {
+  return launch_nodes_one<float>(a, st);
+}
+
 cudaError_t launch_adj_reduce_f32(const ReduceLaunch &a, cudaStream_t st) {
   adj_reduce_kernel<float><<<a.nblocks, kReduceThreads, 0, st>>>(
       static_cast<const float *>(a.mu), static_cast<const float *>(a.u), a.nel, a.S, a.stride,

@@ -44,6 +44,10 @@ cudaError_t allow_x_smem_f64(int maxm, size_t bytes) {
 }
 
 
+cudaError_t launch_nodes_f64(const NodeLaunch &a, cudaStream_t st) {
+  return launch_nodes_one<double>(a, st);
+}
+
 cudaError_t launch_adj_reduce_f64(const ReduceLaunch &a, cudaStream_t st) {
   adj_reduce_kernel<double><<<a.nblocks, kReduceThreads, 0, st>>>(
       static_cast<const double *>(a.mu), static_cast<const double *>(a.u), a.nel, a.S, a.stride,

@@ -53,6 +53,8 @@ def gpu_loss_and_grads(torch, w, n_steps, probes, targets, prec="fp64", ckpt=3):
     dt = torch.float64 if prec == "fp64" else torch.float32
     sim = binding.BioFVM(w.nx, w.ny, w.nz, w.ns, w.dx, w.dt, w.D, w.lam, w.dirichlet_on,
                          w.dirichlet_value, precision=prec)
+    if w.dirichlet_nodes is not None:
+        sim.set_dirichlet_nodes(*w.dirichlet_nodes)
     rho0 = torch.tensor(w.rho0, dtype=torch.float64, device="cuda", requires_grad=True)
     sec = torch.tensor(w.secretion, dtype=torch.float64, device="cuda", requires_grad=True)
     D = torch.tensor(w.D, dtype=torch.float64, device="cuda", requires_grad=True)
@@ -102,6 +104,44 @@ def test_one_adjoint_step_matches_cpu_adjoint(torch, monkeypatch, stream):
     assert rel(dD.cpu().numpy(), dD_c) <= 1e-10
     assert rel(dl.cpu().numpy(), dl_c) <= 1e-10
     assert rel(ds.cpu().numpy(), ds_c.reshape(-1)) <= 1e-10
+
+
+@pytest.mark.parametrize("stream", ["0", "1"])
+def test_adjoint_with_dirichlet_nodes_matches_cpu_adjoint(torch, monkeypatch, stream):
+    """Dirichlet nodes inside, on flagged faces and on agents' voxels: one adjoint step (the
+    gradient zeroed at the nodes at every application, no secretion gradient where a node
+    sits) and a 7-step loss against the CPU adjoint."""
+    from paper_2602_05017_gb300 import binding
+    monkeypatch.setenv("BIOFVM_STREAM", stream)
+    w, probes, targets = _problem(31, shape=(14, 12, 10))
+    rng = np.random.default_rng(32)
+    voxel, sub, val = inputs.random_nodes(rng, 14 * 12 * 10, w.ns, 40)
+    voxel[:5], sub[:5] = w.voxel[:5], 0
+    w.dirichlet_nodes = (voxel, sub, val)
+    p = oracle.Problem(**w.oracle_kwargs())
+    gout = rng.normal(size=w.shape)
+    gin_c, dD_c, dl_c, ds_c, _ = p.adjoint_step(w.rho0, gout)
+    sim = binding.BioFVM.from_workload(w, precision="fp64")
+    saved = torch.empty(4 * sim.n_elem, dtype=torch.float64, device="cuda")
+    sim.step_save(saved)
+    g = torch.tensor(gout, device="cuda")
+    dD = torch.zeros(w.ns, dtype=torch.float64, device="cuda")
+    dl = torch.zeros_like(dD)
+    ds = torch.zeros(w.n_agents * w.ns, dtype=torch.float64, device="cuda")
+    sim.adjoint_step(g, g, dD, dl, ds, saved)
+    sim.sync()
+    assert rel(sim.density(), p.step(w.rho0, 1)) <= 1e-12
+    sim.close()
+    assert rel(g.cpu().numpy(), gin_c) <= 1e-10
+    assert rel(dD.cpu().numpy(), dD_c) <= 1e-10
+    assert rel(dl.cpu().numpy(), dl_c) <= 1e-10
+    assert rel(ds.cpu().numpy(), ds_c.reshape(-1)) <= 1e-10
+    assert np.all(ds.cpu().numpy().reshape(w.n_agents, w.ns)[:5, 0] == 0.0)
+    Lc, gc, dDc, dlc, dsc = cpu_loss_and_grads(w, 7, probes, targets)
+    Lg, gg, dDg, dlg, dsg = gpu_loss_and_grads(torch, w, 7, probes, targets, ckpt=3)
+    assert abs(Lg - Lc) <= 1e-12 * abs(Lc)
+    for a, b in ((gg, gc), (dDg, dDc), (dlg, dlc), (dsg, dsc)):
+        assert rel(a, b) <= 1e-10
 
 
 def test_anisotropic_adjoint_matches_cpu_adjoint(torch):
