@@ -43,8 +43,12 @@ FLOPS_PER_ELEMENT_SWEEP = 5
 # roofline names, from one ncu capture of this bench's 400^3 x 4 workload; valid only for the
 # kernel version they were taken on (re-measure whenever that kernel changes).
 MEASURED_TRAFFIC = {
-    ("f64", "x-sweep"): 2829375232 + 2811293184,   # stream_sweep_kernel<double, 1>, with Src
-    ("f32", "x-sweep"): 1090918912 + 963886592,    # sweep_pipe_kernel<float, 32, 0>
+    ("f64", "x-sweep"): 2858953728 + 2839952384,   # stream_sweep_kernel<double, 1>, with Src
+    ("f64", "y-sweep"): 2693955072 + 2817628160,
+    ("f64", "z-sweep"): 2713343488 + 2828182272,   # inside a renormalisation block
+    ("f32", "x-sweep"): 1090578944 + 963336192,    # sweep_pipe_kernel<float, 32, 0, 4>, with Src
+    ("f32", "y-sweep"): 1024114944 + 959577600,    # sweep_pipe_kernel<float, 32, 1, 0>
+    ("f32", "z-sweep"): 1024157696 + 959642624,
 }
 
 
