@@ -93,14 +93,16 @@ __host__ __device__ inline int pipe_npad(int n) { return (n + 31) / 32 * 32 + 1;
 // back substitution, carry in, c d + y (FP32), Dirichlet, write-back.
 // FULL: the chunk has exactly MAXM positions (no per-position guards).
 // PS > 0: compile-time stride between positions in the staged tile.
-template <typename E, int MAXM, bool FULL, int PS>
+// mid1 runs just before the first carry barrier, mid2 just before the second
+// (the x tiles prepare the next tile's stage there).
+template <typename E, int MAXM, bool FULL, int PS, typename M1, typename M2>
 __device__ __forceinline__ bool pipe_chunk(E *p, const int ps_rt, const int len, const int lo,
                                            const int n, const int t, const int T, const int lane,
                                            const E *Ti, const E *Tm, const E *Tf, const E *Tb,
                                            const E *Tcw, const int S, const int s, const E chi,
                                            const E clo, E *s_end, E *s_beg, const int ncons,
                                            const bool dir, const bool face, const E dval,
-                                           const bool ok) {
+                                           const bool ok, M1 &&mid1, M2 &&mid2) {
   const int ps = PS > 0 ? PS : ps_rt;
   E v[MAXM];
 #pragma unroll
@@ -135,13 +137,20 @@ __device__ __forceinline__ bool pipe_chunk(E *p, const int ps_rt, const int len,
       v[i] = g;
     }
   s_end[t * 32 + lane] = g;
+  mid1();
   // The first carry barrier also ANDs the outcome of every consumer's wait
   // for the tile: on a timeout all consumers leave together, before any
   // write-back (what they computed from the unfinished stage stays local).
   if (!consumers_all(ok, ncons)) return false;
+  // carry weights Tcw[(u*T + t)*S + s] walked with pointer steps (no index
+  // arithmetic per term), in the same order as the closed form's sum
+  const int dw = T * S;
   if (t > 0) {  // chunk 0 enters with a zero carry
     E carry = E(0);
-    for (int u = t - 1; u >= 0; u--) carry = fma(Tcw[(u * T + t) * S + s], s_end[u * 32 + lane], carry);
+    const E *w = Tcw + ((t - 1) * T + t) * S + s;
+    const E *q = s_end + (t - 1) * 32 + lane;
+#pragma unroll 4
+    for (int u = t - 1; u >= 0; u--, w -= dw, q -= 32) carry = fma(__ldg(w), *q, carry);
 #pragma unroll
     for (int i = 0; i < MAXM; i++)
       if (FULL || i < len) v[i] = fma(Tf[i], carry, v[i]);
@@ -154,10 +163,14 @@ __device__ __forceinline__ bool pipe_chunk(E *p, const int ps_rt, const int len,
       v[i] = x;
     }
   s_beg[t * 32 + lane] = x;
+  mid2();
   consumers_sync(ncons);
   if (t + 1 < T) {  // the last chunk enters with a zero carry
     E carry = E(0);
-    for (int u = t + 1; u < T; u++) carry = fma(Tcw[(u * T + t) * S + s], s_beg[u * 32 + lane], carry);
+    const E *w = Tcw + ((t + 1) * T + t) * S + s;
+    const E *q = s_beg + (t + 1) * 32 + lane;
+#pragma unroll 4
+    for (int u = t + 1; u < T; u++, w += dw, q += 32) carry = fma(__ldg(w), *q, carry);
 #pragma unroll
     for (int i = 0; i < MAXM; i++)
       if (FULL || i < len) v[i] = fma(Tb[i], carry, v[i]);
@@ -298,9 +311,9 @@ __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
   // The planner keeps tile, row and column counts below 2^31, so the per-tile
   // index arithmetic below runs in 32 bits (a 64-bit division is a long
   // software sequence, and every consumer thread repeats it per tile).
-  // x tiles: the source entries flow ahead of the tiles -- the offsets of
-  // tile k+2 and this thread's first entry of tile k+1 are loaded while tile
-  // k is solved, so no tile waits on global loads for its sources.
+  // x tiles: the source entries flow ahead of the tiles -- a tile's entry
+  // offsets are loaded two preparations before its own, this thread's first
+  // entry one before, so no preparation waits on global loads.
   const bool srcs = MODE == 0 && (a.flags & kSrc) && a.has_src;
   auto src_range = [&](long long kk, long long &e0, long long &e1) {
     e0 = e1 = 0;
@@ -327,6 +340,64 @@ __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
     src_fetch(n0, n1);
     src_range(1, f0, f1);
   }
+  // Src then B on an x tile's staged rows, before its solve.  Tile 0 is
+  // prepared before the loop; tile k+1 while tile k is solved (its stage
+  // loaded): the source update before tile k's first carry barrier, the
+  // Dirichlet rows (which must see every source update, a source can sit on a
+  // face) between the two barriers, so the second one publishes the prepared
+  // stage and no barrier of its own is needed.
+  const bool dirb = MODE == 0 && (a.flags & kDirBefore);
+  const bool prep = srcs || dirb;
+  auto prep_src = [&](long long kk) {
+    E *const sg = stage0 + (int)(kk % NS) * stage_elems;
+    const long long r0 = (first + kk * gridDim.x) * a.rows_per_tile;
+    if (pv) {  // the prefetched entry, then (rarely) the thread's further ones
+      E *q = sg + (prc.x - r0) * a.pitch + prc.y;
+      *q = (*q + pal) * psc;
+    }
+    for (long long e = n0 + ctid + ncons; e < n1; e += ncons) {
+      const int2 rc = __ldg(a.src_rowcol + e);
+      E *q = sg + (rc.x - r0) * a.pitch + rc.y;
+      *q = (*q + ldg<E>(a.src_alpha, e)) * ldg<E>(a.src_scale, e);
+    }
+    // the next tile's first entries (offsets loaded one tile ago), and the
+    // offsets of the tile after it
+    n0 = f0;
+    n1 = f1;
+    src_fetch(n0, n1);
+    src_range(kk + 2, f0, f1);
+  };
+  auto prep_dir = [&](long long kk) {  // consumer warp t takes rows t, t+T, ...
+    E *const sg = stage0 + (int)(kk % NS) * stage_elems;
+    const long long r0 = (first + kk * gridDim.x) * a.rows_per_tile;
+    const int rows = (int)min((long long)a.rows_per_tile, a.nrows - r0);
+    for (int rr = t; rr < rows; rr += T) {
+      const uint32_t row = (uint32_t)r0 + (uint32_t)rr;
+      const int z = (int)(row / (uint32_t)a.ny), y = (int)row - z * a.ny;
+      E *trow = sg + (size_t)rr * a.pitch;
+      if (y == 0 || y == a.ny - 1 || z == 0 || z == a.nz - 1) {
+        for (int kk2 = lane; kk2 < a.rowlen; kk2 += 32) {
+          const int ss = kk2 % S;
+          if (a.dir_on[ss]) trow[kk2] = dir_value<E>(a.flags, a.dir_val, ss);
+        }
+      } else {
+        for (int kk2 = lane; kk2 < 2 * S; kk2 += 32) {
+          const int ss = kk2 % S;
+          if (a.dir_on[ss])
+            trow[kk2 < S ? ss : (a.nx - 1) * S + ss] = dir_value<E>(a.flags, a.dir_val, ss);
+        }
+      }
+    }
+  };
+  if (MODE == 0 && prep && count > 0) {
+    // (a timed-out wait leaves garbage in the stage; the loop's own wait for
+    // tile 0 then fails too and every consumer leaves at the first barrier)
+    mbar_wait_bounded(&full[0], 0u, a.status);
+    if (srcs) prep_src(0);
+    if (srcs && dirb) consumers_sync(ncons);
+    if (dirb) prep_dir(0);
+    consumers_sync(ncons);
+  }
   for (long long k = 0; k < count; k++) {
     const int st = (int)(k % NS);
     // (a timed-out wait is acted on at the first carry barrier of the chunk
@@ -346,46 +417,6 @@ __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
         const int z = (int)(row / (uint32_t)a.ny), y = (int)row - z * a.ny;
         face = y == 0 || y == a.ny - 1 || z == 0 || z == a.nz - 1;
       }
-      // Src then B on the staged rows, before any solve
-      if (srcs) {
-        if (pv) {  // the prefetched entry, then (rarely) the thread's further ones
-          E *q = stg + (prc.x - r0) * a.pitch + prc.y;
-          *q = (*q + pal) * psc;
-        }
-        for (long long e = n0 + ctid + ncons; e < n1; e += ncons) {
-          const int2 rc = __ldg(a.src_rowcol + e);
-          E *q = stg + (rc.x - r0) * a.pitch + rc.y;
-          *q = (*q + ldg<E>(a.src_alpha, e)) * ldg<E>(a.src_scale, e);
-        }
-        // next tile's first entries (offsets loaded one tile ago), and the
-        // offsets of the tile after it
-        n0 = f0;
-        n1 = f1;
-        src_fetch(n0, n1);
-        src_range(k + 2, f0, f1);
-      }
-      // B must see the source update of every element (a source can sit on a face)
-      if ((a.flags & kSrc) && a.has_src && (a.flags & kDirBefore)) consumers_sync(ncons);
-      if (a.flags & kDirBefore) {  // consumer warp t takes rows t, t+T, ...
-        for (int rr = t; rr < rows; rr += T) {
-          const uint32_t row = (uint32_t)r0 + (uint32_t)rr;
-          const int z = (int)(row / (uint32_t)a.ny), y = (int)row - z * a.ny;
-          E *trow = stg + (size_t)rr * a.pitch;
-          if (y == 0 || y == a.ny - 1 || z == 0 || z == a.nz - 1) {
-            for (int kk = lane; kk < a.rowlen; kk += 32) {
-              const int ss = kk % S;
-              if (a.dir_on[ss]) trow[kk] = dir_value<E>(a.flags, a.dir_val, ss);
-            }
-          } else {
-            for (int kk = lane; kk < 2 * S; kk += 32) {
-              const int ss = kk % S;
-              if (a.dir_on[ss])
-                trow[kk < S ? ss : (a.nx - 1) * S + ss] = dir_value<E>(a.flags, a.dir_val, ss);
-            }
-          }
-        }
-      }
-      if ((a.flags & (kSrc | kDirBefore)) != 0) consumers_sync(ncons);
     } else {
       const int plane = (int)((uint32_t)tile / (uint32_t)a.tiles_per_plane);
       const uint32_t c = ((uint32_t)tile - (uint32_t)plane * (uint32_t)a.tiles_per_plane) * 32u +
@@ -412,15 +443,28 @@ __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
     // the unguarded path only when every lane of the warp has a full chunk:
     // the choice is warp-uniform, so a warp never splits across the paths
     constexpr int PS = MODE == 0 ? PSX : 32;
+    const bool next = MODE == 0 && prep && k + 1 < count;
+    auto mid1 = [&]() {
+      if (next) {
+        const long long k1 = k + 1;
+        mbar_wait_bounded(&full[k1 % NS], (uint32_t)((k1 / NS) & 1), a.status);
+        if (srcs) prep_src(k1);
+      }
+    };
+    auto mid2 = [&]() {
+      if (next && dirb) prep_dir(k + 1);
+    };
     bool solved;
     if (__all_sync(0xffffffffu, len == MAXM))
       solved = pipe_chunk<E, MAXM, true, PS>(p, ps_rt, len, lo, n, t, T, lane, s_inv + rowoff,
                                              s_mul + rowoff, s_pf + rowoff, s_pb + rowoff, Tcw, S,
-                                             s, chi, clo, s_end, s_beg, ncons, dir, face, dval, ok);
+                                             s, chi, clo, s_end, s_beg, ncons, dir, face, dval, ok,
+                                             mid1, mid2);
     else
       solved = pipe_chunk<E, MAXM, false, PS>(p, ps_rt, len, lo, n, t, T, lane, s_inv + rowoff,
                                               s_mul + rowoff, s_pf + rowoff, s_pb + rowoff, Tcw, S,
-                                              s, chi, clo, s_end, s_beg, ncons, dir, face, dval, ok);
+                                              s, chi, clo, s_end, s_beg, ncons, dir, face, dval, ok,
+                                              mid1, mid2);
     if (!solved) break;
     fence_proxy_async_smem();  // generic-proxy writes -> visible to the bulk store
     mbar_arrive(&done[st]);
