@@ -143,13 +143,14 @@ __device__ __forceinline__ bool pipe_chunk(E *p, const int ps_rt, const int len,
   // write-back (what they computed from the unfinished stage stays local).
   if (!consumers_all(ok, ncons)) return false;
   // carry weights Tcw[(u*T + t)*S + s] walked with pointer steps (no index
-  // arithmetic per term), in the same order as the closed form's sum
+  // arithmetic per term), in the same order as the closed form's sum; not
+  // unrolled (unrolling by 4 measured 5% slower on the y/z tiles)
   const int dw = T * S;
   if (t > 0) {  // chunk 0 enters with a zero carry
     E carry = E(0);
     const E *w = Tcw + ((t - 1) * T + t) * S + s;
     const E *q = s_end + (t - 1) * 32 + lane;
-#pragma unroll 4
+#pragma unroll 1
     for (int u = t - 1; u >= 0; u--, w -= dw, q -= 32) carry = fma(__ldg(w), *q, carry);
 #pragma unroll
     for (int i = 0; i < MAXM; i++)
@@ -169,7 +170,7 @@ __device__ __forceinline__ bool pipe_chunk(E *p, const int ps_rt, const int len,
     E carry = E(0);
     const E *w = Tcw + ((t + 1) * T + t) * S + s;
     const E *q = s_beg + (t + 1) * 32 + lane;
-#pragma unroll 4
+#pragma unroll 1
     for (int u = t + 1; u < T; u++, w += dw, q += 32) carry = fma(__ldg(w), *q, carry);
 #pragma unroll
     for (int i = 0; i < MAXM; i++)
