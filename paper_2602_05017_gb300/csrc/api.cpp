@@ -1294,13 +1294,26 @@ biofvm_status biofvm_set_dirichlet_nodes(biofvm_t *h, int64_t n, const int64_t *
   std::vector<std::pair<int64_t, double>> kern = user;
   for (int s = 0; s < S; s++) {
     if (!conv[s]) continue;
-    for (int64_t v = 0; v < nvox; v++) {
-      if (!on_face(v)) continue;
+    auto add = [&](int64_t v) {  // a face voxel, unless the caller listed it
       const int64_t e = v * S + s;
       auto it = std::lower_bound(
           user.begin(), user.end(), e,
           [](const std::pair<int64_t, double> &a, int64_t key) { return a.first < key; });
       if (it == user.end() || it->first != e) kern.push_back({e, h->dir_val[s]});
+    };
+    // the face voxels only (each once): whole z = 0 and z = nz-1 planes, then
+    // the y = 0 and y = ny-1 rows of the planes between, then their x ends
+    for (int z = 0; z < nz; z++) {
+      const bool zf = z == 0 || z == nz - 1;
+      for (int y = 0; y < ny; y++) {
+        const int64_t row = ((int64_t)z * ny + y) * nx;
+        if (zf || y == 0 || y == ny - 1) {
+          for (int x = 0; x < nx; x++) add(row + x);
+        } else {
+          add(row);
+          if (nx > 1) add(row + nx - 1);
+        }
+      }
     }
   }
   std::sort(kern.begin(), kern.end(),
