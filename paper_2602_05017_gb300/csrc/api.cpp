@@ -437,7 +437,8 @@ void plan_pipe(biofvm *h, int axis) {
   }
   const size_t stage = (size_t)p.stage_elems * esz;
   const size_t tab = (size_t)pipe_tab_elems_host(n, (int)S) * esz;
-  const size_t scratch = 2 * (size_t)p.T * 32 * esz + 16 + 2 * 8 * 8;
+  // carry exchange [2][T][32], carry weights [T][T][S], alignment, mbarriers
+  const size_t scratch = (2 * (size_t)p.T * 32 + (size_t)p.T * p.T * S) * esz + 16 + 2 * 8 * 8;
   for (int ns = 4; ns >= 2 && !p.stages; ns--)  // the constants always staged
     if (ns * stage + tab + scratch <= kMaxDynamicSmem) p.stages = ns;
   if (!p.stages) return;

@@ -17,7 +17,7 @@
 //
 // The grid is persistent (tiles strided by gridDim.x), so loads of later
 // tiles overlap the solve and the store of earlier ones.  The axis constants
-// are staged once per CTA when they fit.
+// and the carry weights are staged once per CTA.
 //
 // Every mbarrier wait is bounded (mbar_wait_bounded): on a timeout the status
 // word is set, the consumers agree to stop through an AND-reducing barrier (no
@@ -151,7 +151,7 @@ __device__ __forceinline__ bool pipe_chunk(E *p, const int ps_rt, const int len,
     const E *w = Tcw + ((t - 1) * T + t) * S + s;
     const E *q = s_end + (t - 1) * 32 + lane;
 #pragma unroll 1
-    for (int u = t - 1; u >= 0; u--, w -= dw, q -= 32) carry = fma(__ldg(w), *q, carry);
+    for (int u = t - 1; u >= 0; u--, w -= dw, q -= 32) carry = fma(*w, *q, carry);
 #pragma unroll
     for (int i = 0; i < MAXM; i++)
       if (FULL || i < len) v[i] = fma(Tf[i], carry, v[i]);
@@ -171,7 +171,7 @@ __device__ __forceinline__ bool pipe_chunk(E *p, const int ps_rt, const int len,
     const E *w = Tcw + ((t + 1) * T + t) * S + s;
     const E *q = s_beg + (t + 1) * 32 + lane;
 #pragma unroll 1
-    for (int u = t + 1; u < T; u++, w += dw, q += 32) carry = fma(__ldg(w), *q, carry);
+    for (int u = t + 1; u < T; u++, w += dw, q += 32) carry = fma(*w, *q, carry);
 #pragma unroll
     for (int i = 0; i < MAXM; i++)
       if (FULL || i < len) v[i] = fma(Tb[i], carry, v[i]);
@@ -213,8 +213,9 @@ __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
   E *tab = stage0 + NS * stage_elems;  // [4][S][npad]
   E *s_end = tab + 4 * S * npad;
   E *s_beg = s_end + T * 32;
+  E *s_cw = s_beg + T * 32;  // [T][T][S] carry weights
   uint64_t *full = reinterpret_cast<uint64_t *>(
-      (reinterpret_cast<uintptr_t>(s_beg + T * 32) + 15) & ~uintptr_t(15));
+      (reinterpret_cast<uintptr_t>(s_cw + T * T * S) + 15) & ~uintptr_t(15));
   uint64_t *done = full + NS;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -234,6 +235,8 @@ __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
   {
     const E *gT = static_cast<const E *>(a.tab.tabT);
     for (int q = threadIdx.x; q < 4 * S * npad; q += blockDim.x) tab[q] = __ldg(gT + q);
+    const E *gW = static_cast<const E *>(a.tab.cw);
+    for (int q = threadIdx.x; q < T * T * S; q += blockDim.x) s_cw[q] = __ldg(gW + q);
   }
   __syncthreads();
   const E *s_inv = tab, *s_mul = tab + S * npad, *s_pf = s_mul + S * npad, *s_pb = s_pf + S * npad;
@@ -307,7 +310,7 @@ __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
   const int len_full = min(m, n - lo);
   const int colbase = MODE == 0 ? (lane / S) * a.pitch + lane % S : lane;
   const int ps_rt = MODE == 0 ? S : 32;
-  const E *Tcw = static_cast<const E *>(a.tab.cw);  // [T][T][S], global (L1-resident)
+  const E *Tcw = s_cw;  // [T][T][S], staged beside the other constants
   const bool dir_after = (a.flags & kDirAfter) != 0;
   // The planner keeps tile, row and column counts below 2^31, so the per-tile
   // index arithmetic below runs in 32 bits (a 64-bit division is a long
