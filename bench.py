@@ -46,9 +46,9 @@ MEASURED_TRAFFIC = {
     ("f64", "x-sweep"): 2858953728 + 2839952384,   # stream_sweep_kernel<double, 1>, with Src
     ("f64", "y-sweep"): 2693955072 + 2817628160,
     ("f64", "z-sweep"): 2713343488 + 2828182272,   # inside a renormalisation block
-    ("f32", "x-sweep"): 1089007616 + 961793536,    # sweep_pipe_kernel<float, 32, 0, 4>, with Src
-    ("f32", "y-sweep"): 1024176128 + 959534848,    # sweep_pipe_kernel<float, 32, 1, 0>
-    ("f32", "z-sweep"): 1024121088 + 959601408,
+    ("f32", "x-sweep"): 1088906752 + 961776896,    # sweep_pipe_kernel<float, 32, 0, 4>, with Src
+    ("f32", "y-sweep"): 1024289792 + 960146432,    # sweep_pipe_kernel<float, 32, 1, 0>
+    ("f32", "z-sweep"): 1024184576 + 959291392,
 }
 
 
