@@ -11,18 +11,21 @@
 //     stage (mbarrier `done`), the bulk store of that tile; the stage is
 //     reloaded after the store has finished reading it;
 //   warps 1..T (consumers): chunk t of every column of the staged tile, in
-//     registers.  x tiles first get the source update and the first Dirichlet
-//     application in shared memory.  Halos and chunk carries cross warps
-//     through shared memory between named barriers that only consumers join.
+//     registers.  Halos and chunk carries cross warps through shared memory
+//     between two named barriers per tile that only consumers join.  An x
+//     tile gets the source update and the first Dirichlet application in
+//     shared memory before its solve: the consumers apply them to the next
+//     tile's stage while solving the current one (sources before the first
+//     barrier, Dirichlet rows between the two).
 //
 // The grid is persistent (tiles strided by gridDim.x), so loads of later
 // tiles overlap the solve and the store of earlier ones.  The axis constants
 // and the carry weights are staged once per CTA.
 //
 // Every mbarrier wait is bounded (mbar_wait_bounded): on a timeout the status
-// word is set, the consumers agree to stop through an AND-reducing barrier (no
-// named barrier is left waiting), and the producer drains (bounded) the loads
-// still in flight before the CTA exits.
+// word is set, the consumers agree to stop at the first carry barrier, which
+// ANDs every consumer's wait outcome (no named barrier is left waiting), and
+// the producer drains (bounded) the loads still in flight before the CTA exits.
 #pragma once
 #include <cuda.h>
 
