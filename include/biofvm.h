@@ -194,7 +194,8 @@ biofvm_status biofvm_sync(biofvm_t *h);
  * Errors: ARG. */
 biofvm_status biofvm_density_ptr(biofvm_t *h, void **dev_ptr);
 
-/* Number of kernel launches one time step makes (3: x-, y-, z-sweep). */
+/* Number of kernel launches one time step makes: 3 (x-, y-, z-sweep), plus 4
+ * (one Dirichlet-node launch around each sweep) while Dirichlet nodes are set. */
 int biofvm_launches_per_step(const biofvm_t *h);
 
 /* ------------------------------------------------------------------------
