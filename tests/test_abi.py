@@ -63,6 +63,9 @@ def test_null_handles_are_rejected(lib):
     assert lib.biofvm_sync(None) == binding.ERR_ARG
     assert lib.biofvm_run_stage(None, 0) == binding.ERR_ARG
     assert lib.biofvm_launches_per_step(None) == 0
+    assert lib.biofvm_set_dirichlet_nodes(None, 0, None, None, None) == binding.ERR_ARG
+    assert lib.biofvm_set_spacing(None, 1.0, 1.0, 1.0) == binding.ERR_ARG
+    assert lib.biofvm_set_sources(None, 0, None, None, None, None, None) == binding.ERR_ARG
     lib.biofvm_destroy(None)  # no-op
 
 

@@ -33,3 +33,19 @@ def test_x_candidates_fit_one_warp_per_row():
         for n in (16, 33, 100, 192):
             for m in autotune.candidates(n, S)[:-1]:
                 assert math.ceil(n / m) * S <= 32
+
+
+def test_shipped_cache_is_complete_and_valid():
+    """The cache bench.py uses: every (edge bucket, substrate count) class present, each axis
+    either whole lines or a chunk length the candidates allow for that class."""
+    cache = autotune.load(autotune.default_cache_path())
+    assert cache["precision"] == "fp32"
+    for n in autotune.N_BUCKETS:
+        for S in range(1, 9):
+            m = cache["classes"][f"{n},{S}"]["m"]
+            assert len(m) == 3
+            for a, mm in enumerate(m):
+                if mm == autotune.WHOLE:
+                    continue
+                allowed = autotune.candidates(n, S) if a == 0 else autotune.candidates(n)
+                assert mm in allowed[:-1], (n, S, a, mm)
