@@ -1,26 +1,35 @@
 """Benchmark of the LOD diffusion-decay step on GB300 (one JSON line on rank 0).
 
-Workload: 400 x 400 x 400 voxels x 4 substrates interleaved per voxel, dx = 20 um,
+Headline workload: 400 x 400 x 400 voxels x 4 substrates interleaved per voxel, dx = 20 um,
 dt = 0.01 min, D = {1e5, 1e3, 5e2, 1e2} um^2/min, lambda = {0.1, 0.01, 0.4, 1e-3} /min,
 1M agents with log-uniform secretion/uptake rates, initial field uniform in [0, 38] (seeded).
 A bench step is one full LOD time step (Src, B, X^-1, B, Y^-1, B, Z^-1, B) of that grid.
-The headline runs in FP64 (the paper's precision); the FP32 path is reported beside it.
+The headline runs in FP64 (the paper's precision); FP32 is reported beside it, and the other
+workloads (50^3 x 1 FP64, 1200^3 x 2 FP32 with Dirichlet faces, 256 batched environments,
+the Sect. 5.3 end-to-end run, the adjoint) each get a leg of their own.
 
   value      voxel-substrate updates/s, field resident in HBM, graph-launched steps,
              CUDA events on the library's stream, max over ranks (replicas, weak scaling)
   e2e        the same metric through the C ABI from pinned host buffers: set_density(host),
              K steps, density(host), all inside the timed region
   roofline   dominant kernel: algorithmic bytes (one read + one write of the field per sweep)
-             or FP64 operations per launch / its average CUDA-event duration over K steps
-  cpu_baseline  the FP64 oracle, single-threaded on this host, on a bounded slab sample
+             or FP64 operations per launch / its average CUDA-event duration over K steps; the
+             FP64 arithmetic roof is the FMA rate measured in this run (biofvm_probe_fma_rate)
+  error      every leg states its error: normwise max|got - ref| / max|ref| and the largest
+             per-voxel relative error over voxels with |ref| above a floor, against the FP64
+             oracle (FP64 legs) or the oracle-validated FP64 GPU path (FP32 legs)
+  cpu_baseline  the FP64 oracle, single-threaded on this host, on a bounded slab sample, and
+             its OpenMP copy on all host cores (the paper-style CPU rate)
 
 `--impl reference` times the oracle instead (the reference arm), on the same metric.
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -32,24 +41,29 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 HBM_FALLBACK_GBS = 6800.0
-# FP64 ALU roof of a GB300: 2 FP64 FMA per clock per SM (0.5 per SM sub-partition, measured
-# with an 8-chain FMA probe: 6.28e11 FMA/s) x 152 SMs x 2070 MHz, an FMA counting 2 flops.
-FP64_FMA_PER_CLK_PER_SM = 2.0
-GB300_SMS = 152
 # Floating-point operations of the Thomas algorithm per element and sweep (Sect. 2.1, Eq. 2:
 # forward axpy + division, backward negated axpy).
 FLOPS_PER_ELEMENT_SWEEP = 5
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the kernel each
-# roofline names, from one ncu capture of this bench's 400^3 x 4 workload; valid only for the
-# kernel version they were taken on (re-measure whenever that kernel changes).
+# Sources whose kernels the traffic below was captured on (hash of their contents).
+KERNEL_SOURCES = ["stream.cuh", "sweeps.cuh", "pipe.cuh", "pipe_args.h", "internal.h",
+                  "sweeps_fp64.cu", "sweeps_fp32.cu", "pipe_fp32.cu", "api.cpp"]
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of each sweep kernel of
+# the 400^3 x 4 workload, from one ncu capture; reported only while the kernel sources still
+# hash to `sources_sha256` (otherwise the kernels changed since and traffic is null).
 MEASURED_TRAFFIC = {
-    ("f64", "x-sweep"): 2858953728 + 2839952384,   # stream_sweep_kernel<double, 1>, with Src
-    ("f64", "y-sweep"): 2693955072 + 2817628160,
-    ("f64", "z-sweep"): 2713343488 + 2828182272,   # inside a renormalisation block
-    ("f32", "x-sweep"): 1088906752 + 961776896,    # sweep_pipe_kernel<float, 32, 0, 4>, with Src
-    ("f32", "y-sweep"): 1024289792 + 960146432,    # sweep_pipe_kernel<float, 32, 1, 0>
-    ("f32", "z-sweep"): 1024184576 + 959291392,
+    "sources_sha256": None,
+    "bytes": {},
 }
+UNIT = "voxel-substrate updates/s"
+METRIC = "LOD step voxel-substrate updates/s (HBM GB/s vs peak in roofline)"
+
+
+def kernel_sources_sha256():
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2602_05017_gb300", "csrc", name), "rb") as f:
+            h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()
 
 
 def measured_peaks():
@@ -58,6 +72,26 @@ def measured_peaks():
         with open(p) as f:
             return json.load(f), "measured"
     return {"hbm_gbs": HBM_FALLBACK_GBS, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def error_stats(got, ref, floor_rel):
+    """Normwise max|got - ref| / max|ref|, and the largest |got - ref| / |ref| over elements
+    with |ref| > floor_rel * max|ref| (the per-voxel measure; values near zero excluded)."""
+    got = np.asarray(got, dtype=np.float64).reshape(-1)
+    ref = np.asarray(ref, dtype=np.float64).reshape(-1)
+    d = np.abs(got - ref)
+    m = float(np.abs(ref).max()) if ref.size else 0.0
+    big = np.abs(ref) > floor_rel * m
+    pv = float((d[big] / np.abs(ref[big])).max()) if big.any() else 0.0
+    return {"normwise": float(d.max() / max(m, 1e-300)) if ref.size else 0.0,
+            "per_voxel_max_rel": pv, "per_voxel_floor": f"|ref| > {floor_rel:g} max|ref|"}
+
+
+def merge_errors(parts):
+    """Worst of several error_stats over pieces of one result."""
+    return {"normwise": max(p["normwise"] for p in parts),
+            "per_voxel_max_rel": max(p["per_voxel_max_rel"] for p in parts),
+            "per_voxel_floor": parts[0]["per_voxel_floor"]}
 
 
 class ClockSampler:
@@ -124,12 +158,20 @@ def aggregate(ms_local, world, units_per_rank, steps, device=None):
     return ms_max, world * units_per_rank * steps / (ms_max * 1e-3)
 
 
-def workload_config():
+def workload_config(with_field=True):
     from paper_2602_05017_gb300 import inputs
     if SHAPE is None:
-        return inputs.workload(2, with_field=False)
+        return inputs.workload(2, with_field=with_field)
     nvox = SHAPE[0] * SHAPE[1] * SHAPE[2]
-    return inputs.workload(2, shape=SHAPE, with_field=False, n_agents=nvox // 64)
+    return inputs.workload(2, shape=SHAPE, with_field=with_field, n_agents=nvox // 64)
+
+
+def flush_l2(dev):
+    """Write a buffer larger than the 129 MB L2 (between timed repetitions of small fields)."""
+    import torch
+    buf = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB
+    buf.fill_(1.0)
+    del buf
 
 
 def run_gpu(args):
@@ -153,17 +195,17 @@ def run_gpu(args):
         if world > 1:
             dist.barrier()
 
-    results = {}
+    results = {"fma_rate": {p: binding.probe_fma_rate(p, stream.cuda_stream)
+                            for p in ("fp64", "fp32")}}
+    ref100 = None  # FP64 GPU field after 100 steps (the FP32 leg's reference)
     for prec in ([] if args.batch_only else (args.only or ("fp64", "fp32"))):
         esz = 8 if prec == "fp64" else 4
         tdt = torch.float64 if prec == "fp64" else torch.float32
+        ndt = np.float64 if prec == "fp64" else np.float32
         sim = binding.BioFVM(w.nx, w.ny, w.nz, w.ns, w.dx, w.dt, w.D, w.lam, precision=prec,
                              stream=stream.cuda_stream)
-        g = torch.Generator(device=dev)
-        g.manual_seed(2602050172 + rank)
-        with torch.cuda.stream(stream):
-            rho0 = torch.rand(w.shape, generator=g, device=dev, dtype=tdt) * 38.0
-        stream.synchronize()
+        host_in = torch.from_numpy(w.rho0.astype(ndt)).pin_memory()
+        rho0 = host_in.to(dev)
         sim.set_density(rho0)
         sim.set_sources(w.voxel, w.secretion, w.target, w.uptake)
         sim.step(W)
@@ -199,8 +241,6 @@ def run_gpu(args):
                "launches": sim.launches_per_step() * K, "esz": esz}
         # --- e2e: host buffers through the C ABI ---
         if rank == 0 and not args.no_e2e:
-            host_in = torch.empty(w.shape, dtype=tdt).pin_memory()
-            host_in.copy_(rho0.cpu())
             host_out = torch.empty(w.shape, dtype=tdt).pin_memory()
             ts = []
             for rep in range(1 + args.e2e_reps):
@@ -213,26 +253,75 @@ def run_gpu(args):
                 if rep > 0:
                     ts.append(t1 - t0)
             t = statistics.median(ts)
-            res["e2e"] = {"value": nel * K / t, "unit": "voxel-substrate updates/s",
+            res["e2e"] = {"value": nel * K / t, "unit": UNIT,
                           "h2d_bytes_per_step": nel * esz / K, "d2h_bytes_per_step": nel * esz / K,
                           "seconds_per_job": t,
                           "job": f"set_density(host) + {K} steps + density(host)"}
+        # --- error of this leg (rank 0, full workload only) ---
+        if rank == 0 and not args.no_error and SHAPE is None:
+            n_err = w.n_steps  # 100 steps, the FP32 target's horizon
+            sim.set_density(rho0)
+            if prec == "fp64":
+                sim.step(1)
+                one = sim.density()
+                res["error"] = {"vs_oracle_1_step_full_size":
+                                fp64_vs_oracle_one_step(w, one),
+                                "vs_oracle_100_steps_slab": fp64_slab_vs_oracle(stream)}
+                sim.set_density(rho0)
+                sim.step(n_err)
+                ref100 = sim.density()
+            else:
+                sim.step(n_err)
+                got = sim.density()
+                if ref100 is not None:
+                    res["error"] = {f"vs_fp64_gpu_{n_err}_steps": error_stats(got, ref100, 1e-6),
+                                    "reference": "FP64 GPU path (oracle-validated), same inputs"}
+                del got
         sim.close()
-        del rho0
+        del rho0, host_in
         torch.cuda.empty_cache()
         results[prec] = res
         barrier()
+    del ref100
+    full = not args.shape and not args.only and not args.batch_only
     if not args.no_batch and not args.shape and not args.only:
         results["fp32_batched"] = run_batched(args, stream, dev)
-    if rank == 0 and not args.no_paper_e2e and not args.shape and not args.only \
-            and not args.batch_only:
-        results["paper_e2e"] = {p: run_paper_e2e(p, stream, dev) for p in ("fp64", "fp32")}
-    if rank == 0 and not args.no_adjoint and not args.shape and not args.only \
-            and not args.batch_only:
-        results["adjoint"] = {p: run_adjoint(p, dev) for p in ("fp64", "fp32")}
+    if rank == 0 and full and not args.no_small:
+        results["fp64_small"] = run_small(args, stream, dev)
+    if rank == 0 and full and not args.no_large:
+        results["fp32_large"] = run_large(args, stream, dev)
+    if rank == 0 and full and not args.no_paper_e2e:
+        results["paper_e2e"] = run_paper_e2e_both(args, stream, dev)
+    if rank == 0 and full and not args.no_adjoint:
+        results["adjoint"] = run_adjoint_both(dev)
     if world > 1:
         dist.destroy_process_group()
     return rank, world, results
+
+
+def fp64_vs_oracle_one_step(w, got):
+    """One full-size FP64 step against the oracle (OpenMP copy: the same bits, all cores)."""
+    import oracle
+    t0 = time.perf_counter()
+    ref = oracle.Problem(**w.oracle_kwargs(), parallel=True).step(w.rho0, 1)
+    out = error_stats(got, ref, 1e-9)
+    out["oracle_seconds"] = time.perf_counter() - t0
+    return out
+
+
+def fp64_slab_vs_oracle(stream, steps=100, nz=8):
+    """100 FP64 steps of a 400 x 400 x nz slab of the headline recipe against the oracle."""
+    import oracle
+    from paper_2602_05017_gb300 import binding, inputs
+    w = inputs.workload(2, shape=(400, 400, nz), n_agents=1_000_000 * nz // 400)
+    sim = binding.BioFVM.from_workload(w, precision="fp64", stream=stream.cuda_stream)
+    sim.step(steps)
+    got = sim.density()
+    sim.close()
+    ref = oracle.Problem(**w.oracle_kwargs(), parallel=True).step(w.rho0, steps)
+    out = error_stats(got, ref, 1e-9)
+    out["sample"] = f"400x400x{nz}x4 slab, {steps} steps, {w.n_agents} agents"
+    return out
 
 
 def run_batched(args, stream, dev):
@@ -250,9 +339,12 @@ def run_batched(args, stream, dev):
     b = binding.BioFVMBatch(envs, precision="fp32", tile_m=shapes, stream=stream.cuda_stream)
     g = torch.Generator(device=dev)
     g.manual_seed(2602050174)
+    init = []
     for sim, w in zip(b.envs, envs):
         with torch.cuda.stream(stream):
-            sim.field_tensor().uniform_(0.0, 38.0, generator=g)
+            t = sim.field_tensor()
+            t.uniform_(0.0, 38.0, generator=g)
+            init.append(t.clone())
         sim.set_sources(w.voxel, w.secretion, w.target, w.uptake)
     stream.synchronize()
     b.step(args.warmup)
@@ -275,8 +367,176 @@ def run_batched(args, stream, dev):
            "alg_GBps": 24.0 * n_vs * K / (ms * 1e-3) / 1e9, "clocks": clk.summary(),
            "workload": "256 cubes, edge U{32..192}, 1-8 substrates, D logU[1e2,1e5], "
                        "lambda logU[1e-3,1], agents 1 per 64 voxels, zero-flux"}
+    if not args.no_error:
+        # every environment from its initial field: K batched steps in one launch against K
+        # FP64 steps of the same environment on its own (oracle-validated) FP64 handle
+        for sim, t in zip(b.envs, init):
+            sim.set_density(t)
+        b.step(K)
+        b.sync()
+        parts = []
+        for sim, t, w in zip(b.envs, init, envs):
+            got = sim.density()
+            ref = binding.BioFVM(w.nx, w.ny, w.nz, w.ns, w.dx, w.dt, w.D, w.lam,
+                                 precision="fp64", stream=stream.cuda_stream)
+            ref.set_density(t.double())
+            ref.set_sources(w.voxel, w.secretion, w.target, w.uptake)
+            ref.step(K)
+            parts.append(error_stats(got, ref.density(), 1e-6))
+            ref.close()
+        out["error"] = {f"vs_fp64_gpu_{K}_steps": merge_errors(parts),
+                        "reference": "each environment on its own FP64 GPU handle "
+                                     "(oracle-validated), same inputs; worst environment"}
+    del init
     b.close()
     torch.cuda.empty_cache()
+    return out
+
+
+def _time_job(sim, n_steps, stream, dev, reps, flush):
+    """Median CUDA-event time of `reps` jobs of n_steps graph-launched steps (L2 flushed before
+    each when the field fits in L2), with the clocks sampled."""
+    import torch
+    ts = []
+    with ClockSampler(dev.index or 0) as clk:
+        for _ in range(reps):
+            if flush:
+                flush_l2(dev)
+            torch.cuda.synchronize(dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sim.step(n_steps)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts), clk.summary()
+
+
+def run_small(args, stream, dev):
+    """Workload 1: 50^3 x 1 FP64, 200 cells, 100 steps per job: the launch-bound case (the
+    1 MB field lives in L2; 100 steps are 7 graph launches of at most 16 steps)."""
+    import oracle
+    from paper_2602_05017_gb300 import binding, inputs
+    w = inputs.workload(1)
+    sim = binding.BioFVM.from_workload(w, precision="fp64", stream=stream.cuda_stream)
+    sim.step(w.n_steps)
+    sim.sync()
+    ms, clk = _time_job(sim, w.n_steps, stream, dev, reps=20, flush=True)
+    out = {"value": w.n_vs * w.n_steps / (ms * 1e-3), "unit": UNIT, "dtype": "f64",
+           "ms_per_job": ms, "ms_per_step": ms / w.n_steps, "steps_per_job": w.n_steps,
+           "launches_per_step": sim.launches_per_step(), "clocks": clk,
+           "l2": "field 1 MB < L2: a 256 MB buffer is written before each timed job",
+           "workload": "lod_fp64_50c_s1: 50^3 x 1, D=1e5, lambda=0.1, 200 cells, 100 steps"}
+    if not args.no_error:
+        sim.set_density(w.rho0)
+        sim.step(w.n_steps)
+        got = sim.density()
+        ref = oracle.Problem(**w.oracle_kwargs()).step(w.rho0, w.n_steps)
+        out["error"] = {f"vs_oracle_{w.n_steps}_steps": error_stats(got, ref, 1e-9)}
+    sim.close()
+    return out
+
+
+def run_large(args, stream, dev):
+    """Workload 3: 1200^3 x 2 FP32 (13.8 GB), Dirichlet 38 on substrate 0, 10M agents, 20 steps;
+    the initial field (64 Gaussian blobs) is evaluated on the device."""
+    import torch
+
+    from paper_2602_05017_gb300 import binding, inputs
+    w = inputs.workload(3, with_field=False)
+    field64 = inputs.gaussian_blobs_device(w.extra["blobs"], w.nx, w.ny, w.nz, w.ns, w.dx, dev)
+    field32 = field64.float()
+    sim = binding.BioFVM.from_workload(w, precision="fp32", stream=stream.cuda_stream)
+    sim.set_density(field32)
+    sim.step(args.warmup)
+    sim.sync()
+    ms, clk = _time_job(sim, w.n_steps, stream, dev, reps=3, flush=False)
+    out = {"value": w.n_vs * w.n_steps / (ms * 1e-3), "unit": UNIT, "dtype": "f32",
+           "ms_per_step": ms / w.n_steps, "steps_per_job": w.n_steps,
+           "alg_GBps": 24.0 * w.n_vs * w.n_steps / (ms * 1e-3) / 1e9, "clocks": clk,
+           "launches_per_step": sim.launches_per_step(),
+           "workload": "lod_fp32_1200c_s2_dirichlet: 1200^3 x 2 (13.8 GB FP32; the stated "
+                       "'6.9 GB' would be one substrate), Dirichlet 38 on substrate 0, 64 "
+                       "Gaussian blobs, 10M agents, 20 steps"}
+    if not args.no_error:
+        sim.set_density(field32)
+        sim.step(w.n_steps)
+        got = torch.empty(w.shape, dtype=torch.float32, device=dev)
+        sim.density(got)
+        sim.close()
+        del field32
+        torch.cuda.empty_cache()
+        ref = binding.BioFVM.from_workload(w, precision="fp64", stream=stream.cuda_stream)
+        ref.set_density(field64)
+        del field64
+        torch.cuda.empty_cache()
+        ref.step(w.n_steps)
+        r = ref.field_tensor()
+        torch.cuda.synchronize(dev)
+        out["error"] = {f"vs_fp64_gpu_{w.n_steps}_steps": device_error_stats(got, r, 1e-6),
+                        "reference": "FP64 GPU path (oracle-validated), same inputs",
+                        "fp64_vs_oracle_2_steps_slab": large_slab_vs_oracle(stream)}
+        ref.close()
+        del got, r
+    else:
+        sim.close()
+    torch.cuda.empty_cache()
+    return out
+
+
+def device_error_stats(got, ref, floor_rel):
+    """error_stats on device tensors (fields too large to copy to the host twice)."""
+    import torch
+    m = ref.abs().max().double()
+    d_max = torch.zeros((), dtype=torch.float64, device=ref.device)
+    pv = torch.zeros((), dtype=torch.float64, device=ref.device)
+    g = got.reshape(-1)
+    r = ref.reshape(-1)
+    chunk = 1 << 28
+    for i in range(0, r.numel(), chunk):  # chunked: bounded temporaries
+        rr = r[i:i + chunk].double()
+        dd = (g[i:i + chunk].double() - rr).abs()
+        d_max = torch.maximum(d_max, dd.max())
+        big = rr.abs() > floor_rel * m
+        if bool(big.any()):
+            pv = torch.maximum(pv, (dd[big] / rr[big].abs()).max())
+    return {"normwise": float(d_max / torch.clamp(m, min=1e-300)),
+            "per_voxel_max_rel": float(pv), "per_voxel_floor": f"|ref| > {floor_rel:g} max|ref|"}
+
+
+def large_slab_vs_oracle(stream, nz=8, steps=2):
+    import oracle
+    from paper_2602_05017_gb300 import binding, inputs
+    w = inputs.workload(3, shape=(1200, 1200, nz), n_agents=10_000_000 * nz // 1200)
+    sim = binding.BioFVM.from_workload(w, precision="fp64", stream=stream.cuda_stream)
+    sim.step(steps)
+    got = sim.density()
+    sim.close()
+    ref = oracle.Problem(**w.oracle_kwargs(), parallel=True).step(w.rho0, steps)
+    out = error_stats(got, ref, 1e-9)
+    out["sample"] = f"1200x1200x{nz}x2 slab of the recipe, {steps} steps, {w.n_agents} agents"
+    return out
+
+
+def run_paper_e2e_both(args, stream, dev):
+    out = {p: run_paper_e2e(p, stream, dev) for p in ("fp64", "fp32")}
+    if not args.no_error:
+        import oracle
+        from paper_2602_05017_gb300 import binding, inputs
+        f64, f32 = out["fp64"].pop("_final"), out["fp32"].pop("_final")
+        out["fp32"]["error"] = {"vs_fp64_gpu_500_steps": error_stats(f32, f64, 1e-6)}
+        w = inputs.workload(6)
+        n = 20
+        sim = binding.BioFVM.from_workload(w, precision="fp64", stream=stream.cuda_stream)
+        sim.step(n)
+        got = sim.density()
+        sim.close()
+        ref = oracle.Problem(**w.oracle_kwargs(), parallel=True).step(w.rho0, n)
+        out["fp64"]["error"] = {f"vs_oracle_first_{n}_steps": error_stats(got, ref, 1e-9)}
+    else:
+        for p in out.values():
+            p.pop("_final", None)
     return out
 
 
@@ -321,7 +581,21 @@ def run_paper_e2e(prec, stream, dev):
                                  best)),
             "simulate_vs_per_s": w.n_vs * w.n_steps / best[3],
             "workload": "Sect. 5.3 end-to-end run: 5 mm cube = 250^3 voxels x 1 substrate, "
-                        "1000 agents (500 sources, 500 sinks), 500 steps, Gaussian profile"}
+                        "1000 agents (500 sources, 500 sinks), 500 steps, Gaussian profile",
+            "_final": host_out.numpy().copy()}
+
+
+def run_adjoint_both(dev):
+    out = {}
+    grads = {}
+    for p in ("fp64", "fp32"):
+        out[p], grads[p] = run_adjoint(p, dev)
+    g64, g32 = grads["fp64"], grads["fp32"]
+    out["fp32"]["error"] = {
+        "vs_fp64_gpu": {k: error_stats(g32[k], g64[k], 1e-6) for k in g64},
+        "reference": "FP64 GPU gradients (adjoint checked against the CPU adjoint at 1e-10 and "
+                     "FD at 1e-6 in the tests), same inputs"}
+    return out
 
 
 def run_adjoint(prec, dev):
@@ -340,6 +614,7 @@ def run_adjoint(prec, dev):
     agents = dict(voxel=w.voxel, target=w.target, uptake=w.uptake, weight=w.weight)
     pr = torch.as_tensor(w.extra["probe_index"], device=dev)
     tg = torch.as_tensor(w.extra["probe_target"], device=dev)
+    grads = {}
 
     def run(steps, backward):
         rho0 = torch.tensor(w.rho0, dtype=torch.float64, device=dev, requires_grad=True)
@@ -353,18 +628,22 @@ def run_adjoint(prec, dev):
         if backward:
             loss.backward()
         torch.cuda.synchronize(dev)
-        return time.perf_counter() - t0
+        t = time.perf_counter() - t0
+        if backward and steps == n:
+            for k, v in (("rho0", rho0), ("secretion", sec), ("D", D), ("lambda", lam)):
+                grads[k] = v.grad.detach().cpu().numpy()
+        return t
 
     run(K, True)  # warm-up: graphs, buffers
     t_fwd = min(run(n, False) for _ in range(2))
     t_all = min(run(n, True) for _ in range(2))
     sim.close()
-    return {"seconds_forward": t_fwd, "seconds_forward_and_gradients": t_all,
-            "forward_vs_per_s": w.n_vs * n / t_fwd,
-            "gradient_vs_per_s": w.n_vs * n / (t_all - t_fwd),
-            "dtype": prec.replace("fp", "f"),
-            "workload": "128^3 x 2, 200 steps, checkpoints every 20, 4096-probe loss; gradients "
-                        "w.r.t. initial field, secretion rates, D, lambda"}
+    return ({"seconds_forward": t_fwd, "seconds_forward_and_gradients": t_all,
+             "forward_vs_per_s": w.n_vs * n / t_fwd,
+             "gradient_vs_per_s": w.n_vs * n / (t_all - t_fwd),
+             "dtype": prec.replace("fp", "f"),
+             "workload": "128^3 x 2, 200 steps, checkpoints every 20, 4096-probe loss; gradients "
+                         "w.r.t. initial field, secretion rates, D, lambda"}, grads)
 
 
 def _stage_step(sim, ev, stream, renorm):
@@ -380,23 +659,47 @@ def _stage_step(sim, ev, stream, renorm):
     ev[3].record(stream)
 
 
-def cpu_baseline(args, sample_nz=8):
-    """The FP64 oracle (single thread) on a slab of the workload: 400 x 400 x sample_nz x 4."""
-    import oracle
-    from paper_2602_05017_gb300 import inputs
-    w = inputs.workload(2, shape=(400, 400, sample_nz), n_agents=1_000_000 * sample_nz // 400)
-    p = oracle.Problem(**w.oracle_kwargs())
+def host_description():
+    model = platform.processor() or platform.machine()
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"cpu_count": os.cpu_count(), "lscpu_model": model, "machine": platform.machine()}
+
+
+def _oracle_rate(p, w, seconds):
     p.step(w.rho0, 1)  # warm
     ts = []
-    t_end = time.time() + args.cpu_seconds
+    t_end = time.time() + seconds
     while time.time() < t_end or not ts:
         t0 = time.perf_counter()
         p.step(w.rho0, 1)
         ts.append(time.perf_counter() - t0)
-    t = statistics.median(ts)
-    return {"value": w.n_vs / t, "unit": "voxel-substrate updates/s", "cores": 1, "kind": "oracle",
-            "sample": f"one LOD step of a 400x400x{sample_nz}x4 slab of the workload (FP64, "
-                      f"{len(ts)} repetitions, median {t:.3f} s)"}
+    return w.n_vs / statistics.median(ts), ts
+
+
+def cpu_baseline(args, sample_nz=8):
+    """The FP64 oracle on a slab of the workload (400 x 400 x sample_nz x 4): single-threaded
+    (the parity oracle), and its OpenMP copy on every host core (the paper-style CPU rate)."""
+    import oracle
+    from paper_2602_05017_gb300 import inputs
+    w = inputs.workload(2, shape=(400, 400, sample_nz), n_agents=1_000_000 * sample_nz // 400)
+    v1, ts1 = _oracle_rate(oracle.Problem(**w.oracle_kwargs()), w, args.cpu_seconds)
+    host = host_description()
+    out = {"value": v1, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"one LOD step of a 400x400x{sample_nz}x4 slab of the workload (FP64, "
+                     f"{len(ts1)} repetitions, median {w.n_vs / v1:.3f} s)", "host": host}
+    vp, tsp = _oracle_rate(oracle.Problem(**w.oracle_kwargs(), parallel=True), w,
+                           args.cpu_seconds / 3)
+    out["openmp_all_cores"] = {"value": vp, "unit": UNIT, "cores": host["cpu_count"],
+                               "kind": "oracle, OpenMP copy (line-parallel sweeps)",
+                               "sample": f"same slab, {len(tsp)} repetitions"}
+    return out
 
 
 def run_reference(args):
@@ -430,10 +733,6 @@ def run_reference(args):
     return 0
 
 
-METRIC = "LOD step voxel-substrate updates/s (HBM GB/s vs peak in roofline)"
-UNIT = "voxel-substrate updates/s"
-
-
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -445,6 +744,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-error", action="store_true", help="skip the error checks of every leg")
+    ap.add_argument("--no-small", action="store_true", help="skip the 50^3 x 1 FP64 leg")
+    ap.add_argument("--no-large", action="store_true", help="skip the 1200^3 x 2 FP32 leg")
     ap.add_argument("--no-paper-e2e", action="store_true",
                     help="skip the Sect. 5.3 end-to-end run (time to solution)")
     ap.add_argument("--no-adjoint", action="store_true",
@@ -471,7 +773,7 @@ def main():
         print(json.dumps({"profiling_run": True, "shape": SHAPE, "results": res}), flush=True)
         return 0
     peaks, src = measured_peaks()
-    w = workload_config()
+    w = workload_config(with_field=False)
     line = {"metric": METRIC, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic"}
@@ -485,52 +787,59 @@ def main():
     line["gpu_launches"] = r64["launches"]
     line["clocks"] = r64["clocks"]
     line["e2e"] = r64.get("e2e")
-    line["roofline"] = roofline(r64, w, peaks, src)
+    line["error"] = r64.get("error")
+    fma = res["fma_rate"]
+    line["roofline"] = roofline(r64, w, peaks, src, fma)
     line["fp32"] = {"value": res["fp32"]["value"], "ms_per_step": res["fp32"]["ms_per_step"],
-                    "dtype": "f32", "roofline": roofline(res["fp32"], w, peaks, src),
+                    "dtype": "f32", "roofline": roofline(res["fp32"], w, peaks, src, fma),
                     "e2e": res["fp32"].get("e2e"), "clocks": res["fp32"]["clocks"],
+                    "error": res["fp32"].get("error"),
                     "vs_fp64": res["fp32"]["value"] / r64["value"]}
     if "fp32_batched" in res:
         bt = dict(res["fp32_batched"])
         bt["vs_fp64"] = bt["value"] / r64["value"]
         line["fp32_batched"] = bt
+    for k in ("fp64_small", "fp32_large", "paper_e2e", "adjoint"):
+        if k in res:
+            line[k] = res[k]
     line["kernel_ms"] = {"fp64": dict(zip(("x", "y", "z"), r64["kernel_ms"])),
                          "fp32": dict(zip(("x", "y", "z"), res["fp32"]["kernel_ms"]))}
-    if "paper_e2e" in res:
-        line["paper_e2e"] = res["paper_e2e"]
-    if "adjoint" in res:
-        line["adjoint"] = res["adjoint"]
+    line["fma_rate_measured"] = {"fp64_fma_per_s": fma["fp64"], "fp32_fma_per_s": fma["fp32"],
+                                 "how": "biofvm_probe_fma_rate: independent FMA chains, 32 warps "
+                                        "per SM, best of 3 CUDA-event timings, this run"}
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(args)
     print(json.dumps(line), flush=True)
     return 0
 
 
-def roofline(r, w, peaks, src):
+def roofline(r, w, peaks, src, fma):
     """Roofline of the dominant (longest) sweep kernel.  FP32: HBM-bound, algorithmic bytes =
-    one read + one write of the field.  FP64: bound by the FP64 pipe (its DRAM time, measured
-    traffic included, stays below its FP64-ALU time), algorithmic flops = Eq. 2's 5 per
-    element.  traffic: measured DRAM bytes per launch (full workload only)."""
+    one read + one write of the field.  FP64: bound by the FP64 pipe, algorithmic flops =
+    Eq. 2's 5 per element, against twice the FP64 FMA rate measured in this run.  traffic:
+    ncu-measured DRAM bytes per launch, only while the kernel sources are the ones measured."""
     kms = r["kernel_ms"]
     i = int(np.argmax(kms))
     name = ("x", "y", "z")[i]
-    traffic = None if SHAPE else MEASURED_TRAFFIC.get(("f64" if r["esz"] == 8 else "f32",
-                                                       f"{name}-sweep"))
+    prec = "f64" if r["esz"] == 8 else "f32"
+    traffic = None
+    if SHAPE is None and MEASURED_TRAFFIC["sources_sha256"] == kernel_sources_sha256():
+        traffic = MEASURED_TRAFFIC["bytes"].get(f"{prec}:{name}-sweep")
     dram = None if traffic is None else traffic / (kms[i] * 1e-3) / 1e9
+    alg_gbps = 2 * r["esz"] * w.n_vs / (kms[i] * 1e-3) / 1e9
+    hbm_peak = float(peaks["hbm_gbs"])
     if r["esz"] == 8:
-        clk = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
-        peak = 2.0 * FP64_FMA_PER_CLK_PER_SM * GB300_SMS * clk / 1e12
+        peak = 2.0 * fma["fp64"] / 1e12
         achieved = FLOPS_PER_ELEMENT_SWEEP * w.n_vs / (kms[i] * 1e-3) / 1e12
         return {"bound": "alu", "kernel": f"{name}-sweep", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
-                "peak_source": "FP64 FMA rate 2/clk/SM (measured probe) x 152 SMs x sm_max_mhz",
-                "hbm_GBps": 2 * r["esz"] * w.n_vs / (kms[i] * 1e-3) / 1e9,
+                "peak_source": "measured in this run: 2 x FP64 FMA/s of biofvm_probe_fma_rate",
+                "hbm": {"achieved_alg_GBps": alg_gbps, "peak": hbm_peak,
+                        "frac": alg_gbps / hbm_peak,
+                        "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({src})"},
                 "dram_GBps_measured_traffic": dram}
-    alg_bytes = 2 * r["esz"] * w.n_vs  # one read + one write of the field per sweep
-    achieved = alg_bytes / (kms[i] * 1e-3) / 1e9
-    peak = float(peaks["hbm_gbs"])
-    return {"bound": "hbm", "kernel": f"{name}-sweep", "achieved": achieved, "peak": peak,
-            "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+    return {"bound": "hbm", "kernel": f"{name}-sweep", "achieved": alg_gbps, "peak": hbm_peak,
+            "unit": "GB/s", "frac": alg_gbps / hbm_peak, "traffic": traffic,
             "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({src})",
             "dram_GBps_measured_traffic": dram}
 

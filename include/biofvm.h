@@ -198,6 +198,17 @@ biofvm_status biofvm_density_ptr(biofvm_t *h, void **dev_ptr);
  * (one Dirichlet-node launch around each sweep) while Dirichlet nodes are set. */
 int biofvm_launches_per_step(const biofvm_t *h);
 
+/* Measure the FMA issue rate of the current device in FP64 (prec =
+ * BIOFVM_FP64) or FP32 (BIOFVM_FP32): the arithmetic roof of the Thomas
+ * recurrences (Sect. 2.1, Eq. 2: an axpy and a division forward, an axpy
+ * backward per position; the sweeps issue them as FMAs).  Runs a kernel of
+ * independent FMA chains over the whole device on cuda_stream for about
+ * 0.1 s and writes the best of three CUDA-event timings, in FMA/s, to
+ * *fma_per_second (host).  Waits for the stream.  Allocates no device
+ * memory.  Errors: ARG, CUDA. */
+biofvm_status biofvm_probe_fma_rate(biofvm_precision prec, uintptr_t cuda_stream,
+                                    double *fma_per_second);
+
 /* ------------------------------------------------------------------------
  * Batched microenvironments: many independent grids of uneven size and
  * substrate count, advanced together by ONE persistent kernel launch per
@@ -270,22 +281,26 @@ void biofvm_batch_destroy(biofvm_batch_t *b);
  * arrays, the field layout, double for BIOFVM_FP64 or float for BIOFVM_FP32)
  * along `axis` (0 = x, 1 = y, 2 = z) of an nx x ny x nz grid of n_sub
  * substrates, ACCUMULATES into device doubles
- *     dlambda[s] += -(dt/3)    * sum_elements(s) mu * u
- *     dD[s]      += -(dt/dx^2) * sum_lines(s) sum_i (mu_{i+1}-mu_i)(u_{i+1}-u_i)
- * exactly as biofvm_adjoint_step does for each of its three sweeps, on
- * cuda_stream (async).  It calls no allocator: its per-block partial sums
- * live in one file-scope device array of 256 KB (512 blocks x 2 sums x 32
- * substrates, FP64) that every GPU loading the library holds until the
- * process exits.  Every call overwrites all the partials it reads, so
- * nothing carries over from the previous call; calls whose kernels overlap
- * on the GPU (other streams, other host threads) race on that array.  The
- * first call on each device looks the array's address up
- * (cudaGetSymbolAddress, once per device): make that first call before any
- * stream capture.  Limits: 1 <= n_sub <= 32 (larger is rejected with
- * BIOFVM_ERR_ARG).  Errors: ARG, CUDA. */
+ *     dlambda[s] += -(dt/3)        * sum_elements(s) mu * u
+ *     dD[s]      += -(dt/h_axis^2) * sum_lines(s) sum_i (mu_{i+1}-mu_i)(u_{i+1}-u_i)
+ * where h_axis is the voxel spacing along `axis` (biofvm_create's dx on an
+ * isotropic grid; the dx, dy or dz of biofvm_set_spacing on an anisotropic
+ * one), on cuda_stream (async).  These are the sums biofvm_adjoint_step
+ * forms for each of its three sweeps, but split over a different number of
+ * blocks, so the two agree to rounding (summation order), not bit for bit.
+ * It calls no allocator: its per-block partial sums live in one file-scope
+ * device array of 256 KB (512 blocks x 2 sums x 32 substrates, FP64) that
+ * every GPU loading the library holds until the process exits.  Every call
+ * overwrites all the partials it reads, so nothing carries over from the
+ * previous call; calls whose kernels overlap on the GPU (other streams, other
+ * host threads) race on that array.  The first call on each device, and the
+ * first in each new CUDA context of a device, looks the array's address up
+ * (cudaGetSymbolAddress): make that first call before any stream capture.
+ * Limits: 1 <= n_sub <= 32 (larger is rejected with BIOFVM_ERR_ARG).
+ * Errors: ARG, CUDA. */
 biofvm_status biofvm_param_grad_noalloc(const void *mu, const void *u, int nx, int ny, int nz,
                                         int n_sub, int axis, biofvm_precision prec, double dt,
-                                        double dx, double *dD, double *dlambda,
+                                        double h_axis, double *dD, double *dlambda,
                                         uintptr_t cuda_stream);
 
 /* Free the handle and all device memory it owns (waits for its stream).

@@ -31,30 +31,34 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "biofvm_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _u8p = ctypes.POINTER(ctypes.c_uint8)
 _i64p = ctypes.POINTER(ctypes.c_longlong)
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (no FMA contraction, so x86 and Arm agree bit for bit)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".tmp{os.getpid()}"
+def build(force: bool = False, parallel: bool = False) -> str:
+    """Compile the oracle with gcc (no FMA contraction, so x86 and Arm agree bit for bit).
+
+    parallel=True builds the OpenMP copy (liboracle_omp.so): the same source with its line
+    loops split over the host's cores, the paper-style CPU rate; it gives the same bits."""
+    lib = _LIB_OMP if parallel else _LIB
+    if force or not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(_SRC):
+        tmp = lib + f".tmp{os.getpid()}"
         subprocess.check_call(
-            ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c99", "-shared", "-fPIC",
-             _SRC, "-o", tmp])
-        os.replace(tmp, _LIB)
-    return _LIB
+            ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c99", "-shared", "-fPIC"]
+            + (["-fopenmp"] if parallel else []) + [_SRC, "-o", tmp])
+        os.replace(tmp, lib)
+    return lib
 
 
-_lib = None
+_libs = {}
 
 
-def _get():
-    global _lib
-    if _lib is None:
-        lib = ctypes.CDLL(build())
+def _get(parallel=False):
+    if parallel not in _libs:
+        lib = ctypes.CDLL(build(parallel=parallel))
         i, d, L = ctypes.c_int, ctypes.c_double, ctypes.c_longlong
         lib.oracle_axis_coefficients.argtypes = [i, d, d, _dp, _dp, _dp, _dp, _dp]
         lib.oracle_thomas.argtypes = [i, _dp, _dp, _dp, _dp]
@@ -71,8 +75,8 @@ def _get():
                   lib.oracle_dirichlet, lib.oracle_dirichlet_nodes, lib.oracle_sources,
                   lib.oracle_step, lib.oracle_adjoint_step):
             f.restype = ctypes.c_int
-        _lib = lib
-    return _lib
+        _libs[parallel] = lib
+    return _libs[parallel]
 
 
 def _f64(a, n=None):
@@ -99,11 +103,13 @@ class Problem:
     dirichlet_nodes: None or (voxel, substrate, value) arrays of Dirichlet nodes, overwritten at
     each Dirichlet application after the flagged faces (a repeated (voxel, substrate) takes its
     last value).
+    parallel: run on the OpenMP copy (all host cores; bit-identical results).
     """
 
     def __init__(self, nx, ny, nz, ns, dx, dt, D, lam, dirichlet_on=None, dirichlet_value=None,
                  voxel=None, secretion=None, target=None, uptake=None, weight=None,
-                 dirichlet_nodes=None):
+                 dirichlet_nodes=None, parallel=False):
+        self.parallel = bool(parallel)
         self.nx, self.ny, self.nz, self.ns = int(nx), int(ny), int(nz), int(ns)
         self.h3 = np.ascontiguousarray(np.broadcast_to(np.asarray(dx, dtype=np.float64),
                                                        (3,)).copy())
@@ -159,28 +165,28 @@ class Problem:
 
     def sweep(self, axis, rho):
         out = self._field(rho)
-        _check(_get().oracle_sweep(axis, self.nx, self.ny, self.nz, self.ns,
+        _check(_get(self.parallel).oracle_sweep(axis, self.nx, self.ny, self.nz, self.ns,
                                    float(self.h3[axis]), self.dt,
                                    _ptr(self.D), _ptr(self.lam), _ptr(out)), "sweep")
         return out
 
     def dirichlet(self, rho):
         out = self._field(rho)
-        _check(_get().oracle_dirichlet(self.nx, self.ny, self.nz, self.ns, _ptr(self.on, _u8p),
+        _check(_get(self.parallel).oracle_dirichlet(self.nx, self.ny, self.nz, self.ns, _ptr(self.on, _u8p),
                                        _ptr(self.val), _ptr(out)), "dirichlet")
-        _check(_get().oracle_dirichlet_nodes(self.nx, self.ny, self.nz, self.ns, *self._nodes(),
+        _check(_get(self.parallel).oracle_dirichlet_nodes(self.nx, self.ny, self.nz, self.ns, *self._nodes(),
                                              _ptr(out)), "dirichlet nodes")
         return out
 
     def sources(self, rho):
         out = self._field(rho)
-        _check(_get().oracle_sources(self.nx, self.ny, self.nz, self.ns, self.dt, *self._agents(),
+        _check(_get(self.parallel).oracle_sources(self.nx, self.ny, self.nz, self.ns, self.dt, *self._agents(),
                                      _ptr(out)), "sources")
         return out
 
     def step(self, rho, n_steps=1):
         out = self._field(rho)
-        _check(_get().oracle_step(self.nx, self.ny, self.nz, self.ns, _ptr(self.h3), self.dt,
+        _check(_get(self.parallel).oracle_step(self.nx, self.ny, self.nz, self.ns, _ptr(self.h3), self.dt,
                                   _ptr(self.D), _ptr(self.lam), _ptr(self.on, _u8p),
                                   _ptr(self.val), *self._nodes(), *self._agents(), int(n_steps),
                                   _ptr(out)), "step")
@@ -196,7 +202,7 @@ class Problem:
         na = self.n_agents
         dsec = np.zeros(na * self.ns)
         dupt = np.zeros(na * self.ns)
-        _check(_get().oracle_adjoint_step(
+        _check(_get(self.parallel).oracle_adjoint_step(
             self.nx, self.ny, self.nz, self.ns, _ptr(self.h3), self.dt, _ptr(self.D), _ptr(self.lam),
             _ptr(self.on, _u8p), _ptr(self.val), *self._nodes(), *self._agents(), _ptr(rho_in),
             _ptr(gout),

@@ -42,11 +42,21 @@
  *     makes the update independent of agent order.
  *
  * Layout of every field: rho[((z*ny + y)*nx + x)*ns + s].
+ *
+ * Built plain (single-threaded: the parity oracle) and, as a separate
+ * library, with -fopenmp: the "paper-style" CPU rate, the independent lines
+ * of a sweep and the elements of the source update split over the host's
+ * cores (the paper's own CPU parallelisation is over lines).  Every line and
+ * element is computed by the same statements in both builds, so the two
+ * agree bit for bit.
  * All entry points return 0 on success, -1 on bad arguments, -2 on OOM.
  */
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 typedef long long i64;
 
@@ -157,14 +167,27 @@ int oracle_sweep(int axis, int nx, int ny, int nz, int ns, double dx,
   int n;
   i64 stride, nlines;
   axis_shape(axis, nx, ny, nz, ns, &n, &stride, &nlines);
-  double *a = (double *)malloc(sizeof(double) * (size_t)n * 6);
+  int nthreads = 1; /* one line buffer per thread (the OpenMP build) */
+#ifdef _OPENMP
+  nthreads = omp_get_max_threads();
+#endif
+  double *a = (double *)malloc(sizeof(double) * (size_t)n * (5 + (size_t)nthreads));
   if (!a) return -2;
-  double *b = a + n, *c = b + n, *den = c + n, *cp = den + n, *line = cp + n;
+  double *b = a + n, *c = b + n, *den = c + n, *cp = den + n, *lines = cp + n;
   for (int s = 0; s < ns; s++) {
     double r = D[s] * dt / (dx * dx);
     double lam3 = lambda[s] * dt / 3.0;
     oracle_axis_coefficients(n, r, lam3, a, b, c, den, cp);
+    /* the lines of one substrate are independent systems */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
     for (i64 l = 0; l < nlines; l++) {
+      int tid = 0;
+#ifdef _OPENMP
+      tid = omp_get_thread_num();
+#endif
+      double *line = lines + (size_t)tid * n;
       i64 base = line_base(axis, nx, ny, ns, l, s);
       for (int i = 0; i < n; i++) line[i] = rho[base + i * stride];
       /* forward sweep: g_1 = d_1/denom_1, g_i = (d_i - a_i g_{i-1})/denom_i */
@@ -192,6 +215,9 @@ int oracle_dirichlet(int nx, int ny, int nz, int ns, const unsigned char *on,
   if (!check_grid(nx, ny, nz, ns) || !rho) return -1;
   if (!on) return 0;
   if (!value) return -1;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
   for (int z = 0; z < nz; z++)
     for (int y = 0; y < ny; y++)
       for (int x = 0; x < nx; x++) {
@@ -272,6 +298,9 @@ int oracle_sources(int nx, int ny, int nz, int ns, double dt, i64 n_agents,
   int rc = aggregate_sources(nvox, ns, dt, n_agents, voxel, sec, tgt, upt, w,
                              &alpha, &beta);
   if (rc) return rc;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
   for (i64 e = 0; e < nvox * ns; e++)
     rho[e] = (rho[e] + alpha[e]) / (1.0 + beta[e]);
   free(alpha);

@@ -92,6 +92,7 @@ def load():
                                            ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                            ctypes.c_double, ctypes.c_double, vp, vp,
                                            ctypes.c_size_t]),
+        "biofvm_probe_fma_rate": (st, [ctypes.c_int, ctypes.c_size_t, dp]),
         "biofvm_destroy": (None, [vp]),
         "biofvm_last_error": (ctypes.c_char_p, []),
     }
@@ -101,6 +102,16 @@ def load():
         f.argtypes = args
     _lib = lib
     return lib
+
+
+def probe_fma_rate(precision="fp64", stream=None):
+    """FMA/s of the current device in FP64 or FP32 (biofvm_probe_fma_rate)."""
+    lib = load()
+    out = ctypes.c_double()
+    _check(lib.biofvm_probe_fma_rate(FP64 if precision == "fp64" else FP32,
+                                     _current_stream() if stream is None else int(stream),
+                                     ctypes.byref(out)), lib)
+    return out.value
 
 
 def _check(status, lib=None):

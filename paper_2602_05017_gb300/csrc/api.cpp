@@ -68,6 +68,7 @@ cudaError_t dev_alloc(DevBuf &b, size_t bytes) {
 
 struct ColPlan {
   int T = 1, m = 1, maxm = 8;
+  int nosolve = 0;  // lines too long for register chunks: streaming or pipelined solve only
 };
 // Persistent TMA pipeline of one FP32 sweep (used when rows are 16-byte aligned
 // and a ring of >= 2 stages with the constants fits in shared memory; otherwise
@@ -89,6 +90,7 @@ struct StreamPlan {
 };
 struct XPlan {
   int T = 1, m = 1, maxm = 8, rows_per_warp = 1, warps = 1, rows_per_cta = 1, use_bulk = 0;
+  int nosolve = 0;  // rows too long to cut into register chunks: only non-solve stages
   size_t smem = 0;
 };
 
@@ -291,7 +293,12 @@ bool plan_col(int n, bool fp64, ColPlan &p, int forced_m = 0) {
   return false;
 }
 
-bool plan_x(int nx, int S, bool fp64, XPlan &p, int forced_m = 0) {
+// Plan of the plain x-sweep.  When the rows cannot be cut into register
+// chunks (more than 32/S chunks of the largest capacity) and `allow_nosolve`,
+// the plan still stages rows for the stages that do not solve (the source
+// update alone, a Dirichlet application alone); the solve then has to come
+// from the streaming or pipelined x-sweep.
+bool plan_x(int nx, int S, bool fp64, XPlan &p, int forced_m = 0, bool allow_nosolve = false) {
   const size_t esz = fp64 ? 8 : 4;
   const int Tmax = 32 / S;
   if (Tmax < 1) return false;
@@ -306,11 +313,17 @@ bool plan_x(int nx, int S, bool fp64, XPlan &p, int forced_m = 0) {
   }
   if (forced_m > 0) m = std::min(forced_m, nx);
   T = (nx + m - 1) / m;
-  if (m > largest || T > Tmax) return false;
+  p.nosolve = 0;
+  if (m > largest || T > Tmax) {
+    if (!allow_nosolve || forced_m > 0) return false;
+    T = 1;
+    m = nx;
+    p.nosolve = 1;
+  }
   p.T = T;
   p.m = m;
-  p.maxm = pick_maxm(m, fp64);
-  p.rows_per_warp = 32 / (T * S);
+  p.maxm = p.nosolve ? (fp64 ? kMaxmF64[0] : kMaxmF32[0]) : pick_maxm(m, fp64);
+  p.rows_per_warp = p.nosolve ? 1 : 32 / (T * S);  // lanes per row matter to the solve only
   const size_t rowbytes = (size_t)nx * S * esz;
   const size_t tabbytes = (4 * (size_t)nx * S + (size_t)T * S + 2 * (size_t)S) * esz + 32;
   p.use_bulk = (rowbytes % 16 == 0) ? 1 : 0;
@@ -817,6 +830,7 @@ bool pipe_ok(const biofvm *h, int axis, int flags, int buf) {
 cudaError_t launch_x(const biofvm *h, int flags, cudaStream_t st, void *field = nullptr) {
   if (stream_ok(h, 0, flags)) return launch_stream(h, 0, flags, st, field ? field : h->rho.p);
   if (pipe_ok(h, 0, flags, 0)) return launch_pipe(h, 0, flags, st, field ? field : h->rho.p, 0);
+  if ((flags & kSolve) && h->xp.nosolve) return cudaErrorInvalidConfiguration;
   XLaunch a{};
   a.rho = field ? field : h->rho.p;
   a.nx = h->g.nx;
@@ -872,6 +886,7 @@ cudaError_t launch_col(const biofvm *h, int axis, int flags, cudaStream_t st, in
   a.dir_val = h->dir_val_d.p;
   if (stream_ok(h, axis, flags)) return launch_stream(h, axis, flags, st, a.rho);
   if (pipe_ok(h, axis, flags, buf)) return launch_pipe(h, axis, flags, st, a.rho, buf);
+  if (h->cp[axis].nosolve) return cudaErrorInvalidConfiguration;
   return h->prec == BIOFVM_FP64 ? launch_col_f64(a, st) : launch_col_f32(a, st);
 }
 
@@ -1112,16 +1127,25 @@ biofvm_status create_impl(const biofvm_grid *grid, double dx, double dt, const d
   h->esz = fp64 ? 8 : 4;
   h->nel = (size_t)g.nx * g.ny * g.nz * g.n_sub;
   h->forced = force_m != nullptr;
-  if (!plan_x(g.nx, g.n_sub, fp64, h->xp, force_m ? force_m[0] : 0)) {
+  if (!plan_x(g.nx, g.n_sub, fp64, h->xp, force_m ? force_m[0] : 0, !force_m)) {
     delete h;
     return fail(BIOFVM_ERR_ARG, "x lines too long for the x-sweep tile (nx*n_sub = %d)",
                 g.nx * g.n_sub);
   }
-  if (!plan_col(g.ny, fp64, h->cp[1], force_m ? force_m[1] : 0) ||
-      !plan_col(g.nz, fp64, h->cp[2], force_m ? force_m[2] : 0)) {
-    delete h;
-    return fail(BIOFVM_ERR_ARG, "y or z lines too long for the column sweep (ny=%d nz=%d)", g.ny,
-                g.nz);
+  for (int axis = 1; axis <= 2; axis++) {
+    const int n = axis == 1 ? g.ny : g.nz;
+    if (plan_col(n, fp64, h->cp[axis], force_m ? force_m[axis] : 0)) continue;
+    if (force_m) {
+      delete h;
+      return fail(BIOFVM_ERR_ARG, "y or z lines too long for the column sweep (ny=%d nz=%d)",
+                  g.ny, g.nz);
+    }
+    // the plain column kernel cannot hold these lines; the streaming or pipelined sweep must
+    // (checked once they are planned)
+    h->cp[axis] = ColPlan{};
+    h->cp[axis].T = 1;
+    h->cp[axis].m = n;
+    h->cp[axis].nosolve = 1;
   }
   h->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
 
@@ -1177,6 +1201,17 @@ biofvm_status create_impl(const biofvm_grid *grid, double dx, double dt, const d
     for (int axis = 0; axis < 3; axis++) plan_pipe(h, axis);
   if (!h->forced)
     for (int axis = 0; axis < 3; axis++) plan_stream(h, axis);
+  if (h->xp.nosolve && !h->sp[0].use && !h->pp[0].use) {
+    destroy_impl(h);
+    return fail(BIOFVM_ERR_ARG, "x lines too long for the x-sweep tile (nx*n_sub = %d)",
+                g.nx * g.n_sub);
+  }
+  for (int axis = 1; axis <= 2; axis++)
+    if (h->cp[axis].nosolve && !h->sp[axis].use && !h->pp[axis].use) {
+      destroy_impl(h);
+      return fail(BIOFVM_ERR_ARG, "y or z lines too long for the column sweep (ny=%d nz=%d)",
+                  g.ny, g.nz);
+    }
   if ((st = upload_doubles(h, h->dir_val_d, h->dir_val)) != BIOFVM_OK ||
       (st = upload_constants(h)) != BIOFVM_OK) {
     std::string msg = g_last_error;

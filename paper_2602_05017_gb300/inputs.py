@@ -87,33 +87,74 @@ def random_agents(rng, nvox, ns, n_agents, kind="mixed", rate=(1e-3, 10.0)):
     return voxel, sec, tgt, upt
 
 
-def gaussian_blobs(rng, nx, ny, nz, ns, dx, n_blobs=64, sigma=(100.0, 400.0), amp=(0.0, 38.0),
-                   dtype=np.float64):
-    """Sum of seeded Gaussian blobs (centres uniform in the box, sigma in um, amplitude)."""
-    out = np.zeros((nz, ny, nx, ns), dtype=dtype)
+def blob_params(rng, nx, ny, nz, ns, dx, n_blobs=64, sigma=(100.0, 400.0), amp=(0.0, 38.0)):
+    """Seeded Gaussian blobs: centres uniform in the box (um), sigma (um), amplitude per
+    substrate.  Returns (cx, cy, cz, sigma, amp[n_blobs, ns])."""
     cx = rng.uniform(0, nx * dx, n_blobs)
     cy = rng.uniform(0, ny * dx, n_blobs)
     cz = rng.uniform(0, nz * dx, n_blobs)
     sg = rng.uniform(sigma[0], sigma[1], n_blobs)
     am = rng.uniform(amp[0], amp[1], (n_blobs, ns))
+    return cx, cy, cz, sg, am
+
+
+def _blob_support(g):
+    k = np.nonzero(g > 1e-30)[0]  # only planes/rows where the blob is above 1e-30 of its peak
+    return (k[0], k[-1] + 1) if k.size else None
+
+
+def gaussian_blobs(rng, nx, ny, nz, ns, dx, n_blobs=64, sigma=(100.0, 400.0), amp=(0.0, 38.0),
+                   dtype=np.float64, params=None):
+    """Sum of seeded Gaussian blobs (centres uniform in the box, sigma in um, amplitude), voxel
+    centres at (i + 1/2) dx: [nz, ny, nx, ns] on the host."""
+    cx, cy, cz, sg, am = params or blob_params(rng, nx, ny, nz, ns, dx, n_blobs, sigma, amp)
+    out = np.zeros((nz, ny, nx, ns), dtype=dtype)
     xs = (np.arange(nx) + 0.5) * dx
     ys = (np.arange(ny) + 0.5) * dx
     zs = (np.arange(nz) + 0.5) * dx
-    for b in range(n_blobs):
+    for b in range(len(cx)):
         gx = np.exp(-0.5 * ((xs - cx[b]) / sg[b]) ** 2)
         gy = np.exp(-0.5 * ((ys - cy[b]) / sg[b]) ** 2)
         gz = np.exp(-0.5 * ((zs - cz[b]) / sg[b]) ** 2)
-        # only planes/rows where the blob is above 1e-30 of its peak are touched
-        kz = np.nonzero(gz > 1e-30)[0]
-        ky = np.nonzero(gy > 1e-30)[0]
-        if kz.size == 0 or ky.size == 0:
+        sz, sy = _blob_support(gz), _blob_support(gy)
+        if sz is None or sy is None:
             continue
-        z0, z1, y0, y1 = kz[0], kz[-1] + 1, ky[0], ky[-1] + 1
+        (z0, z1), (y0, y1) = sz, sy
         plane = (gy[y0:y1, None] * gx[None, :])  # [y, x]
         for z in range(z0, z1):
             w = gz[z] * plane
             out[z, y0:y1, :, :] += (w[:, :, None] * am[b][None, None, :]).astype(dtype)
     return out
+
+
+def gaussian_blobs_device(params, nx, ny, nz, ns, dx, device, dtype=None):
+    """The same blob sum evaluated with torch on `device` (for fields too large to draw on the
+    host, e.g. 1200^3 x 2): the separable factors are formed on the host in FP64 exactly as
+    ``gaussian_blobs`` forms them, and the products are accumulated on the device in FP64, so
+    the two agree to rounding of the accumulation order."""
+    import torch
+    dtype = dtype or torch.float64
+    cx, cy, cz, sg, am = params
+    out = torch.zeros((nz, ny, nx, ns), dtype=torch.float64, device=device)
+    xs = (np.arange(nx) + 0.5) * dx
+    ys = (np.arange(ny) + 0.5) * dx
+    zs = (np.arange(nz) + 0.5) * dx
+    for b in range(len(cx)):
+        gx = np.exp(-0.5 * ((xs - cx[b]) / sg[b]) ** 2)
+        gy = np.exp(-0.5 * ((ys - cy[b]) / sg[b]) ** 2)
+        gz = np.exp(-0.5 * ((zs - cz[b]) / sg[b]) ** 2)
+        sz, sy = _blob_support(gz), _blob_support(gy)
+        if sz is None or sy is None:
+            continue
+        (z0, z1), (y0, y1) = sz, sy
+        tz = torch.as_tensor(gz[z0:z1], device=device)
+        ty = torch.as_tensor(gy[y0:y1], device=device)
+        tx = torch.as_tensor(gx, device=device)
+        ta = torch.as_tensor(am[b], device=device)
+        plane = ty[:, None] * tx[None, :]
+        for z in range(z1 - z0):  # one plane at a time bounds the temporaries
+            out[z0 + z, y0:y1] += (tz[z] * plane)[:, :, None] * ta[None, None, :]
+    return out if dtype == torch.float64 else out.to(dtype)
 
 
 # --------------------------------------------------------------------------------------------
@@ -151,8 +192,12 @@ def workload(k: int, shape=None, n_agents=None, with_field=True, field_dtype=np.
                      np.array([1e5, 1e3]), np.array([0.1, 0.01]), 20)
         w.dirichlet_on = np.array([1, 0], dtype=np.uint8)
         w.dirichlet_value = np.array([TARGET_DENSITY, 0.0])
+        # blob parameters are always drawn (so the agents do not depend on with_field);
+        # gaussian_blobs_device evaluates them on a GPU when the host field is not wanted
+        w.extra["blobs"] = blob_params(rng, nx, ny, nz, 2, w.dx)
         if with_field:
-            w.rho0 = gaussian_blobs(rng, nx, ny, nz, 2, w.dx, dtype=field_dtype)
+            w.rho0 = gaussian_blobs(rng, nx, ny, nz, 2, w.dx, dtype=field_dtype,
+                                    params=w.extra["blobs"])
         na = 10_000_000 if n_agents is None else n_agents
         w.voxel, w.secretion, w.target, w.uptake = random_agents(rng, nx * ny * nz, 2, na)
         return w

@@ -58,3 +58,23 @@ def test_random_problem_draws_are_unchanged_by_the_node_option():
     np.testing.assert_array_equal(p.rho0, q.rho0)
     np.testing.assert_array_equal(p.voxel, q.voxel)
     assert p.dirichlet_nodes is None and len(q.dirichlet_nodes[0]) == 9
+
+
+def test_blob_field_draws_do_not_depend_on_with_field():
+    """Workload 3 draws its blob parameters before its agents whether or not the host field is
+    formed, so a device-evaluated field pairs with the same agents."""
+    a = inputs.workload(3, shape=(20, 18, 16), n_agents=50)
+    b = inputs.workload(3, shape=(20, 18, 16), n_agents=50, with_field=False)
+    np.testing.assert_array_equal(a.voxel, b.voxel)
+    np.testing.assert_array_equal(a.secretion, b.secretion)
+    for x, y in zip(a.extra["blobs"], b.extra["blobs"]):
+        np.testing.assert_array_equal(x, y)
+    assert b.rho0 is None and a.rho0.shape == (16, 18, 20, 2) and a.rho0.max() > 0
+
+
+def test_device_blob_evaluator_matches_the_host_one_on_cpu():
+    import torch
+    w = inputs.workload(3, shape=(24, 20, 18), n_agents=10)
+    got = inputs.gaussian_blobs_device(w.extra["blobs"], w.nx, w.ny, w.nz, 2, w.dx, "cpu")
+    np.testing.assert_allclose(got.numpy(), w.rho0, rtol=1e-13, atol=1e-12 * w.rho0.max())
+    assert got.dtype == torch.float64

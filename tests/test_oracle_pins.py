@@ -541,3 +541,16 @@ def test_bad_arguments_are_rejected():
         P(w).step(w.rho0, 1)
     with pytest.raises(ValueError):
         oracle.axis_coefficients(0, 1.0, 0.0)
+
+
+# ---------------------------------------------------------------------------------------------
+# The OpenMP copy (paper-style CPU rate) computes every line with the same statements.
+# ---------------------------------------------------------------------------------------------
+
+def test_openmp_copy_gives_the_same_bits_as_the_plain_oracle():
+    rng = np.random.default_rng(404)
+    w = inputs.random_problem(rng, 23, 19, 17, 3, n_agents=60, dirichlet=True, n_nodes=25)
+    w.spacing = (20.0, 17.0, 26.0)
+    a = P(w).step(w.rho0, 3)
+    b = oracle.Problem(**w.oracle_kwargs(), parallel=True).step(w.rho0, 3)
+    np.testing.assert_array_equal(a, b)

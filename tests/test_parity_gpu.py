@@ -51,6 +51,7 @@ SHAPES = [
     (37, 23, 19, 3), (1, 9, 7, 2), (8, 1, 5, 1), (6, 5, 1, 4), (1, 1, 1, 1), (2, 2, 2, 5),
     (65, 33, 17, 2), (200, 7, 9, 1), (9, 130, 11, 2), (5, 7, 300, 1), (64, 12, 10, 8),
     (31, 3, 4, 7), (513, 3, 2, 1), (50, 50, 50, 1),
+    (1100, 3, 2, 3),  # FP64 x rows too long for register chunks: streaming solve only
 ]
 
 
@@ -66,7 +67,8 @@ def test_step_matches_oracle(binding, shape, prec):
     assert rel_err(got, ref) <= TOL[prec]
 
 
-@pytest.mark.parametrize("shape", [(37, 23, 19, 3), (1, 9, 7, 2), (200, 7, 9, 1), (9, 70, 130, 2)],
+@pytest.mark.parametrize("shape", [(37, 23, 19, 3), (1, 9, 7, 2), (200, 7, 9, 1), (9, 70, 130, 2),
+                                   (1100, 3, 2, 3)],
                          ids=lambda s: "x".join(map(str, s)))
 def test_each_stage_matches_oracle(binding, shape):
     nx, ny, nz, ns = shape
@@ -353,6 +355,70 @@ def test_workload3_full_size_20_steps_fp32_properties(binding):
     err = float((f[..., 1].double() - expect.double()).abs().max()) / 38.0
     sim.close()
     assert err <= 1e-5
+
+
+def _device_rel_err(got, ref):
+    """Normwise error of two device fields, in FP64, in chunks (bounded temporaries)."""
+    import torch
+    g, r = got.reshape(-1), ref.reshape(-1)
+    d = torch.zeros((), dtype=torch.float64, device=r.device)
+    for i in range(0, r.numel(), 1 << 28):
+        d = torch.maximum(d, (g[i:i + (1 << 28)].double() - r[i:i + (1 << 28)].double()).abs().max())
+    return float(d / r.abs().max().double())
+
+
+@pytest.mark.slow
+def test_workload2_full_size_100_steps_fp32_with_agents_vs_fp64(binding):
+    """400^3 x 4 with its 1M agents, 100 steps: FP32 against the FP64 GPU path on the same
+    inputs (that path matches the oracle element by element on a full-size step and over 100
+    steps at reduced size).  Target: normwise <= 1e-5."""
+    import torch
+    w = inputs.workload(2)
+    out = {}
+    for prec in ("fp64", "fp32"):
+        sim = binding.BioFVM.from_workload(w, precision=prec)
+        sim.step(w.n_steps)
+        out[prec] = sim.field_tensor().clone()
+        sim.close()
+    err = _device_rel_err(out["fp32"], out["fp64"])
+    del out
+    torch.cuda.empty_cache()
+    assert err <= 1e-5, err
+
+
+@pytest.mark.slow
+def test_workload3_full_size_20_steps_fp32_with_agents_vs_fp64(binding):
+    """1200^3 x 2 (13.8 GB FP32), Dirichlet 38 on substrate 0, 64 Gaussian blobs and its 10M
+    agents, 20 steps: FP32 against the FP64 GPU path (27.6 GB) on the same inputs, the blob
+    field evaluated on the device.  Target: normwise <= 1e-5."""
+    import torch
+    w = inputs.workload(3, with_field=False)
+    f64 = inputs.gaussian_blobs_device(w.extra["blobs"], w.nx, w.ny, w.nz, w.ns, w.dx, "cuda")
+    sim = binding.BioFVM.from_workload(w, precision="fp32")
+    sim.set_density(f64.float())
+    sim.step(w.n_steps)
+    got = sim.field_tensor().clone()
+    sim.close()
+    torch.cuda.empty_cache()
+    ref = binding.BioFVM.from_workload(w, precision="fp64")
+    ref.set_density(f64)
+    del f64
+    ref.step(w.n_steps)
+    ref.sync()
+    err = _device_rel_err(got, ref.field_tensor())
+    ref.close()
+    del got
+    torch.cuda.empty_cache()
+    assert err <= 1e-5, err
+
+
+def test_workload3_slab_2_steps_fp64_vs_oracle(binding):
+    """A 1200 x 1200 x 8 slab of the 1200^3 recipe (Dirichlet faces, blobs, agents at the same
+    density), 2 steps: the FP64 GPU path against the oracle, every element."""
+    w = inputs.workload(3, shape=(1200, 1200, 8), n_agents=10_000_000 * 8 // 1200)
+    ref = orc(w).step(w.rho0, 2)
+    got = gpu_run(binding, w, "fp64", 2)
+    assert rel_err(got, ref) <= 1e-12
 
 
 @pytest.mark.parametrize("path", list(PATHS))

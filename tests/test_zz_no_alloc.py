@@ -26,14 +26,17 @@ def rel(a, b):
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
 
 
+@pytest.mark.parametrize("spacing", [None, (20.0, 13.0, 31.0)], ids=["isotropic", "anisotropic"])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_noalloc_reduction_matches_adjoint_step_on_two_calls(prec):
+def test_noalloc_reduction_matches_adjoint_step_on_two_calls(prec, spacing):
     import torch
 
     from paper_2602_05017_gb300 import binding
     lib = binding.load()
     rng = np.random.default_rng(31)
     w = inputs.random_problem(rng, 21, 17, 13, 3, n_agents=30)  # zero flux: B is the identity
+    w.spacing = spacing
+    h3 = spacing or (w.dx, w.dx, w.dx)  # the spacing each axis's reduction takes
     fd = torch.float64 if prec == "fp64" else torch.float32
     code = binding.FP64 if prec == "fp64" else binding.FP32
     stream = torch.cuda.current_stream().cuda_stream
@@ -50,6 +53,8 @@ def test_noalloc_reduction_matches_adjoint_step_on_two_calls(prec):
     sim.sync()
 
     aux = binding.BioFVM(w.nx, w.ny, w.nz, w.ns, w.dx, w.dt, w.D, w.lam, precision=prec)
+    if spacing is not None:
+        aux.set_spacing(*spacing)
     for _ in range(2):  # two calls in a row share (and overwrite) the static scratch
         dD = torch.zeros(w.ns, dtype=torch.float64, device="cuda")
         dl = torch.zeros_like(dD)
@@ -60,7 +65,7 @@ def test_noalloc_reduction_matches_adjoint_step_on_two_calls(prec):
             u = saved[k * n:(k + 1) * n]
             st = lib.biofvm_param_grad_noalloc(
                 ctypes.c_void_p(mu.data_ptr()), ctypes.c_void_p(u.data_ptr()), w.nx, w.ny, w.nz,
-                w.ns, axis, code, w.dt, w.dx, ctypes.c_void_p(dD.data_ptr()),
+                w.ns, axis, code, w.dt, h3[axis], ctypes.c_void_p(dD.data_ptr()),
                 ctypes.c_void_p(dl.data_ptr()), stream)
             assert st == binding.OK, lib.biofvm_last_error().decode()
         torch.cuda.synchronize()
