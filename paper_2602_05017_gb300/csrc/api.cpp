@@ -75,6 +75,7 @@ struct ColPlan {
 // the plain kernels).
 struct PipePlan {
   int use = 0, T = 1, m = 1, maxm = 8;
+  int cw = 32, W = 1;  // columns per tile (32, or 16 for long lines); consumer warps
   int box_rows = 0, nbox = 0, rows_per_tile = 0, pitch = 0;
   int stages = 0, grid = 0;
   int64_t stage_elems = 0, ntiles = 0;
@@ -374,7 +375,7 @@ bool encode_pipe_map(biofvm *h, int axis, int buf, void *field) {
   const size_t esz = h->esz;
   cuuint64_t dims[3] = {(cuuint64_t)C, (cuuint64_t)n, (cuuint64_t)nplanes};
   cuuint64_t strides[2] = {(cuuint64_t)(C * esz), (cuuint64_t)(C * esz * n)};
-  cuuint32_t box[3] = {32, (cuuint32_t)p.box_rows, 1};
+  cuuint32_t box[3] = {(cuuint32_t)p.cw, (cuuint32_t)p.box_rows, 1};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = enc(&p.map[buf],
                    esz == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
@@ -404,7 +405,9 @@ int x_tile_conflicts(int pitch, int S, int lanes, size_t esz) {
 }
 
 // Plan the pipelined sweep of axis 0 (x), 1 (y) or 2 (z); leaves pp.use = 0
-// when the plain kernels have to be used instead.
+// when the plain kernels have to be used instead.  Tiles of 32 columns when a
+// ring of >= 2 stages of them fits in shared memory with the constants, else
+// tiles of 16 columns (long lines; two chunks per consumer warp).
 void plan_pipe(biofvm *h, int axis) {
   PipePlan &p = h->pp[axis];
   p = PipePlan{};
@@ -412,58 +415,94 @@ void plan_pipe(biofvm *h, int axis) {
   const size_t esz = h->esz;
   const int n = axis_len(h, axis);
   if (esz != 4) return;  // FP64 streams whole lines instead
-  ColPlan cp;
-  if (h->pipe_chunk > 0) {  // chunk length chosen by the caller (tuning)
-    if (!plan_col(n, false, cp, std::min(h->pipe_chunk, n))) return;
-  } else if (!plan_col(n, false, cp)) {
+  for (int cw : {32, 16}) {
+    PipePlan q{};
+    q.cw = cw;
+    const int cpw = 32 / cw;
+    ColPlan cp;
+    if (h->pipe_chunk > 0) {  // chunk length chosen by the caller (tuning)
+      if (!plan_col(n, false, cp, std::min(h->pipe_chunk, n))) continue;
+    } else if (cw == 32) {
+      if (!plan_col(n, false, cp)) continue;
+    } else {  // 16 columns: chunks of 32 or 64 (the capacities compiled for them)
+      bool found = false;
+      for (int target : {32, 64}) {
+        const int T = std::max(1, (n + target - 1) / target);
+        const int m = T == 1 ? n : target;
+        const int maxm = pick_maxm(m, false);
+        if (maxm != 32 && maxm != 64) continue;
+        if (((T + 1) / 2 + 1) * 32 > pipe_max_threads_f32(maxm)) continue;
+        cp.T = T;
+        cp.m = m;
+        cp.maxm = maxm;
+        found = true;
+        break;
+      }
+      if (!found) continue;
+    }
+    if (cw == 16 && cp.maxm != 32 && cp.maxm != 64) continue;
+    // chunks above 64 registers spill (measured with -Xptxas -v): 16-column tiles instead
+    if (cw == 32 && cp.maxm > 64 && h->pipe_chunk <= 0) continue;
+    const int W = (cp.T + cpw - 1) / cpw;  // consumer warps
+    if ((W + 1) * 32 > pipe_max_threads_f32(cp.maxm)) continue;
+    q.T = cp.T;
+    q.m = cp.m;
+    q.maxm = cp.maxm;
+    if (axis == 0) {
+      const int64_t rowlen = nx * S;
+      if ((rowlen * (int64_t)esz) % 16 != 0 || S > cw) continue;
+      q.rows_per_tile = (int)(cw / S);
+      const int align = (int)(16 / esz);  // pitch in elements keeps every row 16-byte aligned
+      int best = 1 << 30;
+      for (int64_t pitch = (rowlen + align - 1) / align * align; pitch <= rowlen + 64;
+           pitch += align) {
+        const int d = x_tile_conflicts((int)(pitch % 64), (int)S, q.rows_per_tile * (int)S, esz);
+        if (d < best) {
+          best = d;
+          q.pitch = (int)pitch;
+        }
+      }
+      q.stage_elems = (int64_t)q.rows_per_tile * q.pitch;
+      if (ny * nz > (int64_t)0x7fffffff) return;  // the kernel tracks rows in 32 bits
+      q.ntiles = (ny * nz + q.rows_per_tile - 1) / q.rows_per_tile;
+    } else {
+      const int64_t C = axis == 1 ? nx * S : nx * ny * S;
+      const int nplanes = axis == 1 ? (int)nz : 1;
+      if ((C * (int64_t)esz) % 16 != 0 || C > (int64_t)0x7fffffff || nplanes > 65535) return;
+      q.nbox = (n + 255) / 256;
+      q.box_rows = (n + q.nbox - 1) / q.nbox;
+      q.stage_elems = (int64_t)q.nbox * q.box_rows * cw;
+      q.ntiles = (int64_t)nplanes * ((C + cw - 1) / cw);
+      if (q.ntiles > (int64_t)0x7fffffff) return;  // tiles are indexed in 32 bits
+    }
+    const size_t stage = (size_t)q.stage_elems * esz;
+    const size_t tab = (size_t)pipe_tab_elems_host(n, (int)S) * esz;
+    // carry exchange [2][W*32], carry weights [T][T][S], alignment, mbarriers
+    const size_t scratch = (2 * (size_t)W * 32 + (size_t)q.T * q.T * S) * esz + 16 + 2 * 8 * 8;
+    for (int ns = 4; ns >= 2 && !q.stages; ns--)  // the constants always staged
+      if (ns * stage + tab + scratch <= kMaxDynamicSmem) q.stages = ns;
+    if (!q.stages) continue;
+    q.smem = q.stages * stage + tab + scratch;
+    q.W = W;
+    p = q;
+    break;
+  }
+  if (!p.stages) {
+    p = PipePlan{};
     return;
   }
-  if ((cp.T + 1) * 32 > pipe_max_threads_f32(cp.maxm)) return;
-  p.T = cp.T;
-  p.m = cp.m;
-  p.maxm = cp.maxm;
-  if (axis == 0) {
-    const int64_t rowlen = nx * S;
-    if ((rowlen * (int64_t)esz) % 16 != 0 || S > 32) return;
-    p.rows_per_tile = (int)(32 / S);
-    const int align = (int)(16 / esz);  // pitch in elements keeps every row 16-byte aligned
-    int best = 1 << 30;
-    for (int64_t pitch = (rowlen + align - 1) / align * align; pitch <= rowlen + 64; pitch += align) {
-      const int d = x_tile_conflicts((int)(pitch % 64), (int)S, p.rows_per_tile * (int)S, esz);
-      if (d < best) {
-        best = d;
-        p.pitch = (int)pitch;
-      }
-    }
-    p.stage_elems = (int64_t)p.rows_per_tile * p.pitch;
-    if (ny * nz > (int64_t)0x7fffffff) return;  // the kernel tracks rows in 32 bits
-    p.ntiles = (ny * nz + p.rows_per_tile - 1) / p.rows_per_tile;
-  } else {
-    const int64_t C = axis == 1 ? nx * S : nx * ny * S;
-    const int nplanes = axis == 1 ? (int)nz : 1;
-    if ((C * (int64_t)esz) % 16 != 0 || C > (int64_t)0x7fffffff || nplanes > 65535) return;
-    p.nbox = (n + 255) / 256;
-    p.box_rows = (n + p.nbox - 1) / p.nbox;
-    p.stage_elems = (int64_t)p.nbox * p.box_rows * 32;
-    p.ntiles = (int64_t)nplanes * ((C + 31) / 32);
-    if (p.ntiles > (int64_t)0x7fffffff) return;  // tiles are indexed in 32 bits
+  if (axis != 0 && !encode_pipe_map(h, axis, 0, h->rho.p)) {
+    p.use = 0;
+    return;
   }
-  const size_t stage = (size_t)p.stage_elems * esz;
-  const size_t tab = (size_t)pipe_tab_elems_host(n, (int)S) * esz;
-  // carry exchange [2][T][32], carry weights [T][T][S], alignment, mbarriers
-  const size_t scratch = (2 * (size_t)p.T * 32 + (size_t)p.T * p.T * S) * esz + 16 + 2 * 8 * 8;
-  for (int ns = 4; ns >= 2 && !p.stages; ns--)  // the constants always staged
-    if (ns * stage + tab + scratch <= kMaxDynamicSmem) p.stages = ns;
-  if (!p.stages) return;
-  p.smem = p.stages * stage + tab + scratch;
-  if (axis != 0 && !encode_pipe_map(h, axis, 0, h->rho.p)) return;
   // the attribute is per kernel, shared by every handle: always the opt-in maximum
   const cudaError_t e = allow_pipe_smem_f32(p.maxm, kMaxDynamicSmem);
   if (e != cudaSuccess) {
     cudaGetLastError();
+    p.use = 0;
     return;
   }
-  const int threads = (p.T + 1) * 32;
+  const int threads = (p.W + 1) * 32;
   const int regs = p.maxm + 96;
   int per_sm = (int)std::min<size_t>({kMaxDynamicSmem / p.smem, (size_t)(2048 / threads),
                                       (size_t)(65536 / (threads * regs))});
@@ -477,14 +516,18 @@ void plan_pipe(biofvm *h, int axis) {
 // intermediates (32 n elements; FP32: and the field values the backward pass
 // re-reads) in L2 between the two passes, so the warps in flight bound the L2
 // footprint (12 warps per SM at n = 400: about 93 MB on average).  FP64 always
-// (the FP64 step is bound by FP64 operations); FP32 when stream32_enabled,
-// with a field-sized scratch buffer.
+// (the FP64 step is bound by FP64 operations); FP32 when stream32_enabled, or
+// for an axis the pipelined sweep cannot take whose plain kernel would hold
+// chunks of more than 64 positions in registers (or cannot hold the lines at
+// all), with a field-sized scratch buffer.
 void plan_stream(biofvm *h, int axis) {
   StreamPlan &p = h->sp[axis];
   p = StreamPlan{};
   if (!h->stream_enabled) return;
   if (h->prec == BIOFVM_FP32) {
-    if (!h->stream32_enabled) return;
+    const bool plain_slow = axis == 0 ? (h->xp.nosolve || h->xp.maxm > 64)
+                                      : (h->cp[axis].nosolve || h->cp[axis].maxm > 64);
+    if (!h->stream32_enabled && (h->pp[axis].use || !plain_slow)) return;
     if (!h->scratch.p && dev_alloc(h->scratch, h->nel * h->esz) != cudaSuccess) {
       cudaGetLastError();
       return;
@@ -731,7 +774,8 @@ cudaError_t launch_pipe(const biofvm *h, int axis, int flags, cudaStream_t st, v
   b.nz = h->g.nz;
   b.ntiles = p.ntiles;
   b.C = axis == 1 ? (int64_t)h->g.nx * h->g.n_sub : (int64_t)h->g.nx * h->g.ny * h->g.n_sub;
-  b.tiles_per_plane = (int)((b.C + 31) / 32);
+  b.cw = p.cw;
+  b.tiles_per_plane = (int)((b.C + p.cw - 1) / p.cw);
   b.nplanes = axis == 1 ? h->g.nz : 1;
   b.box_rows = p.box_rows;
   b.nbox = p.nbox;

@@ -2,16 +2,19 @@
 //
 // Same arithmetic as the plain kernels of sweeps.cuh -- partitioned Thomas of
 // Algorithm 1 on the App. A system, FP32 in defect-correction form -- but
-// every tile of 32 independent lines ("columns") x n positions moves through
-// a ring of shared-memory stages:
+// every tile of CW independent lines ("columns") x n positions moves through
+// a ring of shared-memory stages.  CW = 32 normally; for lines so long that two
+// stages of 32 columns do not fit in shared memory, tiles of CW = 16 columns,
+// and each consumer warp then solves two chunks, one per half-warp:
 //
 //   warp 0, lane 0 (producer): TMA loads of tile k+NS-1 (cp.async.bulk.tensor
 //     boxes for y/z tiles, one cp.async.bulk per row for x tiles) completing
 //     on mbarrier `full`; once the consumers have written tile k back into its
 //     stage (mbarrier `done`), the bulk store of that tile; the stage is
 //     reloaded after the store has finished reading it;
-//   warps 1..T (consumers): chunk t of every column of the staged tile, in
-//     registers.  Halos and chunk carries cross warps through shared memory
+//   warps 1..ceil(T*CW/32) (consumers): chunk t of every column of the staged
+//     tile, in registers (thread (warp w, lane l): chunk (w-1)*32/CW + l/CW of
+//     column l % CW).  Halos and chunk carries cross warps through shared memory
 //     between two named barriers per tile that only consumers join.  An x
 //     tile gets the source update and the first Dirichlet application in
 //     shared memory before its solve: the consumers apply them to the next
@@ -98,9 +101,9 @@ __host__ __device__ inline int pipe_npad(int n) { return (n + 31) / 32 * 32 + 1;
 // PS > 0: compile-time stride between positions in the staged tile.
 // mid1 runs just before the first carry barrier, mid2 just before the second
 // (the x tiles prepare the next tile's stage there).
-template <typename E, int MAXM, bool FULL, int PS, typename M1, typename M2>
+template <typename E, int MAXM, bool FULL, int PS, int CW, typename M1, typename M2>
 __device__ __forceinline__ bool pipe_chunk(E *p, const int ps_rt, const int len, const int lo,
-                                           const int n, const int t, const int T, const int lane,
+                                           const int n, const int t, const int T, const int c,
                                            const E *Ti, const E *Tm, const E *Tf, const E *Tb,
                                            const E *Tcw, const int S, const int s, const E chi,
                                            const E clo, E *s_end, E *s_beg, const int ncons,
@@ -139,7 +142,7 @@ __device__ __forceinline__ bool pipe_chunk(E *p, const int ps_rt, const int len,
       g = fma(Tm[i], g, v[i] * Ti[i]);
       v[i] = g;
     }
-  s_end[t * 32 + lane] = g;
+  s_end[t * CW + c] = g;
   mid1();
   // The first carry barrier also ANDs the outcome of every consumer's wait
   // for the tile: on a timeout all consumers leave together, before any
@@ -149,12 +152,12 @@ __device__ __forceinline__ bool pipe_chunk(E *p, const int ps_rt, const int len,
   // arithmetic per term), in the same order as the closed form's sum; not
   // unrolled (unrolling by 4 measured 5% slower on the y/z tiles)
   const int dw = T * S;
-  if (t > 0) {  // chunk 0 enters with a zero carry
+  if (t > 0 && t < T) {  // chunk 0 enters with a zero carry (t == T: a half-warp with no chunk)
     E carry = E(0);
     const E *w = Tcw + ((t - 1) * T + t) * S + s;
-    const E *q = s_end + (t - 1) * 32 + lane;
+    const E *q = s_end + (t - 1) * CW + c;
 #pragma unroll 1
-    for (int u = t - 1; u >= 0; u--, w -= dw, q -= 32) carry = fma(*w, *q, carry);
+    for (int u = t - 1; u >= 0; u--, w -= dw, q -= CW) carry = fma(*w, *q, carry);
 #pragma unroll
     for (int i = 0; i < MAXM; i++)
       if (FULL || i < len) v[i] = fma(Tf[i], carry, v[i]);
@@ -166,15 +169,15 @@ __device__ __forceinline__ bool pipe_chunk(E *p, const int ps_rt, const int len,
       x = fma(Tm[i], x, v[i]);
       v[i] = x;
     }
-  s_beg[t * 32 + lane] = x;
+  s_beg[t * CW + c] = x;
   mid2();
   consumers_sync(ncons);
   if (t + 1 < T) {  // the last chunk enters with a zero carry
     E carry = E(0);
     const E *w = Tcw + ((t + 1) * T + t) * S + s;
-    const E *q = s_beg + (t + 1) * 32 + lane;
+    const E *q = s_beg + (t + 1) * CW + c;
 #pragma unroll 1
-    for (int u = t + 1; u < T; u++, w += dw, q += 32) carry = fma(*w, *q, carry);
+    for (int u = t + 1; u < T; u++, w += dw, q += CW) carry = fma(*w, *q, carry);
 #pragma unroll
     for (int i = 0; i < MAXM; i++)
       if (FULL || i < len) v[i] = fma(Tb[i], carry, v[i]);
@@ -204,19 +207,23 @@ __device__ __forceinline__ bool pipe_chunk(E *p, const int ps_rt, const int len,
 // MODE 0: x tiles (per-row bulk copies, Src and B before the solve);
 // MODE 1: y/z tiles (tensor boxes).  PSX > 0 (x tiles only): the substrate
 // count S, known at compile time, so the staged positions (S apart) need no
-// per-access address arithmetic; 0: S read at run time.
-template <typename E, int MAXM, int MODE, int PSX = 0>
+// per-access address arithmetic; 0: S read at run time.  CW: columns per tile
+// (32, or 16 for long lines).
+template <typename E, int MAXM, int MODE, int PSX = 0, int CW = 32>
 __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
     sweep_pipe_kernel(const __grid_constant__ CUtensorMap map, const PipeArgs a) {
+  static_assert(CW == 32 || CW == 16, "tiles of 32 or 16 columns");
+  constexpr int CPW = 32 / CW;  // chunks per consumer warp
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const int T = a.tab.T, m = a.tab.m, n = a.n, S = a.S, NS = a.stages;
   const int64_t stage_elems = a.stage_elems;
   const int npad = pipe_npad(n);
   E *stage0 = reinterpret_cast<E *>(smem_raw);
   E *tab = stage0 + NS * stage_elems;  // [4][S][npad]
-  E *s_end = tab + 4 * S * npad;
-  E *s_beg = s_end + T * 32;
-  E *s_cw = s_beg + T * 32;  // [T][T][S] carry weights
+  const int W = (T + CPW - 1) / CPW;  // consumer warps
+  E *s_end = tab + 4 * S * npad;      // [W*32]: chunk t, column c at t*CW + c
+  E *s_beg = s_end + W * 32;
+  E *s_cw = s_beg + W * 32;  // [T][T][S] carry weights
   uint64_t *full = reinterpret_cast<uint64_t *>(
       (reinterpret_cast<uintptr_t>(s_cw + T * T * S) + 15) & ~uintptr_t(15));
   uint64_t *done = full + NS;
@@ -224,7 +231,7 @@ __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long first = blockIdx.x;
   const long long count = (a.ntiles - first + gridDim.x - 1) / gridDim.x;
-  const int ncons = T * 32;
+  const int ncons = W * 32;
   E *field = static_cast<E *>(a.field);
 
   if (threadIdx.x == 0) {
@@ -263,10 +270,10 @@ __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
                    &full[s]);
       } else {
         const int plane = (int)((uint32_t)tile / (uint32_t)a.tiles_per_plane);
-        const int c0 = (int)((uint32_t)tile % (uint32_t)a.tiles_per_plane) * 32;
+        const int c0 = (int)((uint32_t)tile % (uint32_t)a.tiles_per_plane) * CW;
         mbar_arrive_expect_tx(&full[s], (uint32_t)(stage_elems * sizeof(E)));
         for (int b = 0; b < a.nbox; b++)
-          tma_load_3d(dst + (size_t)b * a.box_rows * 32, &map, c0, b * a.box_rows, plane, &full[s]);
+          tma_load_3d(dst + (size_t)b * a.box_rows * CW, &map, c0, b * a.box_rows, plane, &full[s]);
       }
     };
     auto issue_store = [&](long long k, int s) {
@@ -279,9 +286,9 @@ __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
           bulk_s2g(field + (tile * a.rows_per_tile + r) * a.rowlen, src + (size_t)r * a.pitch, rb);
       } else {
         const int plane = (int)((uint32_t)tile / (uint32_t)a.tiles_per_plane);
-        const int c0 = (int)((uint32_t)tile % (uint32_t)a.tiles_per_plane) * 32;
+        const int c0 = (int)((uint32_t)tile % (uint32_t)a.tiles_per_plane) * CW;
         for (int b = 0; b < a.nbox; b++)
-          tma_store_3d(&map, c0, b * a.box_rows, plane, src + (size_t)b * a.box_rows * 32);
+          tma_store_3d(&map, c0, b * a.box_rows, plane, src + (size_t)b * a.box_rows * CW);
       }
       bulk_commit();
     };
@@ -307,12 +314,14 @@ __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
   }
 
   // ---------------------------------------------------------------- consumers
-  const int t = warp - 1;
+  const int wc = warp - 1;                         // consumer warp
+  const int c = CW == 32 ? lane : (lane & (CW - 1));  // column of the tile
+  const int t = wc * CPW + lane / CW;              // chunk (t == T: no chunk)
   const int ctid = threadIdx.x - 32;
   const int lo = t * m;
-  const int len_full = min(m, n - lo);
-  const int colbase = MODE == 0 ? (lane / S) * a.pitch + lane % S : lane;
-  const int ps_rt = MODE == 0 ? S : 32;
+  const int len_full = t < T ? min(m, n - lo) : 0;
+  const int colbase = MODE == 0 ? (c / S) * a.pitch + c % S : c;
+  const int ps_rt = MODE == 0 ? S : CW;
   const E *Tcw = s_cw;  // [T][T][S], staged beside the other constants
   const bool dir_after = (a.flags & kDirAfter) != 0;
   // The planner keeps tile, row and column counts below 2^31, so the per-tile
@@ -374,11 +383,11 @@ __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
     src_fetch(n0, n1);
     src_range(kk + 2, f0, f1);
   };
-  auto prep_dir = [&](long long kk) {  // consumer warp t takes rows t, t+T, ...
+  auto prep_dir = [&](long long kk) {  // consumer warp wc takes rows wc, wc+W, ...
     E *const sg = stage0 + (int)(kk % NS) * stage_elems;
     const long long r0 = (first + kk * gridDim.x) * a.rows_per_tile;
     const int rows = (int)min((long long)a.rows_per_tile, a.nrows - r0);
-    for (int rr = t; rr < rows; rr += T) {
+    for (int rr = wc; rr < rows; rr += W) {
       const uint32_t row = (uint32_t)r0 + (uint32_t)rr;
       const int z = (int)(row / (uint32_t)a.ny), y = (int)row - z * a.ny;
       E *trow = sg + (size_t)rr * a.pitch;
@@ -417,25 +426,25 @@ __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
     if constexpr (MODE == 0) {
       const long long r0 = tile * a.rows_per_tile;
       const int rows = (int)min((long long)a.rows_per_tile, a.nrows - r0);
-      s = lane % S;
-      active = lane < a.rows_per_tile * S && lane / S < rows;
+      s = c % S;
+      active = c < a.rows_per_tile * S && c / S < rows;
       if (dir_after) {  // (only the Dirichlet application after the solve needs the face)
-        const uint32_t row = (uint32_t)r0 + (uint32_t)(lane / S);
+        const uint32_t row = (uint32_t)r0 + (uint32_t)(c / S);
         const int z = (int)(row / (uint32_t)a.ny), y = (int)row - z * a.ny;
         face = y == 0 || y == a.ny - 1 || z == 0 || z == a.nz - 1;
       }
     } else {
       const int plane = (int)((uint32_t)tile / (uint32_t)a.tiles_per_plane);
-      const uint32_t c = ((uint32_t)tile - (uint32_t)plane * (uint32_t)a.tiles_per_plane) * 32u +
-                         (uint32_t)lane;
-      active = c < (uint32_t)a.C;
-      s = (int)(c % (uint32_t)S);
+      const uint32_t cg = ((uint32_t)tile - (uint32_t)plane * (uint32_t)a.tiles_per_plane) *
+                              (uint32_t)CW + (uint32_t)c;
+      active = cg < (uint32_t)a.C;
+      s = (int)(cg % (uint32_t)S);
       if (dir_after) {
         if (a.mode == 1) {
-          const int x0 = (int)(c / (uint32_t)S);
+          const int x0 = (int)(cg / (uint32_t)S);
           face = (x0 == 0 || x0 == a.nx - 1 || plane == 0 || plane == a.nz - 1);
         } else {
-          const uint32_t vox = c / (uint32_t)S;
+          const uint32_t vox = cg / (uint32_t)S;
           const int x0 = (int)(vox % (uint32_t)a.nx), y = (int)(vox / (uint32_t)a.nx);
           face = (x0 == 0 || x0 == a.nx - 1 || y == 0 || y == a.ny - 1);
         }
@@ -449,7 +458,7 @@ __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
     const E chi = __ldg(g_cfix + s), clo = __ldg(g_cfix + S + s);
     // the unguarded path only when every lane of the warp has a full chunk:
     // the choice is warp-uniform, so a warp never splits across the paths
-    constexpr int PS = MODE == 0 ? PSX : 32;
+    constexpr int PS = MODE == 0 ? PSX : CW;
     const bool next = MODE == 0 && prep && k + 1 < count;
     auto mid1 = [&]() {
       if (next) {
@@ -463,12 +472,12 @@ __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
     };
     bool solved;
     if (__all_sync(0xffffffffu, len == MAXM))
-      solved = pipe_chunk<E, MAXM, true, PS>(p, ps_rt, len, lo, n, t, T, lane, s_inv + rowoff,
+      solved = pipe_chunk<E, MAXM, true, PS, CW>(p, ps_rt, len, lo, n, t, T, c, s_inv + rowoff,
                                              s_mul + rowoff, s_pf + rowoff, s_pb + rowoff, Tcw, S,
                                              s, chi, clo, s_end, s_beg, ncons, dir, face, dval, ok,
                                              mid1, mid2);
     else
-      solved = pipe_chunk<E, MAXM, false, PS>(p, ps_rt, len, lo, n, t, T, lane, s_inv + rowoff,
+      solved = pipe_chunk<E, MAXM, false, PS, CW>(p, ps_rt, len, lo, n, t, T, c, s_inv + rowoff,
                                               s_mul + rowoff, s_pf + rowoff, s_pb + rowoff, Tcw, S,
                                               s, chi, clo, s_end, s_beg, ncons, dir, face, dval, ok,
                                               mid1, mid2);
@@ -484,6 +493,11 @@ template <int MAXM>
 constexpr bool pipe_x_specialised() {
   return MAXM == 32;
 }
+// Tiles of 16 columns (long lines): the chunk capacities the planner offers them.
+template <int MAXM>
+constexpr bool pipe_half_tiles() {
+  return MAXM == 32 || MAXM == 64;
+}
 
 template <typename E, int MAXM>
 cudaError_t allow_pipe_smem(size_t bytes) {
@@ -494,6 +508,10 @@ cudaError_t allow_pipe_smem(size_t bytes) {
   };
   set((const void *)sweep_pipe_kernel<E, MAXM, 0>);
   set((const void *)sweep_pipe_kernel<E, MAXM, 1>);
+  if constexpr (pipe_half_tiles<MAXM>()) {
+    set((const void *)sweep_pipe_kernel<E, MAXM, 0, 0, 16>);
+    set((const void *)sweep_pipe_kernel<E, MAXM, 1, 0, 16>);
+  }
   if constexpr (pipe_x_specialised<MAXM>()) {
     set((const void *)sweep_pipe_kernel<E, MAXM, 0, 1>);
     set((const void *)sweep_pipe_kernel<E, MAXM, 0, 2>);
@@ -506,8 +524,20 @@ cudaError_t allow_pipe_smem(size_t bytes) {
 template <typename E, int MAXM>
 cudaError_t launch_pipe_one(const CUtensorMap &map, const PipeArgs &a, int grid, size_t smem,
                             cudaStream_t st) {
-  if ((a.tab.T + 1) * 32 > PipeBound<E, MAXM>::threads) return cudaErrorInvalidConfiguration;
-  const int threads = (a.tab.T + 1) * 32;
+  const int cpw = a.cw == 16 ? 2 : 1;
+  const int threads = ((a.tab.T + cpw - 1) / cpw + 1) * 32;
+  if (threads > PipeBound<E, MAXM>::threads) return cudaErrorInvalidConfiguration;
+  if (a.cw == 16) {
+    if constexpr (pipe_half_tiles<MAXM>()) {
+      if (a.mode != 0)
+        sweep_pipe_kernel<E, MAXM, 1, 0, 16><<<grid, threads, smem, st>>>(map, a);
+      else
+        sweep_pipe_kernel<E, MAXM, 0, 0, 16><<<grid, threads, smem, st>>>(map, a);
+      return cudaGetLastError();
+    }
+    return cudaErrorInvalidConfiguration;
+  }
+  if (a.cw != 32) return cudaErrorInvalidConfiguration;
   if (a.mode != 0) {
     sweep_pipe_kernel<E, MAXM, 1><<<grid, threads, smem, st>>>(map, a);
     return cudaGetLastError();

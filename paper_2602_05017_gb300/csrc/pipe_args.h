@@ -6,22 +6,24 @@
 
 namespace bfv {
 
-// A tile is 32 "columns" (independent lines) x n positions along the axis.
+// A tile is cw "columns" (independent lines) x n positions along the axis,
+// cw = 32, or 16 for lines too long for two stages of 32 columns.
 //
 //   mode 0 (x-sweep): a column is one (row, substrate) pair of
-//     rows_per_tile = floor(32/S) consecutive rows (y, z); the rows are
+//     rows_per_tile = floor(cw/S) consecutive rows (y, z); the rows are
 //     staged with one cp.async.bulk each into shared memory at a padded
-//     `pitch` (elements) chosen on the host so that the 32 lanes of a warp
-//     hit 32 different banks; element (column c, position x) sits at
+//     `pitch` (elements) chosen on the host so that the lanes of a warp
+//     hit different banks; element (column c, position x) sits at
 //     (c/S)*pitch + x*S + c%S.
-//   mode 1 / 2 (y- / z-sweep): a column is one of 32 consecutive (x, s) or
-//     (x, y, s) entries of a plane; the tile [n][32] is staged with
-//     cp.async.bulk.tensor boxes of box_rows x 32; element (c, j) sits at
-//     j*32 + c.
+//   mode 1 / 2 (y- / z-sweep): a column is one of cw consecutive (x, s) or
+//     (x, y, s) entries of a plane; the tile [n][cw] is staged with
+//     cp.async.bulk.tensor boxes of box_rows x cw; element (c, j) sits at
+//     j*cw + c.
 //
 // Tile k of a CTA is tile blockIdx.x + k*gridDim.x of ntiles.
 struct PipeArgs {
   int mode, n, S, nx, ny, nz;
+  int cw;  // columns per tile: 32 or 16
   int64_t ntiles;
   // mode 1 / 2
   int64_t C;

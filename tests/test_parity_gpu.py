@@ -423,7 +423,10 @@ def test_workload3_slab_2_steps_fp64_vs_oracle(binding):
 
 @pytest.mark.parametrize("path", list(PATHS))
 @pytest.mark.parametrize("shape", [(40, 36, 28, 4), (64, 300, 9, 2), (8, 8, 520, 1), (16, 70, 70, 3),
-                                   (33, 1, 47, 5), (1, 65, 2, 7), (100, 30, 20, 8)],
+                                   (33, 1, 47, 5), (1, 65, 2, 7), (100, 30, 20, 8),
+                                   # long lines: pipelined tiles of 16 columns
+                                   (12, 10, 1100, 1), (1000, 6, 5, 2), (9, 900, 7, 3),
+                                   (1300, 3, 2, 1)],
                          ids=lambda s: "x".join(map(str, s)) if isinstance(s, tuple) else s)
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_sweep_paths_match_oracle(binding, monkeypatch, shape, path, prec):
@@ -439,5 +442,12 @@ def test_sweep_paths_match_oracle(binding, monkeypatch, shape, path, prec):
     rng = np.random.default_rng(17)
     w = inputs.random_problem(rng, nx, ny, nz, ns, n_agents=100, dirichlet=True)
     ref = orc(w).step(w.rho0, 3)
-    got = gpu_run(binding, w, prec, 3)
+    try:
+        got = gpu_run(binding, w, prec, 3)
+    except binding.BioFVMError as e:
+        # only the plain kernels alone may refuse a grid: lines longer than their register
+        # chunks hold (the library then needs the streaming or pipelined sweep)
+        if path == "plain" and e.status == binding.ERR_ARG and "too long" in str(e):
+            pytest.skip(f"plain kernels cannot hold these lines: {e}")
+        raise
     assert rel_err(got, ref) <= TOL[prec]
