@@ -601,8 +601,9 @@ def run_adjoint_both(dev):
 def run_adjoint(prec, dev):
     """Workload 5 (128^3 x 2, 200 steps, checkpoints every 20): the forward run alone, then the
     forward run plus the gradients of a probe loss with respect to the initial field, the
-    per-voxel secretion rates, D and lambda (LODSteps: checkpoints, recomputation with
-    biofvm_step_save, biofvm_adjoint_step), timed on the host with the device synchronised."""
+    per-voxel secretion and uptake rates, D and lambda (LODSteps: checkpoints, recomputation
+    with biofvm_step_save, biofvm_adjoint_step_rates), timed on the host with the device
+    synchronised."""
     import torch
 
     from paper_2602_05017_gb300 import binding, inputs
@@ -611,7 +612,7 @@ def run_adjoint(prec, dev):
     n, K = w.n_steps, w.extra["checkpoint_every"]
     fdt = torch.float64 if prec == "fp64" else torch.float32
     sim = binding.BioFVM(w.nx, w.ny, w.nz, w.ns, w.dx, w.dt, w.D, w.lam, precision=prec)
-    agents = dict(voxel=w.voxel, target=w.target, uptake=w.uptake, weight=w.weight)
+    agents = dict(voxel=w.voxel, target=w.target, weight=w.weight)
     pr = torch.as_tensor(w.extra["probe_index"], device=dev)
     tg = torch.as_tensor(w.extra["probe_target"], device=dev)
     grads = {}
@@ -621,16 +622,18 @@ def run_adjoint(prec, dev):
         sec = torch.tensor(w.secretion, dtype=torch.float64, device=dev, requires_grad=True)
         D = torch.tensor(w.D, dtype=torch.float64, device=dev, requires_grad=True)
         lam = torch.tensor(w.lam, dtype=torch.float64, device=dev, requires_grad=True)
+        upt = torch.tensor(w.uptake, dtype=torch.float64, device=dev, requires_grad=True)
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        out = lod_steps(rho0.to(fdt), sec, D, lam, sim, agents, steps, K)
+        out = lod_steps(rho0.to(fdt), sec, D, lam, sim, agents, steps, K, uptake=upt)
         loss = ((out.reshape(-1).double()[pr] - tg) ** 2).sum()
         if backward:
             loss.backward()
         torch.cuda.synchronize(dev)
         t = time.perf_counter() - t0
         if backward and steps == n:
-            for k, v in (("rho0", rho0), ("secretion", sec), ("D", D), ("lambda", lam)):
+            for k, v in (("rho0", rho0), ("secretion", sec), ("uptake", upt), ("D", D),
+                         ("lambda", lam)):
                 grads[k] = v.grad.detach().cpu().numpy()
         return t
 
@@ -643,7 +646,7 @@ def run_adjoint(prec, dev):
              "gradient_vs_per_s": w.n_vs * n / (t_all - t_fwd),
              "dtype": prec.replace("fp", "f"),
              "workload": "128^3 x 2, 200 steps, checkpoints every 20, 4096-probe loss; gradients "
-                         "w.r.t. initial field, secretion rates, D, lambda"}, grads)
+                         "w.r.t. initial field, secretion and uptake rates, D, lambda"}, grads)
 
 
 def _stage_step(sim, ev, stream, renorm):

@@ -185,6 +185,16 @@ biofvm_status biofvm_step_save(biofvm_t *h, void *saved);
 biofvm_status biofvm_adjoint_step(biofvm_t *h, const void *grad_out, void *grad_in, double *dD,
                                   double *dlambda, double *dsecretion, const void *saved);
 
+/* biofvm_adjoint_step that also ACCUMULATES, if duptake is not NULL, the
+ * gradient with respect to each agent's uptake rate into the device FP64 array
+ * duptake[n_agents*n_sub] (Sect. 5.3 sinks; in the source update
+ * rho <- (rho + alpha)/(1 + beta) an uptake rate U_k enters beta only, so
+ * d rho'/d U_k = -dt w_k rho' / (1 + beta)).  biofvm_adjoint_step is this call
+ * with duptake = NULL.  Errors: as biofvm_adjoint_step. */
+biofvm_status biofvm_adjoint_step_rates(biofvm_t *h, const void *grad_out, void *grad_in,
+                                        double *dD, double *dlambda, double *dsecretion,
+                                        double *duptake, const void *saved);
+
 /* Wait for the handle's stream and check the device status word.
  * Errors: CUDA, TIMEOUT. */
 biofvm_status biofvm_sync(biofvm_t *h);

@@ -78,6 +78,7 @@ def load():
         "biofvm_launches_per_step": (ctypes.c_int, [vp]),
         "biofvm_step_save": (st, [vp, vp]),
         "biofvm_adjoint_step": (st, [vp, vp, vp, vp, vp, vp, vp]),
+        "biofvm_adjoint_step_rates": (st, [vp, vp, vp, vp, vp, vp, vp, vp]),
         "biofvm_batch_create": (st, [ctypes.c_int, ctypes.POINTER(Grid), dp, dp, dp, dp,
                                      ctypes.c_int, ctypes.c_size_t,
                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(vp)]),
@@ -280,15 +281,17 @@ class BioFVM:
         _check(self.lib.biofvm_step_save(self.h, self._dev(saved, 4 * self.n_elem,
                                                               self._field_dtype())), self.lib)
 
-    def adjoint_step(self, grad_out, grad_in, dD, dlam, dsec, saved):
-        """Reverse mode of one step; accumulates into dD, dlam (and dsec if given), FP64 CUDA."""
+    def adjoint_step(self, grad_out, grad_in, dD, dlam, dsec, saved, dupt=None):
+        """Reverse mode of one step; accumulates into dD, dlam (and dsec, dupt if given: the
+        agents' secretion and uptake rates), FP64 CUDA tensors."""
         import torch
         fd = self._field_dtype()
         ns = self.shape[3]
-        _check(self.lib.biofvm_adjoint_step(
+        _check(self.lib.biofvm_adjoint_step_rates(
             self.h, self._dev(grad_out, self.n_elem, fd), self._dev(grad_in, self.n_elem, fd),
             self._dev(dD, ns, torch.float64), self._dev(dlam, ns, torch.float64),
             None if dsec is None else self._dev(dsec, dsec.numel(), torch.float64),
+            None if dupt is None else self._dev(dupt, dupt.numel(), torch.float64),
             self._dev(saved, 4 * self.n_elem, fd)), self.lib)
 
     def set_spacing(self, dx, dy, dz):

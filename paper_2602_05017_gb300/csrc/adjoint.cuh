@@ -13,7 +13,8 @@
 //
 // Src: u1 = (u0 + alpha) / (1 + beta) per element, alpha = sum_k dt w_k S_k
 // rho*_k, beta = sum_k dt w_k (S_k + U_k).  Hence du1/du0 = 1/(1+beta) and,
-// for agent k in that voxel, du1/dS_k = dt w_k (rho*_k - u1) / (1 + beta).
+// for agent k in that voxel, du1/dS_k = dt w_k (rho*_k - u1) / (1 + beta) and
+// du1/dU_k = -dt w_k u1 / (1 + beta).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -78,9 +79,10 @@ __global__ void adj_reduce_final_kernel(const double *__restrict__ partial, int 
   dD[s] += scale_D * b;
 }
 
-// Secretion gradient per (agent, substrate): one thread each, no reduction.
-// elem[k*S+s] = voxel_k*S + s; entry[k*S+s] = index of that element in the
-// aggregated source list (its 1/(1+beta)), or -1 when the element has none.
+// Secretion and uptake gradients per (agent, substrate): one thread each, no
+// reduction.  elem[k*S+s] = voxel_k*S + s; entry[k*S+s] = index of that
+// element in the aggregated source list (its 1/(1+beta)), or -1 when the
+// element has none.  dsec or dupt may be NULL.
 template <typename E>
 __global__ void src_adjoint_agents_kernel(const E *__restrict__ gbar, const E *__restrict__ u1,
                                           const int64_t *__restrict__ elem,
@@ -88,13 +90,16 @@ __global__ void src_adjoint_agents_kernel(const E *__restrict__ gbar, const E *_
                                           const E *__restrict__ src_scale,
                                           const double *__restrict__ weight,
                                           const double *__restrict__ target, long long n, double dt,
-                                          int S, double *__restrict__ dsec) {
+                                          int S, double *__restrict__ dsec,
+                                          double *__restrict__ dupt) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const long long e = elem[i], ent = entry[i];
   const double scale = ent >= 0 ? (double)src_scale[ent] : 1.0;
   const double w = weight ? weight[i / S] : 1.0;
-  dsec[i] += (double)gbar[e] * dt * w * (target[i] - (double)u1[e]) * scale;
+  const double gw = (double)gbar[e] * dt * w * scale, u = (double)u1[e];
+  if (dsec) dsec[i] += gw * (target[i] - u);
+  if (dupt) dupt[i] -= gw * u;
 }
 
 // gbar <- gbar / (1 + beta) on the elements that have a source entry.

@@ -1580,6 +1580,12 @@ biofvm_status biofvm_step_save(biofvm_t *h, void *saved) {
 
 biofvm_status biofvm_adjoint_step(biofvm_t *h, const void *grad_out, void *grad_in, double *dD,
                                   double *dlambda, double *dsecretion, const void *saved) {
+  return biofvm_adjoint_step_rates(h, grad_out, grad_in, dD, dlambda, dsecretion, nullptr, saved);
+}
+
+biofvm_status biofvm_adjoint_step_rates(biofvm_t *h, const void *grad_out, void *grad_in,
+                                        double *dD, double *dlambda, double *dsecretion,
+                                        double *duptake, const void *saved) {
   if (!h || !grad_out || !grad_in || !dD || !dlambda || !saved)
     return fail(BIOFVM_ERR_ARG, "NULL handle, gradient or saved-state pointer");
   CK(cudaSetDevice(h->device));
@@ -1673,6 +1679,7 @@ biofvm_status biofvm_adjoint_step(biofvm_t *h, const void *grad_out, void *grad_
   a.dt = h->dt;
   a.S = S;
   a.dsec = dsecretion;
+  a.dupt = duptake;
   CK(h->prec == BIOFVM_FP64 ? launch_src_adjoint_f64(a, st) : launch_src_adjoint_f32(a, st));
   CK(cudaMemcpyAsync(grad_in, h->adj.p, bytes, cudaMemcpyDeviceToDevice, st));
   return BIOFVM_OK;

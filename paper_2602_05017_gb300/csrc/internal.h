@@ -157,6 +157,7 @@ struct SrcAdjLaunch {
   double dt;
   int S;
   double *dsec;                        // [n] accumulated (device) or NULL
+  double *dupt;                        // [n] accumulated (device) or NULL
 };
 
 // Batched persistent step (batch.cuh).

@@ -65,10 +65,11 @@ cudaError_t launch_adj_reduce_f32(const ReduceLaunch &a, cudaStream_t st) {
 }
 
 cudaError_t launch_src_adjoint_f32(const SrcAdjLaunch &a, cudaStream_t st) {
-  if (a.dsec && a.n > 0)
+  if ((a.dsec || a.dupt) && a.n > 0)
     src_adjoint_agents_kernel<float><<<(unsigned)((a.n + 255) / 256), 256, 0, st>>>(
         static_cast<const float *>(a.gbar), static_cast<const float *>(a.u1), a.elem, a.entry,
-        static_cast<const float *>(a.src_scale), a.weight, a.target, a.n, a.dt, a.S, a.dsec);
+        static_cast<const float *>(a.src_scale), a.weight, a.target, a.n, a.dt, a.S, a.dsec,
+        a.dupt);
   if (a.n_entries > 0)
     src_adjoint_scale_kernel<float><<<(unsigned)((a.n_entries + 255) / 256), 256, 0, st>>>(
         static_cast<float *>(a.gbar), a.src_elem, static_cast<const float *>(a.src_scale),

@@ -276,7 +276,7 @@ def test_anisotropic_adjoint_D_matches_finite_differences():
     w.spacing = (15.0, 22.0, 30.0)
     probes = RNG.choice(w.rho0.size, 20, replace=False)
     targets = RNG.uniform(0, 38, 20)
-    L0, _, dD, dl, _ = _loss_and_grads(w, 2, probes, targets)
+    L0, _, dD, dl, _, _ = _loss_and_grads(w, 2, probes, targets)
     import copy
     for s in range(2):
         h = 1e-6 * max(1.0, abs(w.D[s]))
@@ -468,12 +468,14 @@ def _loss_and_grads(w, n_steps, probes, targets):
     dD = np.zeros(w.ns)
     dl = np.zeros(w.ns)
     ds = np.zeros((w.n_agents, w.ns))
+    du = np.zeros((w.n_agents, w.ns))
     for k in range(n_steps - 1, -1, -1):
-        g, a, b, c, _ = p.adjoint_step(states[k], g)
+        g, a, b, c, u = p.adjoint_step(states[k], g)
         dD += a
         dl += b
         ds += c
-    return loss, g, dD, dl, ds
+        du += u
+    return loss, g, dD, dl, ds, du
 
 
 @pytest.mark.parametrize("nodes", [0, 8])
@@ -490,7 +492,7 @@ def test_adjoint_matches_central_finite_differences(nodes):
     nsteps = 3
     probes = RNG.choice(w.rho0.size, 25, replace=False)
     targets = RNG.uniform(0, 38, 25)
-    L0, g0, dD, dl, ds = _loss_and_grads(w, nsteps, probes, targets)
+    L0, g0, dD, dl, ds, du = _loss_and_grads(w, nsteps, probes, targets)
 
     def loss_with(**kw):
         import copy
@@ -520,6 +522,13 @@ def test_adjoint_matches_central_finite_differences(nodes):
             dn[k, s] -= h
             check(ds[k, s], (loss_with(secretion=up) - loss_with(secretion=dn)) / (2 * h), h,
                   ("sec", k, s))
+            # uptake rate: the sinks' rates and the sources' zero uptake alike
+            h = 1e-5 * max(1.0, abs(w.uptake[k, s]))
+            up, dn = w.uptake.copy(), w.uptake.copy()
+            up[k, s] += h
+            dn[k, s] -= h
+            check(du[k, s], (loss_with(uptake=up) - loss_with(uptake=dn)) / (2 * h), h,
+                  ("upt", k, s))
     flat = w.rho0.reshape(-1)
     for e in RNG.choice(flat.size, 12, replace=False):
         h = 1e-5 * max(1.0, abs(flat[e]))
