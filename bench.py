@@ -521,6 +521,8 @@ def large_slab_vs_oracle(stream, nz=8, steps=2):
 
 def run_paper_e2e_both(args, stream, dev):
     out = {p: run_paper_e2e(p, stream, dev) for p in ("fp64", "fp32")}
+    for p in ("fp64", "fp32"):
+        out[p]["moving_agents"] = run_paper_e2e_moving(p, stream, dev, not args.no_error)
     if not args.no_error:
         import oracle
         from paper_2602_05017_gb300 import binding, inputs
@@ -583,6 +585,79 @@ def run_paper_e2e(prec, stream, dev):
             "workload": "Sect. 5.3 end-to-end run: 5 mm cube = 250^3 voxels x 1 substrate, "
                         "1000 agents (500 sources, 500 sinks), 500 steps, Gaussian profile",
             "_final": host_out.numpy().copy()}
+
+
+def _walk(x, y, z, shape, gen):
+    """One random-walk move per agent: one voxel along a random axis, clamped to the box
+    (the agents' motion is an input of the step, drawn on the device)."""
+    import torch
+    nx, ny, nz = shape
+    ax = torch.randint(0, 3, x.shape, generator=gen, device=x.device)
+    d = torch.randint(0, 2, x.shape, generator=gen, device=x.device) * 2 - 1
+    x = (x + d * (ax == 0)).clamp_(0, nx - 1)
+    y = (y + d * (ax == 1)).clamp_(0, ny - 1)
+    z = (z + d * (ax == 2)).clamp_(0, nz - 1)
+    return x, y, z, (z * ny + y) * nx + x
+
+
+def run_paper_e2e_moving(prec, stream, dev, with_error):
+    """The Sect. 5.3 run with its 1000 agents moving every step (a random walk drawn on the
+    device): before each of the 500 steps the source lists are rebuilt on the device from the
+    agents' new voxels (biofvm_set_sources_device), then one step; field resident in HBM,
+    CUDA events around the 500 steps."""
+    import torch
+
+    from paper_2602_05017_gb300 import binding, inputs
+    w = inputs.workload(6, field_dtype=np.float64 if prec == "fp64" else np.float32)
+    sim = binding.BioFVM(w.nx, w.ny, w.nz, w.ns, w.dx, w.dt, w.D, w.lam, precision=prec,
+                         stream=stream.cuda_stream)
+    sim.reserve_agents(w.n_agents)
+    sec, tgt, upt = (torch.as_tensor(a, device=dev) for a in (w.secretion, w.target, w.uptake))
+    v0 = torch.as_tensor(w.voxel, device=dev)
+    x0, y0, z0 = v0 % w.nx, (v0 // w.nx) % w.ny, v0 // (w.nx * w.ny)
+
+    def run(n_steps, seed, record=False):
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(seed)
+        x, y, z = x0.clone(), y0.clone(), z0.clone()
+        lists = []
+        with torch.cuda.stream(stream):
+            sim.set_density(torch.as_tensor(w.rho0, device=dev))
+            for _ in range(n_steps):
+                x, y, z, vox = _walk(x, y, z, (w.nx, w.ny, w.nz), gen)
+                if record:
+                    lists.append(vox.cpu().numpy())
+                sim.set_sources_device(vox, sec, tgt, upt)
+                sim.step(1)
+        return lists
+
+    run(5, 1)  # warm-up: graphs, buffers
+    stream.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    run(w.n_steps, 2602050176)
+    e1.record(stream)
+    e1.synchronize()
+    sim.sync()
+    ms = e0.elapsed_time(e1)
+    out = {"simulate_vs_per_s": w.n_vs * w.n_steps / (ms * 1e-3), "simulate_ms": ms,
+           "launches_per_step": "source-list rebuild (about 20 kernels for 1000 agents) + "
+                                f"{sim.launches_per_step()} sweep kernels",
+           "agents": "random walk, one voxel per step along a random axis, drawn on the device"}
+    if with_error:
+        import oracle
+        n = 10
+        lists = run(n, 7, record=True)
+        got = sim.density()
+        ref = w.rho0.astype(np.float64)
+        for vox in lists:
+            w.voxel = vox
+            ref = oracle.Problem(**w.oracle_kwargs(), parallel=True).step(ref, 1)
+        out["error"] = {f"vs_oracle_first_{n}_steps_same_moves":
+                        error_stats(got, ref, 1e-9 if prec == "fp64" else 1e-6)}
+    sim.close()
+    return out
 
 
 def run_adjoint_both(dev):

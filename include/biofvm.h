@@ -107,6 +107,31 @@ biofvm_status biofvm_set_sources(biofvm_t *h, int64_t n, const int64_t *voxel,
                                  const double *secretion, const double *target,
                                  const double *uptake, const double *weight);
 
+/* Moving agents (the end-to-end run of Sect. 5.3 moves its cells between
+ * steps): reserve device buffers for up to n_max >= 0 agents, so that
+ * biofvm_set_sources_device can rebuild the source lists on the device without
+ * allocating.  Waits for the stream.  If device-built lists were in use they
+ * are replaced by an empty agent set.  Not for batched environments (STATE).
+ * Errors: ARG (n_max * n_sub must stay below 2^32), OOM, CUDA, STATE. */
+biofvm_status biofvm_reserve_agents(biofvm_t *h, int64_t n_max);
+
+/* Replace the agents from DEVICE arrays, entirely on the handle's stream
+ * (async: no host synchronisation, no allocation; a graph may capture it).
+ * Same arrays and meaning as biofvm_set_sources (voxel[n] int64;
+ * secretion, target, uptake [n*n_sub] double, each may be NULL = 0; weight[n]
+ * double, NULL = 1), which must stay valid until the stream has run the call.
+ * 0 <= n <= the reserved n_max.  The per-(voxel, substrate) entries are formed,
+ * sorted by element (a stable radix sort) and summed in agent order on the
+ * device: the same lists, to the bit, as biofvm_set_sources builds on the host.
+ * Entries on Dirichlet nodes are left out (the nodes current at this call).
+ * An invalid agent (voxel out of range, a negative or non-finite rate or
+ * weight) is left out and makes the next synchronising call return ARG.
+ * While device-built lists are in use biofvm_adjoint_step returns STATE.
+ * Errors: ARG, CUDA, STATE (nothing reserved, or a batched environment). */
+biofvm_status biofvm_set_sources_device(biofvm_t *h, int64_t n, const int64_t *voxel,
+                                        const double *secretion, const double *target,
+                                        const double *uptake, const double *weight);
+
 /* Advance n_steps >= 0 time steps (async).  Steps run as CUDA graphs captured
  * on first use (after create or a parameter change): a block of K steps
  * (K = 1; with the FP64 streaming sweeps up to 16, the steps between which the

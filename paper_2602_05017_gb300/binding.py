@@ -66,6 +66,8 @@ def load():
                                ctypes.POINTER(vp)]),
         "biofvm_set_density": (st, [vp, vp, ctypes.c_int]),
         "biofvm_set_sources": (st, [vp, ctypes.c_int64, i64p, dp, dp, dp, dp]),
+        "biofvm_reserve_agents": (st, [vp, ctypes.c_int64]),
+        "biofvm_set_sources_device": (st, [vp, ctypes.c_int64, vp, vp, vp, vp, vp]),
         "biofvm_step": (st, [vp, ctypes.c_int]),
         "biofvm_density": (st, [vp, vp, ctypes.c_int]),
         "biofvm_set_params": (st, [vp, dp, dp]),
@@ -239,6 +241,36 @@ class BioFVM:
         _check(self.lib.biofvm_set_sources(
             self.h, n, vox.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)) if n else None,
             *[_dptr(a) for a in arrs], _dptr(w)), self.lib)
+
+    def reserve_agents(self, n_max):
+        """Device buffers for up to n_max agents given by set_sources_device."""
+        _check(self.lib.biofvm_reserve_agents(self.h, int(n_max)), self.lib)
+
+    def set_sources_device(self, voxel, secretion=None, target=None, uptake=None, weight=None):
+        """Agents from CUDA tensors (voxel int64 [n]; rates float64 [n, n_sub]; weight [n]),
+        rebuilt into source lists on the device, stream-ordered (the tensors are kept alive
+        until the next call)."""
+        import torch
+        ns = self.shape[3]
+        vox = voxel.contiguous()
+        n = vox.numel()
+        if vox.dtype != torch.int64 or not vox.is_cuda:
+            raise ValueError("voxel must be a CUDA int64 tensor")
+        keep = [vox]
+
+        def rate(a, count):
+            if a is None:
+                return None
+            t = a.contiguous()
+            if t.dtype != torch.float64 or not t.is_cuda or t.numel() != count:
+                raise ValueError(f"expected a CUDA float64 tensor of {count} values")
+            keep.append(t)
+            return ctypes.c_void_p(t.data_ptr())
+        args = [rate(secretion, n * ns), rate(target, n * ns), rate(uptake, n * ns),
+                rate(weight, n)]
+        _check(self.lib.biofvm_set_sources_device(self.h, n, ctypes.c_void_p(vox.data_ptr()),
+                                                  *args), self.lib)
+        self._keep_agents = keep
 
     def set_dirichlet_nodes(self, voxel, substrate, value):
         """Dirichlet nodes (voxel, substrate, value), overwritten at every Dirichlet application

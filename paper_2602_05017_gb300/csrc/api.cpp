@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "../../include/biofvm.h"
+#include "agents.h"
 #include "batch_args.h"
 #include "pipe_args.h"
 #include "internal.h"
@@ -133,6 +134,13 @@ struct biofvm {
   // sources
   int64_t n_entries = 0;
   DevBuf src_row_off, src_elem, src_rowcol, src_alpha, src_scale;
+  // source lists rebuilt on the device from device agent arrays (biofvm_set_sources_device):
+  // buffers reserved for up to agents_max agents, used instead of the host-built lists while
+  // sources_device is set (their length lives on the device: dsrc_count)
+  int64_t agents_max = 0;
+  bool sources_device = false;
+  DevBuf dsrc_row_off, dsrc_elem, dsrc_rowcol, dsrc_alpha, dsrc_scale, dsrc_count;
+  DevBuf ag_key[2], ag_idx[2], ag_ea, ag_eb, ag_head, ag_pos, ag_hist, ag_part, ag_count32;
   // step graphs: [0] a block of renorm_k steps, [r] a tail of r < renorm_k steps
   cudaGraph_t graph[kMaxRenorm + 1] = {};
   cudaGraphExec_t gexec[kMaxRenorm + 1] = {};
@@ -737,6 +745,35 @@ biofvm_status upload_constants(biofvm *h) {
   return BIOFVM_OK;
 }
 
+// The source lists the kernels read: host-built (biofvm_set_sources) or rebuilt on the device
+// (biofvm_set_sources_device; their length is only known on the device, so `has` is set and
+// the kernels take the range from the row offsets).
+struct SrcLists {
+  const int64_t *row_off, *elem;
+  const int2 *rowcol;
+  const void *alpha, *scale;
+  int has;
+};
+SrcLists src_lists(const biofvm *h) {
+  SrcLists l;
+  if (h->sources_device) {
+    l.row_off = static_cast<const int64_t *>(h->dsrc_row_off.p);
+    l.elem = static_cast<const int64_t *>(h->dsrc_elem.p);
+    l.rowcol = static_cast<const int2 *>(h->dsrc_rowcol.p);
+    l.alpha = h->dsrc_alpha.p;
+    l.scale = h->dsrc_scale.p;
+    l.has = 1;
+  } else {
+    l.row_off = static_cast<const int64_t *>(h->src_row_off.p);
+    l.elem = static_cast<const int64_t *>(h->src_elem.p);
+    l.rowcol = static_cast<const int2 *>(h->src_rowcol.p);
+    l.alpha = h->src_alpha.p;
+    l.scale = h->src_scale.p;
+    l.has = h->n_entries > 0;
+  }
+  return l;
+}
+
 AxisTab axis_tab(const biofvm *h, int axis) {
   const int n = axis_len(h, axis), S = h->g.n_sub;
   const char *base = static_cast<const char *>(h->tab[axis].p);
@@ -791,12 +828,13 @@ cudaError_t launch_pipe(const biofvm *h, int axis, int flags, cudaStream_t st, v
   b.tab.m = p.m;
   b.flags = flags;
   if (!h->any_dir) b.flags &= ~(kDirBefore | kDirAfter);
-  b.src_row_off = static_cast<const int64_t *>(h->src_row_off.p);
-  b.src_elem = static_cast<const int64_t *>(h->src_elem.p);
-  b.src_rowcol = static_cast<const int2 *>(h->src_rowcol.p);
-  b.src_alpha = h->src_alpha.p;
-  b.src_scale = h->src_scale.p;
-  b.has_src = h->n_entries > 0;
+  const SrcLists sl = src_lists(h);
+  b.src_row_off = sl.row_off;
+  b.src_elem = sl.elem;
+  b.src_rowcol = sl.rowcol;
+  b.src_alpha = sl.alpha;
+  b.src_scale = sl.scale;
+  b.has_src = sl.has;
   b.dir_on = static_cast<const uint8_t *>(h->dir_on_d.p);
   b.dir_val = h->dir_val_d.p;
   b.status = static_cast<int *>(h->status.p);
@@ -839,11 +877,12 @@ cudaError_t launch_stream(const biofvm *h, int axis, int flags, cudaStream_t st,
   a.out = !scaled ? 0 : (axis == 2 && !(flags & kKeepScale)) ? 2 : 1;
   a.k0 = h->stream_k0[axis];
   a.interior = static_cast<const char *>(h->stream_const_d.p) + (size_t)axis * 2 * S * h->esz;
-  a.src_row_off = static_cast<const int64_t *>(h->src_row_off.p);
-  a.src_elem = static_cast<const int64_t *>(h->src_elem.p);
-  a.src_alpha = h->src_alpha.p;
-  a.src_scale = h->src_scale.p;
-  a.has_src = h->n_entries > 0;
+  const SrcLists sl = src_lists(h);
+  a.src_row_off = sl.row_off;
+  a.src_elem = sl.elem;
+  a.src_alpha = sl.alpha;
+  a.src_scale = sl.scale;
+  a.has_src = sl.has;
   a.dir_on = static_cast<const uint8_t *>(h->dir_on_d.p);
   a.dir_val = a.dir_val_in = h->dir_val_d.p;
   if (scaled) {  // the step's row of the renormalisation table (upload_constants)
@@ -890,11 +929,12 @@ cudaError_t launch_x(const biofvm *h, int flags, cudaStream_t st, void *field = 
   a.smem_bytes = h->xp.smem;
   a.flags = flags;
   if (!h->any_dir) a.flags &= ~(kDirBefore | kDirAfter);
-  a.has_src = h->n_entries > 0;
-  a.src_row_off = static_cast<const int64_t *>(h->src_row_off.p);
-  a.src_elem = static_cast<const int64_t *>(h->src_elem.p);
-  a.src_alpha = h->src_alpha.p;
-  a.src_scale = h->src_scale.p;
+  const SrcLists sl = src_lists(h);
+  a.has_src = sl.has;
+  a.src_row_off = sl.row_off;
+  a.src_elem = sl.elem;
+  a.src_alpha = sl.alpha;
+  a.src_scale = sl.scale;
   a.dir_on = static_cast<const uint8_t *>(h->dir_on_d.p);
   a.dir_val = h->dir_val_d.p;
   a.status = static_cast<int *>(h->status.p);
@@ -1048,6 +1088,7 @@ biofvm_status build_sources(biofvm *h) {
   }
   h->n_entries = (int64_t)u;
   h->h_src_elem = elem;
+  h->sources_device = false;
   h->agents_on_device = false;  // the adjoint's agent-to-entry map follows the list
   h->generation++;
   drop_graphs(h);  // kernel arguments changed
@@ -1059,6 +1100,10 @@ biofvm_status check_status(biofvm *h) {
   CK(cudaMemcpy(&st, h->status.p, sizeof(int), cudaMemcpyDeviceToHost));
   if (st != kStatusOk) {
     CK(cudaMemset(h->status.p, 0, sizeof(int)));
+    if (st == kStatusBadInput)
+      return fail(BIOFVM_ERR_ARG, "a device agent array held an invalid agent (voxel out of "
+                                  "range, or a negative or non-finite rate or weight); it was "
+                                  "left out of the source lists");
     return fail(BIOFVM_ERR_TIMEOUT, "a bounded device-side wait timed out (status %d)", st);
   }
   return BIOFVM_OK;
@@ -1082,7 +1127,11 @@ void destroy_impl(biofvm *h) {
                     &h->stream_const_d, &h->scratch, &h->dir_on_d, &h->dir_val_d,
                     &h->status, &h->src_row_off, &h->src_elem, &h->src_rowcol, &h->src_alpha, &h->src_scale,
                     &h->adj, &h->partial, &h->ag_elem, &h->ag_entry, &h->ag_weight,
-                    &h->ag_target, &h->dn_elem, &h->dn_val})
+                    &h->ag_target, &h->dn_elem, &h->dn_val, &h->dsrc_row_off, &h->dsrc_elem,
+                    &h->dsrc_rowcol, &h->dsrc_alpha, &h->dsrc_scale, &h->dsrc_count,
+                    &h->ag_key[0], &h->ag_key[1], &h->ag_idx[0], &h->ag_idx[1], &h->ag_ea,
+                    &h->ag_eb, &h->ag_head, &h->ag_pos, &h->ag_hist, &h->ag_part,
+                    &h->ag_count32})
     b->release();
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   delete h;
@@ -1429,6 +1478,11 @@ biofvm_status biofvm_set_dirichlet_nodes(biofvm_t *h, int64_t n, const int64_t *
     h->any_dir = h->any_dir || h->dir_on_k[s];
   }
   CK(cudaMemcpy(h->dir_on_d.p, h->dir_on_k.data(), (size_t)S, cudaMemcpyHostToDevice));
+  if (h->sources_device) {  // device-built lists: the next biofvm_set_sources_device drops nodes
+    h->generation++;
+    drop_graphs(h);
+    return BIOFVM_OK;
+  }
   return build_sources(h);  // no source entry on a node element; new graphs
 }
 
@@ -1466,6 +1520,106 @@ biofvm_status biofvm_set_sources(biofvm_t *h, int64_t n, const int64_t *voxel,
   if (secretion) std::copy(secretion, secretion + (size_t)n * S, h->h_secretion.begin());
   if (uptake) std::copy(uptake, uptake + (size_t)n * S, h->h_uptake.begin());
   return build_sources(h);
+}
+
+biofvm_status biofvm_reserve_agents(biofvm_t *h, int64_t n_max) {
+  if (!h) return fail(BIOFVM_ERR_ARG, "NULL handle");
+  if (h->forced) return fail(BIOFVM_ERR_STATE, "batched environments take host agent arrays");
+  const int S = h->g.n_sub;
+  if (n_max < 0 || n_max * (int64_t)S >= (int64_t)0xffffffffLL)
+    return fail(BIOFVM_ERR_ARG, "n_max must be in [0, 2^32 / n_sub)");
+  CK(cudaSetDevice(h->device));
+  CK(cudaStreamSynchronize(h->stream));  // launches in flight may read the old buffers
+  const int64_t N = std::max<int64_t>(1, n_max * S);
+  const int64_t nrows = (int64_t)h->g.ny * h->g.nz;
+  const long long nb = agent_sort_blocks(N);
+  const long long parts = std::max(agent_scan_blocks(N), agent_scan_blocks(256 * nb));
+  struct {
+    DevBuf *b;
+    size_t bytes;
+  } want[] = {{&h->dsrc_row_off, (size_t)(nrows + 1) * 8}, {&h->dsrc_elem, (size_t)N * 8},
+              {&h->dsrc_rowcol, (size_t)N * 8},          {&h->dsrc_alpha, (size_t)N * h->esz},
+              {&h->dsrc_scale, (size_t)N * h->esz},      {&h->dsrc_count, 8},
+              {&h->ag_key[0], (size_t)N * 8},            {&h->ag_key[1], (size_t)N * 8},
+              {&h->ag_idx[0], (size_t)N * 4},            {&h->ag_idx[1], (size_t)N * 4},
+              {&h->ag_ea, (size_t)N * 8},                {&h->ag_eb, (size_t)N * 8},
+              {&h->ag_head, (size_t)N * 4},              {&h->ag_pos, (size_t)N * 4},
+              {&h->ag_hist, (size_t)256 * nb * 4},       {&h->ag_part, (size_t)parts * 4},
+              {&h->ag_count32, 4}};
+  if (h->sources_device) {  // the kernels read the reserved lists: switch to empty host lists
+    h->sources_device = false;
+    h->h_voxel.clear();
+    h->h_weight.clear();
+    h->h_target.clear();
+    h->h_secretion.clear();
+    h->h_uptake.clear();
+    biofvm_status st = build_sources(h);
+    if (st) return st;
+  }
+  for (auto &w : want)
+    if (dev_alloc(*w.b, w.bytes) != cudaSuccess) {
+      for (auto &v : want) v.b->release();
+      h->agents_max = 0;
+      return fail(BIOFVM_ERR_OOM, "device allocation for %lld agents failed", (long long)n_max);
+    }
+  h->agents_max = n_max;
+  return BIOFVM_OK;
+}
+
+biofvm_status biofvm_set_sources_device(biofvm_t *h, int64_t n, const int64_t *voxel,
+                                        const double *secretion, const double *target,
+                                        const double *uptake, const double *weight) {
+  if (!h) return fail(BIOFVM_ERR_ARG, "NULL handle");
+  if (h->forced) return fail(BIOFVM_ERR_STATE, "batched environments take host agent arrays");
+  if (n < 0 || n > h->agents_max)
+    return fail(BIOFVM_ERR_ARG, "n = %lld agents: reserve them first (biofvm_reserve_agents: %lld)",
+                (long long)n, (long long)h->agents_max);
+  if (n > 0 && !voxel) return fail(BIOFVM_ERR_ARG, "voxel is NULL");
+  if (h->agents_max == 0) return fail(BIOFVM_ERR_STATE, "no agent buffers reserved");
+  CK(cudaSetDevice(h->device));
+  const int S = h->g.n_sub;
+  AgentBuild b{};
+  b.voxel = voxel;
+  b.secretion = secretion;
+  b.target = target;
+  b.uptake = uptake;
+  b.weight = weight;
+  b.n_entries_max = (long long)n * S;
+  b.S = S;
+  b.nvox = (int64_t)h->g.nx * h->g.ny * h->g.nz;
+  b.rowlen = (int64_t)h->g.nx * S;
+  b.nrows = (int64_t)h->g.ny * h->g.nz;
+  b.dt = h->dt;
+  b.sentinel = (uint64_t)h->nel;
+  b.node_elem = static_cast<const int64_t *>(h->dn_elem.p);
+  b.n_nodes = h->n_dnode;
+  for (int i = 0; i < 2; i++) {
+    b.key[i] = static_cast<uint64_t *>(h->ag_key[i].p);
+    b.idx[i] = static_cast<uint32_t *>(h->ag_idx[i].p);
+  }
+  b.ea = static_cast<double *>(h->ag_ea.p);
+  b.eb = static_cast<double *>(h->ag_eb.p);
+  b.head = static_cast<uint32_t *>(h->ag_head.p);
+  b.pos = static_cast<uint32_t *>(h->ag_pos.p);
+  b.hist = static_cast<uint32_t *>(h->ag_hist.p);
+  b.part = static_cast<uint32_t *>(h->ag_part.p);
+  b.count32 = static_cast<uint32_t *>(h->ag_count32.p);
+  b.src_elem = static_cast<int64_t *>(h->dsrc_elem.p);
+  b.src_alpha = h->dsrc_alpha.p;
+  b.src_scale = h->dsrc_scale.p;
+  b.src_rowcol = static_cast<int2 *>(h->dsrc_rowcol.p);
+  b.src_row_off = static_cast<int64_t *>(h->dsrc_row_off.p);
+  b.count = static_cast<int64_t *>(h->dsrc_count.p);
+  b.status = static_cast<int *>(h->status.p);
+  CK(build_sources_device(b, h->prec == BIOFVM_FP64, h->stream));
+  if (!h->sources_device) {  // the kernels' source pointers change once: new graphs
+    h->sources_device = true;
+    h->n_entries = 0;
+    h->agents_on_device = false;
+    h->generation++;
+    drop_graphs(h);
+  }
+  return BIOFVM_OK;
 }
 
 biofvm_status biofvm_step(biofvm_t *h, int n_steps) {
@@ -1588,6 +1742,9 @@ biofvm_status biofvm_adjoint_step_rates(biofvm_t *h, const void *grad_out, void 
                                         double *duptake, const void *saved) {
   if (!h || !grad_out || !grad_in || !dD || !dlambda || !saved)
     return fail(BIOFVM_ERR_ARG, "NULL handle, gradient or saved-state pointer");
+  if (h->sources_device)
+    return fail(BIOFVM_ERR_STATE, "the adjoint needs the agents given through "
+                                  "biofvm_set_sources (the device-built lists have no host copy)");
   CK(cudaSetDevice(h->device));
   cudaStream_t st = h->stream;
   const size_t bytes = h->nel * h->esz;
