@@ -55,6 +55,9 @@ MEASURED_TRAFFIC = {
     "bytes": {},
 }
 UNIT = "voxel-substrate updates/s"
+# the headline workload's precisions: FP64 (the paper's), FP32, and 16-bit storage with FP32
+# arithmetic
+PRECISIONS = ("fp64", "fp32", "bf16", "fp16")
 METRIC = "LOD step voxel-substrate updates/s (HBM GB/s vs peak in roofline)"
 
 
@@ -198,13 +201,13 @@ def run_gpu(args):
     results = {"fma_rate": {p: binding.probe_fma_rate(p, stream.cuda_stream)
                             for p in ("fp64", "fp32")}}
     ref100 = None  # FP64 GPU field after 100 steps (the FP32 leg's reference)
-    for prec in ([] if args.batch_only else (args.only or ("fp64", "fp32"))):
-        esz = 8 if prec == "fp64" else 4
-        tdt = torch.float64 if prec == "fp64" else torch.float32
-        ndt = np.float64 if prec == "fp64" else np.float32
+    for prec in ([] if args.batch_only else (args.only or PRECISIONS)):
+        esz = {"fp64": 8, "fp32": 4, "bf16": 2, "fp16": 2}[prec]
+        tdt = {"fp64": torch.float64, "fp32": torch.float32, "bf16": torch.bfloat16,
+               "fp16": torch.float16}[prec]
         sim = binding.BioFVM(w.nx, w.ny, w.nz, w.ns, w.dx, w.dt, w.D, w.lam, precision=prec,
                              stream=stream.cuda_stream)
-        host_in = torch.from_numpy(w.rho0.astype(ndt)).pin_memory()
+        host_in = torch.from_numpy(w.rho0).to(tdt).pin_memory()
         rho0 = host_in.to(dev)
         sim.set_density(rho0)
         sim.set_sources(w.voxel, w.secretion, w.target, w.uptake)
@@ -238,7 +241,7 @@ def run_gpu(args):
         res = {"ms_total": ms_max, "ms_per_step": ms_max / K,
                "value": world * nel * K / (ms_max * 1e-3), "kernel_ms": kms,
                "z_renorm_ms": z_renorm, "clocks": clk.summary(),
-               "launches": sim.launches_per_step() * K, "esz": esz}
+               "launches": sim.launches_per_step() * K, "esz": esz, "prec": prec}
         # --- e2e: host buffers through the C ABI ---
         if rank == 0 and not args.no_e2e:
             host_out = torch.empty(w.shape, dtype=tdt).pin_memory()
@@ -272,10 +275,14 @@ def run_gpu(args):
                 ref100 = sim.density()
             else:
                 sim.step(n_err)
-                got = sim.density()
+                got = torch.empty(w.shape, dtype=tdt)
+                sim.density(got)
                 if ref100 is not None:
-                    res["error"] = {f"vs_fp64_gpu_{n_err}_steps": error_stats(got, ref100, 1e-6),
-                                    "reference": "FP64 GPU path (oracle-validated), same inputs"}
+                    res["error"] = {f"vs_fp64_gpu_{n_err}_steps":
+                                    error_stats(got.double().numpy(), ref100, 1e-6),
+                                    "reference": "FP64 GPU path (oracle-validated) from the same "
+                                                 "FP64 initial field (the storage rounding of the "
+                                                 "initial field included)"}
                 del got
         sim.close()
         del rho0, host_in
@@ -835,7 +842,7 @@ def main():
                     help="run only the batched leg (profiling only; not a bench line)")
     ap.add_argument("--shape", type=int, nargs=3, metavar=("NX", "NY", "NZ"),
                     help="smaller grid of the same recipe (profiling only; not a bench line)")
-    ap.add_argument("--only", nargs="+", choices=["fp64", "fp32"],
+    ap.add_argument("--only", nargs="+", choices=list(PRECISIONS),
                     help="run only these precisions (profiling only; not a bench line)")
     args = ap.parse_args()
     global SHAPE
@@ -868,11 +875,14 @@ def main():
     line["error"] = r64.get("error")
     fma = res["fma_rate"]
     line["roofline"] = roofline(r64, w, peaks, src, fma)
-    line["fp32"] = {"value": res["fp32"]["value"], "ms_per_step": res["fp32"]["ms_per_step"],
-                    "dtype": "f32", "roofline": roofline(res["fp32"], w, peaks, src, fma),
-                    "e2e": res["fp32"].get("e2e"), "clocks": res["fp32"]["clocks"],
-                    "error": res["fp32"].get("error"),
-                    "vs_fp64": res["fp32"]["value"] / r64["value"]}
+    for p, dt in (("fp32", "f32"), ("bf16", "bf16 storage, f32 arithmetic"),
+                  ("fp16", "f16 storage, f32 arithmetic")):
+        r = res[p]
+        line[p] = {"value": r["value"], "ms_per_step": r["ms_per_step"], "dtype": dt,
+                   "roofline": roofline(r, w, peaks, src, fma), "e2e": r.get("e2e"),
+                   "clocks": r["clocks"], "error": r.get("error"),
+                   "kernel_ms": dict(zip(("x", "y", "z"), r["kernel_ms"])),
+                   "vs_fp64": r["value"] / r64["value"]}
     if "fp32_batched" in res:
         bt = dict(res["fp32_batched"])
         bt["vs_fp64"] = bt["value"] / r64["value"]
@@ -899,10 +909,9 @@ def roofline(r, w, peaks, src, fma):
     kms = r["kernel_ms"]
     i = int(np.argmax(kms))
     name = ("x", "y", "z")[i]
-    prec = "f64" if r["esz"] == 8 else "f32"
     traffic = None
     if SHAPE is None and MEASURED_TRAFFIC["sources_sha256"] == kernel_sources_sha256():
-        traffic = MEASURED_TRAFFIC["bytes"].get(f"{prec}:{name}-sweep")
+        traffic = MEASURED_TRAFFIC["bytes"].get(f"{r['prec']}:{name}-sweep")
     dram = None if traffic is None else traffic / (kms[i] * 1e-3) / 1e9
     alg_gbps = 2 * r["esz"] * w.n_vs / (kms[i] * 1e-3) / 1e9
     hbm_peak = float(peaks["hbm_gbs"])

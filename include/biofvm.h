@@ -23,8 +23,9 @@
  * Field layout (Sect. 3.1, one contiguous 4D array): element (x, y, z, s) is
  * at index ((z*ny + y)*nx + x)*n_sub + s -- substrates interleaved per voxel,
  * x the fastest of the three axes.  The element type is double for
- * BIOFVM_FP64 and float for BIOFVM_FP32 (Thomas constants are always computed
- * in double on the host, then rounded to the element type).
+ * BIOFVM_FP64, float for BIOFVM_FP32, and a 16-bit bfloat16 / IEEE half for
+ * BIOFVM_BF16 / BIOFVM_FP16 (Thomas constants are always computed in double on
+ * the host, then rounded to the arithmetic type: double or float).
  *
  * Conventions of every call:
  *   - Errors are returned as a biofvm_status, never thrown; the thread-local
@@ -57,7 +58,19 @@ typedef enum {
   BIOFVM_ERR_STATE = 5    /* call not valid in the handle's current state  */
 } biofvm_status;
 
-typedef enum { BIOFVM_FP64 = 0, BIOFVM_FP32 = 1 } biofvm_precision;
+/* BIOFVM_BF16 / BIOFVM_FP16: the field stored in 16 bits (bfloat16 / IEEE
+ * half) with FP32 arithmetic and FP32 constants -- half the bytes of FP32, at
+ * the storage rounding of 2^-8 (bf16) or 2^-11 (fp16) per stored value.  These
+ * handles run whole steps (and the solve stages) on the pipelined sweep only:
+ * create fails with ARG unless nx*n_sub and nx*ny*n_sub are multiples of 8
+ * and the lines fit its tiles; Dirichlet nodes, the adjoint, stages 0 and 4
+ * and batched environments are refused (STATE or ARG). */
+typedef enum {
+  BIOFVM_FP64 = 0,
+  BIOFVM_FP32 = 1,
+  BIOFVM_BF16 = 2,
+  BIOFVM_FP16 = 3
+} biofvm_precision;
 
 typedef struct {
   int nx, ny, nz; /* voxels per axis, each >= 1                          */

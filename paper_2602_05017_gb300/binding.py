@@ -18,7 +18,8 @@ LIB_PATH = os.path.join(HERE, "libbiofvm.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "biofvm.h")
 
 OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_STATE = range(6)
-FP64, FP32 = 0, 1
+FP64, FP32, BF16, FP16 = 0, 1, 2, 3
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16": BF16, "fp16": FP16}
 STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_TIMEOUT",
                 5: "ERR_STATE"}
 
@@ -142,15 +143,20 @@ def _current_stream():
 class BioFVM:
     """One microenvironment on the GPU behind the C ABI (see include/biofvm.h).
 
-    Field layout ``[nz, ny, nx, n_sub]``; ``precision`` is "fp64" or "fp32".
+    Field layout ``[nz, ny, nx, n_sub]``; ``precision`` is "fp64", "fp32", or "bf16" / "fp16"
+    (16-bit storage, FP32 arithmetic: fields are exchanged as torch bfloat16 / float16 tensors;
+    numpy float16 also works for "fp16").
     """
 
     def __init__(self, nx, ny, nz, n_sub, dx, dt, D, lam, dirichlet_on=None,
                  dirichlet_value=None, precision="fp64", stream=None, _handle=None):
         self.lib = load()
         self.shape = (int(nz), int(ny), int(nx), int(n_sub))
+        if precision not in PRECISIONS:
+            raise ValueError(f"precision must be one of {sorted(PRECISIONS)}")
         self.precision = precision
-        self.dtype = np.float64 if precision == "fp64" else np.float32
+        self.dtype = {"fp64": np.float64, "fp32": np.float32, "fp16": np.float16,
+                      "bf16": None}[precision]
         self.n_elem = int(np.prod(self.shape))
         self._owned = _handle is None
         if _handle is not None:  # an environment of a batch (the batch owns it)
@@ -169,8 +175,7 @@ class BioFVM:
         h = ctypes.c_void_p()
         st = self.lib.biofvm_create(ctypes.byref(grid), float(dx), float(dt), _dptr(D), _dptr(lam),
                                     ctypes.byref(bc) if bc is not None else None,
-                                    FP64 if precision == "fp64" else FP32, self.stream,
-                                    ctypes.byref(h))
+                                    PRECISIONS[precision], self.stream, ctypes.byref(h))
         _check(st, self.lib)
         self.h = h
 
@@ -179,9 +184,9 @@ class BioFVM:
         """rho: torch tensor (CUDA or CPU) or numpy array with n_elem elements."""
         try:
             import torch
-            if isinstance(rho, torch.Tensor):
-                t = rho.detach().to(dtype=torch.float64 if self.precision == "fp64"
-                                    else torch.float32).contiguous()
+            if isinstance(rho, torch.Tensor) or self.dtype is None:
+                t = rho if isinstance(rho, torch.Tensor) else torch.as_tensor(np.asarray(rho))
+                t = t.detach().to(dtype=self._field_dtype()).contiguous()
                 if t.numel() != self.n_elem:
                     raise ValueError("field has the wrong size")
                 _check(self.lib.biofvm_set_density(self.h, ctypes.c_void_p(t.data_ptr()),
@@ -199,7 +204,11 @@ class BioFVM:
     def density(self, out=None):
         """Copy the field out: into ``out`` (torch tensor or numpy array) or a new numpy array."""
         if out is None:
-            out = np.empty(self.shape, dtype=self.dtype)
+            if self.dtype is None:  # bf16: a torch CPU tensor (numpy has no bfloat16)
+                import torch
+                out = torch.empty(self.shape, dtype=torch.bfloat16)
+            else:
+                out = np.empty(self.shape, dtype=self.dtype)
         try:
             import torch
             if isinstance(out, torch.Tensor):
@@ -225,11 +234,13 @@ class BioFVM:
         class _CAI:
             pass
         obj = _CAI()
+        typestr = {"fp64": "<f8", "fp32": "<f4", "fp16": "<f2", "bf16": "<i2"}[self.precision]
         obj.__cuda_array_interface__ = {
-            "shape": self.shape, "typestr": "<f8" if self.precision == "fp64" else "<f4",
+            "shape": self.shape, "typestr": typestr,
             "data": (self.density_ptr(), False), "version": 3, "strides": None,
             "stream": None}
-        return torch.as_tensor(obj, device="cuda")
+        t = torch.as_tensor(obj, device="cuda")
+        return t.view(torch.bfloat16) if self.precision == "bf16" else t
 
     # -- agents and parameters --------------------------------------------------------------
     def set_sources(self, voxel, secretion=None, target=None, uptake=None, weight=None):
@@ -306,7 +317,8 @@ class BioFVM:
 
     def _field_dtype(self):
         import torch
-        return torch.float64 if self.precision == "fp64" else torch.float32
+        return {"fp64": torch.float64, "fp32": torch.float32, "bf16": torch.bfloat16,
+                "fp16": torch.float16}[self.precision]
 
     def step_save(self, saved):
         """One step that also writes the adjoint's forward states into `saved` (4 fields)."""

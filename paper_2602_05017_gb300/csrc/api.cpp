@@ -107,7 +107,8 @@ struct biofvm {
   std::vector<double> dir_val;
   bool any_dir = false;
   biofvm_precision prec = BIOFVM_FP64;
-  size_t esz = 8;
+  size_t esz = 8;  // field element (storage): 8, 4, or 2 for bf16 / fp16
+  size_t csz = 8;  // arithmetic and constants: 8 for FP64, else 4
   int device = 0;
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;
@@ -385,8 +386,12 @@ bool encode_pipe_map(biofvm *h, int axis, int buf, void *field) {
   cuuint64_t strides[2] = {(cuuint64_t)(C * esz), (cuuint64_t)(C * esz * n)};
   cuuint32_t box[3] = {(cuuint32_t)p.cw, (cuuint32_t)p.box_rows, 1};
   cuuint32_t estr[3] = {1, 1, 1};
-  CUresult r = enc(&p.map[buf],
-                   esz == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+  const CUtensorMapDataType dtype =
+      h->prec == BIOFVM_FP64   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+      : h->prec == BIOFVM_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+      : h->prec == BIOFVM_FP16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                               : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  CUresult r = enc(&p.map[buf], dtype, 3,
                    field, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -399,6 +404,20 @@ bool encode_pipe_map(biofvm *h, int axis, int buf, void *field) {
 // pair within a half warp (FP64).
 int x_tile_conflicts(int pitch, int S, int lanes, size_t esz) {
   int worst = 0;
+  if (esz == 2) {  // two elements per 4-byte bank word: distinct words per bank
+    int cnt[32] = {0};
+    int word_seen[32][32];
+    for (int c = 0; c < lanes; c++) {
+      const int word = ((c / S) * pitch + c % S) >> 1, bank = word & 31;
+      bool dup = false;
+      for (int j = 0; j < cnt[bank]; j++) dup = dup || word_seen[bank][j] == word;
+      if (!dup) {
+        word_seen[bank][cnt[bank]] = word;
+        worst = std::max(worst, ++cnt[bank]);
+      }
+    }
+    return worst;
+  }
   if (esz == 4) {
     int cnt[32] = {0};
     for (int c = 0; c < lanes; c++) worst = std::max(worst, ++cnt[((c / S) * pitch + c % S) & 31]);
@@ -420,9 +439,10 @@ void plan_pipe(biofvm *h, int axis) {
   PipePlan &p = h->pp[axis];
   p = PipePlan{};
   const int64_t nx = h->g.nx, ny = h->g.ny, nz = h->g.nz, S = h->g.n_sub;
-  const size_t esz = h->esz;
+  const size_t esz = h->esz, csz = h->csz;
   const int n = axis_len(h, axis);
-  if (esz != 4) return;  // FP64 streams whole lines instead
+  if (h->prec == BIOFVM_FP64) return;  // FP64 streams whole lines instead
+  const bool h16 = esz == 2;  // 16-bit storage: chunk capacities 32 and 64 compiled
   for (int cw : {32, 16}) {
     PipePlan q{};
     q.cw = cw;
@@ -448,6 +468,8 @@ void plan_pipe(biofvm *h, int axis) {
       }
       if (!found) continue;
     }
+    if (h16 && cp.maxm < 32) cp.maxm = 32;  // short chunks run on the guarded path
+    if (h16 && cp.maxm > 64) continue;
     if (cw == 16 && cp.maxm != 32 && cp.maxm != 64) continue;
     // chunks above 64 registers spill (measured with -Xptxas -v): 16-column tiles instead
     if (cw == 32 && cp.maxm > 64 && h->pipe_chunk <= 0) continue;
@@ -484,9 +506,9 @@ void plan_pipe(biofvm *h, int axis) {
       if (q.ntiles > (int64_t)0x7fffffff) return;  // tiles are indexed in 32 bits
     }
     const size_t stage = (size_t)q.stage_elems * esz;
-    const size_t tab = (size_t)pipe_tab_elems_host(n, (int)S) * esz;
+    const size_t tab = (size_t)pipe_tab_elems_host(n, (int)S) * csz + 16;  // + alignment
     // carry exchange [2][W*32], carry weights [T][T][S], alignment, mbarriers
-    const size_t scratch = (2 * (size_t)W * 32 + (size_t)q.T * q.T * S) * esz + 16 + 2 * 8 * 8;
+    const size_t scratch = (2 * (size_t)W * 32 + (size_t)q.T * q.T * S) * csz + 16 + 2 * 8 * 8;
     for (int ns = 4; ns >= 2 && !q.stages; ns--)  // the constants always staged
       if (ns * stage + tab + scratch <= kMaxDynamicSmem) q.stages = ns;
     if (!q.stages) continue;
@@ -504,7 +526,9 @@ void plan_pipe(biofvm *h, int axis) {
     return;
   }
   // the attribute is per kernel, shared by every handle: always the opt-in maximum
-  const cudaError_t e = allow_pipe_smem_f32(p.maxm, kMaxDynamicSmem);
+  const cudaError_t e = h->prec == BIOFVM_BF16   ? allow_pipe_smem_bf16(p.maxm, kMaxDynamicSmem)
+                        : h->prec == BIOFVM_FP16 ? allow_pipe_smem_fp16(p.maxm, kMaxDynamicSmem)
+                                                 : allow_pipe_smem_f32(p.maxm, kMaxDynamicSmem);
   if (e != cudaSuccess) {
     cudaGetLastError();
     p.use = 0;
@@ -531,7 +555,7 @@ void plan_pipe(biofvm *h, int axis) {
 void plan_stream(biofvm *h, int axis) {
   StreamPlan &p = h->sp[axis];
   p = StreamPlan{};
-  if (!h->stream_enabled) return;
+  if (!h->stream_enabled || h->esz == 2) return;  // 16-bit fields: the pipelined sweep only
   if (h->prec == BIOFVM_FP32) {
     const bool plain_slow = axis == 0 ? (h->xp.nosolve || h->xp.maxm > 64)
                                       : (h->cp[axis].nosolve || h->cp[axis].maxm > 64);
@@ -562,8 +586,8 @@ std::vector<E> cast_vec(const std::vector<double> &v) {
 }
 
 biofvm_status upload_doubles(biofvm *h, DevBuf &b, const std::vector<double> &v) {
-  if (dev_alloc(b, v.size() * h->esz) != cudaSuccess)
-    return fail(BIOFVM_ERR_OOM, "device allocation of %zu bytes failed", v.size() * h->esz);
+  if (dev_alloc(b, v.size() * h->csz) != cudaSuccess)
+    return fail(BIOFVM_ERR_OOM, "device allocation of %zu bytes failed", v.size() * h->csz);
   if (h->prec == BIOFVM_FP64) {
     CK(cudaMemcpyAsync(b.p, v.data(), v.size() * 8, cudaMemcpyHostToDevice, h->stream));
   } else {
@@ -665,10 +689,11 @@ biofvm_status upload_constants(biofvm *h) {
   for (int axis = 0; axis < 3; axis++) {
     int T, m;
     axis_partition(h, axis, T, m);
-    axis_tables(h, axis, T, m, h->prec == BIOFVM_FP32, t);
+    const bool f32 = h->prec != BIOFVM_FP64;  // float arithmetic: FP32 and 16-bit storage
+    axis_tables(h, axis, T, m, f32, t);
     biofvm_status st = upload_doubles(h, h->tab[axis], t);
     if (st) return st;
-    if (h->prec == BIOFVM_FP32)
+    if (f32)
       stream_consts_f32(h, axis, t, &c32[(size_t)axis * 2 * h->g.n_sub], h->stream_k0[axis]);
     // the same inv, mul, pf, pb substrate-major [4][S][npad] for the pipelined kernel
     const int n = axis_len(h, axis), S = h->g.n_sub, npad = pipe_npad_host(n);
@@ -680,7 +705,7 @@ biofvm_status upload_constants(biofvm *h) {
     st = upload_doubles(h, h->tabT[axis], tt);
     if (st) return st;
   }
-  if (h->prec == BIOFVM_FP32) {
+  if (h->prec != BIOFVM_FP64) {
     biofvm_status st = upload_doubles(h, h->stream_const_d, c32);
     if (st) return st;
   }
@@ -777,7 +802,7 @@ SrcLists src_lists(const biofvm *h) {
 AxisTab axis_tab(const biofvm *h, int axis) {
   const int n = axis_len(h, axis), S = h->g.n_sub;
   const char *base = static_cast<const char *>(h->tab[axis].p);
-  const size_t blk = (size_t)n * S * h->esz;
+  const size_t blk = (size_t)n * S * h->csz;
   AxisTab t;
   t.inv = base;
   t.mul = base + blk;
@@ -786,8 +811,8 @@ AxisTab axis_tab(const biofvm *h, int axis) {
   t.pc = base + 4 * blk;
   int T, m;
   axis_partition(h, axis, T, m);
-  t.cfix = base + 4 * blk + (size_t)T * S * h->esz;
-  t.cw = base + 4 * blk + ((size_t)T * S + 2 * (size_t)S) * h->esz;
+  t.cfix = base + 4 * blk + (size_t)T * S * h->csz;
+  t.cw = base + 4 * blk + ((size_t)T * S + 2 * (size_t)S) * h->csz;
   t.tabT = h->tabT[axis].p;
   t.n = n;
   t.T = T;
@@ -839,6 +864,8 @@ cudaError_t launch_pipe(const biofvm *h, int axis, int flags, cudaStream_t st, v
   b.dir_val = h->dir_val_d.p;
   b.status = static_cast<int *>(h->status.p);
   const CUtensorMap &map = p.map[axis == 0 ? 0 : buf];
+  if (h->prec == BIOFVM_BF16) return launch_pipe_bf16(map, b, p.maxm, p.grid, p.smem, st);
+  if (h->prec == BIOFVM_FP16) return launch_pipe_fp16(map, b, p.maxm, p.grid, p.smem, st);
   return launch_pipe_f32(map, b, p.maxm, p.grid, p.smem, st);
 }
 
@@ -876,7 +903,7 @@ cudaError_t launch_stream(const biofvm *h, int axis, int flags, cudaStream_t st,
   const bool scaled = fp64 && (flags & kScaled);
   a.out = !scaled ? 0 : (axis == 2 && !(flags & kKeepScale)) ? 2 : 1;
   a.k0 = h->stream_k0[axis];
-  a.interior = static_cast<const char *>(h->stream_const_d.p) + (size_t)axis * 2 * S * h->esz;
+  a.interior = static_cast<const char *>(h->stream_const_d.p) + (size_t)axis * 2 * S * h->csz;
   const SrcLists sl = src_lists(h);
   a.src_row_off = sl.row_off;
   a.src_elem = sl.elem;
@@ -887,8 +914,8 @@ cudaError_t launch_stream(const biofvm *h, int axis, int flags, cudaStream_t st,
   a.dir_val = a.dir_val_in = h->dir_val_d.p;
   if (scaled) {  // the step's row of the renormalisation table (upload_constants)
     const int m = (flags >> 8) & 0xff;
-    const char *row = static_cast<const char *>(h->renorm_d.p) + (size_t)m * kRenormRows * S * h->esz;
-    auto at = [&](int k) { return static_cast<const void *>(row + (size_t)k * S * h->esz); };
+    const char *row = static_cast<const char *>(h->renorm_d.p) + (size_t)m * kRenormRows * S * h->csz;
+    auto at = [&](int k) { return static_cast<const void *>(row + (size_t)k * S * h->csz); };
     if (axis == 0) {
       a.src_fac = m > 0 ? at(0) : nullptr;
       a.dir_val_in = at(1);
@@ -991,7 +1018,7 @@ cudaError_t launch_nodes(const biofvm *h, cudaStream_t st, int m, int row, bool 
   a.val = h->dn_val.p;
   a.scale = row < 0 ? nullptr
                     : static_cast<const char *>(h->renorm_d.p) +
-                          ((size_t)m * kRenormRows + row) * h->g.n_sub * h->esz;
+                          ((size_t)m * kRenormRows + row) * h->g.n_sub * h->csz;
   a.n = h->n_dnode;
   a.S = h->g.n_sub;
   a.zero = zero ? 1 : 0;
@@ -1180,8 +1207,10 @@ biofvm_status create_impl(const biofvm_grid *grid, double dx, double dt, const d
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(BIOFVM_ERR_ARG, "dt must be > 0");
   if (!valid_params(g.n_sub, D, lambda))
     return fail(BIOFVM_ERR_ARG, "D and lambda must be finite, >= 0 and non-NULL");
-  if (prec != BIOFVM_FP64 && prec != BIOFVM_FP32)
+  if (prec != BIOFVM_FP64 && prec != BIOFVM_FP32 && prec != BIOFVM_BF16 && prec != BIOFVM_FP16)
     return fail(BIOFVM_ERR_ARG, "unknown precision %d", (int)prec);
+  if (force_m && (prec == BIOFVM_BF16 || prec == BIOFVM_FP16))
+    return fail(BIOFVM_ERR_ARG, "batched environments are FP64 or FP32");
   const bool fp64 = prec == BIOFVM_FP64;
   const double nel_d = (double)g.nx * g.ny * g.nz * g.n_sub;
   if (nel_d > 9.0e18 / 8) return fail(BIOFVM_ERR_ARG, "grid too large");
@@ -1217,7 +1246,8 @@ biofvm_status create_impl(const biofvm_grid *grid, double dx, double dt, const d
   }
   h->dir_on_k = h->dir_on;
   h->prec = prec;
-  h->esz = fp64 ? 8 : 4;
+  h->esz = fp64 ? 8 : (prec == BIOFVM_FP32 ? 4 : 2);
+  h->csz = fp64 ? 8 : 4;
   h->nel = (size_t)g.nx * g.ny * g.nz * g.n_sub;
   h->forced = force_m != nullptr;
   if (!plan_x(g.nx, g.n_sub, fp64, h->xp, force_m ? force_m[0] : 0, !force_m)) {
@@ -1305,6 +1335,12 @@ biofvm_status create_impl(const biofvm_grid *grid, double dx, double dt, const d
       return fail(BIOFVM_ERR_ARG, "y or z lines too long for the column sweep (ny=%d nz=%d)",
                   g.ny, g.nz);
     }
+  if (h->esz == 2 && !(h->pp[0].use && h->pp[1].use && h->pp[2].use)) {
+    destroy_impl(h);
+    return fail(BIOFVM_ERR_ARG,
+                "16-bit storage runs on the pipelined sweep only: nx*n_sub and nx*n_sub*ny "
+                "must be multiples of 8 elements and the lines short enough for its tiles");
+  }
   if ((st = upload_doubles(h, h->dir_val_d, h->dir_val)) != BIOFVM_OK ||
       (st = upload_constants(h)) != BIOFVM_OK) {
     std::string msg = g_last_error;
@@ -1380,6 +1416,7 @@ biofvm_status biofvm_set_spacing(biofvm_t *h, double dx, double dy, double dz) {
 biofvm_status biofvm_set_dirichlet_nodes(biofvm_t *h, int64_t n, const int64_t *voxel,
                                          const int32_t *substrate, const double *value) {
   if (!h) return fail(BIOFVM_ERR_ARG, "NULL handle");
+  if (h->esz == 2) return fail(BIOFVM_ERR_STATE, "16-bit fields take no Dirichlet nodes");
   if (n < 0) return fail(BIOFVM_ERR_ARG, "negative node count");
   if (n > 0 && (!voxel || !substrate || !value))
     return fail(BIOFVM_ERR_ARG, "voxel, substrate or value is NULL");
@@ -1538,8 +1575,8 @@ biofvm_status biofvm_reserve_agents(biofvm_t *h, int64_t n_max) {
     DevBuf *b;
     size_t bytes;
   } want[] = {{&h->dsrc_row_off, (size_t)(nrows + 1) * 8}, {&h->dsrc_elem, (size_t)N * 8},
-              {&h->dsrc_rowcol, (size_t)N * 8},          {&h->dsrc_alpha, (size_t)N * h->esz},
-              {&h->dsrc_scale, (size_t)N * h->esz},      {&h->dsrc_count, 8},
+              {&h->dsrc_rowcol, (size_t)N * 8},          {&h->dsrc_alpha, (size_t)N * h->csz},
+              {&h->dsrc_scale, (size_t)N * h->csz},      {&h->dsrc_count, 8},
               {&h->ag_key[0], (size_t)N * 8},            {&h->ag_key[1], (size_t)N * 8},
               {&h->ag_idx[0], (size_t)N * 4},            {&h->ag_idx[1], (size_t)N * 4},
               {&h->ag_ea, (size_t)N * 8},                {&h->ag_eb, (size_t)N * 8},
@@ -1665,6 +1702,8 @@ biofvm_status biofvm_run_stage(biofvm_t *h, int stage) {
   if (!h) return fail(BIOFVM_ERR_ARG, "NULL handle");
   CK(cudaSetDevice(h->device));
   if (stage < 0 || stage > 12) return fail(BIOFVM_ERR_ARG, "stage must be in [0, 12] (got %d)", stage);
+  if (h->esz == 2 && (stage == 0 || stage == 4))
+    return fail(BIOFVM_ERR_STATE, "16-bit fields run only the stages that solve");
   cudaStream_t st = h->stream;
   const int sc = step_scaled(h);
   // Dirichlet nodes: after Src (stage 0), after each solve followed by B, and
@@ -1706,6 +1745,7 @@ biofvm_status biofvm_run_stage(biofvm_t *h, int stage) {
 
 biofvm_status biofvm_step_save(biofvm_t *h, void *saved) {
   if (!h || !saved) return fail(BIOFVM_ERR_ARG, "NULL handle or saved buffer");
+  if (h->esz == 2) return fail(BIOFVM_ERR_STATE, "the adjoint takes FP64 or FP32 fields");
   CK(cudaSetDevice(h->device));
   const size_t bytes = h->nel * h->esz;
   char *sv = static_cast<char *>(saved);
@@ -1742,6 +1782,7 @@ biofvm_status biofvm_adjoint_step_rates(biofvm_t *h, const void *grad_out, void 
                                         double *duptake, const void *saved) {
   if (!h || !grad_out || !grad_in || !dD || !dlambda || !saved)
     return fail(BIOFVM_ERR_ARG, "NULL handle, gradient or saved-state pointer");
+  if (h->esz == 2) return fail(BIOFVM_ERR_STATE, "the adjoint takes FP64 or FP32 fields");
   if (h->sources_device)
     return fail(BIOFVM_ERR_STATE, "the adjoint needs the agents given through "
                                   "biofvm_set_sources (the device-built lists have no host copy)");
@@ -1951,7 +1992,7 @@ biofvm_status batch_upload(biofvm_batch *b) {
       x.group[ph] = x.whole[ph] ? kBatchWarps : std::max(1, kBatchWarps / x.T[ph]);
       x.items[ph] = (x.tiles[ph] + x.group[ph] - 1) / x.group[ph];
       x.stab[ph] = fp64 ? h->tabS[ph].p : h->tab[ph].p;
-      x.sint[ph] = static_cast<const char *>(h->stream_const_d.p) + (size_t)ph * 2 * x.S * h->esz;
+      x.sint[ph] = static_cast<const char *>(h->stream_const_d.p) + (size_t)ph * 2 * x.S * h->csz;
       x.cfix[ph] = axis_tab(h, ph).cfix;
       x.k0[ph] = h->stream_k0[ph];
     }

@@ -198,6 +198,14 @@ cudaError_t launch_batch_f64(const BatchArgs &a, int maxm, int grid, cudaStream_
 cudaError_t launch_batch_f32(const BatchArgs &a, int maxm, int grid, cudaStream_t st);
 cudaError_t batch_occupancy_f64(int maxm, int *out);
 cudaError_t batch_occupancy_f32(int maxm, int *out);
+// The same sweep for fields stored in 16 bits (bf16 / fp16), FP32 arithmetic;
+// chunk capacities 32 and 64.
+cudaError_t allow_pipe_smem_bf16(int maxm, size_t bytes);
+cudaError_t allow_pipe_smem_fp16(int maxm, size_t bytes);
+cudaError_t launch_pipe_bf16(const CUtensorMap &map, const PipeArgs &a, int maxm, int grid,
+                             size_t smem, cudaStream_t st);
+cudaError_t launch_pipe_fp16(const CUtensorMap &map, const PipeArgs &a, int maxm, int grid,
+                             size_t smem, cudaStream_t st);
 // Largest CTA the FP32 pipelined sweep with chunk capacity maxm may use.
 int pipe_max_threads_f32(int maxm);
 // Substrate-major constants of the pipelined sweep (elements): [4][S][npad].

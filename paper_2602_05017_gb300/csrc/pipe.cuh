@@ -31,11 +31,31 @@
 // the producer drains (bounded) the loads still in flight before the CTA exits.
 #pragma once
 #include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <type_traits>
 
 #include "pipe_args.h"
 #include "sweeps.cuh"
 
 namespace bfv {
+
+// Field storage H and arithmetic E: the same type, or 16-bit storage (bf16,
+// fp16) with FP32 arithmetic -- values are widened on their way from the
+// staged tile into registers and rounded to nearest on their way back.
+template <typename E, typename H>
+__device__ __forceinline__ E widen(H v) {
+  if constexpr (std::is_same<H, __nv_bfloat16>::value) return __bfloat162float(v);
+  else if constexpr (std::is_same<H, __half>::value) return __half2float(v);
+  else return v;
+}
+template <typename H, typename E>
+__device__ __forceinline__ H narrow(E v) {
+  if constexpr (std::is_same<H, __nv_bfloat16>::value) return __float2bfloat16_rn(v);
+  else if constexpr (std::is_same<H, __half>::value) return __float2half_rn(v);
+  else return v;
+}
 
 __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int c0, int c1,
                                             int c2, uint64_t *bar) {
@@ -101,8 +121,8 @@ __host__ __device__ inline int pipe_npad(int n) { return (n + 31) / 32 * 32 + 1;
 // PS > 0: compile-time stride between positions in the staged tile.
 // mid1 runs just before the first carry barrier, mid2 just before the second
 // (the x tiles prepare the next tile's stage there).
-template <typename E, int MAXM, bool FULL, int PS, int CW, typename M1, typename M2>
-__device__ __forceinline__ bool pipe_chunk(E *p, const int ps_rt, const int len, const int lo,
+template <typename E, int MAXM, bool FULL, int PS, int CW, typename H, typename M1, typename M2>
+__device__ __forceinline__ bool pipe_chunk(H *p, const int ps_rt, const int len, const int lo,
                                            const int n, const int t, const int T, const int c,
                                            const E *Ti, const E *Tm, const E *Tf, const E *Tb,
                                            const E *Tcw, const int S, const int s, const E chi,
@@ -113,18 +133,18 @@ __device__ __forceinline__ bool pipe_chunk(E *p, const int ps_rt, const int len,
   E v[MAXM];
 #pragma unroll
   for (int i = 0; i < MAXM; i++)
-    if (FULL || i < len) v[i] = p[i * ps];
+    if (FULL || i < len) v[i] = widen<E>(p[i * ps]);
   if constexpr (kDefect<E>) {
     // e = L_N d.  At the two ends of the line the zero-flux rows equal the
     // interior formula with a mirrored ghost value (d_{-1} = d_0,
     // d_n = d_{n-1}), so no position needs a branch.
     E prev = E(0), after = E(0);
     if (len > 0) {
-      prev = lo > 0 ? p[-ps] : v[0];
+      prev = lo > 0 ? widen<E>(p[-ps]) : v[0];
       // (the last value is re-read from the tile: selecting v[len-1] would
       // index the register array dynamically)
-      const E last = FULL ? v[MAXM - 1] : p[(len - 1) * ps];
-      after = lo + len < n ? p[(FULL ? MAXM : len) * ps] : last;
+      const E last = FULL ? v[MAXM - 1] : widen<E>(p[(len - 1) * ps]);
+      after = lo + len < n ? widen<E>(p[(FULL ? MAXM : len) * ps]) : last;
     }
 #pragma unroll
     for (int i = 0; i < MAXM; i++)
@@ -186,7 +206,7 @@ __device__ __forceinline__ bool pipe_chunk(E *p, const int ps_rt, const int len,
 #pragma unroll
     for (int i = 0; i < MAXM; i++)
       if (FULL || i < len) {
-        const E d = p[i * ps];
+        const E d = widen<E>(p[i * ps]);
         v[i] = fma(chi, d, fma(clo, d, v[i]));
       }
   }
@@ -200,7 +220,7 @@ __device__ __forceinline__ bool pipe_chunk(E *p, const int ps_rt, const int len,
   // carry arrays are rewritten only after barriers every warp has passed.
 #pragma unroll
   for (int i = 0; i < MAXM; i++)
-    if (FULL || i < len) p[i * ps] = v[i];
+    if (FULL || i < len) p[i * ps] = narrow<H>(v[i]);
   return true;
 }
 
@@ -208,8 +228,9 @@ __device__ __forceinline__ bool pipe_chunk(E *p, const int ps_rt, const int len,
 // MODE 1: y/z tiles (tensor boxes).  PSX > 0 (x tiles only): the substrate
 // count S, known at compile time, so the staged positions (S apart) need no
 // per-access address arithmetic; 0: S read at run time.  CW: columns per tile
-// (32, or 16 for long lines).
-template <typename E, int MAXM, int MODE, int PSX = 0, int CW = 32>
+// (32, or 16 for long lines).  H: the field's storage type (E, or bf16 / fp16
+// with E = float): stages and TMA copies hold H, registers and constants E.
+template <typename E, int MAXM, int MODE, int PSX = 0, int CW = 32, typename H = E>
 __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
     sweep_pipe_kernel(const __grid_constant__ CUtensorMap map, const PipeArgs a) {
   static_assert(CW == 32 || CW == 16, "tiles of 32 or 16 columns");
@@ -218,8 +239,11 @@ __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
   const int T = a.tab.T, m = a.tab.m, n = a.n, S = a.S, NS = a.stages;
   const int64_t stage_elems = a.stage_elems;
   const int npad = pipe_npad(n);
-  E *stage0 = reinterpret_cast<E *>(smem_raw);
-  E *tab = stage0 + NS * stage_elems;  // [4][S][npad]
+  H *stage0 = reinterpret_cast<H *>(smem_raw);
+  // [4][S][npad], 16-byte aligned after the stages: offset arithmetic on the shared array itself
+  // (a pointer rounded through an integer would hide from the compiler that the constants and
+  // carry arrays derived from it live in shared memory, turning their loads into generic ones)
+  E *tab = reinterpret_cast<E *>(smem_raw + ((size_t)NS * stage_elems * sizeof(H) + 15) / 16 * 16);
   const int W = (T + CPW - 1) / CPW;  // consumer warps
   E *s_end = tab + 4 * S * npad;      // [W*32]: chunk t, column c at t*CW + c
   E *s_beg = s_end + W * 32;
@@ -232,7 +256,7 @@ __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
   const long long first = blockIdx.x;
   const long long count = (a.ntiles - first + gridDim.x - 1) / gridDim.x;
   const int ncons = W * 32;
-  E *field = static_cast<E *>(a.field);
+  H *field = static_cast<H *>(a.field);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < NS; s++) {
@@ -260,10 +284,10 @@ __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
     };
     auto issue_load = [&](long long k, int s) {
       const long long tile = first + k * gridDim.x;
-      E *dst = stage0 + s * stage_elems;
+      H *dst = stage0 + s * stage_elems;
       if constexpr (MODE == 0) {
         const int rows = rows_of(tile);
-        const uint32_t rb = (uint32_t)(a.rowlen * sizeof(E));
+        const uint32_t rb = (uint32_t)(a.rowlen * sizeof(H));
         mbar_arrive_expect_tx(&full[s], rb * rows);
         for (int r = 0; r < rows; r++)
           bulk_g2s(dst + (size_t)r * a.pitch, field + (tile * a.rows_per_tile + r) * a.rowlen, rb,
@@ -271,17 +295,17 @@ __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
       } else {
         const int plane = (int)((uint32_t)tile / (uint32_t)a.tiles_per_plane);
         const int c0 = (int)((uint32_t)tile % (uint32_t)a.tiles_per_plane) * CW;
-        mbar_arrive_expect_tx(&full[s], (uint32_t)(stage_elems * sizeof(E)));
+        mbar_arrive_expect_tx(&full[s], (uint32_t)(stage_elems * sizeof(H)));
         for (int b = 0; b < a.nbox; b++)
           tma_load_3d(dst + (size_t)b * a.box_rows * CW, &map, c0, b * a.box_rows, plane, &full[s]);
       }
     };
     auto issue_store = [&](long long k, int s) {
       const long long tile = first + k * gridDim.x;
-      const E *src = stage0 + s * stage_elems;
+      const H *src = stage0 + s * stage_elems;
       if constexpr (MODE == 0) {
         const int rows = rows_of(tile);
-        const uint32_t rb = (uint32_t)(a.rowlen * sizeof(E));
+        const uint32_t rb = (uint32_t)(a.rowlen * sizeof(H));
         for (int r = 0; r < rows; r++)
           bulk_s2g(field + (tile * a.rows_per_tile + r) * a.rowlen, src + (size_t)r * a.pitch, rb);
       } else {
@@ -365,16 +389,16 @@ __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
   const bool dirb = MODE == 0 && (a.flags & kDirBefore);
   const bool prep = srcs || dirb;
   auto prep_src = [&](long long kk) {
-    E *const sg = stage0 + (int)(kk % NS) * stage_elems;
+    H *const sg = stage0 + (int)(kk % NS) * stage_elems;
     const long long r0 = (first + kk * gridDim.x) * a.rows_per_tile;
     if (pv) {  // the prefetched entry, then (rarely) the thread's further ones
-      E *q = sg + (prc.x - r0) * a.pitch + prc.y;
-      *q = (*q + pal) * psc;
+      H *q = sg + (prc.x - r0) * a.pitch + prc.y;
+      *q = narrow<H>((widen<E>(*q) + pal) * psc);
     }
     for (long long e = n0 + ctid + ncons; e < n1; e += ncons) {
       const int2 rc = __ldg(a.src_rowcol + e);
-      E *q = sg + (rc.x - r0) * a.pitch + rc.y;
-      *q = (*q + ldg<E>(a.src_alpha, e)) * ldg<E>(a.src_scale, e);
+      H *q = sg + (rc.x - r0) * a.pitch + rc.y;
+      *q = narrow<H>((widen<E>(*q) + ldg<E>(a.src_alpha, e)) * ldg<E>(a.src_scale, e));
     }
     // the next tile's first entries (offsets loaded one tile ago), and the
     // offsets of the tile after it
@@ -384,23 +408,24 @@ __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
     src_range(kk + 2, f0, f1);
   };
   auto prep_dir = [&](long long kk) {  // consumer warp wc takes rows wc, wc+W, ...
-    E *const sg = stage0 + (int)(kk % NS) * stage_elems;
+    H *const sg = stage0 + (int)(kk % NS) * stage_elems;
     const long long r0 = (first + kk * gridDim.x) * a.rows_per_tile;
     const int rows = (int)min((long long)a.rows_per_tile, a.nrows - r0);
     for (int rr = wc; rr < rows; rr += W) {
       const uint32_t row = (uint32_t)r0 + (uint32_t)rr;
       const int z = (int)(row / (uint32_t)a.ny), y = (int)row - z * a.ny;
-      E *trow = sg + (size_t)rr * a.pitch;
+      H *trow = sg + (size_t)rr * a.pitch;
       if (y == 0 || y == a.ny - 1 || z == 0 || z == a.nz - 1) {
         for (int kk2 = lane; kk2 < a.rowlen; kk2 += 32) {
           const int ss = kk2 % S;
-          if (a.dir_on[ss]) trow[kk2] = dir_value<E>(a.flags, a.dir_val, ss);
+          if (a.dir_on[ss]) trow[kk2] = narrow<H>(dir_value<E>(a.flags, a.dir_val, ss));
         }
       } else {
         for (int kk2 = lane; kk2 < 2 * S; kk2 += 32) {
           const int ss = kk2 % S;
           if (a.dir_on[ss])
-            trow[kk2 < S ? ss : (a.nx - 1) * S + ss] = dir_value<E>(a.flags, a.dir_val, ss);
+            trow[kk2 < S ? ss : (a.nx - 1) * S + ss] =
+                narrow<H>(dir_value<E>(a.flags, a.dir_val, ss));
         }
       }
     }
@@ -420,7 +445,7 @@ __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
     // solve; the steps before it only touch this stage and registers)
     const bool ok = mbar_wait_bounded(&full[st], (uint32_t)((k / NS) & 1), a.status);
     const long long tile = first + k * gridDim.x;
-    E *const stg = stage0 + st * stage_elems;
+    H *const stg = stage0 + st * stage_elems;
     int s;
     bool active, face = false;
     if constexpr (MODE == 0) {
@@ -451,7 +476,7 @@ __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
       }
     }
     const int len = active ? len_full : 0;
-    E *p = stg + colbase + lo * ps_rt;
+    H *p = stg + colbase + lo * ps_rt;
     const int rowoff = s * npad + lo;
     const bool dir = dir_after && a.dir_on[s];
     const E dval = dir ? dir_value<E>(a.flags, a.dir_val, s) : E(0);
@@ -499,20 +524,20 @@ constexpr bool pipe_half_tiles() {
   return MAXM == 32 || MAXM == 64;
 }
 
-template <typename E, int MAXM>
+template <typename E, int MAXM, typename H = E>
 cudaError_t allow_pipe_smem(size_t bytes) {
   cudaError_t e = cudaSuccess;
   auto set = [&](const void *f) {
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   };
-  set((const void *)sweep_pipe_kernel<E, MAXM, 0>);
-  set((const void *)sweep_pipe_kernel<E, MAXM, 1>);
+  set((const void *)sweep_pipe_kernel<E, MAXM, 0, 0, 32, H>);
+  set((const void *)sweep_pipe_kernel<E, MAXM, 1, 0, 32, H>);
   if constexpr (pipe_half_tiles<MAXM>()) {
-    set((const void *)sweep_pipe_kernel<E, MAXM, 0, 0, 16>);
-    set((const void *)sweep_pipe_kernel<E, MAXM, 1, 0, 16>);
+    set((const void *)sweep_pipe_kernel<E, MAXM, 0, 0, 16, H>);
+    set((const void *)sweep_pipe_kernel<E, MAXM, 1, 0, 16, H>);
   }
-  if constexpr (pipe_x_specialised<MAXM>()) {
+  if constexpr (std::is_same<H, E>::value && pipe_x_specialised<MAXM>()) {
     set((const void *)sweep_pipe_kernel<E, MAXM, 0, 1>);
     set((const void *)sweep_pipe_kernel<E, MAXM, 0, 2>);
     set((const void *)sweep_pipe_kernel<E, MAXM, 0, 4>);
@@ -521,7 +546,7 @@ cudaError_t allow_pipe_smem(size_t bytes) {
   return e;
 }
 
-template <typename E, int MAXM>
+template <typename E, int MAXM, typename H = E>
 cudaError_t launch_pipe_one(const CUtensorMap &map, const PipeArgs &a, int grid, size_t smem,
                             cudaStream_t st) {
   const int cpw = a.cw == 16 ? 2 : 1;
@@ -530,19 +555,19 @@ cudaError_t launch_pipe_one(const CUtensorMap &map, const PipeArgs &a, int grid,
   if (a.cw == 16) {
     if constexpr (pipe_half_tiles<MAXM>()) {
       if (a.mode != 0)
-        sweep_pipe_kernel<E, MAXM, 1, 0, 16><<<grid, threads, smem, st>>>(map, a);
+        sweep_pipe_kernel<E, MAXM, 1, 0, 16, H><<<grid, threads, smem, st>>>(map, a);
       else
-        sweep_pipe_kernel<E, MAXM, 0, 0, 16><<<grid, threads, smem, st>>>(map, a);
+        sweep_pipe_kernel<E, MAXM, 0, 0, 16, H><<<grid, threads, smem, st>>>(map, a);
       return cudaGetLastError();
     }
     return cudaErrorInvalidConfiguration;
   }
   if (a.cw != 32) return cudaErrorInvalidConfiguration;
   if (a.mode != 0) {
-    sweep_pipe_kernel<E, MAXM, 1><<<grid, threads, smem, st>>>(map, a);
+    sweep_pipe_kernel<E, MAXM, 1, 0, 32, H><<<grid, threads, smem, st>>>(map, a);
     return cudaGetLastError();
   }
-  if constexpr (pipe_x_specialised<MAXM>()) {
+  if constexpr (std::is_same<H, E>::value && pipe_x_specialised<MAXM>()) {
     switch (a.S) {
       case 1: sweep_pipe_kernel<E, MAXM, 0, 1><<<grid, threads, smem, st>>>(map, a); return cudaGetLastError();
       case 2: sweep_pipe_kernel<E, MAXM, 0, 2><<<grid, threads, smem, st>>>(map, a); return cudaGetLastError();
@@ -551,7 +576,7 @@ cudaError_t launch_pipe_one(const CUtensorMap &map, const PipeArgs &a, int grid,
       default: break;
     }
   }
-  sweep_pipe_kernel<E, MAXM, 0><<<grid, threads, smem, st>>>(map, a);
+  sweep_pipe_kernel<E, MAXM, 0, 0, 32, H><<<grid, threads, smem, st>>>(map, a);
   return cudaGetLastError();
 }
 
