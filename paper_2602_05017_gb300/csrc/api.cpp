@@ -451,7 +451,22 @@ void plan_pipe(biofvm *h, int axis) {
     if (h->pipe_chunk > 0) {  // chunk length chosen by the caller (tuning)
       if (!plan_col(n, false, cp, std::min(h->pipe_chunk, n))) continue;
     } else if (cw == 32) {
-      if (!plan_col(n, false, cp)) continue;
+      // a field that stays in L2 makes the sweep latency-bound: there the shortest chunk, 16
+      // then 24 positions, whose CTA fits (more consumer warps per SM; measured: 250^3 x 1
+      // z-sweep 0.036 against 0.050 ms); in the HBM-bound regime chunks of 32 (at 256^3 x 4
+      // chunks of 16 took the x-sweep from 0.139 to 0.211 ms)
+      const bool l2_resident = (double)h->nel * (double)esz <= 96.0e6;
+      bool shortc = false;
+      for (int target : {16, 24}) {
+        const int T = (n + target - 1) / target;
+        if (!l2_resident || h16 || T < 2 || (T + 1) * 32 > pipe_max_threads_f32(target)) continue;
+        cp.T = T;
+        cp.m = target;
+        cp.maxm = target;
+        shortc = true;
+        break;
+      }
+      if (!shortc && !plan_col(n, false, cp)) continue;
     } else {  // 16 columns: chunks of 32 or 64 (the capacities compiled for them)
       bool found = false;
       for (int target : {32, 64}) {
