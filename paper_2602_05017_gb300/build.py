@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libbiofvm.so")
 SOURCES = ["api.cpp", "sweeps_fp64.cu", "sweeps_fp32.cu", "pipe_fp32.cu", "pipe_h16.cu", "noalloc.cu",
-           "probe.cu", "agents.cu"]
+           "probe.cu", "agents.cu", "small.cu"]
 HEADERS = ["internal.h", "sweeps.cuh", "pipe.cuh", "pipe_args.h", "adjoint.cuh", "batch.cuh", "batch_args.h",
            "stream.cuh", "agents.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -128,6 +128,10 @@ struct biofvm {
   int stream_ctas_per_sm = 3;
   int stream_ks = 64;        // FP64: positions of each line's intermediate kept in shared memory
   int stream32_enabled = 0;  // FP32 streaming sweeps instead of the pipelined ones
+  // small FP64 grids: whole biofvm_step calls in one cooperative launch (small.cu)
+  int small_enabled = 1, small_use = 0, small_grid = 0;
+  size_t small_smem = 0;
+  DevBuf small_bar;
   int pipe_chunk = 0;        // FP32 pipelined sweeps: chunk length (0: the planner's)
   DevBuf scratch;            // FP32 streaming: forward intermediate, field-sized
   int forced = 0;  // chunk lengths fixed by the caller (batched environments)
@@ -588,6 +592,30 @@ void plan_stream(biofvm *h, int axis) {
   }
   p.grid = h->num_sms * std::max(1, h->stream_ctas_per_sm);
   p.use = 1;
+}
+
+// Small FP64 grids (a field of at most 32 MB whose z-planes fit in shared
+// memory): biofvm_step runs all its steps in one cooperative launch.  The grid covers the z-planes and at least one CTA
+// per SM, within what can be co-resident.
+void plan_small(biofvm *h) {
+  h->small_use = 0;
+  if (!h->small_enabled || h->prec != BIOFVM_FP64 || h->forced) return;
+  const int nx = h->g.nx, ny = h->g.ny, nz = h->g.nz, S = h->g.n_sub;
+  if ((double)h->nel * 8.0 > 32.0e6 || !h->sp[2].use) return;
+  const size_t smem = small_smem_bytes(nx, ny, S);
+  if (smem > 200 * 1024) return;
+  int per_sm = 0;
+  if (small_max_blocks(&per_sm, smem) != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    return;
+  }
+  if (dev_alloc(h->small_bar, 16) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  h->small_smem = smem;
+  h->small_grid = std::min(h->num_sms * per_sm, std::max(nz, h->num_sms));
+  h->small_use = 1;
 }
 
 // ---------------------------------------------------------------------------
@@ -1173,7 +1201,7 @@ void destroy_impl(biofvm *h) {
                     &h->dsrc_rowcol, &h->dsrc_alpha, &h->dsrc_scale, &h->dsrc_count,
                     &h->ag_key[0], &h->ag_key[1], &h->ag_idx[0], &h->ag_idx[1], &h->ag_ea,
                     &h->ag_eb, &h->ag_head, &h->ag_pos, &h->ag_hist, &h->ag_part,
-                    &h->ag_count32})
+                    &h->ag_count32, &h->small_bar})
     b->release();
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   delete h;
@@ -1356,6 +1384,8 @@ biofvm_status create_impl(const biofvm_grid *grid, double dx, double dt, const d
                 "16-bit storage runs on the pipelined sweep only: nx*n_sub and nx*n_sub*ny "
                 "must be multiples of 8 elements and the lines short enough for its tiles");
   }
+  if (const char *env = getenv("BIOFVM_SMALL")) h->small_enabled = atoi(env) != 0;
+  plan_small(h);
   if ((st = upload_doubles(h, h->dir_val_d, h->dir_val)) != BIOFVM_OK ||
       (st = upload_constants(h)) != BIOFVM_OK) {
     std::string msg = g_last_error;
@@ -1404,7 +1434,9 @@ biofvm_status biofvm_density_ptr(biofvm_t *h, void **dev_ptr) {
 }
 
 int biofvm_launches_per_step(const biofvm_t *h) {
-  return h ? 3 + (h->n_dnode > 0 ? 4 : 0) : 0;  // the sweeps (+ the Dirichlet nodes)
+  if (!h) return 0;
+  if (h->small_use && h->n_dnode == 0) return 1;  // one launch runs every step of a call
+  return 3 + (h->n_dnode > 0 ? 4 : 0);             // the sweeps (+ the Dirichlet nodes)
 }
 
 biofvm_status biofvm_set_params(biofvm_t *h, const double *D, const double *lambda) {
@@ -1679,6 +1711,33 @@ biofvm_status biofvm_step(biofvm_t *h, int n_steps) {
   if (n_steps < 0) return fail(BIOFVM_ERR_ARG, "n_steps must be >= 0");
   if (n_steps == 0) return BIOFVM_OK;
   CK(cudaSetDevice(h->device));
+  if (h->small_use && h->n_dnode == 0) {  // one cooperative launch for all the steps
+    SmallArgs a{};
+    a.rho = static_cast<double *>(h->rho.p);
+    a.nx = h->g.nx;
+    a.ny = h->g.ny;
+    a.nz = h->g.nz;
+    a.S = h->g.n_sub;
+    for (int axis = 0; axis < 3; axis++) a.tab[axis] = static_cast<const double *>(h->tab[axis].p);
+    a.ztab = static_cast<const double *>(h->tabS[2].p);
+    a.zint = static_cast<const double *>(h->stream_const_d.p) + (size_t)2 * 2 * h->g.n_sub;
+    a.zk0 = h->stream_k0[2];
+    const SrcLists sl = src_lists(h);
+    a.src_row_off = sl.row_off;
+    a.src_elem = sl.elem;
+    a.src_alpha = static_cast<const double *>(sl.alpha);
+    a.src_scale = static_cast<const double *>(sl.scale);
+    a.has_src = sl.has;
+    a.dir_on = static_cast<const uint8_t *>(h->dir_on_d.p);
+    a.dir_val = static_cast<const double *>(h->dir_val_d.p);
+    a.any_dir = h->any_dir ? 1 : 0;
+    a.n_steps = n_steps;
+    a.bar = static_cast<unsigned *>(h->small_bar.p);
+    a.status = static_cast<int *>(h->status.p);
+    CK(cudaMemsetAsync(h->small_bar.p, 0, 16, h->stream));
+    CK(launch_small_f64(a, h->small_grid, h->small_smem, h->stream));
+    return BIOFVM_OK;
+  }
   // graphs of K steps (a renormalisation block) and of a shorter tail, each
   // ending with the true field; K = 1 unless the FP64 streaming step applies
   const int K = step_scaled(h) ? h->renorm_k : 1;

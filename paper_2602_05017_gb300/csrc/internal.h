@@ -185,6 +185,30 @@ cudaError_t launch_pipe_f32(const CUtensorMap &map, const PipeArgs &a, int maxm,
 cudaError_t allow_stream_smem_f64();
 cudaError_t launch_stream_f64(const StreamArgs &a, int grid, cudaStream_t st);
 cudaError_t launch_stream_f32(const StreamArgs &a, int grid, cudaStream_t st);
+// Small FP64 grids: all steps of a call in one cooperative launch (small.cu).
+// Planes of nx*ny*S elements in shared memory for the x and y solves, z-lines
+// by the streaming line solver; bar: 3 words (arrivals, generation, abort) of
+// the bounded grid barrier, zeroed before each launch.
+struct SmallArgs {
+  double *rho;
+  int nx, ny, nz, S;
+  const double *tab[3];  // per axis: inv [n][S] then mul [n][S]
+  const double *ztab;    // z: the streaming tables inv, mul, q [3][nz][S]
+  const double *zint;    // z: interior constants [2][S] (sigma, r sigma) from position zk0
+  int zk0;
+  const int64_t *src_row_off, *src_elem;
+  const double *src_alpha, *src_scale;
+  int has_src;
+  const uint8_t *dir_on;
+  const double *dir_val;
+  int any_dir;
+  int n_steps;
+  unsigned *bar;
+  int *status;
+};
+size_t small_smem_bytes(int nx, int ny, int S);
+cudaError_t small_max_blocks(int *blocks_per_sm, size_t smem);
+cudaError_t launch_small_f64(const SmallArgs &a, int grid, size_t smem, cudaStream_t st);
 // Sets the thread-local message biofvm_last_error() returns.
 void set_error_message(const char *msg);
 

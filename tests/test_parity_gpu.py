@@ -93,6 +93,34 @@ def test_each_stage_matches_oracle(binding, shape):
         assert rel_err(got, fn(w.rho0)) <= 1e-13, stage
 
 
+@pytest.mark.parametrize("shape", [(50, 50, 50, 1), (17, 23, 9, 3), (40, 8, 70, 2), (1, 1, 5, 1),
+                                   (12, 12, 1, 2), (7, 1, 30, 4)],
+                         ids=lambda s: "x".join(map(str, s)))
+def test_small_grid_cooperative_path_matches_oracle(binding, monkeypatch, shape):
+    """Small FP64 grids run every step of a call in one cooperative launch (z-planes in shared
+    memory, a bounded grid barrier between the plane and z-line phases): against the oracle
+    over calls of 2 and 3 steps, and against the per-sweep kernels (BIOFVM_SMALL=0)."""
+    nx, ny, nz, ns = shape
+    rng = np.random.default_rng(nx * 31 + nz)
+    w = inputs.random_problem(rng, nx, ny, nz, ns, n_agents=max(1, nx * ny * nz // 25),
+                              dirichlet=True)
+    ref = orc(w).step(w.rho0, 5)
+    sim = binding.BioFVM.from_workload(w, precision="fp64")
+    assert sim.launches_per_step() == 1  # the cooperative path
+    sim.step(2)
+    sim.step(3)
+    got = sim.density()
+    sim.close()
+    assert rel_err(got, ref) <= 1e-12
+    monkeypatch.setenv("BIOFVM_SMALL", "0")
+    sim = binding.BioFVM.from_workload(w, precision="fp64")
+    assert sim.launches_per_step() == 3
+    sim.step(5)
+    other = sim.density()
+    sim.close()
+    assert rel_err(got, other) <= 1e-13
+
+
 @pytest.mark.parametrize("stream", ["0", "1"])
 def test_graph_steps_equal_stage_sequence(binding, monkeypatch, stream):
     """Graph-launched steps against the same stages launched one by one.  Without the
