@@ -51,8 +51,13 @@ KERNEL_SOURCES = ["stream.cuh", "sweeps.cuh", "pipe.cuh", "pipe_args.h", "intern
 # the 400^3 x 4 workload, from one ncu capture; reported only while the kernel sources still
 # hash to `sources_sha256` (otherwise the kernels changed since and traffic is null).
 MEASURED_TRAFFIC = {
-    "sources_sha256": None,
-    "bytes": {},
+    "sources_sha256": "a2510969894c0ec4ed027c68d75c00679e7cd959ece0b34f56b146504dabb7cd",
+    "bytes": {
+        "fp64:x-sweep": 5716324608, "fp64:y-sweep": 5511279104, "fp64:z-sweep": 5529953024,
+        "fp32:x-sweep": 2050955520, "fp32:y-sweep": 1983489024, "fp32:z-sweep": 1983777024,
+        "bf16:x-sweep": 1027049216, "bf16:y-sweep": 967136512, "bf16:z-sweep": 967069952,
+        "fp16:x-sweep": 1027403520, "fp16:y-sweep": 966989568, "fp16:z-sweep": 967088640,
+    },
 }
 UNIT = "voxel-substrate updates/s"
 # the headline workload's precisions: FP64 (the paper's), FP32, and 16-bit storage with FP32

@@ -133,6 +133,7 @@ struct biofvm {
   size_t small_smem = 0;
   DevBuf small_bar;
   int pipe_chunk = 0;        // FP32 pipelined sweeps: chunk length (0: the planner's)
+  int pipe_cw = 0;           // FP32 pipelined sweeps: lines per tile, 32 or 16 (0: the planner's)
   DevBuf scratch;            // FP32 streaming: forward intermediate, field-sized
   int forced = 0;  // chunk lengths fixed by the caller (batched environments)
   unsigned generation = 0;  // bumped when kernel arguments change (sources, constants)
@@ -448,6 +449,7 @@ void plan_pipe(biofvm *h, int axis) {
   if (h->prec == BIOFVM_FP64) return;  // FP64 streams whole lines instead
   const bool h16 = esz == 2;  // 16-bit storage: chunk capacities 32 and 64 compiled
   for (int cw : {32, 16}) {
+    if (h->pipe_cw && cw != h->pipe_cw) continue;
     PipePlan q{};
     q.cw = cw;
     const int cpw = 32 / cw;
@@ -1359,6 +1361,7 @@ biofvm_status create_impl(const biofvm_grid *grid, double dx, double dt, const d
   // sweep selection and tuning knobs (environment, read once per handle)
   if (const char *env = getenv("BIOFVM_PIPELINE")) h->pipe_enabled = atoi(env) != 0;
   if (const char *env = getenv("BIOFVM_PIPE_CHUNK")) h->pipe_chunk = atoi(env);
+  if (const char *env = getenv("BIOFVM_PIPE_CW")) h->pipe_cw = atoi(env);
   if (const char *env = getenv("BIOFVM_STREAM")) h->stream_enabled = atoi(env) != 0;
   if (const char *env = getenv("BIOFVM_STREAM_CTAS")) h->stream_ctas_per_sm = atoi(env);
   if (const char *env = getenv("BIOFVM_STREAM32")) h->stream32_enabled = atoi(env) != 0;
