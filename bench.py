@@ -654,8 +654,10 @@ def run_paper_e2e_moving(prec, stream, dev, with_error):
     sim.sync()
     ms = e0.elapsed_time(e1)
     out = {"simulate_vs_per_s": w.n_vs * w.n_steps / (ms * 1e-3), "simulate_ms": ms,
-           "launches_per_step": "source-list rebuild (about 20 kernels for 1000 agents) + "
-                                f"{sim.launches_per_step()} sweep kernels",
+           "launches_per_step": "source-list rebuild (2 kernels up to 2048 agent entries, "
+                                "about 30 above) + "
+                                f"{sim.launches_per_step()} sweep kernels, plus the torch "
+                                "kernels that draw the moves",
            "agents": "random walk, one voxel per step along a random axis, drawn on the device"}
     if with_error:
         import oracle

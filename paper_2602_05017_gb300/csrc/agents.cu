@@ -21,6 +21,11 @@
 //      alpha and beta in entry order -- the host builder's order, so the two
 //      give the same bits;
 //   4. row offsets by a binary search per row.
+// Up to kSmallBuild entries (n agents x S substrates) take one CTA instead --
+// entries in shared memory, a bitonic sort of (element, entry index) pairs
+// (unique, so the order is the radix sort's), block scans, the same sums --
+// and one more launch for the row offsets: two launches instead of about
+// thirty, which at a thousand agents are mostly launch time.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -284,6 +289,130 @@ __global__ void count_to_i64_kernel(const uint32_t *__restrict__ c, int64_t *__r
   *out = (int64_t)*c;
 }
 
+// ---------------------------------------------------------------------------
+// One-CTA rebuild for up to kSmallBuild entries.
+// ---------------------------------------------------------------------------
+constexpr int kSmallBuild = 2048;  // entries: 32 KB of static shared memory
+constexpr int kSmallBuildThreads = 1024;
+
+// Entry of agent k, substrate s (i = k*S + s): its key, alpha, beta (the first
+// step of the multi-CTA path, one entry).
+__device__ __forceinline__ uint64_t entry_of(const AgentBuild &b, long long i, double &alpha,
+                                             double &beta) {
+  const long long k = i / b.S;
+  const int s = (int)(i - k * b.S);
+  alpha = beta = 0.0;
+  const int64_t v = b.voxel[k];
+  const double sv = b.secretion ? b.secretion[i] : 0.0;
+  const double uv = b.uptake ? b.uptake[i] : 0.0;
+  const double tv = b.target ? b.target[i] : 0.0;
+  const double w = b.weight ? b.weight[k] : 1.0;
+  const bool valid = v >= 0 && v < b.nvox && sv >= 0.0 && uv >= 0.0 && w >= 0.0 &&
+                     isfinite(sv) && isfinite(uv) && isfinite(tv) && isfinite(w);
+  if (!valid) {
+    atomicCAS(b.status, 0, kStatusBadInput);
+    return b.sentinel;
+  }
+  const double dtw = __dmul_rn(b.dt, w);
+  alpha = __dmul_rn(__dmul_rn(dtw, sv), tv);
+  beta = __dmul_rn(dtw, __dadd_rn(sv, uv));
+  const int64_t e = v * b.S + s;
+  if ((alpha != 0.0 || beta != 0.0) && !sorted_contains(b.node_elem, b.n_nodes, e))
+    return (uint64_t)e;
+  return b.sentinel;
+}
+
+template <typename E>
+__global__ void __launch_bounds__(kSmallBuildThreads) small_build_kernel(AgentBuild b) {
+  __shared__ uint64_t key[kSmallBuild];
+  __shared__ uint32_t idx[kSmallBuild];
+  __shared__ uint32_t pos[kSmallBuild];
+  __shared__ uint32_t warp_tot[32];
+  const int N = (int)b.n_entries_max;
+  int P = 1;
+  while (P < N) P <<= 1;
+  for (int i = threadIdx.x; i < P; i += blockDim.x) {
+    if (i < N) {
+      double al, be;
+      key[i] = entry_of(b, i, al, be);
+      b.ea[i] = al;
+      b.eb[i] = be;
+    } else {
+      key[i] = ~0ull;  // padding sorts last
+    }
+    idx[i] = (uint32_t)i;
+  }
+  __syncthreads();
+  // bitonic sort of (key, idx) -- distinct pairs, so the result is unique
+  for (int k = 2; k <= P; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        const int l = i ^ j;
+        if (l > i) {
+          const bool up = (i & k) == 0;
+          const bool gt = key[i] > key[l] || (key[i] == key[l] && idx[i] > idx[l]);
+          if (gt == up) {
+            const uint64_t tk = key[i];
+            key[i] = key[l];
+            key[l] = tk;
+            const uint32_t ti = idx[i];
+            idx[i] = idx[l];
+            idx[l] = ti;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  // run heads and their exclusive scan (four entries per thread, in order)
+  const int per = (P + blockDim.x - 1) / blockDim.x;
+  const int i0 = threadIdx.x * per;
+  uint32_t cnt = 0;
+  for (int i = i0; i < i0 + per && i < N; i++)
+    cnt += (key[i] != b.sentinel && (i == 0 || key[i - 1] != key[i])) ? 1u : 0u;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t x = cnt;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t y = __shfl_up_sync(kFull, x, d);
+    if (lane >= d) x += y;
+  }
+  if (lane == 31) warp_tot[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t t = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0u;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(kFull, t, d);
+      if (lane >= d) t += y;
+    }
+    warp_tot[lane] = t;
+  }
+  __syncthreads();
+  uint32_t run = (warp ? warp_tot[warp - 1] : 0u) + x - cnt;
+  for (int i = i0; i < i0 + per && i < N; i++) {
+    pos[i] = run;
+    run += (key[i] != b.sentinel && (i == 0 || key[i - 1] != key[i])) ? 1u : 0u;
+  }
+  if (threadIdx.x == 0) *b.count = (int64_t)warp_tot[(blockDim.x >> 5) - 1];
+  __syncthreads();
+  // one thread per run: sums in entry order
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    const uint64_t e = key[j];
+    if (e == b.sentinel || (j > 0 && key[j - 1] == e)) continue;
+    double a = 0.0, be = 0.0;
+    for (int t = j; t < N && key[t] == e; t++) {
+      const uint32_t q = idx[t];
+      a = t == j ? b.ea[q] : __dadd_rn(a, b.ea[q]);
+      be = t == j ? b.eb[q] : __dadd_rn(be, b.eb[q]);
+    }
+    const uint32_t o = pos[j];
+    b.src_elem[o] = (int64_t)e;
+    static_cast<E *>(b.src_alpha)[o] = (E)a;
+    static_cast<E *>(b.src_scale)[o] = (E)__ddiv_rn(1.0, __dadd_rn(1.0, be));
+    b.src_rowcol[o] = make_int2((int)((int64_t)e / b.rowlen), (int)((int64_t)e % b.rowlen));
+  }
+}
+
 }  // namespace
 
 int radix_passes(uint64_t sentinel) {
@@ -298,7 +427,12 @@ long long agent_scan_blocks(long long n) { return (n + kScanTile - 1) / kScanTil
 cudaError_t build_sources_device(AgentBuild b, bool fp64, cudaStream_t st) {
   const long long N = b.n_entries_max;
   const unsigned g256 = (unsigned)((N + 255) / 256);
-  if (N > 0) {
+  if (N > 0 && N <= kSmallBuild) {  // one CTA, then the row offsets
+    if (fp64)
+      small_build_kernel<double><<<1, kSmallBuildThreads, 0, st>>>(b);
+    else
+      small_build_kernel<float><<<1, kSmallBuildThreads, 0, st>>>(b);
+  } else if (N > 0) {
     agent_entries_kernel<<<g256, 256, 0, st>>>(b);
     const int nb = (int)agent_sort_blocks(N);
     const int passes = radix_passes(b.sentinel);
