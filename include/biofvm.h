@@ -243,8 +243,24 @@ biofvm_status biofvm_sync(biofvm_t *h);
 biofvm_status biofvm_density_ptr(biofvm_t *h, void **dev_ptr);
 
 /* Number of kernel launches one time step makes: 3 (x-, y-, z-sweep), plus 4
- * (one Dirichlet-node launch around each sweep) while Dirichlet nodes are set. */
+ * (one Dirichlet-node launch around each sweep) while Dirichlet nodes are set;
+ * 1 for the cooperative small-grid step.  A call on a row-padded copy (see
+ * biofvm_describe) adds two copy launches per call, not per step. */
 int biofvm_launches_per_step(const biofvm_t *h);
+
+/* Which kernels biofvm_step runs for this handle, as a NUL-terminated ASCII
+ * line written to the host buffer out[len]: "cooperative" (small FP64 grids:
+ * all steps of a call in one launch), or "x=K y=K z=K" with K one of stream
+ * (whole-line streaming sweep), pipe (TMA-pipelined tiles, followed by
+ * "/cwC/mM": C lines per tile, chunks of M positions) or plain (register-chunk
+ * kernels), then " scaled" when the FP64 steps carry the renormalisation
+ * factor, " pitched" when the steps run on a row-padded copy of the field (an
+ * FP32 field whose rows of nx*n_sub elements are not 16-byte multiples,
+ * copied in and back once per call), " nodes" while Dirichlet nodes are set.
+ * Diagnostic only; the text may change between versions.  Errors: ARG (NULL
+ * handle or buffer, or len too small for the line; out then holds a
+ * truncated line if len > 0). */
+biofvm_status biofvm_describe(const biofvm_t *h, char *out, size_t len);
 
 /* Measure the FMA issue rate of the current device in FP64 (prec =
  * BIOFVM_FP64) or FP32 (BIOFVM_FP32): the arithmetic roof of the Thomas

@@ -79,6 +79,7 @@ def load():
         "biofvm_sync": (st, [vp]),
         "biofvm_density_ptr": (st, [vp, ctypes.POINTER(vp)]),
         "biofvm_launches_per_step": (ctypes.c_int, [vp]),
+        "biofvm_describe": (st, [vp, ctypes.c_char_p, ctypes.c_size_t]),
         "biofvm_step_save": (st, [vp, vp]),
         "biofvm_adjoint_step": (st, [vp, vp, vp, vp, vp, vp, vp]),
         "biofvm_adjoint_step_rates": (st, [vp, vp, vp, vp, vp, vp, vp, vp]),
@@ -350,6 +351,12 @@ class BioFVM:
 
     def launches_per_step(self):
         return int(self.lib.biofvm_launches_per_step(self.h))
+
+    def describe(self):
+        """The kernels biofvm_step runs for this handle (biofvm_describe)."""
+        buf = ctypes.create_string_buffer(256)
+        _check(self.lib.biofvm_describe(self.h, buf, len(buf)), self.lib)
+        return buf.value.decode()
 
     def close(self):
         if getattr(self, "h", None):

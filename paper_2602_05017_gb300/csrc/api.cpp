@@ -121,6 +121,15 @@ struct biofvm {
   XPlan xp;
   ColPlan cp[3];  // [1] = y, [2] = z
   PipePlan pp[3];
+  // FP32 fields whose rows (nx*S elements) are not 16-byte multiples, which the TMA copies
+  // need: biofvm_step runs the pipelined sweeps on a row-padded working copy (rows gpitch
+  // elements apart, the padding zero), copied in at the start of the call and back at its
+  // end.  ppx: the plans over that copy; tabP / tabTP: their axis tables when a plan's chunk
+  // partition differs from the one the handle's own tables follow (tabP_own)
+  int pitched = 0, gpitch = 0, pitched_enabled = 1;
+  DevBuf prow, tabP[3], tabTP[3];
+  int tabP_own[3] = {0, 0, 0};
+  PipePlan ppx[3];
   StreamPlan sp[3];
   int num_sms = 0;
   int pipe_enabled = 1;
@@ -377,18 +386,19 @@ EncodeTiledFn encode_tiled() {
   return fn;
 }
 
-// Tensor map of axis 1/2 over `field` ([nplanes][n][C] elements, box 32 x
-// box_rows) into pp[axis].map[buf].
-bool encode_pipe_map(biofvm *h, int axis, int buf, void *field) {
-  PipePlan &p = h->pp[axis];
+// Tensor map of axis 1/2 over `field` with rows gp elements apart ([nplanes][n]
+// lines of C columns: y: C = nx*S columns of a row, rows gp apart; z: C = ny*gp
+// columns of a plane) into p.map[buf]; box cw x box_rows.
+bool encode_pipe_map(biofvm *h, PipePlan &p, int axis, int buf, void *field, int64_t gp) {
   EncodeTiledFn enc = encode_tiled();
   if (!enc) return false;
   const int64_t nx = h->g.nx, ny = h->g.ny, nz = h->g.nz, S = h->g.n_sub;
-  const int64_t C = axis == 1 ? nx * S : nx * ny * S;
+  const int64_t C = axis == 1 ? nx * S : ny * gp;
   const int64_t n = axis == 1 ? ny : nz, nplanes = axis == 1 ? nz : 1;
+  const int64_t lstride = axis == 1 ? gp : ny * gp;  // elements between positions of a line
   const size_t esz = h->esz;
   cuuint64_t dims[3] = {(cuuint64_t)C, (cuuint64_t)n, (cuuint64_t)nplanes};
-  cuuint64_t strides[2] = {(cuuint64_t)(C * esz), (cuuint64_t)(C * esz * n)};
+  cuuint64_t strides[2] = {(cuuint64_t)(lstride * esz), (cuuint64_t)(lstride * esz * n)};
   cuuint32_t box[3] = {(cuuint32_t)p.cw, (cuuint32_t)p.box_rows, 1};
   cuuint32_t estr[3] = {1, 1, 1};
   const CUtensorMapDataType dtype =
@@ -436,12 +446,12 @@ int x_tile_conflicts(int pitch, int S, int lanes, size_t esz) {
   return worst;
 }
 
-// Plan the pipelined sweep of axis 0 (x), 1 (y) or 2 (z); leaves pp.use = 0
-// when the plain kernels have to be used instead.  Tiles of 32 columns when a
-// ring of >= 2 stages of them fits in shared memory with the constants, else
-// tiles of 16 columns (long lines; two chunks per consumer warp).
-void plan_pipe(biofvm *h, int axis) {
-  PipePlan &p = h->pp[axis];
+// Plan the pipelined sweep of axis 0 (x), 1 (y) or 2 (z) over `field`, whose
+// rows (nx*S elements) start gp elements apart; leaves p.use = 0 when the plain
+// kernels have to be used instead.  Tiles of 32 columns when a ring of >= 2
+// stages of them fits in shared memory with the constants, else tiles of 16
+// columns (long lines; two chunks per consumer warp).
+void plan_pipe(biofvm *h, int axis, PipePlan &p, int64_t gp, void *field) {
   p = PipePlan{};
   const int64_t nx = h->g.nx, ny = h->g.ny, nz = h->g.nz, S = h->g.n_sub;
   const size_t esz = h->esz, csz = h->csz;
@@ -500,13 +510,13 @@ void plan_pipe(biofvm *h, int axis) {
     q.m = cp.m;
     q.maxm = cp.maxm;
     if (axis == 0) {
-      const int64_t rowlen = nx * S;
-      if ((rowlen * (int64_t)esz) % 16 != 0 || S > cw) continue;
+      if ((gp * (int64_t)esz) % 16 != 0 || S > cw) continue;
       q.rows_per_tile = (int)(cw / S);
-      const int align = (int)(16 / esz);  // pitch in elements keeps every row 16-byte aligned
+      // the staged rows: gp elements each (a 16-byte multiple), at a shared-memory pitch in
+      // elements that keeps every row 16-byte aligned
+      const int align = (int)(16 / esz);
       int best = 1 << 30;
-      for (int64_t pitch = (rowlen + align - 1) / align * align; pitch <= rowlen + 64;
-           pitch += align) {
+      for (int64_t pitch = gp; pitch <= gp + 64; pitch += align) {
         const int d = x_tile_conflicts((int)(pitch % 64), (int)S, q.rows_per_tile * (int)S, esz);
         if (d < best) {
           best = d;
@@ -517,11 +527,20 @@ void plan_pipe(biofvm *h, int axis) {
       if (ny * nz > (int64_t)0x7fffffff) return;  // the kernel tracks rows in 32 bits
       q.ntiles = (ny * nz + q.rows_per_tile - 1) / q.rows_per_tile;
     } else {
-      const int64_t C = axis == 1 ? nx * S : nx * ny * S;
+      const int64_t C = axis == 1 ? nx * S : ny * gp;
       const int nplanes = axis == 1 ? (int)nz : 1;
-      if ((C * (int64_t)esz) % 16 != 0 || C > (int64_t)0x7fffffff || nplanes > 65535) return;
+      // the map's stride between a line's positions must be a 16-byte multiple: y: the row
+      // pitch gp; z: the plane, C = ny * gp (the inner extent C of a y map need not be)
+      const int64_t lstride = axis == 1 ? gp : C;
+      if ((lstride * (int64_t)esz) % 16 != 0 || C > (int64_t)0x7fffffff || nplanes > 65535)
+        return;
+      // boxes of at most 256 rows; a tensor copy's shared-memory destination must be
+      // 128-byte aligned, so box_rows * cw * esz is rounded up to a 128-byte multiple (rows
+      // past the line's end are filled with zeros on load and skipped on store)
       q.nbox = (n + 255) / 256;
-      q.box_rows = (n + q.nbox - 1) / q.nbox;
+      const int rgran = std::max(1, (int)(128 / ((size_t)cw * esz)));
+      q.box_rows = ((n + q.nbox - 1) / q.nbox + rgran - 1) / rgran * rgran;
+      if (((size_t)q.box_rows * cw * esz) % 128 != 0 || q.box_rows > 256) continue;
       q.stage_elems = (int64_t)q.nbox * q.box_rows * cw;
       q.ntiles = (int64_t)nplanes * ((C + cw - 1) / cw);
       if (q.ntiles > (int64_t)0x7fffffff) return;  // tiles are indexed in 32 bits
@@ -542,7 +561,7 @@ void plan_pipe(biofvm *h, int axis) {
     p = PipePlan{};
     return;
   }
-  if (axis != 0 && !encode_pipe_map(h, axis, 0, h->rho.p)) {
+  if (axis != 0 && !encode_pipe_map(h, p, axis, 0, field, gp)) {
     p.use = 0;
     return;
   }
@@ -618,6 +637,37 @@ void plan_small(biofvm *h) {
   h->small_smem = smem;
   h->small_grid = std::min(h->num_sms * per_sm, std::max(nz, h->num_sms));
   h->small_use = 1;
+}
+
+// FP32 fields whose rows are not 16-byte multiples (the TMA copies' unit): a
+// row-padded working copy for biofvm_step (biofvm::pitched), when the three
+// pipelined sweeps can all run on it.
+void plan_pitched(biofvm *h) {
+  h->pitched = 0;
+  const int64_t rowlen = (int64_t)h->g.nx * h->g.n_sub;
+  if (h->prec != BIOFVM_FP32 || h->forced || !h->pipe_enabled || !h->pitched_enabled ||
+      h->stream32_enabled || (rowlen * (int64_t)h->esz) % 16 == 0)
+    return;
+  const int64_t align = 16 / (int64_t)h->esz;
+  const int64_t gp = (rowlen + align - 1) / align * align;
+  const size_t bytes = (size_t)h->g.ny * h->g.nz * gp * h->esz;
+  if (dev_alloc(h->prow, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  h->gpitch = (int)gp;
+  bool all = true;
+  for (int axis = 0; axis < 3; axis++) {
+    plan_pipe(h, axis, h->ppx[axis], gp, h->prow.p);
+    all = all && h->ppx[axis].use;
+  }
+  if (!all || cudaMemsetAsync(h->prow.p, 0, bytes, h->stream) != cudaSuccess) {
+    cudaGetLastError();
+    h->prow.release();
+    for (int axis = 0; axis < 3; axis++) h->ppx[axis] = PipePlan{};
+    return;
+  }
+  h->pitched = 1;
 }
 
 // ---------------------------------------------------------------------------
@@ -741,14 +791,25 @@ biofvm_status upload_constants(biofvm *h) {
     if (f32)
       stream_consts_f32(h, axis, t, &c32[(size_t)axis * 2 * h->g.n_sub], h->stream_k0[axis]);
     // the same inv, mul, pf, pb substrate-major [4][S][npad] for the pipelined kernel
-    const int n = axis_len(h, axis), S = h->g.n_sub, npad = pipe_npad_host(n);
-    std::vector<double> tt((size_t)4 * S * npad, 0.0);
-    for (int w = 0; w < 4; w++)
-      for (int i = 0; i < n; i++)
-        for (int s = 0; s < S; s++)
-          tt[((size_t)w * S + s) * npad + i] = t[(size_t)w * n * S + (size_t)i * S + s];
-    st = upload_doubles(h, h->tabT[axis], tt);
-    if (st) return st;
+    auto upload_T = [&](DevBuf &dst) {
+      const int n = axis_len(h, axis), S = h->g.n_sub, npad = pipe_npad_host(n);
+      std::vector<double> tt((size_t)4 * S * npad, 0.0);
+      for (int w = 0; w < 4; w++)
+        for (int i = 0; i < n; i++)
+          for (int s = 0; s < S; s++)
+            tt[((size_t)w * S + s) * npad + i] = t[(size_t)w * n * S + (size_t)i * S + s];
+      return upload_doubles(h, dst, tt);
+    };
+    if ((st = upload_T(h->tabT[axis])) != BIOFVM_OK) return st;
+    // the row-padded working copy's plans: tables of their own partition where it differs
+    const PipePlan &q = h->ppx[axis];
+    h->tabP_own[axis] = h->pitched && (q.T != T || q.m != m);
+    if (h->tabP_own[axis]) {
+      axis_tables(h, axis, q.T, q.m, f32, t);
+      if ((st = upload_doubles(h, h->tabP[axis], t)) != BIOFVM_OK ||
+          (st = upload_T(h->tabTP[axis])) != BIOFVM_OK)
+        return st;
+    }
   }
   if (h->prec != BIOFVM_FP64) {
     biofvm_status st = upload_doubles(h, h->stream_const_d, c32);
@@ -844,9 +905,11 @@ SrcLists src_lists(const biofvm *h) {
   return l;
 }
 
-AxisTab axis_tab(const biofvm *h, int axis) {
+// The tables of an axis (layout of axis_tables, chunk partition T x m) as kernel arguments.
+AxisTab axis_tab_of(const biofvm *h, int axis, const DevBuf &tab, const DevBuf &tabT, int T,
+                    int m) {
   const int n = axis_len(h, axis), S = h->g.n_sub;
-  const char *base = static_cast<const char *>(h->tab[axis].p);
+  const char *base = static_cast<const char *>(tab.p);
   const size_t blk = (size_t)n * S * h->csz;
   AxisTab t;
   t.inv = base;
@@ -854,24 +917,30 @@ AxisTab axis_tab(const biofvm *h, int axis) {
   t.pf = base + 2 * blk;
   t.pb = base + 3 * blk;
   t.pc = base + 4 * blk;
-  int T, m;
-  axis_partition(h, axis, T, m);
   t.cfix = base + 4 * blk + (size_t)T * S * h->csz;
   t.cw = base + 4 * blk + ((size_t)T * S + 2 * (size_t)S) * h->csz;
-  t.tabT = h->tabT[axis].p;
+  t.tabT = tabT.p;
   t.n = n;
   t.T = T;
   t.m = m;
   return t;
 }
 
+AxisTab axis_tab(const biofvm *h, int axis) {
+  int T, m;
+  axis_partition(h, axis, T, m);
+  return axis_tab_of(h, axis, h->tab[axis], h->tabT[axis], T, m);
+}
+
 // ---------------------------------------------------------------------------
 // Kernel launches.
 // ---------------------------------------------------------------------------
-// Launch the pipelined sweep of `axis` on `field` (buf selects the y/z tensor map).
+// Launch the pipelined sweep of `axis` on `field` (buf selects the y/z tensor map).  The
+// row-padded working copy (`pitched`): the plans ppx over it, rows gpitch elements apart.
 cudaError_t launch_pipe(const biofvm *h, int axis, int flags, cudaStream_t st, void *field,
-                        int buf) {
-  const PipePlan &p = h->pp[axis];
+                        int buf, bool pitched = false) {
+  const PipePlan &p = pitched ? h->ppx[axis] : h->pp[axis];
+  const int gp = pitched ? h->gpitch : h->g.nx * h->g.n_sub;
   PipeArgs b{};
   b.mode = axis;
   b.n = axis_len(h, axis);
@@ -880,7 +949,7 @@ cudaError_t launch_pipe(const biofvm *h, int axis, int flags, cudaStream_t st, v
   b.ny = h->g.ny;
   b.nz = h->g.nz;
   b.ntiles = p.ntiles;
-  b.C = axis == 1 ? (int64_t)h->g.nx * h->g.n_sub : (int64_t)h->g.nx * h->g.ny * h->g.n_sub;
+  b.C = axis == 1 ? (int64_t)h->g.nx * h->g.n_sub : (int64_t)h->g.ny * gp;
   b.cw = p.cw;
   b.tiles_per_plane = (int)((b.C + p.cw - 1) / p.cw);
   b.nplanes = axis == 1 ? h->g.nz : 1;
@@ -889,11 +958,14 @@ cudaError_t launch_pipe(const biofvm *h, int axis, int flags, cudaStream_t st, v
   b.rows_per_tile = p.rows_per_tile;
   b.rowlen = h->g.nx * h->g.n_sub;
   b.pitch = p.pitch;
+  b.gpitch = gp;
   b.nrows = (int64_t)h->g.ny * h->g.nz;
   b.field = field;
   b.stages = p.stages;
   b.stage_elems = p.stage_elems;
-  b.tab = axis_tab(h, axis);
+  b.tab = pitched && h->tabP_own[axis]
+              ? axis_tab_of(h, axis, h->tabP[axis], h->tabTP[axis], p.T, p.m)
+              : axis_tab(h, axis);
   b.tab.T = p.T;
   b.tab.m = p.m;
   b.flags = flags;
@@ -1078,7 +1150,16 @@ cudaError_t launch_nodes(const biofvm *h, cudaStream_t st, int m, int row, bool 
 // x-sweep stands for the node part of the application between Src and X^-1
 // (the source list holds no node element, and the fused face application
 // skips every substrate with a node on its faces, so the order holds).
-biofvm_status launch_step(const biofvm *h, cudaStream_t st, int m = 0, bool renorm = true) {
+// `pitched`: the three pipelined sweeps on the row-padded working copy (no
+// Dirichlet nodes then).
+biofvm_status launch_step(const biofvm *h, cudaStream_t st, int m = 0, bool renorm = true,
+                          bool pitched = false) {
+  if (pitched) {
+    CK(launch_pipe(h, 0, kSrc | kDirBefore | kSolve | kDirAfter, st, h->prow.p, 0, true));
+    CK(launch_pipe(h, 1, kSolve | kDirAfter, st, h->prow.p, 0, true));
+    CK(launch_pipe(h, 2, kSolve | kDirAfter, st, h->prow.p, 0, true));
+    return BIOFVM_OK;
+  }
   const int sc = step_scaled(h);
   const int mf = sc ? (m << 8) : 0;
   CK(launch_nodes(h, st, m, sc ? 0 : -1));
@@ -1203,7 +1284,8 @@ void destroy_impl(biofvm *h) {
                     &h->dsrc_rowcol, &h->dsrc_alpha, &h->dsrc_scale, &h->dsrc_count,
                     &h->ag_key[0], &h->ag_key[1], &h->ag_idx[0], &h->ag_idx[1], &h->ag_ea,
                     &h->ag_eb, &h->ag_head, &h->ag_pos, &h->ag_hist, &h->ag_part,
-                    &h->ag_count32, &h->small_bar})
+                    &h->ag_count32, &h->small_bar, &h->prow, &h->tabP[0], &h->tabP[1],
+                    &h->tabP[2], &h->tabTP[0], &h->tabTP[1], &h->tabTP[2]})
     b->release();
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   delete h;
@@ -1367,7 +1449,8 @@ biofvm_status create_impl(const biofvm_grid *grid, double dx, double dt, const d
   if (const char *env = getenv("BIOFVM_STREAM32")) h->stream32_enabled = atoi(env) != 0;
   if (const char *env = getenv("BIOFVM_STREAM_KS")) h->stream_ks = atoi(env) / 16 * 16;
   if (h->pipe_enabled && !h->forced)
-    for (int axis = 0; axis < 3; axis++) plan_pipe(h, axis);
+    for (int axis = 0; axis < 3; axis++)
+      plan_pipe(h, axis, h->pp[axis], (int64_t)g.nx * g.n_sub, h->rho.p);
   if (!h->forced)
     for (int axis = 0; axis < 3; axis++) plan_stream(h, axis);
   if (h->xp.nosolve && !h->sp[0].use && !h->pp[0].use) {
@@ -1389,6 +1472,8 @@ biofvm_status create_impl(const biofvm_grid *grid, double dx, double dt, const d
   }
   if (const char *env = getenv("BIOFVM_SMALL")) h->small_enabled = atoi(env) != 0;
   plan_small(h);
+  if (const char *env = getenv("BIOFVM_PITCHED")) h->pitched_enabled = atoi(env) != 0;
+  plan_pitched(h);
   if ((st = upload_doubles(h, h->dir_val_d, h->dir_val)) != BIOFVM_OK ||
       (st = upload_constants(h)) != BIOFVM_OK) {
     std::string msg = g_last_error;
@@ -1440,6 +1525,37 @@ int biofvm_launches_per_step(const biofvm_t *h) {
   if (!h) return 0;
   if (h->small_use && h->n_dnode == 0) return 1;  // one launch runs every step of a call
   return 3 + (h->n_dnode > 0 ? 4 : 0);             // the sweeps (+ the Dirichlet nodes)
+}
+
+biofvm_status biofvm_describe(const biofvm_t *h, char *out, size_t len) {
+  if (!h || !out) return fail(BIOFVM_ERR_ARG, "NULL handle or buffer");
+  std::string d;
+  if (h->small_use && h->n_dnode == 0) {
+    d = "cooperative";
+  } else {
+    const bool pitched = h->pitched && h->n_dnode == 0;
+    const char *names[3] = {"x=", " y=", " z="};
+    for (int axis = 0; axis < 3; axis++) {
+      d += names[axis];
+      const bool stream = !pitched && h->sp[axis].use;
+      const PipePlan &p = pitched ? h->ppx[axis] : h->pp[axis];
+      if (stream) {
+        d += "stream";
+      } else if (p.use) {
+        char b[48];
+        snprintf(b, sizeof b, "pipe/cw%d/m%d", p.cw, p.m);
+        d += b;
+      } else {
+        d += "plain";
+      }
+    }
+    if (step_scaled(h)) d += " scaled";
+    if (pitched) d += " pitched";
+    if (h->n_dnode > 0) d += " nodes";
+  }
+  if (len > 0) snprintf(out, len, "%s", d.c_str());
+  if (d.size() + 1 > len) return fail(BIOFVM_ERR_ARG, "buffer of %zu bytes too small", len);
+  return BIOFVM_OK;
 }
 
 biofvm_status biofvm_set_params(biofvm_t *h, const double *D, const double *lambda) {
@@ -1742,14 +1858,21 @@ biofvm_status biofvm_step(biofvm_t *h, int n_steps) {
     return BIOFVM_OK;
   }
   // graphs of K steps (a renormalisation block) and of a shorter tail, each
-  // ending with the true field; K = 1 unless the FP64 streaming step applies
+  // ending with the true field; K = 1 unless the FP64 streaming step applies.
+  // A field with unaligned rows: the steps run on the row-padded copy (the
+  // graphs are dropped whenever nodes are set, so they never mix the two forms)
   const int K = step_scaled(h) ? h->renorm_k : 1;
+  const bool pitched = h->pitched && h->n_dnode == 0;
+  const int64_t rows = (int64_t)h->g.ny * h->g.nz;
+  const int rowlen = h->g.nx * h->g.n_sub;
+  const int cgrid = (int)std::max<int64_t>(1, std::min<int64_t>((rows + 7) / 8, 8 * h->num_sms));
   auto ensure = [&](int r) -> biofvm_status {  // graph slot 0: K steps; slot r: r < K steps
     const int slot = r == K ? 0 : r;
     if (h->gexec[slot]) return BIOFVM_OK;
     CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
     biofvm_status st = BIOFVM_OK;
-    for (int m = 0; m < r && st == BIOFVM_OK; m++) st = launch_step(h, h->cap_stream, m, m == r - 1);
+    for (int m = 0; m < r && st == BIOFVM_OK; m++)
+      st = launch_step(h, h->cap_stream, m, m == r - 1, pitched);
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(h->cap_stream, &graph);
     if (st != BIOFVM_OK) {
@@ -1770,8 +1893,14 @@ biofvm_status biofvm_step(biofvm_t *h, int n_steps) {
   biofvm_status st;
   if (blocks > 0 && (st = ensure(K)) != BIOFVM_OK) return st;
   if (tail > 0 && (st = ensure(tail)) != BIOFVM_OK) return st;
+  if (pitched)
+    CK(launch_pitch_rows(h->rho.p, h->prow.p, rows, rowlen, rowlen, h->gpitch, h->esz, cgrid,
+                         h->stream));
   for (int b = 0; b < blocks; b++) CK(cudaGraphLaunch(h->gexec[0], h->stream));
   if (tail > 0) CK(cudaGraphLaunch(h->gexec[tail], h->stream));
+  if (pitched)
+    CK(launch_pitch_rows(h->prow.p, h->rho.p, rows, rowlen, h->gpitch, rowlen, h->esz, cgrid,
+                         h->stream));
   return BIOFVM_OK;
 }
 
@@ -1872,7 +2001,8 @@ biofvm_status biofvm_adjoint_step_rates(biofvm_t *h, const void *grad_out, void 
     if (dev_alloc(h->adj, bytes) != cudaSuccess)
       return fail(BIOFVM_ERR_OOM, "device allocation of the adjoint field failed");
     for (int axis = 1; axis <= 2; axis++)
-      if (h->pp[axis].use) encode_pipe_map(h, axis, 1, h->adj.p);  // x tiles need no map
+      if (h->pp[axis].use)  // x tiles need no map
+        encode_pipe_map(h, h->pp[axis], axis, 1, h->adj.p, (int64_t)h->g.nx * h->g.n_sub);
   }
   if (!h->partial.p) {
     h->reduce_blocks = 4 * h->num_sms;

@@ -230,6 +230,11 @@ cudaError_t launch_pipe_bf16(const CUtensorMap &map, const PipeArgs &a, int maxm
                              size_t smem, cudaStream_t st);
 cudaError_t launch_pipe_fp16(const CUtensorMap &map, const PipeArgs &a, int maxm, int grid,
                              size_t smem, cudaStream_t st);
+// Copy `rows` rows of `len` elements of esz (4 or 2) bytes from rows spitch
+// elements apart into rows dpitch elements apart (the row-padded working copy
+// of a field whose rows are not 16-byte multiples).
+cudaError_t launch_pitch_rows(const void *src, void *dst, int64_t rows, int len, int spitch,
+                              int dpitch, size_t esz, int grid, cudaStream_t st);
 // Largest CTA the FP32 pipelined sweep with chunk capacity maxm may use.
 int pipe_max_threads_f32(int maxm);
 // Substrate-major constants of the pipelined sweep (elements): [4][S][npad].

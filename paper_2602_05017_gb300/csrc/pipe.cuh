@@ -7,11 +7,12 @@
 // stages of 32 columns do not fit in shared memory, tiles of CW = 16 columns,
 // and each consumer warp then solves two chunks, one per half-warp:
 //
-//   warp 0, lane 0 (producer): TMA loads of tile k+NS-1 (cp.async.bulk.tensor
-//     boxes for y/z tiles, one cp.async.bulk per row for x tiles) completing
-//     on mbarrier `full`; once the consumers have written tile k back into its
-//     stage (mbarrier `done`), the bulk store of that tile; the stage is
-//     reloaded after the store has finished reading it;
+//   warp 0 (producer): TMA loads of tile k+NS-1 (cp.async.bulk.tensor boxes
+//     for y/z tiles, issued by lane 0; one cp.async.bulk per row for x tiles,
+//     the rows spread over the 32 lanes) completing on mbarrier `full`; once
+//     the consumers have written tile k back into its stage (mbarrier `done`),
+//     the bulk store of that tile; the stage is reloaded after the store has
+//     finished reading it;
 //   warps 1..ceil(T*CW/32) (consumers): chunk t of every column of the staged
 //     tile, in registers (thread (warp w, lane l): chunk (w-1)*32/CW + l/CW of
 //     column l % CW).  Halos and chunk carries cross warps through shared memory
@@ -277,7 +278,13 @@ __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
   const E *g_cfix = static_cast<const E *>(a.tab.cfix);
 
   if (warp == 0) {  // ------------------------------------------------ producer
-    if (lane != 0) return;
+    // x tiles: up to 32 rows per tile, one bulk copy each, issued by the lanes
+    // in parallel (one thread issuing them in turn bounds the short-row tiles);
+    // y/z tiles: one or two tensor boxes, lane 0 alone.  Each lane waits for
+    // the stage itself (its own acquire of the consumers' writes) and for its
+    // own stores; the lanes agree on the outcome of every bounded wait.
+    constexpr unsigned pmask = MODE == 0 ? 0xffffffffu : 1u;
+    if (MODE != 0 && lane != 0) return;
     auto rows_of = [&](long long tile) {
       const long long r0 = tile * a.rows_per_tile;
       return (int)min((long long)a.rows_per_tile, a.nrows - r0);
@@ -287,10 +294,13 @@ __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
       H *dst = stage0 + s * stage_elems;
       if constexpr (MODE == 0) {
         const int rows = rows_of(tile);
-        const uint32_t rb = (uint32_t)(a.rowlen * sizeof(H));
-        mbar_arrive_expect_tx(&full[s], rb * rows);
-        for (int r = 0; r < rows; r++)
-          bulk_g2s(dst + (size_t)r * a.pitch, field + (tile * a.rows_per_tile + r) * a.rowlen, rb,
+        const uint32_t rb = (uint32_t)(a.gpitch * sizeof(H));
+        // the expected bytes before any copy is issued: the phase cannot
+        // complete while the producer's own arrival is pending
+        if (lane == 0) mbar_arrive_expect_tx(&full[s], rb * rows);
+        __syncwarp();
+        for (int r = lane; r < rows; r += 32)
+          bulk_g2s(dst + (size_t)r * a.pitch, field + (tile * a.rows_per_tile + r) * a.gpitch, rb,
                    &full[s]);
       } else {
         const int plane = (int)((uint32_t)tile / (uint32_t)a.tiles_per_plane);
@@ -305,9 +315,9 @@ __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
       const H *src = stage0 + s * stage_elems;
       if constexpr (MODE == 0) {
         const int rows = rows_of(tile);
-        const uint32_t rb = (uint32_t)(a.rowlen * sizeof(H));
-        for (int r = 0; r < rows; r++)
-          bulk_s2g(field + (tile * a.rows_per_tile + r) * a.rowlen, src + (size_t)r * a.pitch, rb);
+        const uint32_t rb = (uint32_t)(a.gpitch * sizeof(H));
+        for (int r = lane; r < rows; r += 32)
+          bulk_s2g(field + (tile * a.rows_per_tile + r) * a.gpitch, src + (size_t)r * a.pitch, rb);
       } else {
         const int plane = (int)((uint32_t)tile / (uint32_t)a.tiles_per_plane);
         const int c0 = (int)((uint32_t)tile % (uint32_t)a.tiles_per_plane) * CW;
@@ -322,14 +332,19 @@ __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
     bool ok = true;
     for (; k < count; k++) {
       const int s = (int)(k % NS);
-      if (!(ok = mbar_wait_bounded(&done[s], (uint32_t)((k / NS) & 1), a.status))) break;
+      ok = mbar_wait_bounded(&done[s], (uint32_t)((k / NS) & 1), a.status);
+      if (!__all_sync(pmask, ok)) {
+        ok = false;
+        break;
+      }
       issue_store(k, s);
       if (k + NS < count) {
-        bulk_wait_read_all();  // the stage is free once the store has read it
+        bulk_wait_read_all();  // the stage is free once every lane's store has read it
+        __syncwarp(pmask);
         issue_load(k + NS, s);
       }
     }
-    if (!ok) {  // drain the loads still in flight (bounded) before exiting
+    if (!ok && lane == 0) {  // drain the loads still in flight (bounded) before exiting
       for (long long j = k; j < count && j < k + NS; j++)
         mbar_wait_bounded(&full[j % NS], (uint32_t)((j / NS) & 1), a.status);
     }
@@ -462,16 +477,20 @@ __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
       const int plane = (int)((uint32_t)tile / (uint32_t)a.tiles_per_plane);
       const uint32_t cg = ((uint32_t)tile - (uint32_t)plane * (uint32_t)a.tiles_per_plane) *
                               (uint32_t)CW + (uint32_t)c;
-      active = cg < (uint32_t)a.C;
-      s = (int)(cg % (uint32_t)S);
-      if (dir_after) {
-        if (a.mode == 1) {
+      if (a.mode == 1) {
+        active = cg < (uint32_t)a.C;
+        s = (int)(cg % (uint32_t)S);
+        if (dir_after) {
           const int x0 = (int)(cg / (uint32_t)S);
           face = (x0 == 0 || x0 == a.nx - 1 || plane == 0 || plane == a.nz - 1);
-        } else {
-          const uint32_t vox = cg / (uint32_t)S;
-          const int x0 = (int)(vox % (uint32_t)a.nx), y = (int)(vox / (uint32_t)a.nx);
-          face = (x0 == 0 || x0 == a.nx - 1 || y == 0 || y == a.ny - 1);
+        }
+      } else {  // a plane of ny rows gpitch apart: padding columns are not lines
+        const uint32_t y = cg / (uint32_t)a.gpitch, xs = cg - y * (uint32_t)a.gpitch;
+        active = cg < (uint32_t)a.C && xs < (uint32_t)a.rowlen;
+        s = (int)(xs % (uint32_t)S);
+        if (dir_after) {
+          const int x0 = (int)(xs / (uint32_t)S);
+          face = (x0 == 0 || x0 == a.nx - 1 || y == 0 || (int)y == a.ny - 1);
         }
       }
     }

@@ -9,14 +9,20 @@ namespace bfv {
 // A tile is cw "columns" (independent lines) x n positions along the axis,
 // cw = 32, or 16 for lines too long for two stages of 32 columns.
 //
+// The field's rows (fixed y, z: rowlen = nx*S elements) start gpitch elements
+// apart in global memory: gpitch = rowlen, or rowlen rounded up to 16 bytes for
+// a row-padded copy of a field whose rows are not 16-byte multiples (TMA copies
+// need 16-byte aligned rows); the padding elements are carried along untouched.
+//
 //   mode 0 (x-sweep): a column is one (row, substrate) pair of
-//     rows_per_tile = floor(cw/S) consecutive rows (y, z); the rows are
-//     staged with one cp.async.bulk each into shared memory at a padded
-//     `pitch` (elements) chosen on the host so that the lanes of a warp
-//     hit different banks; element (column c, position x) sits at
-//     (c/S)*pitch + x*S + c%S.
-//   mode 1 / 2 (y- / z-sweep): a column is one of cw consecutive (x, s) or
-//     (x, y, s) entries of a plane; the tile [n][cw] is staged with
+//     rows_per_tile = floor(cw/S) consecutive rows (y, z); the rows (gpitch
+//     elements each) are staged with one cp.async.bulk each, issued by the
+//     lanes of the producer warp, into shared memory at a padded `pitch`
+//     (elements) chosen on the host so that the lanes of a warp hit different
+//     banks; element (column c, position x) sits at (c/S)*pitch + x*S + c%S.
+//   mode 1 / 2 (y- / z-sweep): a column is one of cw consecutive (x, s)
+//     entries of a row (mode 1) or entries of a plane, C = ny*gpitch
+//     including any padding (mode 2); the tile [n][cw] is staged with
 //     cp.async.bulk.tensor boxes of box_rows x cw; element (c, j) sits at
 //     j*cw + c.
 //
@@ -30,6 +36,7 @@ struct PipeArgs {
   int tiles_per_plane, nplanes, box_rows, nbox;
   // mode 0
   int rows_per_tile, rowlen, pitch;
+  int gpitch;  // elements between consecutive rows of the field (rowlen, or padded)
   int64_t nrows;
   void *field;
   // ring of stages

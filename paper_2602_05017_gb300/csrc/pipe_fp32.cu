@@ -34,6 +34,41 @@ cudaError_t launch_pipe_f32(const CUtensorMap &map, const PipeArgs &a, int maxm,
   return cudaErrorInvalidValue;
 }
 
+namespace {
+// Rows of `len` elements from a field with rows `spitch` apart into one with
+// rows `dpitch` apart: one warp per row, lanes along the row (coalesced);
+// T is a 4- or 2-byte element (the copy moves bits, no arithmetic).
+template <typename T>
+__global__ void __launch_bounds__(256) pitch_rows_kernel(const T *__restrict__ src,
+                                                         T *__restrict__ dst, int64_t rows,
+                                                         int len, int spitch, int dpitch) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < rows;
+       r += warps) {
+    const T *s = src + r * spitch;
+    T *d = dst + r * dpitch;
+    for (int i = lane; i < len; i += 32) d[i] = s[i];
+  }
+}
+}  // namespace
+
+cudaError_t launch_pitch_rows(const void *src, void *dst, int64_t rows, int len, int spitch,
+                              int dpitch, size_t esz, int grid, cudaStream_t st) {
+  if (rows <= 0 || len <= 0) return cudaSuccess;
+  if (esz == 4)
+    pitch_rows_kernel<uint32_t><<<grid, 256, 0, st>>>(static_cast<const uint32_t *>(src),
+                                                     static_cast<uint32_t *>(dst), rows, len,
+                                                     spitch, dpitch);
+  else if (esz == 2)
+    pitch_rows_kernel<uint16_t><<<grid, 256, 0, st>>>(static_cast<const uint16_t *>(src),
+                                                     static_cast<uint16_t *>(dst), rows, len,
+                                                     spitch, dpitch);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
 int pipe_max_threads_f32(int maxm) {  // mirrors PipeBound<float, maxm>
   const int regs = maxm * 4 / 4 + 96;
   const int raw = 65536 / regs;

@@ -87,15 +87,20 @@ def test_one_voxel_holding_many_agents(binding, prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_agents_moving_every_step_match_the_oracle(binding, prec):
+@pytest.mark.parametrize("shape", [(30, 26, 22, 2), (31, 26, 22, 2)],
+                         ids=["rows-aligned", "rows-unaligned"])
+def test_agents_moving_every_step_match_the_oracle(binding, prec, shape):
     """A random walk of 300 agents (one voxel along a random axis per step, clamped to the
     box), 12 steps, Dirichlet faces: each step's agent list goes to the oracle and, as device
-    arrays, to the library before that step."""
-    nx, ny, nz, ns = 30, 26, 22, 2
+    arrays, to the library before that step.  31 x 2 floats per row is no 16-byte multiple:
+    the FP32 steps then run on the row-padded copy."""
+    nx, ny, nz, ns = shape
     rng = np.random.default_rng(21)
     w = inputs.random_problem(rng, nx, ny, nz, ns, dirichlet=True)
     voxel, sec, tgt, upt, wt = agents_with_collisions(rng, nx * ny * nz, ns, 300)
     sim = binding.BioFVM.from_workload(w, precision=prec)
+    if prec == "fp32":
+        assert ("pitched" in sim.describe()) == (nx * ns * 4 % 16 != 0), sim.describe()
     sim.reserve_agents(300)
     ref = w.rho0.copy()
     x, y, z = voxel % nx, (voxel // nx) % ny, voxel // (nx * ny)

@@ -479,3 +479,48 @@ def test_sweep_paths_match_oracle(binding, monkeypatch, shape, path, prec):
             pytest.skip(f"plain kernels cannot hold these lines: {e}")
         raise
     assert rel_err(got, ref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("shape", [(37, 23, 19, 3), (250, 20, 16, 1), (9, 130, 11, 2),
+                                   (31, 17, 9, 3), (101, 5, 300, 1), (3, 4, 5, 1)],
+                         ids=lambda s: "x".join(map(str, s)))
+def test_unaligned_rows_run_pitched_and_match_oracle(binding, monkeypatch, shape):
+    """FP32 fields whose rows (nx * n_sub floats) are no 16-byte multiple: biofvm_step runs the
+    pipelined sweeps on a row-padded copy of the field.  Against the oracle (sources, Dirichlet
+    faces) over calls of 1 and 2 steps, and against the same problem without the padded copy
+    (BIOFVM_PITCHED=0: the plain kernels along x and y)."""
+    nx, ny, nz, ns = shape
+    rng = np.random.default_rng(nx + 7 * ns)
+    w = inputs.random_problem(rng, nx, ny, nz, ns, n_agents=150, dirichlet=True)
+    ref = orc(w).step(w.rho0, 3)
+    outs = []
+    for pitched in ("1", "0"):
+        monkeypatch.setenv("BIOFVM_PITCHED", pitched)
+        sim = binding.BioFVM.from_workload(w, precision="fp32")
+        d = sim.describe()
+        assert ("pitched" in d) == (pitched == "1"), d
+        sim.step(1)
+        sim.step(2)
+        outs.append(sim.density().astype(np.float64))
+        sim.close()
+        assert rel_err(outs[-1], ref) <= 1e-5, (pitched, d)
+    assert rel_err(outs[0], outs[1]) <= 1e-5
+
+
+def test_describe_names_the_step_kernels(binding, monkeypatch):
+    rng = np.random.default_rng(5)
+    w = inputs.random_problem(rng, 40, 36, 28, 4, n_agents=50)
+    sim = binding.BioFVM.from_workload(w, precision="fp32")
+    assert sim.describe().startswith("x=pipe/cw32/m") and "pitched" not in sim.describe()
+    sim.close()
+    monkeypatch.setenv("BIOFVM_SMALL", "0")
+    sim = binding.BioFVM.from_workload(w, precision="fp64")
+    assert sim.describe() == "x=stream y=stream z=stream scaled"
+    sim.set_dirichlet_nodes([5], [1], [2.0])
+    assert sim.describe().endswith(" nodes")
+    sim.close()
+    monkeypatch.setenv("BIOFVM_SMALL", "1")
+    small = inputs.workload(1)
+    sim = binding.BioFVM.from_workload(small, precision="fp64")
+    assert sim.describe() == "cooperative"
+    sim.close()
