@@ -136,6 +136,9 @@ struct biofvm {
   int stream_enabled = 1;
   int stream_ctas_per_sm = 3;
   int stream_ks = 64;        // FP64: positions of each line's intermediate kept in shared memory
+  // FP64 x-sweep at S = 1, 2 (BIOFVM_STREAM_XT=4: also 4): coalesced rows through per-warp
+  // transpose buffers, with slabs of stream_ks_xt positions
+  int stream_xt = 2, stream_ks_xt = 32;
   int stream32_enabled = 0;  // FP32 streaming sweeps instead of the pipelined ones
   // small FP64 grids: whole biofvm_step calls in one cooperative launch (small.cu)
   int small_enabled = 1, small_use = 0, small_grid = 0;
@@ -1015,6 +1018,8 @@ cudaError_t launch_stream(const biofvm *h, int axis, int flags, cudaStream_t st,
   a.cfix = fp64 ? nullptr : axis_tab(h, axis).cfix;
   a.scratch = h->scratch.p;
   a.ks = std::max(0, std::min(h->stream_ks, 208));  // 4 warps x ks x 256 B <= 208 KB
+  a.xt = (fp64 && axis == 0 && (S == 1 || S == 2 || S == 4) && S <= h->stream_xt) ? (int)S : 0;
+  if (a.xt) a.ks = std::max(0, std::min(h->stream_ks_xt, 192));  // + 4 x 4.25 KB buffers
   a.flags = flags;
   if (!h->any_dir) a.flags &= ~(kDirBefore | kDirAfter);
   const bool scaled = fp64 && (flags & kScaled);
@@ -1448,6 +1453,8 @@ biofvm_status create_impl(const biofvm_grid *grid, double dx, double dt, const d
   if (const char *env = getenv("BIOFVM_STREAM_CTAS")) h->stream_ctas_per_sm = atoi(env);
   if (const char *env = getenv("BIOFVM_STREAM32")) h->stream32_enabled = atoi(env) != 0;
   if (const char *env = getenv("BIOFVM_STREAM_KS")) h->stream_ks = atoi(env) / 16 * 16;
+  if (const char *env = getenv("BIOFVM_STREAM_XT")) h->stream_xt = atoi(env);
+  if (const char *env = getenv("BIOFVM_STREAM_KS_XT")) h->stream_ks_xt = atoi(env) / 16 * 16;
   if (h->pipe_enabled && !h->forced)
     for (int axis = 0; axis < 3; axis++)
       plan_pipe(h, axis, h->pp[axis], (int64_t)g.nx * g.n_sub, h->rho.p);

@@ -106,6 +106,7 @@ struct StreamArgs {
   const void *cfix;       // FP32 [2][S] c_hi, c_lo (defect form)
   void *scratch;          // FP32: field-sized scratch for the forward intermediate
   int ks;                 // FP64: positions whose intermediate stays in shared memory
+  int xt;                 // FP64 x-sweep at S = 1, 2, 4: S (coalesced rows), else 0
   int flags;
   const int64_t *src_row_off, *src_elem;
   const void *src_alpha, *src_scale;

@@ -250,6 +250,178 @@ __device__ __forceinline__ void solve_lines_f64(double *line, int n, long long s
   }
 }
 
+// x-sweep at a substrate count XS of 1, 2 or 4 (compile time), FP64: the same
+// solve as solve_lines_f64 (lane = (row, substrate), 32/XS rows per warp), but
+// the warp's global loads and stores are contiguous row segments.  Lanes owning
+// rows would make every load instruction touch 32/XS rows (32 cache lines at
+// XS = 1); here a block of R positions of the warp's rows is read as R*XS
+// consecutive elements per row ("flat": element j*32 + lane of the block is
+// row f / (R*XS), offset f % (R*XS)) and transposed through the warp's buffer
+// tb ([32][R+1] doubles: lane, block index) to one line per lane, and the
+// results go the opposite way.  The intermediate of positions below KS stays in
+// the lane's shared-memory slab hsm as in solve_lines_f64.
+//   wbase: the warp's first row (position 0); nrows_w: its rows in the grid.
+template <int OUT, int XS, int R = kStreamR>
+__device__ __forceinline__ void solve_rows_f64(double *wbase, long long rowlen, int nrows_w,
+                                               int n, bool active, const LineCoef<double> &cf,
+                                               const LineDir &dr, double dval_in, double dval,
+                                               double *hsm, int KS, double *tb, int lane) {
+  static_assert(XS == 1 || XS == 2 || XS == 4, "rows of 1, 2 or 4 substrates");
+  constexpr int B = R * XS;  // elements of one row in a block
+  constexpr int P = R + 1;   // tb pitch: lanes reading their rows hit distinct bank pairs
+  const int k0 = cf.k0, ngrp = (n + R - 1) / R;
+  const L2Pol pol = make_l2pol();
+  const bool dBf = dr.before && dr.face, dAf = dr.after && dr.face;
+  // flat element j of the block: (row, offset w in the row's segment)
+  auto flat = [&](int j, int &row, int &w) {
+    const int f = j * 32 + lane;
+    row = f / B;
+    w = f % B;
+  };
+  // global -> registers (flat) for positions p0 .. p0+R-1
+  auto gload = [&](double(&buf)[R], int p0) {
+#pragma unroll
+    for (int j = 0; j < R; j++) {
+      int row, w;
+      flat(j, row, w);
+      const int pos = p0 + w / XS;
+      buf[j] = (row < nrows_w && pos >= 0 && pos < n)
+                   ? wbase[row * rowlen + (long long)p0 * XS + w]
+                   : 0.0;
+    }
+  };
+  // flat registers -> this lane's line: buf[k] = position p0 + k (rev: p0 + R-1-k)
+  auto to_lanes = [&](double(&buf)[R], bool rev) {
+#pragma unroll
+    for (int j = 0; j < R; j++) {
+      int row, w;
+      flat(j, row, w);
+      const int k = w / XS, dl = row * XS + w % XS;
+      tb[dl * P + (rev ? R - 1 - k : k)] = buf[j];
+    }
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < R; k++) buf[k] = tb[lane * P + k];
+    __syncwarp();
+  };
+  auto out_lane = [&](int k, double v) { tb[lane * P + k] = v; };
+  // this block's results (out_lane) -> global, positions p0 .. p0+R-1
+  auto flush = [&](int p0, bool rev, unsigned long long policy) {
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < R; j++) {
+      int row, w;
+      flat(j, row, w);
+      const int k = w / XS, dl = row * XS + w % XS, pos = p0 + k;
+      if (row < nrows_w && pos >= 0 && pos < n)
+        st_hint(wbase + row * rowlen + (long long)p0 * XS + w, tb[dl * P + (rev ? R - 1 - k : k)],
+                policy);
+    }
+    __syncwarp();
+  };
+  double h = 0.0, mp = 0.0;
+  auto fwd_group = [&](int g, double(&buf)[R]) {
+    const int i0 = g * R;
+    to_lanes(buf, false);
+    const bool sm = KS > 0 && i0 < KS;  // the whole group (KS is a multiple of R)
+    if (active) {
+      if (i0 - 1 >= k0 && i0 + R < n) {  // interior: mul_{i-1} = r sigma (warp-uniform)
+#pragma unroll
+        for (int k = 0; k < R; k++) {
+          h = fma(cf.c1, h, dBf ? dval_in : buf[k]);
+          if (sm) hsm[(i0 + k) * 32] = h; else out_lane(k, h);
+        }
+        mp = cf.c1;
+      } else {
+#pragma unroll
+        for (int k = 0; k < R; k++) {
+          const int i = i0 + k;
+          if (i < n) {
+            double d = buf[k];
+            if (dr.before && (dr.face || i == 0 || i == n - 1)) d = dval_in;
+            h = fma(mp, h, d);
+            const double hv = (OUT != 0 && i == n - 1) ? __ldg(cf.q + (size_t)i * XS) * h : h;
+            if (sm) hsm[i * 32] = hv; else out_lane(k, hv);
+            mp = __ldg(cf.mul + (size_t)i * XS);
+          }
+        }
+      }
+    }
+    if (!sm) flush(i0, false, pol.keep);
+  };
+  double x = 0.0;
+  // backward blocks run down from n-1, so one can straddle KS: positions below
+  // KS come from the lane's slab, the others from the field
+  auto in_slab = [&](int i1) { return KS > 0 && i1 < KS; };
+  auto bwd_group = [&](int g, double(&buf)[R]) {
+    const int i1 = n - 1 - g * R;
+    if (!in_slab(i1)) {
+      to_lanes(buf, true);
+      if (KS > 0 && i1 - R + 1 < KS) {
+#pragma unroll
+        for (int k = 0; k < R; k++) {
+          const int i = i1 - k;
+          if (active && i >= 0 && i < KS) buf[k] = hsm[i * 32];
+        }
+      }
+    }
+    if (active) {
+      if (i1 - R + 1 >= max(k0, 1) && (OUT != 0 || i1 < n - 1)) {
+#pragma unroll
+        for (int k = 0; k < R; k++) {
+          x = fma(cf.c1, x, OUT == 0 ? cf.c0 * buf[k] : buf[k]);
+          out_lane(k, dAf ? dval : (OUT == 2 ? cf.om * x : x));
+        }
+        if (dr.after && i1 == n - 1) out_lane(0, dval);
+      } else {
+#pragma unroll
+        for (int k = 0; k < R; k++) {
+          const int i = i1 - k;
+          if (i >= 0) {
+            const double hv = buf[k];
+            const double t = OUT == 0 ? __ldg(cf.inv + (size_t)i * XS) * hv
+                                      : (i == n - 1 ? hv : __ldg(cf.q + (size_t)i * XS) * hv);
+            x = fma(__ldg(cf.mul + (size_t)i * XS), x, t);
+            out_lane(k, (dr.after && (dr.face || i == 0 || i == n - 1)) ? dval
+                                                                        : (OUT == 2 ? cf.om * x : x));
+          }
+        }
+      }
+    }
+    flush(i1 - R + 1, true, pol.drop);
+  };
+  double A[R], Bf[R];
+  // backward blocks wholly below KS from the slab; the others from the field
+  // (loaded flat, transposed at use)
+  auto bload = [&](double(&buf)[R], int i1) {
+    if (in_slab(i1)) {
+#pragma unroll
+      for (int k = 0; k < R; k++) {
+        const int i = i1 - k;
+        buf[k] = (active && i >= 0 && i < n) ? hsm[i * 32] : 0.0;
+      }
+    } else {
+      gload(buf, i1 - R + 1);
+    }
+  };
+  pass_barrier();
+  gload(A, 0);
+  for (int g = 0; g < ngrp; g += 2) {
+    gload(Bf, (g + 1) * R);
+    fwd_group(g, A);
+    gload(A, (g + 2) * R);
+    if (g + 1 < ngrp) fwd_group(g + 1, Bf);
+  }
+  pass_barrier();
+  bload(A, n - 1);
+  for (int g = 0; g < ngrp; g += 2) {
+    bload(Bf, n - 1 - (g + 1) * R);
+    bwd_group(g, A);
+    bload(A, n - 1 - (g + 2) * R);
+    if (g + 1 < ngrp) bwd_group(g + 1, Bf);
+  }
+}
+
 // FP32 defect-correction solve of a warp's lines (see the header); sline is
 // the scratch field at the same offset as line.  KS > 0: for positions below
 // KS (a multiple of R) both g and d stay in shared memory (gsm, dsm: this
@@ -394,8 +566,10 @@ __device__ __forceinline__ void warp_rows_src(E *rho, long long r0, long long r1
 
 // Single-grid streaming sweep, persistent grid of 128-thread CTAs; E = double
 // (OUT as above) or float (defect form, OUT 0, scratch field a.scratch).
+// XS > 0 (FP64 x-sweep at S = XS = 1, 2 or 4): coalesced rows (solve_rows_f64),
+// each warp's transpose buffer after the CTA's slabs.
 
-template <typename E, int OUT>
+template <typename E, int OUT, int XS = 0>
 __global__ void __launch_bounds__(kStreamThreads, sizeof(E) == 8 ? 3 : 4)
     stream_sweep_kernel(const StreamArgs a) {
   extern __shared__ __align__(16) unsigned char stream_smem[];
@@ -436,8 +610,18 @@ __global__ void __launch_bounds__(kStreamThreads, sizeof(E) == 8 ? 3 : 4)
       cf.om = (OUT == 2 && L.active) ? ldg<E>(a.omega, L.s) : E(1);
       double *hsm = reinterpret_cast<double *>(stream_smem) +
                     (size_t)(threadIdx.x >> 5) * a.ks * 32 + lane;
-      solve_lines_f64<OUT, kStreamR>(line, n, a.stride, L.active, cf, dr, dval_in, dval, hsm,
-                                     a.ks);
+      if constexpr (XS > 0) {  // x-sweep, S = XS
+        const long long r0 = grp * a.rows_per_warp;
+        double *tb = reinterpret_cast<double *>(stream_smem) +
+                     (size_t)(kStreamThreads / 32) * a.ks * 32 +
+                     (size_t)(threadIdx.x >> 5) * 32 * (kStreamR + 1);
+        solve_rows_f64<OUT, XS, kStreamR>(rho + r0 * rowlen, rowlen,
+                                          (int)min((long long)a.rows_per_warp, nrows - r0), n,
+                                          L.active, cf, dr, dval_in, dval, hsm, a.ks, tb, lane);
+      } else {
+        solve_lines_f64<OUT, kStreamR>(line, n, a.stride, L.active, cf, dr, dval_in, dval, hsm,
+                                       a.ks);
+      }
     } else {
       cf.om = L.active ? ldg<E>(a.cfix, L.s) : E(0);
       cf.clo = L.active ? ldg<E>(a.cfix, S + L.s) : E(0);
@@ -447,9 +631,12 @@ __global__ void __launch_bounds__(kStreamThreads, sizeof(E) == 8 ? 3 : 4)
   }
 }
 
-// Shared memory of one CTA: the warps' slabs of ks positions (FP64).
-inline size_t stream_smem_bytes(int ks, size_t esz) {
-  return esz == 8 ? (size_t)(kStreamThreads / 32) * ks * 32 * sizeof(double) : 0;
+// Shared memory of one CTA: the warps' slabs of ks positions (FP64), and with
+// xs > 0 their transpose buffers.
+inline size_t stream_smem_bytes(int ks, size_t esz, int xs = 0) {
+  if (esz != 8) return 0;
+  return (size_t)(kStreamThreads / 32) *
+         ((size_t)ks * 32 + (xs > 0 ? (size_t)32 * (kStreamR + 1) : 0)) * sizeof(double);
 }
 
 // Raise the dynamic shared-memory limit of the FP64 instantiations (once per
@@ -457,15 +644,39 @@ inline size_t stream_smem_bytes(int ks, size_t esz) {
 template <typename E>
 cudaError_t allow_stream_smem() {
   cudaError_t e = cudaSuccess;
-  for (auto f : {stream_sweep_kernel<E, 0>, stream_sweep_kernel<E, 1>, stream_sweep_kernel<E, 2>})
+  auto set = [&](const void *f) {
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)kMaxDynamicSmem);
+  };
+  set((const void *)stream_sweep_kernel<E, 0>);
+  set((const void *)stream_sweep_kernel<E, 1>);
+  set((const void *)stream_sweep_kernel<E, 2>);
+  if constexpr (sizeof(E) == 8) {
+    set((const void *)stream_sweep_kernel<E, 0, 1>);
+    set((const void *)stream_sweep_kernel<E, 1, 1>);
+    set((const void *)stream_sweep_kernel<E, 0, 2>);
+    set((const void *)stream_sweep_kernel<E, 1, 2>);
+    set((const void *)stream_sweep_kernel<E, 0, 4>);
+    set((const void *)stream_sweep_kernel<E, 1, 4>);
+  }
   return e;
 }
 
+// a.xt (FP64 x-sweep): 1, 2 or 4 for the coalesced-row form, else 0.  The
+// x-sweep never renormalises (OUT 2), so only OUT 0 and 1 have that form.
 template <typename E, int OUT>
 cudaError_t launch_stream_one(const StreamArgs &a, int grid, cudaStream_t st) {
+  if constexpr (sizeof(E) == 8 && OUT != 2) {
+    const size_t sm = stream_smem_bytes(a.ks, sizeof(E), a.xt);
+    switch (a.xt) {
+      case 1: stream_sweep_kernel<E, OUT, 1><<<grid, kStreamThreads, sm, st>>>(a); return cudaGetLastError();
+      case 2: stream_sweep_kernel<E, OUT, 2><<<grid, kStreamThreads, sm, st>>>(a); return cudaGetLastError();
+      case 4: stream_sweep_kernel<E, OUT, 4><<<grid, kStreamThreads, sm, st>>>(a); return cudaGetLastError();
+      default: break;
+    }
+  }
+  if (a.xt != 0) return cudaErrorInvalidValue;
   stream_sweep_kernel<E, OUT><<<grid, kStreamThreads, stream_smem_bytes(a.ks, sizeof(E)), st>>>(a);
   return cudaGetLastError();
 }
