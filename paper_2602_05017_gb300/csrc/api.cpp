@@ -146,6 +146,7 @@ struct biofvm {
   DevBuf small_bar;
   int pipe_chunk = 0;        // FP32 pipelined sweeps: chunk length (0: the planner's)
   int pipe_cw = 0;           // FP32 pipelined sweeps: lines per tile, 32 or 16 (0: the planner's)
+  int pipe_ns = 4;           // FP32 pipelined sweeps: most ring stages per CTA
   DevBuf scratch;            // FP32 streaming: forward intermediate, field-sized
   int forced = 0;  // chunk lengths fixed by the caller (batched environments)
   unsigned generation = 0;  // bumped when kernel arguments change (sources, constants)
@@ -419,9 +420,21 @@ bool encode_pipe_map(biofvm *h, PipePlan &p, int axis, int buf, void *field, int
 
 // Bank-conflict degree of 32 lanes reading column c at (c/S)*pitch + c%S
 // (x tiles): the largest number of lanes that share a bank (FP32) or a bank
-// pair within a half warp (FP64).
-int x_tile_conflicts(int pitch, int S, int lanes, size_t esz) {
+// pair within a half warp (FP64).  half_off >= 0 (tiles of 16 columns): lanes
+// 16..31 read columns 0..15 of the next chunk, half_off elements further on.
+int x_tile_conflicts(int pitch, int S, int lanes, size_t esz, int half_off = -1) {
   int worst = 0;
+  if (half_off >= 0) {
+    int cnt[32] = {0};
+    for (int l = 0; l < 32; l++) {
+      const int c = l & 15;
+      if (c >= lanes) continue;
+      const int e = (c / S) * pitch + c % S + (l >= 16 ? half_off : 0);
+      const int bank = esz == 2 ? (e >> 1) & 31 : esz == 4 ? e & 31 : (2 * e) & 31;
+      worst = std::max(worst, ++cnt[bank]);
+    }
+    return worst;
+  }
   if (esz == 2) {  // two elements per 4-byte bank word: distinct words per bank
     int cnt[32] = {0};
     int word_seen[32][32];
@@ -466,6 +479,7 @@ void plan_pipe(biofvm *h, int axis, PipePlan &p, int64_t gp, void *field) {
     PipePlan q{};
     q.cw = cw;
     const int cpw = 32 / cw;
+    const int extra = axis == 0 ? 2 : 1;  // warps besides the consumers: producer (+ preparer)
     ColPlan cp;
     if (h->pipe_chunk > 0) {  // chunk length chosen by the caller (tuning)
       if (!plan_col(n, false, cp, std::min(h->pipe_chunk, n))) continue;
@@ -478,7 +492,8 @@ void plan_pipe(biofvm *h, int axis, PipePlan &p, int64_t gp, void *field) {
       bool shortc = false;
       for (int target : {16, 24}) {
         const int T = (n + target - 1) / target;
-        if (!l2_resident || h16 || T < 2 || (T + 1) * 32 > pipe_max_threads_f32(target)) continue;
+        if (!l2_resident || h16 || T < 2 || (T + extra) * 32 > pipe_max_threads_f32(target))
+          continue;
         cp.T = T;
         cp.m = target;
         cp.maxm = target;
@@ -493,7 +508,7 @@ void plan_pipe(biofvm *h, int axis, PipePlan &p, int64_t gp, void *field) {
         const int m = T == 1 ? n : target;
         const int maxm = pick_maxm(m, false);
         if (maxm != 32 && maxm != 64) continue;
-        if (((T + 1) / 2 + 1) * 32 > pipe_max_threads_f32(maxm)) continue;
+        if (((T + 1) / 2 + extra) * 32 > pipe_max_threads_f32(maxm)) continue;
         cp.T = T;
         cp.m = m;
         cp.maxm = maxm;
@@ -508,7 +523,7 @@ void plan_pipe(biofvm *h, int axis, PipePlan &p, int64_t gp, void *field) {
     // chunks above 64 registers spill (measured with -Xptxas -v): 16-column tiles instead
     if (cw == 32 && cp.maxm > 64 && h->pipe_chunk <= 0) continue;
     const int W = (cp.T + cpw - 1) / cpw;  // consumer warps
-    if ((W + 1) * 32 > pipe_max_threads_f32(cp.maxm)) continue;
+    if ((W + extra) * 32 > pipe_max_threads_f32(cp.maxm)) continue;
     q.T = cp.T;
     q.m = cp.m;
     q.maxm = cp.maxm;
@@ -520,7 +535,10 @@ void plan_pipe(biofvm *h, int axis, PipePlan &p, int64_t gp, void *field) {
       const int align = (int)(16 / esz);
       int best = 1 << 30;
       for (int64_t pitch = gp; pitch <= gp + 64; pitch += align) {
-        const int d = x_tile_conflicts((int)(pitch % 64), (int)S, q.rows_per_tile * (int)S, esz);
+        const int d = cw == 16 ? x_tile_conflicts((int)(pitch % 64), (int)S,
+                                                  q.rows_per_tile * (int)S, esz, (q.m * (int)S) % 64)
+                               : x_tile_conflicts((int)(pitch % 64), (int)S,
+                                                  q.rows_per_tile * (int)S, esz);
         if (d < best) {
           best = d;
           q.pitch = (int)pitch;
@@ -551,8 +569,9 @@ void plan_pipe(biofvm *h, int axis, PipePlan &p, int64_t gp, void *field) {
     const size_t stage = (size_t)q.stage_elems * esz;
     const size_t tab = (size_t)pipe_tab_elems_host(n, (int)S) * csz + 16;  // + alignment
     // carry exchange [2][W*32], carry weights [T][T][S], alignment, mbarriers
-    const size_t scratch = (2 * (size_t)W * 32 + (size_t)q.T * q.T * S) * csz + 16 + 2 * 8 * 8;
-    for (int ns = 4; ns >= 2 && !q.stages; ns--)  // the constants always staged
+    // (mbarriers: full, done, ready per stage, at most 8 stages)
+    const size_t scratch = (2 * (size_t)W * 32 + (size_t)q.T * q.T * S) * csz + 16 + 3 * 8 * 8;
+    for (int ns = std::max(2, std::min(h->pipe_ns, 8)); ns >= 2 && !q.stages; ns--)  // the constants always staged
       if (ns * stage + tab + scratch <= kMaxDynamicSmem) q.stages = ns;
     if (!q.stages) continue;
     q.smem = q.stages * stage + tab + scratch;
@@ -577,7 +596,7 @@ void plan_pipe(biofvm *h, int axis, PipePlan &p, int64_t gp, void *field) {
     p.use = 0;
     return;
   }
-  const int threads = (p.W + 1) * 32;
+  const int threads = (p.W + (axis == 0 ? 2 : 1)) * 32;
   const int regs = p.maxm + 96;
   int per_sm = (int)std::min<size_t>({kMaxDynamicSmem / p.smem, (size_t)(2048 / threads),
                                       (size_t)(65536 / (threads * regs))});
@@ -980,6 +999,7 @@ cudaError_t launch_pipe(const biofvm *h, int axis, int flags, cudaStream_t st, v
   b.src_alpha = sl.alpha;
   b.src_scale = sl.scale;
   b.has_src = sl.has;
+  b.prep_warp = axis == 0 && (((b.flags & kSrc) && b.has_src) || (b.flags & kDirBefore)) ? 1 : 0;
   b.dir_on = static_cast<const uint8_t *>(h->dir_on_d.p);
   b.dir_val = h->dir_val_d.p;
   b.status = static_cast<int *>(h->status.p);
@@ -1449,6 +1469,7 @@ biofvm_status create_impl(const biofvm_grid *grid, double dx, double dt, const d
   if (const char *env = getenv("BIOFVM_PIPELINE")) h->pipe_enabled = atoi(env) != 0;
   if (const char *env = getenv("BIOFVM_PIPE_CHUNK")) h->pipe_chunk = atoi(env);
   if (const char *env = getenv("BIOFVM_PIPE_CW")) h->pipe_cw = atoi(env);
+  if (const char *env = getenv("BIOFVM_PIPE_NS")) h->pipe_ns = atoi(env);
   if (const char *env = getenv("BIOFVM_STREAM")) h->stream_enabled = atoi(env) != 0;
   if (const char *env = getenv("BIOFVM_STREAM_CTAS")) h->stream_ctas_per_sm = atoi(env);
   if (const char *env = getenv("BIOFVM_STREAM32")) h->stream32_enabled = atoi(env) != 0;

@@ -13,14 +13,15 @@
 //     the consumers have written tile k back into its stage (mbarrier `done`),
 //     the bulk store of that tile; the stage is reloaded after the store has
 //     finished reading it;
-//   warps 1..ceil(T*CW/32) (consumers): chunk t of every column of the staged
+//   warp 1 (preparer, x tiles with a source update or a Dirichlet application
+//     before the solve): applies them in shared memory to each tile once it
+//     has landed -- running ahead of the consumers, who solve earlier tiles --
+//     and arrives on mbarrier `ready`, which the consumers then wait for
+//     instead of `full`;
+//   the next ceil(T*CW/32) warps (consumers): chunk t of every column of the staged
 //     tile, in registers (thread (warp w, lane l): chunk (w-1)*32/CW + l/CW of
 //     column l % CW).  Halos and chunk carries cross warps through shared memory
-//     between two named barriers per tile that only consumers join.  An x
-//     tile gets the source update and the first Dirichlet application in
-//     shared memory before its solve: the consumers apply them to the next
-//     tile's stage while solving the current one (sources before the first
-//     barrier, Dirichlet rows between the two).
+//     between two named barriers per tile that only consumers join.
 //
 // The grid is persistent (tiles strided by gridDim.x), so loads of later
 // tiles overlap the solve and the store of earlier ones.  The axis constants
@@ -120,16 +121,14 @@ __host__ __device__ inline int pipe_npad(int n) { return (n + 31) / 32 * 32 + 1;
 // back substitution, carry in, c d + y (FP32), Dirichlet, write-back.
 // FULL: the chunk has exactly MAXM positions (no per-position guards).
 // PS > 0: compile-time stride between positions in the staged tile.
-// mid1 runs just before the first carry barrier, mid2 just before the second
-// (the x tiles prepare the next tile's stage there).
-template <typename E, int MAXM, bool FULL, int PS, int CW, typename H, typename M1, typename M2>
+template <typename E, int MAXM, bool FULL, int PS, int CW, typename H>
 __device__ __forceinline__ bool pipe_chunk(H *p, const int ps_rt, const int len, const int lo,
                                            const int n, const int t, const int T, const int c,
                                            const E *Ti, const E *Tm, const E *Tf, const E *Tb,
                                            const E *Tcw, const int S, const int s, const E chi,
                                            const E clo, E *s_end, E *s_beg, const int ncons,
                                            const bool dir, const bool face, const E dval,
-                                           const bool ok, M1 &&mid1, M2 &&mid2) {
+                                           const bool ok) {
   const int ps = PS > 0 ? PS : ps_rt;
   E v[MAXM];
 #pragma unroll
@@ -164,7 +163,6 @@ __device__ __forceinline__ bool pipe_chunk(H *p, const int ps_rt, const int len,
       v[i] = g;
     }
   s_end[t * CW + c] = g;
-  mid1();
   // The first carry barrier also ANDs the outcome of every consumer's wait
   // for the tile: on a timeout all consumers leave together, before any
   // write-back (what they computed from the unfinished stage stays local).
@@ -191,7 +189,6 @@ __device__ __forceinline__ bool pipe_chunk(H *p, const int ps_rt, const int len,
       v[i] = x;
     }
   s_beg[t * CW + c] = x;
-  mid2();
   consumers_sync(ncons);
   if (t + 1 < T) {  // the last chunk enters with a zero carry
     E carry = E(0);
@@ -252,6 +249,7 @@ __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
   uint64_t *full = reinterpret_cast<uint64_t *>(
       (reinterpret_cast<uintptr_t>(s_cw + T * T * S) + 15) & ~uintptr_t(15));
   uint64_t *done = full + NS;
+  uint64_t *ready = done + NS;  // x tiles with a preparation: the stage is prepared
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long first = blockIdx.x;
@@ -263,6 +261,7 @@ __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
     for (int s = 0; s < NS; s++) {
       mbar_init(&full[s], 1);
       mbar_init(&done[s], ncons);
+      mbar_init(&ready[s], 1);
     }
     fence_mbar_init();
     fence_proxy_async_smem();
@@ -276,6 +275,14 @@ __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
   __syncthreads();
   const E *s_inv = tab, *s_mul = tab + S * npad, *s_pf = s_mul + S * npad, *s_pb = s_pf + S * npad;
   const E *g_cfix = static_cast<const E *>(a.tab.cfix);
+
+  // x tiles: Src and B before the solve, applied by warp 1 (the preparer) when
+  // the launch has one (a.prep_warp: the host sets it exactly when there is a
+  // source update or a Dirichlet application before the solve)
+  const bool prep = MODE == 0 && a.prep_warp != 0;
+  const bool srcs = prep && (a.flags & kSrc) && a.has_src;
+  const bool dirb = prep && (a.flags & kDirBefore);
+  const int cons0 = prep ? 2 : 1;  // first consumer warp
 
   if (warp == 0) {  // ------------------------------------------------ producer
     // x tiles: up to 32 rows per tile, one bulk copy each, issued by the lanes
@@ -352,113 +359,122 @@ __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
     return;
   }
 
+  if (prep && warp == 1) {  // ---------------------------------------- preparer
+    constexpr unsigned pmask = 0xffffffffu;
+    // Src then B on tile kk's stage once it has landed (x tiles), then `ready`.
+    // The source entries are unique elements (aggregated on the host or the
+    // device), so the lanes update them independently.  They flow ahead of the
+    // tiles: the entry range of a tile is loaded two preparations before its
+    // own, its first 32*PF entries (PF per lane) one preparation before, so a
+    // preparation waits on global memory only for a tile with more entries.
+    // The Dirichlet rows follow the sources (a source can sit on a face).
+    constexpr int PF = 8;
+    int2 prc[PF];
+    E pal[PF], psc[PF];
+    long long pe0 = 0, pe1 = 0, qe0 = 0, qe1 = 0;  // entry ranges: the next tile, the one after
+    auto fetch_range = [&](long long kk, long long &e0, long long &e1) {
+      e0 = e1 = 0;
+      if (!srcs || kk >= count) return;
+      const long long r0 = (first + kk * gridDim.x) * a.rows_per_tile;
+      e0 = __ldg(a.src_row_off + r0);
+      e1 = __ldg(a.src_row_off + min(r0 + (long long)a.rows_per_tile, (long long)a.nrows));
+    };
+    auto fetch_entries = [&]() {
+#pragma unroll
+      for (int j = 0; j < PF; j++) {
+        const long long e = pe0 + lane + 32 * j;
+        const bool v = e < pe1;
+        prc[j] = v ? __ldg(a.src_rowcol + e) : make_int2(-1, 0);
+        pal[j] = v ? ldg<E>(a.src_alpha, e) : E(0);
+        psc[j] = v ? ldg<E>(a.src_scale, e) : E(0);
+      }
+    };
+    if (srcs) {
+      fetch_range(0, pe0, pe1);
+      fetch_entries();
+      fetch_range(1, qe0, qe1);
+    }
+    auto prepare = [&](long long kk) -> bool {
+      const int s = (int)(kk % NS);
+      bool okw = mbar_wait_bounded(&full[s], (uint32_t)((kk / NS) & 1), a.status);
+      if (!__all_sync(pmask, okw)) return false;
+      H *const sg = stage0 + s * stage_elems;
+      const long long r0 = (first + kk * gridDim.x) * a.rows_per_tile;
+      const int rows = (int)min((long long)a.rows_per_tile, a.nrows - r0);
+      if (srcs) {
+#pragma unroll
+        for (int j = 0; j < PF; j++)
+          if (prc[j].x >= 0) {
+            H *q = sg + (prc[j].x - r0) * a.pitch + prc[j].y;
+            *q = narrow<H>((widen<E>(*q) + pal[j]) * psc[j]);
+          }
+        for (long long e = pe0 + 32 * PF + lane; e < pe1; e += 32) {  // beyond the prefetch
+          const int2 rc = __ldg(a.src_rowcol + e);
+          H *q = sg + (rc.x - r0) * a.pitch + rc.y;
+          *q = narrow<H>((widen<E>(*q) + ldg<E>(a.src_alpha, e)) * ldg<E>(a.src_scale, e));
+        }
+        __syncwarp();
+        pe0 = qe0;  // the next tile's entries, the range of the one after it
+        pe1 = qe1;
+        fetch_entries();
+        fetch_range(kk + 2, qe0, qe1);
+      }
+      if (dirb) {
+        for (int rr = 0; rr < rows; rr++) {
+          const uint32_t row = (uint32_t)r0 + (uint32_t)rr;
+          const int z = (int)(row / (uint32_t)a.ny), y = (int)row - z * a.ny;
+          H *trow = sg + (size_t)rr * a.pitch;
+          if (y == 0 || y == a.ny - 1 || z == 0 || z == a.nz - 1) {
+            for (int q = lane; q < a.rowlen; q += 32) {
+              const int ss = q % S;
+              if (a.dir_on[ss]) trow[q] = narrow<H>(dir_value<E>(a.flags, a.dir_val, ss));
+            }
+          } else {
+            for (int q = lane; q < 2 * S; q += 32) {
+              const int ss = q % S;
+              if (a.dir_on[ss])
+                trow[q < S ? ss : (a.nx - 1) * S + ss] =
+                    narrow<H>(dir_value<E>(a.flags, a.dir_val, ss));
+            }
+          }
+        }
+        __syncwarp();
+      }
+      if (lane == 0) mbar_arrive(&ready[s]);  // release: the warp's writes, ordered by __syncwarp
+      return true;
+    };
+    for (long long k = 0; k < count; k++)
+      if (!prepare(k)) break;  // (a timeout: the consumers' bounded wait on `ready` ends too)
+    return;
+  }
+
   // ---------------------------------------------------------------- consumers
-  const int wc = warp - 1;                         // consumer warp
+  const int wc = warp - cons0;                     // consumer warp
   const int c = CW == 32 ? lane : (lane & (CW - 1));  // column of the tile
   const int t = wc * CPW + lane / CW;              // chunk (t == T: no chunk)
-  const int ctid = threadIdx.x - 32;
   const int lo = t * m;
   const int len_full = t < T ? min(m, n - lo) : 0;
   const int colbase = MODE == 0 ? (c / S) * a.pitch + c % S : c;
   const int ps_rt = MODE == 0 ? S : CW;
   const E *Tcw = s_cw;  // [T][T][S], staged beside the other constants
   const bool dir_after = (a.flags & kDirAfter) != 0;
+  // A thread's substrate is the same in every tile when S divides the tile width (and, for
+  // z tiles, the row pitch): its per-substrate constants are then loaded once, not per tile.
+  const bool s_fixed = MODE == 0 || (CW % S == 0 && (a.mode == 1 || a.gpitch % S == 0));
+  const int sf = c % S;
+  const E chi_f = s_fixed ? __ldg(g_cfix + sf) : E(0), clo_f = s_fixed ? __ldg(g_cfix + S + sf) : E(0);
+  const bool dir_f = s_fixed && dir_after && a.dir_on[sf];
+  const E dval_f = dir_f ? dir_value<E>(a.flags, a.dir_val, sf) : E(0);
   // The planner keeps tile, row and column counts below 2^31, so the per-tile
   // index arithmetic below runs in 32 bits (a 64-bit division is a long
   // software sequence, and every consumer thread repeats it per tile).
-  // x tiles: the source entries flow ahead of the tiles -- a tile's entry
-  // offsets are loaded two preparations before its own, this thread's first
-  // entry one before, so no preparation waits on global loads.
-  const bool srcs = MODE == 0 && (a.flags & kSrc) && a.has_src;
-  auto src_range = [&](long long kk, long long &e0, long long &e1) {
-    e0 = e1 = 0;
-    if (!srcs || kk >= count) return;
-    const long long r0 = (first + kk * gridDim.x) * a.rows_per_tile;
-    e0 = __ldg(a.src_row_off + r0);
-    e1 = __ldg(a.src_row_off + min(r0 + (long long)a.rows_per_tile, (long long)a.nrows));
-  };
-  long long n0 = 0, n1 = 0, f0 = 0, f1 = 0;  // ranges of the next tile and the one after
-  int2 prc = make_int2(0, 0);
-  E pal = E(0), psc = E(0);
-  bool pv = false;  // this thread's prefetched entry of the next tile
-  auto src_fetch = [&](long long e0, long long e1) {
-    const long long e = e0 + ctid;
-    pv = e < e1;
-    if (pv) {
-      prc = __ldg(a.src_rowcol + e);
-      pal = ldg<E>(a.src_alpha, e);
-      psc = ldg<E>(a.src_scale, e);
-    }
-  };
-  if (srcs) {
-    src_range(0, n0, n1);
-    src_fetch(n0, n1);
-    src_range(1, f0, f1);
-  }
-  // Src then B on an x tile's staged rows, before its solve.  Tile 0 is
-  // prepared before the loop; tile k+1 while tile k is solved (its stage
-  // loaded): the source update before tile k's first carry barrier, the
-  // Dirichlet rows (which must see every source update, a source can sit on a
-  // face) between the two barriers, so the second one publishes the prepared
-  // stage and no barrier of its own is needed.
-  const bool dirb = MODE == 0 && (a.flags & kDirBefore);
-  const bool prep = srcs || dirb;
-  auto prep_src = [&](long long kk) {
-    H *const sg = stage0 + (int)(kk % NS) * stage_elems;
-    const long long r0 = (first + kk * gridDim.x) * a.rows_per_tile;
-    if (pv) {  // the prefetched entry, then (rarely) the thread's further ones
-      H *q = sg + (prc.x - r0) * a.pitch + prc.y;
-      *q = narrow<H>((widen<E>(*q) + pal) * psc);
-    }
-    for (long long e = n0 + ctid + ncons; e < n1; e += ncons) {
-      const int2 rc = __ldg(a.src_rowcol + e);
-      H *q = sg + (rc.x - r0) * a.pitch + rc.y;
-      *q = narrow<H>((widen<E>(*q) + ldg<E>(a.src_alpha, e)) * ldg<E>(a.src_scale, e));
-    }
-    // the next tile's first entries (offsets loaded one tile ago), and the
-    // offsets of the tile after it
-    n0 = f0;
-    n1 = f1;
-    src_fetch(n0, n1);
-    src_range(kk + 2, f0, f1);
-  };
-  auto prep_dir = [&](long long kk) {  // consumer warp wc takes rows wc, wc+W, ...
-    H *const sg = stage0 + (int)(kk % NS) * stage_elems;
-    const long long r0 = (first + kk * gridDim.x) * a.rows_per_tile;
-    const int rows = (int)min((long long)a.rows_per_tile, a.nrows - r0);
-    for (int rr = wc; rr < rows; rr += W) {
-      const uint32_t row = (uint32_t)r0 + (uint32_t)rr;
-      const int z = (int)(row / (uint32_t)a.ny), y = (int)row - z * a.ny;
-      H *trow = sg + (size_t)rr * a.pitch;
-      if (y == 0 || y == a.ny - 1 || z == 0 || z == a.nz - 1) {
-        for (int kk2 = lane; kk2 < a.rowlen; kk2 += 32) {
-          const int ss = kk2 % S;
-          if (a.dir_on[ss]) trow[kk2] = narrow<H>(dir_value<E>(a.flags, a.dir_val, ss));
-        }
-      } else {
-        for (int kk2 = lane; kk2 < 2 * S; kk2 += 32) {
-          const int ss = kk2 % S;
-          if (a.dir_on[ss])
-            trow[kk2 < S ? ss : (a.nx - 1) * S + ss] =
-                narrow<H>(dir_value<E>(a.flags, a.dir_val, ss));
-        }
-      }
-    }
-  };
-  if (MODE == 0 && prep && count > 0) {
-    // (a timed-out wait leaves garbage in the stage; the loop's own wait for
-    // tile 0 then fails too and every consumer leaves at the first barrier)
-    mbar_wait_bounded(&full[0], 0u, a.status);
-    if (srcs) prep_src(0);
-    if (srcs && dirb) consumers_sync(ncons);
-    if (dirb) prep_dir(0);
-    consumers_sync(ncons);
-  }
   for (long long k = 0; k < count; k++) {
     const int st = (int)(k % NS);
     // (a timed-out wait is acted on at the first carry barrier of the chunk
     // solve; the steps before it only touch this stage and registers)
-    const bool ok = mbar_wait_bounded(&full[st], (uint32_t)((k / NS) & 1), a.status);
+    // (x tiles with a preparation: the producer's `ready`, after its own wait for the data)
+    const bool ok = mbar_wait_bounded(prep ? &ready[st] : &full[st], (uint32_t)((k / NS) & 1),
+                                      a.status);
     const long long tile = first + k * gridDim.x;
     H *const stg = stage0 + st * stage_elems;
     int s;
@@ -497,34 +513,21 @@ __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
     const int len = active ? len_full : 0;
     H *p = stg + colbase + lo * ps_rt;
     const int rowoff = s * npad + lo;
-    const bool dir = dir_after && a.dir_on[s];
-    const E dval = dir ? dir_value<E>(a.flags, a.dir_val, s) : E(0);
-    const E chi = __ldg(g_cfix + s), clo = __ldg(g_cfix + S + s);
+    const bool dir = s_fixed ? dir_f : dir_after && a.dir_on[s];
+    const E dval = s_fixed ? dval_f : dir ? dir_value<E>(a.flags, a.dir_val, s) : E(0);
+    const E chi = s_fixed ? chi_f : __ldg(g_cfix + s), clo = s_fixed ? clo_f : __ldg(g_cfix + S + s);
     // the unguarded path only when every lane of the warp has a full chunk:
     // the choice is warp-uniform, so a warp never splits across the paths
     constexpr int PS = MODE == 0 ? PSX : CW;
-    const bool next = MODE == 0 && prep && k + 1 < count;
-    auto mid1 = [&]() {
-      if (next) {
-        const long long k1 = k + 1;
-        mbar_wait_bounded(&full[k1 % NS], (uint32_t)((k1 / NS) & 1), a.status);
-        if (srcs) prep_src(k1);
-      }
-    };
-    auto mid2 = [&]() {
-      if (next && dirb) prep_dir(k + 1);
-    };
     bool solved;
     if (__all_sync(0xffffffffu, len == MAXM))
       solved = pipe_chunk<E, MAXM, true, PS, CW>(p, ps_rt, len, lo, n, t, T, c, s_inv + rowoff,
                                              s_mul + rowoff, s_pf + rowoff, s_pb + rowoff, Tcw, S,
-                                             s, chi, clo, s_end, s_beg, ncons, dir, face, dval, ok,
-                                             mid1, mid2);
+                                             s, chi, clo, s_end, s_beg, ncons, dir, face, dval, ok);
     else
       solved = pipe_chunk<E, MAXM, false, PS, CW>(p, ps_rt, len, lo, n, t, T, c, s_inv + rowoff,
                                               s_mul + rowoff, s_pf + rowoff, s_pb + rowoff, Tcw, S,
-                                              s, chi, clo, s_end, s_beg, ncons, dir, face, dval, ok,
-                                              mid1, mid2);
+                                              s, chi, clo, s_end, s_beg, ncons, dir, face, dval, ok);
     if (!solved) break;
     fence_proxy_async_smem();  // generic-proxy writes -> visible to the bulk store
     mbar_arrive(&done[st]);
@@ -562,6 +565,12 @@ cudaError_t allow_pipe_smem(size_t bytes) {
     set((const void *)sweep_pipe_kernel<E, MAXM, 0, 4>);
     set((const void *)sweep_pipe_kernel<E, MAXM, 0, 8>);
   }
+  if constexpr (std::is_same<H, E>::value && pipe_half_tiles<MAXM>()) {
+    set((const void *)sweep_pipe_kernel<E, MAXM, 0, 1, 16>);
+    set((const void *)sweep_pipe_kernel<E, MAXM, 0, 2, 16>);
+    set((const void *)sweep_pipe_kernel<E, MAXM, 0, 4, 16>);
+    set((const void *)sweep_pipe_kernel<E, MAXM, 0, 8, 16>);
+  }
   return e;
 }
 
@@ -569,14 +578,24 @@ template <typename E, int MAXM, typename H = E>
 cudaError_t launch_pipe_one(const CUtensorMap &map, const PipeArgs &a, int grid, size_t smem,
                             cudaStream_t st) {
   const int cpw = a.cw == 16 ? 2 : 1;
-  const int threads = ((a.tab.T + cpw - 1) / cpw + 1) * 32;
+  const int threads = ((a.tab.T + cpw - 1) / cpw + 1 + a.prep_warp) * 32;
   if (threads > PipeBound<E, MAXM>::threads) return cudaErrorInvalidConfiguration;
   if (a.cw == 16) {
     if constexpr (pipe_half_tiles<MAXM>()) {
-      if (a.mode != 0)
+      if (a.mode != 0) {
         sweep_pipe_kernel<E, MAXM, 1, 0, 16, H><<<grid, threads, smem, st>>>(map, a);
-      else
-        sweep_pipe_kernel<E, MAXM, 0, 0, 16, H><<<grid, threads, smem, st>>>(map, a);
+        return cudaGetLastError();
+      }
+      if constexpr (std::is_same<H, E>::value) {  // x tiles: S at compile time where it can be
+        switch (a.S) {
+          case 1: sweep_pipe_kernel<E, MAXM, 0, 1, 16><<<grid, threads, smem, st>>>(map, a); return cudaGetLastError();
+          case 2: sweep_pipe_kernel<E, MAXM, 0, 2, 16><<<grid, threads, smem, st>>>(map, a); return cudaGetLastError();
+          case 4: sweep_pipe_kernel<E, MAXM, 0, 4, 16><<<grid, threads, smem, st>>>(map, a); return cudaGetLastError();
+          case 8: sweep_pipe_kernel<E, MAXM, 0, 8, 16><<<grid, threads, smem, st>>>(map, a); return cudaGetLastError();
+          default: break;
+        }
+      }
+      sweep_pipe_kernel<E, MAXM, 0, 0, 16, H><<<grid, threads, smem, st>>>(map, a);
       return cudaGetLastError();
     }
     return cudaErrorInvalidConfiguration;

@@ -49,6 +49,7 @@ struct PipeArgs {
   const int2 *src_rowcol;  // (row, position in the row) of each entry
   const void *src_alpha, *src_scale;
   int has_src;
+  int prep_warp;  // mode 0: a warp of its own applies Src and B before the solve (1) or none (0)
   const uint8_t *dir_on;
   const void *dir_val;
   int *status;
