@@ -559,11 +559,11 @@ cudaError_t allow_pipe_smem(size_t bytes) {
     set((const void *)sweep_pipe_kernel<E, MAXM, 0, 0, 16, H>);
     set((const void *)sweep_pipe_kernel<E, MAXM, 1, 0, 16, H>);
   }
-  if constexpr (std::is_same<H, E>::value && pipe_x_specialised<MAXM>()) {
-    set((const void *)sweep_pipe_kernel<E, MAXM, 0, 1>);
-    set((const void *)sweep_pipe_kernel<E, MAXM, 0, 2>);
-    set((const void *)sweep_pipe_kernel<E, MAXM, 0, 4>);
-    set((const void *)sweep_pipe_kernel<E, MAXM, 0, 8>);
+  if constexpr (pipe_x_specialised<MAXM>()) {
+    set((const void *)sweep_pipe_kernel<E, MAXM, 0, 1, 32, H>);
+    set((const void *)sweep_pipe_kernel<E, MAXM, 0, 2, 32, H>);
+    set((const void *)sweep_pipe_kernel<E, MAXM, 0, 4, 32, H>);
+    set((const void *)sweep_pipe_kernel<E, MAXM, 0, 8, 32, H>);
   }
   if constexpr (std::is_same<H, E>::value && pipe_half_tiles<MAXM>()) {
     set((const void *)sweep_pipe_kernel<E, MAXM, 0, 1, 16>);
@@ -605,12 +605,12 @@ cudaError_t launch_pipe_one(const CUtensorMap &map, const PipeArgs &a, int grid,
     sweep_pipe_kernel<E, MAXM, 1, 0, 32, H><<<grid, threads, smem, st>>>(map, a);
     return cudaGetLastError();
   }
-  if constexpr (std::is_same<H, E>::value && pipe_x_specialised<MAXM>()) {
+  if constexpr (pipe_x_specialised<MAXM>()) {
     switch (a.S) {
-      case 1: sweep_pipe_kernel<E, MAXM, 0, 1><<<grid, threads, smem, st>>>(map, a); return cudaGetLastError();
-      case 2: sweep_pipe_kernel<E, MAXM, 0, 2><<<grid, threads, smem, st>>>(map, a); return cudaGetLastError();
-      case 4: sweep_pipe_kernel<E, MAXM, 0, 4><<<grid, threads, smem, st>>>(map, a); return cudaGetLastError();
-      case 8: sweep_pipe_kernel<E, MAXM, 0, 8><<<grid, threads, smem, st>>>(map, a); return cudaGetLastError();
+      case 1: sweep_pipe_kernel<E, MAXM, 0, 1, 32, H><<<grid, threads, smem, st>>>(map, a); return cudaGetLastError();
+      case 2: sweep_pipe_kernel<E, MAXM, 0, 2, 32, H><<<grid, threads, smem, st>>>(map, a); return cudaGetLastError();
+      case 4: sweep_pipe_kernel<E, MAXM, 0, 4, 32, H><<<grid, threads, smem, st>>>(map, a); return cudaGetLastError();
+      case 8: sweep_pipe_kernel<E, MAXM, 0, 8, 32, H><<<grid, threads, smem, st>>>(map, a); return cudaGetLastError();
       default: break;
     }
   }
