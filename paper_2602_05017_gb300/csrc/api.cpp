@@ -89,6 +89,7 @@ constexpr int kRenormRows = 9;  // per-step constant rows of the scaled FP64 ste
 
 struct StreamPlan {
   int use = 0, grid = 0;
+  int r8 = 0;  // FP64: 8-position register blocks at four CTAs per SM (else 16 at three)
 };
 struct XPlan {
   int T = 1, m = 1, maxm = 8, rows_per_warp = 1, warps = 1, rows_per_cta = 1, use_bulk = 0;
@@ -139,6 +140,9 @@ struct biofvm {
   // FP64 x-sweep at S = 1, 2 (BIOFVM_STREAM_XT=4: also 4): coalesced rows through per-warp
   // transpose buffers, with slabs of stream_ks_xt positions
   int stream_xt = 2, stream_ks_xt = 32;
+  // FP64: 8-position register blocks at four CTAs per SM instead of 16 at three (per axis,
+  // StreamPlan::r8; -1: chosen by the planner, 0 / 1 forced)
+  int stream_r8_mode = -1;
   int stream32_enabled = 0;  // FP32 streaming sweeps instead of the pipelined ones
   // small FP64 grids: whole biofvm_step calls in one cooperative launch (small.cu)
   int small_enabled = 1, small_use = 0, small_grid = 0;
@@ -633,7 +637,21 @@ void plan_stream(biofvm *h, int axis) {
     cudaGetLastError();
     return;
   }
-  p.grid = h->num_sms * std::max(1, h->stream_ctas_per_sm);
+  // FP64: a warp takes one group of 32 lines at a time.  When the groups just overflow the
+  // warps of three 4-warp CTAs per SM but fit those of four, the second round would hold a
+  // few groups run at a single group's latency: there the 8-position blocks at four CTAs per
+  // SM take every group in one round (250^3 x 1: 1953 groups per axis, step 0.41 -> 0.30 ms).
+  // Otherwise the 16-position blocks (measured 4-5% faster at 200^3 x 4 and 400^3 x 4).
+  p.r8 = 0;
+  if (h->prec == BIOFVM_FP64) {
+    const int64_t nx = h->g.nx, ny = h->g.ny, nz = h->g.nz;
+    const int64_t rpw = 32 / S;
+    const int64_t C = axis == 1 ? nx * S : nx * ny * S;  // as launch_stream counts them
+    const int64_t groups = axis == 0 ? (ny * nz + rpw - 1) / rpw : (C + 31) / 32 * (axis == 1 ? nz : 1);
+    const int64_t warps3 = (int64_t)h->num_sms * 3 * 4, warps4 = (int64_t)h->num_sms * 4 * 4;
+    p.r8 = h->stream_r8_mode >= 0 ? h->stream_r8_mode : (groups > warps3 && groups <= warps4);
+  }
+  p.grid = h->num_sms * (p.r8 ? 4 : std::max(1, h->stream_ctas_per_sm));
   p.use = 1;
 }
 
@@ -1038,8 +1056,12 @@ cudaError_t launch_stream(const biofvm *h, int axis, int flags, cudaStream_t st,
   a.cfix = fp64 ? nullptr : axis_tab(h, axis).cfix;
   a.scratch = h->scratch.p;
   a.ks = std::max(0, std::min(h->stream_ks, 208));  // 4 warps x ks x 256 B <= 208 KB
-  a.xt = (fp64 && axis == 0 && (S == 1 || S == 2 || S == 4) && S <= h->stream_xt) ? (int)S : 0;
-  if (a.xt) a.ks = std::max(0, std::min(h->stream_ks_xt, 192));  // + 4 x 4.25 KB buffers
+  a.r8 = fp64 && p.r8 ? 1 : 0;
+  // (8-position blocks: XS 1 and 2 only; slabs of at most 48 positions keep four CTAs per SM)
+  a.xt = (fp64 && axis == 0 && (S == 1 || S == 2 || (S == 4 && !a.r8)) && S <= h->stream_xt)
+             ? (int)S : 0;
+  if (a.r8) a.ks = std::min(a.ks, 48);
+  if (a.xt) a.ks = std::max(0, std::min(h->stream_ks_xt, a.r8 ? 32 : 192));  // + 4 transpose buffers
   a.flags = flags;
   if (!h->any_dir) a.flags &= ~(kDirBefore | kDirAfter);
   const bool scaled = fp64 && (flags & kScaled);
@@ -1476,6 +1498,7 @@ biofvm_status create_impl(const biofvm_grid *grid, double dx, double dt, const d
   if (const char *env = getenv("BIOFVM_STREAM_KS")) h->stream_ks = atoi(env) / 16 * 16;
   if (const char *env = getenv("BIOFVM_STREAM_XT")) h->stream_xt = atoi(env);
   if (const char *env = getenv("BIOFVM_STREAM_KS_XT")) h->stream_ks_xt = atoi(env) / 16 * 16;
+  if (const char *env = getenv("BIOFVM_STREAM_R")) h->stream_r8_mode = atoi(env) == 8 ? 1 : 0;
   if (h->pipe_enabled && !h->forced)
     for (int axis = 0; axis < 3; axis++)
       plan_pipe(h, axis, h->pp[axis], (int64_t)g.nx * g.n_sub, h->rho.p);

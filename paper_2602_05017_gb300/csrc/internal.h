@@ -107,6 +107,7 @@ struct StreamArgs {
   void *scratch;          // FP32: field-sized scratch for the forward intermediate
   int ks;                 // FP64: positions whose intermediate stays in shared memory
   int xt;                 // FP64 x-sweep at S = 1, 2, 4: S (coalesced rows), else 0
+  int r8;                 // FP64: 8-position register blocks, four CTAs per SM (else 16, three)
   int flags;
   const int64_t *src_row_off, *src_elem;
   const void *src_alpha, *src_scale;

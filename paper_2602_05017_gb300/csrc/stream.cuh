@@ -48,6 +48,12 @@ namespace bfv {
 
 constexpr int kStreamThreads = 128;
 constexpr int kStreamR = 16;  // positions per register block
+// FP64: 16-position blocks at three CTAs per SM (168 registers), or 8-position
+// blocks at four (128 registers), for grids whose lines fill few rounds of warps
+template <int R>
+constexpr int stream_min_blocks() {
+  return R == 8 ? 4 : 3;
+}
 
 // One lane's line within the warp's group of 32 lines.
 struct LaneLine {
@@ -567,10 +573,11 @@ __device__ __forceinline__ void warp_rows_src(E *rho, long long r0, long long r1
 // Single-grid streaming sweep, persistent grid of 128-thread CTAs; E = double
 // (OUT as above) or float (defect form, OUT 0, scratch field a.scratch).
 // XS > 0 (FP64 x-sweep at S = XS = 1, 2 or 4): coalesced rows (solve_rows_f64),
-// each warp's transpose buffer after the CTA's slabs.
+// each warp's transpose buffer after the CTA's slabs.  R: positions per
+// register block (FP64: 16, or 8 at four CTAs per SM).
 
-template <typename E, int OUT, int XS = 0>
-__global__ void __launch_bounds__(kStreamThreads, sizeof(E) == 8 ? 3 : 4)
+template <typename E, int OUT, int XS = 0, int R = kStreamR>
+__global__ void __launch_bounds__(kStreamThreads, sizeof(E) == 8 ? stream_min_blocks<R>() : 4)
     stream_sweep_kernel(const StreamArgs a) {
   extern __shared__ __align__(16) unsigned char stream_smem[];
   const int S = a.S, n = a.n, flags = a.flags;
@@ -614,13 +621,12 @@ __global__ void __launch_bounds__(kStreamThreads, sizeof(E) == 8 ? 3 : 4)
         const long long r0 = grp * a.rows_per_warp;
         double *tb = reinterpret_cast<double *>(stream_smem) +
                      (size_t)(kStreamThreads / 32) * a.ks * 32 +
-                     (size_t)(threadIdx.x >> 5) * 32 * (kStreamR + 1);
-        solve_rows_f64<OUT, XS, kStreamR>(rho + r0 * rowlen, rowlen,
+                     (size_t)(threadIdx.x >> 5) * 32 * (R + 1);
+        solve_rows_f64<OUT, XS, R>(rho + r0 * rowlen, rowlen,
                                           (int)min((long long)a.rows_per_warp, nrows - r0), n,
                                           L.active, cf, dr, dval_in, dval, hsm, a.ks, tb, lane);
       } else {
-        solve_lines_f64<OUT, kStreamR>(line, n, a.stride, L.active, cf, dr, dval_in, dval, hsm,
-                                       a.ks);
+        solve_lines_f64<OUT, R>(line, n, a.stride, L.active, cf, dr, dval_in, dval, hsm, a.ks);
       }
     } else {
       cf.om = L.active ? ldg<E>(a.cfix, L.s) : E(0);
@@ -632,11 +638,11 @@ __global__ void __launch_bounds__(kStreamThreads, sizeof(E) == 8 ? 3 : 4)
 }
 
 // Shared memory of one CTA: the warps' slabs of ks positions (FP64), and with
-// xs > 0 their transpose buffers.
-inline size_t stream_smem_bytes(int ks, size_t esz, int xs = 0) {
+// xs > 0 their transpose buffers of blocks of r positions.
+inline size_t stream_smem_bytes(int ks, size_t esz, int xs = 0, int r = kStreamR) {
   if (esz != 8) return 0;
   return (size_t)(kStreamThreads / 32) *
-         ((size_t)ks * 32 + (xs > 0 ? (size_t)32 * (kStreamR + 1) : 0)) * sizeof(double);
+         ((size_t)ks * 32 + (xs > 0 ? (size_t)32 * (r + 1) : 0)) * sizeof(double);
 }
 
 // Raise the dynamic shared-memory limit of the FP64 instantiations (once per
@@ -659,14 +665,37 @@ cudaError_t allow_stream_smem() {
     set((const void *)stream_sweep_kernel<E, 1, 2>);
     set((const void *)stream_sweep_kernel<E, 0, 4>);
     set((const void *)stream_sweep_kernel<E, 1, 4>);
+    set((const void *)stream_sweep_kernel<E, 0, 0, 8>);
+    set((const void *)stream_sweep_kernel<E, 1, 0, 8>);
+    set((const void *)stream_sweep_kernel<E, 2, 0, 8>);
+    set((const void *)stream_sweep_kernel<E, 0, 1, 8>);
+    set((const void *)stream_sweep_kernel<E, 1, 1, 8>);
+    set((const void *)stream_sweep_kernel<E, 0, 2, 8>);
+    set((const void *)stream_sweep_kernel<E, 1, 2, 8>);
   }
   return e;
 }
 
 // a.xt (FP64 x-sweep): 1, 2 or 4 for the coalesced-row form, else 0.  The
 // x-sweep never renormalises (OUT 2), so only OUT 0 and 1 have that form.
+// a.r8 (FP64): 8-position blocks at four CTAs per SM (XS 0, 1, 2 only).
 template <typename E, int OUT>
 cudaError_t launch_stream_one(const StreamArgs &a, int grid, cudaStream_t st) {
+  if constexpr (sizeof(E) == 8) {
+    if (a.r8) {
+      const size_t sm = stream_smem_bytes(a.ks, sizeof(E), a.xt, 8);
+      if constexpr (OUT != 2) {
+        switch (a.xt) {
+          case 1: stream_sweep_kernel<E, OUT, 1, 8><<<grid, kStreamThreads, sm, st>>>(a); return cudaGetLastError();
+          case 2: stream_sweep_kernel<E, OUT, 2, 8><<<grid, kStreamThreads, sm, st>>>(a); return cudaGetLastError();
+          default: break;
+        }
+      }
+      if (a.xt != 0) return cudaErrorInvalidValue;
+      stream_sweep_kernel<E, OUT, 0, 8><<<grid, kStreamThreads, sm, st>>>(a);
+      return cudaGetLastError();
+    }
+  }
   if constexpr (sizeof(E) == 8 && OUT != 2) {
     const size_t sm = stream_smem_bytes(a.ks, sizeof(E), a.xt);
     switch (a.xt) {
@@ -676,7 +705,7 @@ cudaError_t launch_stream_one(const StreamArgs &a, int grid, cudaStream_t st) {
       default: break;
     }
   }
-  if (a.xt != 0) return cudaErrorInvalidValue;
+  if (a.xt != 0 || a.r8) return cudaErrorInvalidValue;
   stream_sweep_kernel<E, OUT><<<grid, kStreamThreads, stream_smem_bytes(a.ks, sizeof(E)), st>>>(a);
   return cudaGetLastError();
 }

@@ -530,22 +530,25 @@ def test_describe_names_the_step_kernels(binding, monkeypatch):
     sim.close()
 
 
+@pytest.mark.parametrize("r", ["16", "8"])
 @pytest.mark.parametrize("xt,ks", [("2", "32"), ("4", "48"), ("4", "0"), ("2", "16"), ("0", "64")],
                          ids=lambda v: v)
 @pytest.mark.parametrize("shape", [(37, 23, 19, 1), (70, 9, 11, 2), (250, 6, 5, 1),
                                    (33, 17, 9, 4), (19, 13, 7, 2)],
                          ids=lambda s: "x".join(map(str, s)))
-def test_fp64_streaming_x_sweep_row_forms_match_oracle(binding, monkeypatch, shape, xt, ks):
+def test_fp64_streaming_x_sweep_row_forms_match_oracle(binding, monkeypatch, shape, xt, ks, r):
     """The FP64 streaming x-sweep with the warp's rows moved as contiguous segments through the
-    swizzled transpose buffer (S <= BIOFVM_STREAM_XT, S in 1, 2, 4) and with lane-owned rows
-    (BIOFVM_STREAM_XT=0), slabs of BIOFVM_STREAM_KS_XT positions (0: none; 16, 48: a backward
-    block straddles the slab's end on these lengths): against the oracle over calls of 1 and 2
-    steps, with sources and Dirichlet faces, rows that do not fill a warp, and line lengths that
-    are no multiple of the 16-position blocks.  Small grids would take the cooperative step, so
-    the per-sweep kernels are forced."""
+    transpose buffer (S <= BIOFVM_STREAM_XT, S in 1, 2, 4; S = 4 with 16-position blocks only)
+    and with lane-owned rows (BIOFVM_STREAM_XT=0), slabs of BIOFVM_STREAM_KS_XT positions (0:
+    none; 16, 48: a backward block straddles the slab's end on these lengths), register blocks
+    of 16 or 8 positions (BIOFVM_STREAM_R): against the oracle over calls of 1 and 2 steps, with
+    sources and Dirichlet faces, rows that do not fill a warp, and line lengths that are no
+    multiple of the blocks.  Small grids would take the cooperative step, so the per-sweep
+    kernels are forced."""
     monkeypatch.setenv("BIOFVM_SMALL", "0")
     monkeypatch.setenv("BIOFVM_STREAM_XT", xt)
     monkeypatch.setenv("BIOFVM_STREAM_KS_XT", ks)
+    monkeypatch.setenv("BIOFVM_STREAM_R", r)
     nx, ny, nz, ns = shape
     rng = np.random.default_rng(nx * 3 + ns)
     w = inputs.random_problem(rng, nx, ny, nz, ns, n_agents=120, dirichlet=True)
