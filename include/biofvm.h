@@ -275,17 +275,27 @@ biofvm_status biofvm_probe_fma_rate(biofvm_precision prec, uintptr_t cuda_stream
 
 /* ------------------------------------------------------------------------
  * Batched microenvironments: many independent grids of uneven size and
- * substrate count, advanced together by ONE persistent kernel launch per
- * biofvm_batch_step call (all environments, all steps; captured in a CUDA
- * graph).  Each environment is an ordinary handle (zero-flux boundaries)
- * reachable through biofvm_batch_env, so biofvm_set_density,
+ * substrate count, advanced together.  Two modes, fixed at create:
+ *   persistent (mode 0): ONE persistent kernel launch per biofvm_batch_step
+ *     call (all environments, all steps; captured in a CUDA graph), for many
+ *     small environments;
+ *   per-environment graph (mode 1): each environment runs the single-grid
+ *     sweeps (pipelined or streaming, as biofvm_step would), and a batch step
+ *     is ONE CUDA graph of every environment's three sweep launches on
+ *     parallel branches, launched once per step -- for environments large
+ *     enough to fill the GPU in a few concurrent launches.
+ * The mode is taken from the environment variable BIOFVM_BATCH_MODE (graph or
+ * persistent) if set, else mode 1 when the mean environment holds at least
+ * 2^20 voxel-substrates.  Each environment is an ordinary handle (zero-flux
+ * boundaries) reachable through biofvm_batch_env, so biofvm_set_density,
  * biofvm_set_sources, biofvm_density (and even biofvm_step) work on it.
  * ---------------------------------------------------------------------- */
 typedef struct biofvm_batch biofvm_batch_t;
 
 /* Create n_env >= 1 environments: grids[e] (host), dx[e], dt[e], and
  * D_flat / lambda_flat holding the n_sub of environment 0, then of
- * environment 1, ... (host).  tile_m: NULL or [n_env][3] tile shapes along
+ * environment 1, ... (host).  tile_m (persistent mode only; ignored in the
+ * per-environment mode): NULL or [n_env][3] tile shapes along
  * x, y, z per environment -- the shapes an autotuner chooses: a value >= the
  * axis length solves whole lines (one warp streams 32 lines, no chunks; FP32
  * then allocates a field-sized scratch for the environment); a smaller value
@@ -302,27 +312,37 @@ biofvm_status biofvm_batch_create(int n_env, const biofvm_grid *grids, const dou
 /* The handle of environment e (owned by the batch; do not destroy it). */
 biofvm_status biofvm_batch_env(biofvm_batch_t *b, int e, biofvm_t **env);
 
-/* Advance every environment n_steps >= 0 steps in one persistent launch
- * (async).  Work items (step, sweep, environment, tile of 32 lines) are
+/* Advance every environment n_steps >= 0 steps (async).  Persistent mode:
+ * one launch; work items (step, sweep, environment, tile of 32 lines) are
  * spread over a resident grid; each waits, with a bounded spin, for the
- * previous sweep of its own environment.  Errors: ARG, CUDA; a timed-out wait
- * is reported by biofvm_batch_sync as TIMEOUT. */
+ * previous sweep of its own environment.  Per-environment mode: n_steps
+ * launches of the one-step graph (captured at the first call and whenever an
+ * environment's sources or constants change), plus, for environments whose
+ * rows are no 16-byte multiple, one copy into and out of their row-padded
+ * copies per call.  Errors: ARG (Dirichlet nodes set on an environment), CUDA;
+ * a timed-out wait is reported by biofvm_batch_sync as TIMEOUT. */
 biofvm_status biofvm_batch_step(biofvm_batch_t *b, int n_steps);
 
-/* Wait for the batch's stream and check its status word.  Errors: CUDA,
- * TIMEOUT. */
+/* Wait for the batch's stream and check its status word (per-environment
+ * mode: every environment's).  Errors: CUDA, TIMEOUT. */
 biofvm_status biofvm_batch_sync(biofvm_batch_t *b);
 
 /* Change the tile shapes (same rules as tile_m of biofvm_batch_create) of
  * every environment without touching the fields or agents: re-partitions the
  * App. A constants.  Used by the autotuner.  Waits for the stream.  Errors:
- * ARG (nothing changed), OOM (scratch), CUDA. */
+ * ARG (nothing changed), OOM (scratch), CUDA, STATE (per-environment mode). */
 biofvm_status biofvm_batch_set_tiles(biofvm_batch_t *b, const int *tile_m);
 
-/* CTAs of the persistent batched launch (resident at once). */
+/* CTAs of the persistent batched launch (resident at once); 0 in the
+ * per-environment mode. */
 int biofvm_batch_grid(const biofvm_batch_t *b);
 
-/* Failure-detection test hook: with on != 0, every following batched launch
+/* The batch's mode: 0 persistent kernel, 1 per-environment graph; -1 for a
+ * NULL handle. */
+int biofvm_batch_mode(const biofvm_batch_t *b);
+
+/* Failure-detection test hook (persistent mode; STATE in the per-environment
+ * mode): with on != 0, every following batched launch
  * makes the first y-sweep tile of environment 0 wait for a completion count
  * that never comes.  Its bounded wait gives up after about two seconds, the
  * kernel sets the status word and every CTA stops at its next item (results

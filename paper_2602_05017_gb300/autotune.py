@@ -74,7 +74,9 @@ def tune(precision="fp32", n_buckets=N_BUCKETS, subs=range(1, 9), target_vs=1.2e
             cands = candidates(n)
             cands_x = candidates(n, S)
             m_x = cands_x[0]
-            b = binding.BioFVMBatch(envs, precision=precision, tile_m=[[m_x, cands[0], cands[0]]] * k)
+            # the tiles being tuned are the persistent kernel's
+            b = binding.BioFVMBatch(envs, precision=precision,
+                                    tile_m=[[m_x, cands[0], cands[0]]] * k, mode="persistent")
             try:
                 for e in b.envs:
                     e.field_tensor().uniform_(0.0, 38.0)

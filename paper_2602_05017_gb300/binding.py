@@ -90,6 +90,7 @@ def load():
         "biofvm_batch_step": (st, [vp, ctypes.c_int]),
         "biofvm_batch_sync": (st, [vp]),
         "biofvm_batch_grid": (ctypes.c_int, [vp]),
+        "biofvm_batch_mode": (ctypes.c_int, [vp]),
         "biofvm_batch_test_stall": (st, [vp, ctypes.c_int]),
         "biofvm_batch_set_tiles": (st, [vp, ctypes.POINTER(ctypes.c_int)]),
         "biofvm_batch_destroy": (None, [vp]),
@@ -387,14 +388,19 @@ class BioFVM:
 
 
 class BioFVMBatch:
-    """Many microenvironments advanced by one persistent launch per step() call.
+    """Many microenvironments advanced together: one persistent launch per step() call, or one
+    graph of per-environment sweep launches per step (large environments).
 
     envs: list of ``inputs.Workload`` (grids, dx, dt, D, lambda; zero-flux).  tile_m: optional
-    [n_env][3] chunk lengths (x, y, z) -- from ``autotune`` -- else library defaults.
+    [n_env][3] chunk lengths (x, y, z) of the persistent kernel -- from ``autotune`` -- else
+    library defaults.  mode: None (the library's choice), "persistent" or "graph" (passed to
+    biofvm_batch_create through BIOFVM_BATCH_MODE).
     """
 
-    def __init__(self, envs, precision="fp32", tile_m=None, stream=None):
+    def __init__(self, envs, precision="fp32", tile_m=None, stream=None, mode=None):
         self.lib = load()
+        if mode is not None and mode not in ("persistent", "graph"):
+            raise ValueError("mode must be None, 'persistent' or 'graph'")
         n = len(envs)
         grids = (Grid * n)(*[Grid(w.nx, w.ny, w.nz, w.ns) for w in envs])
         dx = _f64([w.dx for w in envs])
@@ -407,9 +413,19 @@ class BioFVMBatch:
             tm = self._tm.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
         self.stream = _current_stream() if stream is None else int(stream)
         h = ctypes.c_void_p()
-        _check(self.lib.biofvm_batch_create(n, grids, _dptr(dx), _dptr(dt), _dptr(D), _dptr(lam),
-                                            FP64 if precision == "fp64" else FP32, self.stream,
-                                            tm, ctypes.byref(h)), self.lib)
+        saved = os.environ.get("BIOFVM_BATCH_MODE")
+        if mode is not None:
+            os.environ["BIOFVM_BATCH_MODE"] = mode
+        try:
+            _check(self.lib.biofvm_batch_create(n, grids, _dptr(dx), _dptr(dt), _dptr(D),
+                                                _dptr(lam), FP64 if precision == "fp64" else FP32,
+                                                self.stream, tm, ctypes.byref(h)), self.lib)
+        finally:
+            if mode is not None:
+                if saved is None:
+                    os.environ.pop("BIOFVM_BATCH_MODE", None)
+                else:
+                    os.environ["BIOFVM_BATCH_MODE"] = saved
         self.h = h
         self.precision = precision
         self.envs = []
@@ -431,6 +447,10 @@ class BioFVMBatch:
 
     def grid(self):
         return int(self.lib.biofvm_batch_grid(self.h))
+
+    def mode(self):
+        """'persistent' or 'graph' (biofvm_batch_mode)."""
+        return "graph" if self.lib.biofvm_batch_mode(self.h) == 1 else "persistent"
 
     def set_tiles(self, tile_m):
         """Re-partition every environment with [n_env][3] chunk lengths (fields kept)."""

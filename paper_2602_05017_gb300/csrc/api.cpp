@@ -1197,6 +1197,17 @@ cudaError_t launch_nodes(const biofvm *h, cudaStream_t st, int m, int row, bool 
 // x-sweep stands for the node part of the application between Src and X^-1
 // (the source list holds no node element, and the fused face application
 // skips every substrate with a node on its faces, so the order holds).
+// The field into its row-padded working copy (in) or back (out).
+cudaError_t pitch_copy(const biofvm *h, bool in, cudaStream_t st) {
+  const int64_t rows = (int64_t)h->g.ny * h->g.nz;
+  const int rowlen = h->g.nx * h->g.n_sub;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((rows + 7) / 8, 8 * h->num_sms));
+  return in ? launch_pitch_rows(h->rho.p, h->prow.p, rows, rowlen, rowlen, h->gpitch, h->esz,
+                                grid, st)
+            : launch_pitch_rows(h->prow.p, h->rho.p, rows, rowlen, h->gpitch, rowlen, h->esz,
+                                grid, st);
+}
+
 // `pitched`: the three pipelined sweeps on the row-padded working copy (no
 // Dirichlet nodes then).
 biofvm_status launch_step(const biofvm *h, cudaStream_t st, int m = 0, bool renorm = true,
@@ -1914,9 +1925,6 @@ biofvm_status biofvm_step(biofvm_t *h, int n_steps) {
   // graphs are dropped whenever nodes are set, so they never mix the two forms)
   const int K = step_scaled(h) ? h->renorm_k : 1;
   const bool pitched = h->pitched && h->n_dnode == 0;
-  const int64_t rows = (int64_t)h->g.ny * h->g.nz;
-  const int rowlen = h->g.nx * h->g.n_sub;
-  const int cgrid = (int)std::max<int64_t>(1, std::min<int64_t>((rows + 7) / 8, 8 * h->num_sms));
   auto ensure = [&](int r) -> biofvm_status {  // graph slot 0: K steps; slot r: r < K steps
     const int slot = r == K ? 0 : r;
     if (h->gexec[slot]) return BIOFVM_OK;
@@ -1944,14 +1952,10 @@ biofvm_status biofvm_step(biofvm_t *h, int n_steps) {
   biofvm_status st;
   if (blocks > 0 && (st = ensure(K)) != BIOFVM_OK) return st;
   if (tail > 0 && (st = ensure(tail)) != BIOFVM_OK) return st;
-  if (pitched)
-    CK(launch_pitch_rows(h->rho.p, h->prow.p, rows, rowlen, rowlen, h->gpitch, h->esz, cgrid,
-                         h->stream));
+  if (pitched) CK(pitch_copy(h, true, h->stream));
   for (int b = 0; b < blocks; b++) CK(cudaGraphLaunch(h->gexec[0], h->stream));
   if (tail > 0) CK(cudaGraphLaunch(h->gexec[tail], h->stream));
-  if (pitched)
-    CK(launch_pitch_rows(h->prow.p, h->rho.p, rows, rowlen, h->gpitch, rowlen, h->esz, cgrid,
-                         h->stream));
+  if (pitched) CK(pitch_copy(h, false, h->stream));
   return BIOFVM_OK;
 }
 
@@ -2161,6 +2165,17 @@ struct biofvm_batch {
   cudaGraphExec_t gexec = nullptr;
   int graph_steps = -1;
   int stall_test = 0;
+  // Per-environment mode (graph_mode): each environment is an ordinary handle with the
+  // single-grid plans (pipelined or streaming sweeps), and a batch step is one CUDA graph of
+  // every environment's three sweep launches, environments on parallel branches (forked
+  // over kForks capture streams); the persistent kernel is not used.
+  int graph_mode = 0;
+  std::vector<cudaStream_t> fork;
+  std::vector<cudaEvent_t> fork_ev;  // [0] fork, [1 + f] join of branch f
+  std::vector<int> fork_of;          // environment -> branch (largest first to the least loaded)
+  // graphs of K = 1..kGraphSteps steps of every environment (slot K)
+  cudaGraph_t ggraph[9] = {};
+  cudaGraphExec_t gg[9] = {};
 };
 
 namespace {
@@ -2206,15 +2221,69 @@ void batch_drop_graph(biofvm_batch *b) {
   b->graph_steps = -1;
 }
 
+void batch_drop_graph_mode(biofvm_batch *b);
+
 void batch_destroy_impl(biofvm_batch *b) {
   if (!b) return;
   cudaSetDevice(b->device);
   cudaStreamSynchronize(b->stream);
   batch_drop_graph(b);
+  batch_drop_graph_mode(b);
   for (biofvm *h : b->env) destroy_impl(h);
   for (DevBuf *d : {&b->envs_d, &b->tile_off_d, &b->done_d, &b->flags_d}) d->release();
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  for (cudaStream_t s : b->fork) cudaStreamDestroy(s);
+  for (cudaEvent_t e : b->fork_ev) cudaEventDestroy(e);
   delete b;
+}
+
+constexpr int kForks = 32;       // parallel capture streams of the per-environment mode
+constexpr int kGraphSteps = 8;   // steps of every environment in one graph
+
+void batch_drop_graph_mode(biofvm_batch *b) {
+  for (int k = 0; k <= kGraphSteps; k++) {
+    if (b->gg[k]) cudaGraphExecDestroy(b->gg[k]);
+    if (b->ggraph[k]) cudaGraphDestroy(b->ggraph[k]);
+    b->gg[k] = nullptr;
+    b->ggraph[k] = nullptr;
+  }
+}
+
+// K steps of every environment as one CUDA graph (per-environment mode): environment e's K
+// steps (x-, y-, z-sweep launches each) on capture stream fork_of[e], forked from and joined
+// back to the batch's capture stream, so environments run through their K steps without
+// waiting for one another.  A field with unaligned rows steps on its row-padded copy (copied
+// in and out by biofvm_batch_step around all the steps of the call).
+biofvm_status batch_capture_graph_mode(biofvm_batch *b, int K) {
+  const int ne = (int)b->env.size(), nf = (int)b->fork.size();
+  CK(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+  biofvm_status st = BIOFVM_OK;
+  cudaError_t e = cudaEventRecord(b->fork_ev[0], b->cap_stream);
+  for (int f = 0; f < nf && e == cudaSuccess; f++) e = cudaStreamWaitEvent(b->fork[f], b->fork_ev[0], 0);
+  for (int i = 0; i < ne && e == cudaSuccess && st == BIOFVM_OK; i++) {
+    const biofvm *h = b->env[i];
+    for (int k = 0; k < K && st == BIOFVM_OK; k++)
+      st = launch_step(h, b->fork[b->fork_of[i]], 0, true, h->pitched != 0);
+  }
+  for (int f = 0; f < nf && e == cudaSuccess; f++) {
+    e = cudaEventRecord(b->fork_ev[1 + f], b->fork[f]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->cap_stream, b->fork_ev[1 + f], 0);
+  }
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &graph);
+  if (st != BIOFVM_OK || e != cudaSuccess || e2 != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    if (st != BIOFVM_OK) return st;
+    return fail(BIOFVM_ERR_CUDA, "batch graph capture failed: %s",
+                cudaGetErrorString(e != cudaSuccess ? e : e2));
+  }
+  const cudaError_t e3 = cudaGraphInstantiate(&b->gg[K], graph, 0);
+  if (e3 != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    return fail(BIOFVM_ERR_CUDA, "cudaGraphInstantiate failed: %s", cudaGetErrorString(e3));
+  }
+  b->ggraph[K] = graph;
+  return BIOFVM_OK;
 }
 
 // Environment descriptors (device pointers of every environment's field,
@@ -2288,16 +2357,30 @@ biofvm_status biofvm_batch_create(int n_env, const biofvm_grid *grids, const dou
   if (!b) return fail(BIOFVM_ERR_OOM, "host allocation failed");
   b->prec = prec;
   b->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  // mode: BIOFVM_BATCH_MODE=graph / persistent, else per-environment graphs when the mean
+  // environment holds >= 2^20 voxel-substrates (enough for the single-grid sweeps to fill the
+  // GPU in a few concurrent launches), the persistent kernel for smaller ones
+  {
+    const char *env = getenv("BIOFVM_BATCH_MODE");
+    if (env && (!strcmp(env, "graph") || !strcmp(env, "persistent"))) {
+      b->graph_mode = !strcmp(env, "graph");
+    } else {
+      double total = 0.0;
+      for (int e = 0; e < n_env; e++)
+        total += (double)grids[e].nx * grids[e].ny * grids[e].nz * grids[e].n_sub;
+      b->graph_mode = total / n_env >= 1048576.0;
+    }
+  }
   int64_t off = 0;
   for (int e = 0; e < n_env; e++) {
     const biofvm_grid &g = grids[e];
-    int m[3], whole[3];
+    int m[3] = {0, 0, 0}, whole[3] = {0, 0, 0};
     const int ns[3] = {g.nx, g.ny, g.nz};
     if (g.n_sub < 1 || g.n_sub > 32) {
       batch_destroy_impl(b);
       return fail(BIOFVM_ERR_ARG, "environment %d: n_sub must be in [1, 32]", e);
     }
-    for (int a = 0; a < 3; a++)
+    for (int a = 0; a < 3 && !b->graph_mode; a++)
       if (!batch_axis_shape(e, a, ns[a], g.n_sub, tile_m ? tile_m[3 * e + a] : 0, m[a],
                             whole[a])) {
         const biofvm_status st = BIOFVM_ERR_ARG;
@@ -2306,7 +2389,7 @@ biofvm_status biofvm_batch_create(int n_env, const biofvm_grid *grids, const dou
       }
     biofvm *h = nullptr;
     biofvm_status st = create_impl(&g, dx[e], dt[e], D_flat + off, lambda_flat + off, nullptr,
-                                   prec, cuda_stream, m, &h);
+                                   prec, cuda_stream, b->graph_mode ? nullptr : m, &h);
     if (st != BIOFVM_OK) {
       std::string msg = g_last_error;
       batch_destroy_impl(b);
@@ -2323,12 +2406,44 @@ biofvm_status biofvm_batch_create(int n_env, const biofvm_grid *grids, const dou
     }
     off += g.n_sub;
   }
+  b->device = b->env[0]->device;
+  if (b->graph_mode) {  // capture streams and fork / join events; no persistent-kernel state
+    const int nf = std::min(n_env, kForks);
+    cudaError_t e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+    for (int f = 0; f < nf && e == cudaSuccess; f++) {
+      cudaStream_t s = nullptr;
+      e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+      if (e == cudaSuccess) b->fork.push_back(s);
+    }
+    for (int f = 0; f <= nf && e == cudaSuccess; f++) {
+      cudaEvent_t ev = nullptr;
+      e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+      if (e == cudaSuccess) b->fork_ev.push_back(ev);
+    }
+    if (e != cudaSuccess) {
+      batch_destroy_impl(b);
+      return fail(BIOFVM_ERR_CUDA, "batch set-up failed: %s", cudaGetErrorString(e));
+    }
+    // branches balanced by voxel-substrates: largest environment first, to the least loaded
+    std::vector<int> order(n_env);
+    for (int i = 0; i < n_env; i++) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return b->env[x]->nel > b->env[y]->nel; });
+    std::vector<double> load(nf, 0.0);
+    b->fork_of.assign(n_env, 0);
+    for (int i : order) {
+      const int f = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+      b->fork_of[i] = f;
+      load[f] += (double)b->env[i]->nel;
+    }
+    *out = b;
+    return BIOFVM_OK;
+  }
   for (int c : kBatchMaxm)
     if (c >= b->maxm) {
       b->maxm = c;
       break;
     }
-  b->device = b->env[0]->device;
   const bool fp64 = prec == BIOFVM_FP64;
   int per_sm = 0;
   cudaError_t e = fp64 ? batch_occupancy_f64(b->maxm, &per_sm) : batch_occupancy_f32(b->maxm, &per_sm);
@@ -2374,6 +2489,29 @@ biofvm_status biofvm_batch_step(biofvm_batch_t *b, int n_steps) {
   CK(cudaSetDevice(b->device));
   bool stale = false;
   for (size_t e = 0; e < b->env.size(); e++) stale |= b->env[e]->generation != b->env_gen[e];
+  if (b->graph_mode) {  // one graph of one step for all environments, launched n_steps times
+    for (size_t e = 0; e < b->env.size(); e++)
+      if (b->env[e]->n_dnode > 0)
+        return fail(BIOFVM_ERR_ARG, "environment %zu: Dirichlet nodes are not supported in "
+                                    "batched environments", e);
+    if (stale) {
+      batch_drop_graph_mode(b);
+      for (size_t e = 0; e < b->env.size(); e++) b->env_gen[e] = b->env[e]->generation;
+    }
+    const int K = std::min(n_steps, kGraphSteps), blocks = n_steps / K, tail = n_steps % K;
+    for (int k : {K, tail})
+      if (k > 0 && !b->gg[k]) {
+        biofvm_status st = batch_capture_graph_mode(b, k);
+        if (st) return st;
+      }
+    for (const biofvm *h : b->env)
+      if (h->pitched) CK(pitch_copy(h, true, b->stream));
+    for (int k = 0; k < blocks; k++) CK(cudaGraphLaunch(b->gg[K], b->stream));
+    if (tail > 0) CK(cudaGraphLaunch(b->gg[tail], b->stream));
+    for (const biofvm *h : b->env)
+      if (h->pitched) CK(pitch_copy(h, false, b->stream));
+    return BIOFVM_OK;
+  }
   if (stale) {
     CK(cudaStreamSynchronize(b->stream));  // descriptors are read by launches in flight
     biofvm_status st = batch_upload(b);
@@ -2422,6 +2560,13 @@ biofvm_status biofvm_batch_sync(biofvm_batch_t *b) {
   if (!b) return fail(BIOFVM_ERR_ARG, "NULL batch handle");
   CK(cudaSetDevice(b->device));
   CK(cudaStreamSynchronize(b->stream));
+  if (b->graph_mode) {  // every environment's own status word
+    for (biofvm *h : b->env) {
+      biofvm_status st = check_status(h);
+      if (st) return st;
+    }
+    return BIOFVM_OK;
+  }
   int st = 0;
   CK(cudaMemcpy(&st, static_cast<int *>(b->flags_d.p) + 1, sizeof(int), cudaMemcpyDeviceToHost));
   if (st != kStatusOk) {
@@ -2431,10 +2576,15 @@ biofvm_status biofvm_batch_sync(biofvm_batch_t *b) {
   return BIOFVM_OK;
 }
 
-int biofvm_batch_grid(const biofvm_batch_t *b) { return b ? b->grid : 0; }
+int biofvm_batch_grid(const biofvm_batch_t *b) { return b && !b->graph_mode ? b->grid : 0; }
+
+int biofvm_batch_mode(const biofvm_batch_t *b) { return b ? b->graph_mode : -1; }
 
 biofvm_status biofvm_batch_set_tiles(biofvm_batch_t *b, const int *tile_m) {
   if (!b || !tile_m) return fail(BIOFVM_ERR_ARG, "NULL batch handle or tile shapes");
+  if (b->graph_mode)
+    return fail(BIOFVM_ERR_STATE, "per-environment graph mode: the environments use the "
+                                  "single-grid plans, there are no batched tiles to set");
   CK(cudaSetDevice(b->device));
   CK(cudaStreamSynchronize(b->stream));
   const bool fp64 = b->prec == BIOFVM_FP64;
@@ -2484,6 +2634,8 @@ biofvm_status biofvm_batch_set_tiles(biofvm_batch_t *b, const int *tile_m) {
 
 biofvm_status biofvm_batch_test_stall(biofvm_batch_t *b, int on) {
   if (!b) return fail(BIOFVM_ERR_ARG, "NULL batch handle");
+  if (b->graph_mode)
+    return fail(BIOFVM_ERR_STATE, "the stall hook belongs to the persistent batched kernel");
   b->stall_test = on ? 1 : 0;
   batch_drop_graph(b);  // the hook is a kernel argument
   return BIOFVM_OK;

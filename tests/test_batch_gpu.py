@@ -185,3 +185,56 @@ def test_bounded_wait_expires_reports_timeout_and_context_stays_usable(binding):
         ref = oracle.Problem(**w.oracle_kwargs()).step(w.rho0, 2)
         assert rel(sim.density(), ref) <= 1e-12
     b.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_batch_graph_mode_matches_oracle(binding, prec):
+    """Per-environment graph mode (each environment on the single-grid sweeps, one graph of
+    every environment's launches per step): against the oracle environment by environment,
+    over calls of 4 and 2 steps with the sources replaced in between (a new graph), including
+    environments whose FP32 rows are no 16-byte multiple (row-padded copies)."""
+    envs = _envs(21, SHAPES)
+    b = binding.BioFVMBatch(envs, precision=prec, mode="graph")
+    assert b.mode() == "graph" and b.grid() == 0
+    for sim, w in zip(b.envs, envs):
+        sim.set_density(w.rho0)
+        sim.set_sources(w.voxel, w.secretion, w.target, w.uptake, w.weight)
+    b.step(4)
+    b.sync()
+    mid = []
+    for sim, w in zip(b.envs, envs):
+        ref = oracle.Problem(**w.oracle_kwargs()).step(w.rho0, 4)
+        got = sim.density()
+        assert rel(got, ref) <= TOL[prec], w.name
+        mid.append(np.asarray(got, dtype=np.float64))
+    rng = np.random.default_rng(5)
+    for sim, w in zip(b.envs, envs):  # new agents: the graph is captured again
+        w.secretion = w.secretion * rng.uniform(0.5, 1.5, w.secretion.shape)
+        sim.set_sources(w.voxel, w.secretion, w.target, w.uptake, w.weight)
+    b.step(2)
+    b.sync()
+    for sim, w, m in zip(b.envs, envs, mid):
+        ref = oracle.Problem(**w.oracle_kwargs()).step(m, 2)
+        assert rel(sim.density(), ref) <= TOL[prec], w.name
+    with pytest.raises(binding.BioFVMError) as e:
+        b.set_tiles([[8, 8, 8]] * len(envs))
+    assert e.value.status == binding.ERR_STATE
+    with pytest.raises(binding.BioFVMError) as e:
+        b.test_stall(True)
+    assert e.value.status == binding.ERR_STATE
+    b.envs[1].set_dirichlet_nodes([3], [0], [1.0])
+    with pytest.raises(binding.BioFVMError) as e:
+        b.step(1)
+    assert e.value.status == binding.ERR_ARG
+    b.close()
+
+
+def test_batch_mode_follows_environment_size(binding):
+    """Without an explicit mode: the persistent kernel for small environments, per-environment
+    graphs once the mean environment holds 2^20 voxel-substrates."""
+    small = binding.BioFVMBatch(_envs(22, [(20, 20, 20, 2), (30, 10, 10, 1)], agents=False))
+    assert small.mode() == "persistent" and small.grid() > 0
+    small.close()
+    big = binding.BioFVMBatch(_envs(23, [(128, 128, 64, 1), (64, 64, 64, 8)], agents=False))
+    assert big.mode() == "graph"
+    big.close()
