@@ -46,17 +46,17 @@ HBM_FALLBACK_GBS = 6800.0
 FLOPS_PER_ELEMENT_SWEEP = 5
 # Sources whose kernels the traffic below was captured on (hash of their contents).
 KERNEL_SOURCES = ["stream.cuh", "sweeps.cuh", "pipe.cuh", "pipe_args.h", "internal.h",
-                  "sweeps_fp64.cu", "sweeps_fp32.cu", "pipe_fp32.cu", "api.cpp"]
+                  "sweeps_fp64.cu", "sweeps_fp32.cu", "pipe_fp32.cu", "pipe_h16.cu", "api.cpp"]
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of each sweep kernel of
 # the 400^3 x 4 workload, from one ncu capture; reported only while the kernel sources still
 # hash to `sources_sha256` (otherwise the kernels changed since and traffic is null).
 MEASURED_TRAFFIC = {
-    "sources_sha256": "a2510969894c0ec4ed027c68d75c00679e7cd959ece0b34f56b146504dabb7cd",
+    "sources_sha256": "b1714bc30f9c2cd15d3d997fd14d8b0b67b512bed15d46585035bb2f5002ebc7",
     "bytes": {
-        "fp64:x-sweep": 5716324608, "fp64:y-sweep": 5511279104, "fp64:z-sweep": 5529953024,
-        "fp32:x-sweep": 2050955520, "fp32:y-sweep": 1983489024, "fp32:z-sweep": 1983777024,
-        "bf16:x-sweep": 1027049216, "bf16:y-sweep": 967136512, "bf16:z-sweep": 967069952,
-        "fp16:x-sweep": 1027403520, "fp16:y-sweep": 966989568, "fp16:z-sweep": 967088640,
+        "fp64:x-sweep": 5715298048, "fp64:y-sweep": 5515307520, "fp64:z-sweep": 5539715584,
+        "fp32:x-sweep": 2051327232, "fp32:y-sweep": 1983514624, "fp32:z-sweep": 1983630592,
+        "bf16:x-sweep": 1027097088, "bf16:y-sweep": 966284288, "bf16:z-sweep": 967206400,
+        "fp16:x-sweep": 1027561216, "fp16:y-sweep": 966683136, "fp16:z-sweep": 967169536,
     },
 }
 UNIT = "voxel-substrate updates/s"
