@@ -423,45 +423,30 @@ bool encode_pipe_map(biofvm *h, PipePlan &p, int axis, int buf, void *field, int
 }
 
 // Bank-conflict degree of 32 lanes reading column c at (c/S)*pitch + c%S
-// (x tiles): the largest number of lanes that share a bank (FP32) or a bank
-// pair within a half warp (FP64).  half_off >= 0 (tiles of 16 columns): lanes
-// 16..31 read columns 0..15 of the next chunk, half_off elements further on.
-int x_tile_conflicts(int pitch, int S, int lanes, size_t esz, int half_off = -1) {
+// (x tiles, pitch in elements): the largest number of distinct 4-byte words a
+// bank serves (lanes on one word share it: 16-bit elements pair up), or for
+// FP64 the largest number of lanes sharing a bank pair within a half warp.
+// half_off >= 0 (tiles of 16 columns): lanes 16..31 read columns 0..15 of the
+// next chunk, half_off elements further on.
+int x_tile_conflicts(int64_t pitch, int S, int lanes, size_t esz, int64_t half_off = -1) {
   int worst = 0;
-  if (half_off >= 0) {
-    int cnt[32] = {0};
-    for (int l = 0; l < 32; l++) {
-      const int c = l & 15;
-      if (c >= lanes) continue;
-      const int e = (c / S) * pitch + c % S + (l >= 16 ? half_off : 0);
-      const int bank = esz == 2 ? (e >> 1) & 31 : esz == 4 ? e & 31 : (2 * e) & 31;
-      worst = std::max(worst, ++cnt[bank]);
-    }
-    return worst;
-  }
-  if (esz == 2) {  // two elements per 4-byte bank word: distinct words per bank
-    int cnt[32] = {0};
-    int word_seen[32][32];
-    for (int c = 0; c < lanes; c++) {
-      const int word = ((c / S) * pitch + c % S) >> 1, bank = word & 31;
-      bool dup = false;
-      for (int j = 0; j < cnt[bank]; j++) dup = dup || word_seen[bank][j] == word;
-      if (!dup) {
-        word_seen[bank][cnt[bank]] = word;
-        worst = std::max(worst, ++cnt[bank]);
-      }
-    }
-    return worst;
-  }
-  if (esz == 4) {
-    int cnt[32] = {0};
-    for (int c = 0; c < lanes; c++) worst = std::max(worst, ++cnt[((c / S) * pitch + c % S) & 31]);
-  } else {
+  if (esz == 8) {
     for (int half = 0; half < 2; half++) {
       int cnt[16] = {0};
       for (int c = half * 16; c < std::min(lanes, half * 16 + 16); c++)
-        worst = std::max(worst, ++cnt[((c / S) * pitch + c % S) & 15]);
+        worst = std::max(worst, ++cnt[(int)(((c / S) * pitch + c % S) & 15)]);
     }
+    return worst;
+  }
+  std::vector<int64_t> words[32];
+  for (int l = 0; l < 32; l++) {
+    const int c = half_off >= 0 ? (l & 15) : l;
+    if (c >= lanes) continue;
+    const int64_t e = (c / S) * pitch + c % S + (half_off >= 0 && l >= 16 ? half_off : 0);
+    const int64_t word = e * (int64_t)esz / 4;
+    std::vector<int64_t> &w = words[word & 31];
+    if (std::find(w.begin(), w.end(), word) == w.end()) w.push_back(word);
+    worst = std::max(worst, (int)w.size());
   }
   return worst;
 }
@@ -539,10 +524,9 @@ void plan_pipe(biofvm *h, int axis, PipePlan &p, int64_t gp, void *field) {
       const int align = (int)(16 / esz);
       int best = 1 << 30;
       for (int64_t pitch = gp; pitch <= gp + 64; pitch += align) {
-        const int d = cw == 16 ? x_tile_conflicts((int)(pitch % 64), (int)S,
-                                                  q.rows_per_tile * (int)S, esz, (q.m * (int)S) % 64)
-                               : x_tile_conflicts((int)(pitch % 64), (int)S,
-                                                  q.rows_per_tile * (int)S, esz);
+        const int d = cw == 16 ? x_tile_conflicts(pitch, (int)S, q.rows_per_tile * (int)S, esz,
+                                                  (int64_t)q.m * S)
+                               : x_tile_conflicts(pitch, (int)S, q.rows_per_tile * (int)S, esz);
         if (d < best) {
           best = d;
           q.pitch = (int)pitch;
