@@ -283,6 +283,48 @@ __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
   const bool srcs = prep && (a.flags & kSrc) && a.has_src;
   const bool dirb = prep && (a.flags & kDirBefore);
   const int cons0 = prep ? 2 : 1;  // first consumer warp
+  // A tile with more source entries than the preparer holds prefetched (32 * kPF: dense agents)
+  // gets its Src and B from all the consumers instead, before its solve.  Preparer and
+  // consumers decide from the tile's entry count in the row offsets (read-only global data),
+  // so they always agree, whatever the outcome of any wait.
+  constexpr int kPF = 8;
+  auto tile_range = [&](long long kk, long long &e0, long long &e1) {
+    e0 = e1 = 0;
+    if (!srcs || kk >= count) return;
+    const long long r0 = (first + kk * gridDim.x) * a.rows_per_tile;
+    e0 = __ldg(a.src_row_off + r0);
+    e1 = __ldg(a.src_row_off + min(r0 + (long long)a.rows_per_tile, (long long)a.nrows));
+  };
+  auto is_dense = [&](long long e0, long long e1) { return e1 - e0 > 32 * kPF; };
+  // B before the solve on a tile's staged rows: warp w of nw takes rows w, w + nw, ...; the
+  // lanes walk a face row (a lane's substrate is fixed when S divides 32: flag and value once)
+  auto dir_rows = [&](H *sg, long long r0, int rows, int w, int nw) {
+    const bool lane_s = 32 % S == 0;
+    const bool on_l = lane_s && a.dir_on[lane % S];
+    const H val_l = on_l ? narrow<H>(dir_value<E>(a.flags, a.dir_val, lane % S)) : H(0);
+    for (int rr = w; rr < rows; rr += nw) {
+      const uint32_t row = (uint32_t)r0 + (uint32_t)rr;
+      const int z = (int)(row / (uint32_t)a.ny), y = (int)row - z * a.ny;
+      H *trow = sg + (size_t)rr * a.pitch;
+      if (y == 0 || y == a.ny - 1 || z == 0 || z == a.nz - 1) {
+        if (lane_s) {
+          if (on_l)
+            for (int q = lane; q < a.rowlen; q += 32) trow[q] = val_l;
+        } else {
+          for (int q = lane; q < a.rowlen; q += 32) {
+            const int ss = q % S;
+            if (a.dir_on[ss]) trow[q] = narrow<H>(dir_value<E>(a.flags, a.dir_val, ss));
+          }
+        }
+      } else {
+        for (int q = lane; q < 2 * S; q += 32) {
+          const int ss = q % S;
+          if (a.dir_on[ss])
+            trow[q < S ? ss : (a.nx - 1) * S + ss] = narrow<H>(dir_value<E>(a.flags, a.dir_val, ss));
+        }
+      }
+    }
+  };
 
   if (warp == 0) {  // ------------------------------------------------ producer
     // x tiles: up to 32 rows per tile, one bulk copy each, issued by the lanes
@@ -368,31 +410,24 @@ __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
     // own, its first 32*PF entries (PF per lane) one preparation before, so a
     // preparation waits on global memory only for a tile with more entries.
     // The Dirichlet rows follow the sources (a source can sit on a face).
-    constexpr int PF = 8;
+    constexpr int PF = kPF;
     int2 prc[PF];
     E pal[PF], psc[PF];
     long long pe0 = 0, pe1 = 0, qe0 = 0, qe1 = 0;  // entry ranges: the next tile, the one after
-    auto fetch_range = [&](long long kk, long long &e0, long long &e1) {
-      e0 = e1 = 0;
-      if (!srcs || kk >= count) return;
-      const long long r0 = (first + kk * gridDim.x) * a.rows_per_tile;
-      e0 = __ldg(a.src_row_off + r0);
-      e1 = __ldg(a.src_row_off + min(r0 + (long long)a.rows_per_tile, (long long)a.nrows));
-    };
     auto fetch_entries = [&]() {
 #pragma unroll
       for (int j = 0; j < PF; j++) {
         const long long e = pe0 + lane + 32 * j;
-        const bool v = e < pe1;
+        const bool v = e < pe1 && !is_dense(pe0, pe1);
         prc[j] = v ? __ldg(a.src_rowcol + e) : make_int2(-1, 0);
         pal[j] = v ? ldg<E>(a.src_alpha, e) : E(0);
         psc[j] = v ? ldg<E>(a.src_scale, e) : E(0);
       }
     };
     if (srcs) {
-      fetch_range(0, pe0, pe1);
+      tile_range(0, pe0, pe1);
       fetch_entries();
-      fetch_range(1, qe0, qe1);
+      tile_range(1, qe0, qe1);
     }
     auto prepare = [&](long long kk) -> bool {
       const int s = (int)(kk % NS);
@@ -401,43 +436,24 @@ __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
       H *const sg = stage0 + s * stage_elems;
       const long long r0 = (first + kk * gridDim.x) * a.rows_per_tile;
       const int rows = (int)min((long long)a.rows_per_tile, a.nrows - r0);
+      const bool dense = srcs && is_dense(pe0, pe1);  // then the consumers prepare the tile
       if (srcs) {
+        if (!dense) {
 #pragma unroll
-        for (int j = 0; j < PF; j++)
-          if (prc[j].x >= 0) {
-            H *q = sg + (prc[j].x - r0) * a.pitch + prc[j].y;
-            *q = narrow<H>((widen<E>(*q) + pal[j]) * psc[j]);
-          }
-        for (long long e = pe0 + 32 * PF + lane; e < pe1; e += 32) {  // beyond the prefetch
-          const int2 rc = __ldg(a.src_rowcol + e);
-          H *q = sg + (rc.x - r0) * a.pitch + rc.y;
-          *q = narrow<H>((widen<E>(*q) + ldg<E>(a.src_alpha, e)) * ldg<E>(a.src_scale, e));
+          for (int j = 0; j < PF; j++)
+            if (prc[j].x >= 0) {
+              H *q = sg + (prc[j].x - r0) * a.pitch + prc[j].y;
+              *q = narrow<H>((widen<E>(*q) + pal[j]) * psc[j]);
+            }
+          __syncwarp();
         }
-        __syncwarp();
         pe0 = qe0;  // the next tile's entries, the range of the one after it
         pe1 = qe1;
         fetch_entries();
-        fetch_range(kk + 2, qe0, qe1);
+        tile_range(kk + 2, qe0, qe1);
       }
-      if (dirb) {
-        for (int rr = 0; rr < rows; rr++) {
-          const uint32_t row = (uint32_t)r0 + (uint32_t)rr;
-          const int z = (int)(row / (uint32_t)a.ny), y = (int)row - z * a.ny;
-          H *trow = sg + (size_t)rr * a.pitch;
-          if (y == 0 || y == a.ny - 1 || z == 0 || z == a.nz - 1) {
-            for (int q = lane; q < a.rowlen; q += 32) {
-              const int ss = q % S;
-              if (a.dir_on[ss]) trow[q] = narrow<H>(dir_value<E>(a.flags, a.dir_val, ss));
-            }
-          } else {
-            for (int q = lane; q < 2 * S; q += 32) {
-              const int ss = q % S;
-              if (a.dir_on[ss])
-                trow[q < S ? ss : (a.nx - 1) * S + ss] =
-                    narrow<H>(dir_value<E>(a.flags, a.dir_val, ss));
-            }
-          }
-        }
+      if (dirb && !dense) {
+        dir_rows(sg, r0, rows, 0, 1);
         __syncwarp();
       }
       if (lane == 0) mbar_arrive(&ready[s]);  // release: the warp's writes, ordered by __syncwarp
@@ -458,6 +474,9 @@ __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
   const int ps_rt = MODE == 0 ? S : CW;
   const E *Tcw = s_cw;  // [T][T][S], staged beside the other constants
   const bool dir_after = (a.flags & kDirAfter) != 0;
+  const int ctid = threadIdx.x - 32 * cons0;  // consumer thread
+  long long cn0 = 0, cn1 = 0;                 // entry range of the next tile (dense check)
+  if (srcs) tile_range(0, cn0, cn1);
   // A thread's substrate is the same in every tile when S divides the tile width (and, for
   // z tiles, the row pitch): its per-substrate constants are then loaded once, not per tile.
   const bool s_fixed = MODE == 0 || (CW % S == 0 && (a.mode == 1 || a.gpitch % S == 0));
@@ -472,11 +491,43 @@ __global__ void __launch_bounds__(PipeBound<E, MAXM>::threads)
     const int st = (int)(k % NS);
     // (a timed-out wait is acted on at the first carry barrier of the chunk
     // solve; the steps before it only touch this stage and registers)
-    // (x tiles with a preparation: the producer's `ready`, after its own wait for the data)
+    // (x tiles with a preparation: the preparer's `ready`, after its own wait for the data)
     const bool ok = mbar_wait_bounded(prep ? &ready[st] : &full[st], (uint32_t)((k / NS) & 1),
                                       a.status);
     const long long tile = first + k * gridDim.x;
     H *const stg = stage0 + st * stage_elems;
+    if (srcs) {
+      const long long c0 = cn0, c1 = cn1;
+      tile_range(k + 1, cn0, cn1);  // the next tile's range, used one tile later
+      if (is_dense(c0, c1)) {       // every consumer agrees (global data); done whatever `ok`
+        const long long r0 = tile * a.rows_per_tile;
+        const int rows = (int)min((long long)a.rows_per_tile, a.nrows - r0);
+        constexpr int U = 4;
+        for (long long eb = c0 + ctid; eb < c1; eb += (long long)ncons * U) {
+          int2 rc[U];
+          E al[U], sc[U];
+#pragma unroll
+          for (int j = 0; j < U; j++) {
+            const long long e = eb + (long long)ncons * j;
+            const bool v = e < c1;
+            rc[j] = v ? __ldg(a.src_rowcol + e) : make_int2(-1, 0);
+            al[j] = v ? ldg<E>(a.src_alpha, e) : E(0);
+            sc[j] = v ? ldg<E>(a.src_scale, e) : E(0);
+          }
+#pragma unroll
+          for (int j = 0; j < U; j++)
+            if (rc[j].x >= 0) {
+              H *q = stg + (rc[j].x - r0) * a.pitch + rc[j].y;
+              *q = narrow<H>((widen<E>(*q) + al[j]) * sc[j]);
+            }
+        }
+        consumers_sync(ncons);
+        if (dirb) {
+          dir_rows(stg, r0, rows, wc, W);
+          consumers_sync(ncons);
+        }
+      }
+    }
     int s;
     bool active, face = false;
     if constexpr (MODE == 0) {

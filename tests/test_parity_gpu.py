@@ -560,3 +560,30 @@ def test_fp64_streaming_x_sweep_row_forms_match_oracle(binding, monkeypatch, sha
     got = sim.density()
     sim.close()
     assert rel_err(got, ref) <= 1e-12
+
+
+@pytest.mark.parametrize("shape", [(40, 20, 16, 2), (37, 22, 14, 3), (64, 10, 12, 4)],
+                         ids=lambda s: "x".join(map(str, s)))
+def test_fp32_x_tiles_dense_and_sparse_sources_match_oracle(binding, shape):
+    """Pipelined x tiles whose rows hold more source entries than the preparer warp prefetches
+    (the consumers then apply the tile's sources and Dirichlet rows) beside sparse tiles (the
+    preparer applies them) in one launch: agents packed into the lowest z-planes, a few more
+    scattered, Dirichlet faces; rows aligned or on the row-padded copy.  Against the oracle."""
+    nx, ny, nz, ns = shape
+    rng = np.random.default_rng(nx + nz)
+    w = inputs.random_problem(rng, nx, ny, nz, ns, n_agents=0, dirichlet=True)
+    dense = rng.integers(0, nx * ny * 3, 6 * nx * ny)      # z < 3: several per voxel
+    sparse = rng.integers(nx * ny * 3, nx * ny * nz, 40)   # elsewhere: a few
+    w.voxel = np.concatenate([dense, sparse]).astype(np.int64)
+    n = w.voxel.size
+    w.secretion = rng.uniform(0.1, 10.0, (n, ns))
+    w.target = rng.uniform(1.0, 38.0, (n, ns))
+    w.uptake = rng.uniform(0.0, 1.0, (n, ns))
+    w.weight = rng.uniform(0.5, 1.0, n)
+    ref = orc(w).step(w.rho0, 3)
+    sim = binding.BioFVM.from_workload(w, precision="fp32")
+    assert sim.describe().startswith("x=pipe"), sim.describe()
+    sim.step(3)
+    got = sim.density()
+    sim.close()
+    assert rel_err(got, ref) <= 1e-5
