@@ -148,6 +148,8 @@ struct biofvm {
   int small_enabled = 1, small_use = 0, small_grid = 0;
   size_t small_smem = 0;
   DevBuf small_bar;
+  int small_T[3] = {1, 1, 1}, small_m[3] = {1, 1, 1};  // chunks per axis of the small step
+  DevBuf small_tab[3];                                   // their axis tables
   int pipe_chunk = 0;        // FP32 pipelined sweeps: chunk length (0: the planner's)
   int pipe_cw = 0;           // FP32 pipelined sweeps: lines per tile, 32 or 16 (0: the planner's)
   int pipe_ns = 4;           // FP32 pipelined sweeps: most ring stages per CTA
@@ -647,7 +649,15 @@ void plan_small(biofvm *h) {
   if (!h->small_enabled || h->prec != BIOFVM_FP64 || h->forced) return;
   const int nx = h->g.nx, ny = h->g.ny, nz = h->g.nz, S = h->g.n_sub;
   if ((double)h->nel * 8.0 > 32.0e6 || !h->sp[2].use) return;
-  const size_t smem = small_smem_bytes(nx, ny, S);
+  // chunks: x-lines ny*S per plane, y-lines nx*S, z-lines in groups of 32
+  const int n3[3] = {nx, ny, nz}, L3[3] = {ny * S, nx * S, 32};
+  int T[3];
+  for (int a = 0; a < 3; a++) {
+    T[a] = small_chunks(n3[a], L3[a]);
+    h->small_T[a] = T[a];
+    h->small_m[a] = (n3[a] + T[a] - 1) / T[a];
+  }
+  const size_t smem = small_smem_bytes(nx, ny, nz, S, T);
   if (smem > 200 * 1024) return;
   int per_sm = 0;
   if (small_max_blocks(&per_sm, smem) != cudaSuccess || per_sm < 1) {
@@ -825,6 +835,11 @@ biofvm_status upload_constants(biofvm *h) {
       return upload_doubles(h, dst, tt);
     };
     if ((st = upload_T(h->tabT[axis])) != BIOFVM_OK) return st;
+    if (h->small_use) {  // the small step's own chunk partition
+      std::vector<double> ts;
+      axis_tables(h, axis, h->small_T[axis], h->small_m[axis], false, ts);
+      if ((st = upload_doubles(h, h->small_tab[axis], ts)) != BIOFVM_OK) return st;
+    }
     // the row-padded working copy's plans: tables of their own partition where it differs
     const PipePlan &q = h->ppx[axis];
     h->tabP_own[axis] = h->pitched && (q.T != T || q.m != m);
@@ -1326,7 +1341,8 @@ void destroy_impl(biofvm *h) {
                     &h->dsrc_rowcol, &h->dsrc_alpha, &h->dsrc_scale, &h->dsrc_count,
                     &h->ag_key[0], &h->ag_key[1], &h->ag_idx[0], &h->ag_idx[1], &h->ag_ea,
                     &h->ag_eb, &h->ag_head, &h->ag_pos, &h->ag_hist, &h->ag_part,
-                    &h->ag_count32, &h->small_bar, &h->prow, &h->tabP[0], &h->tabP[1],
+                    &h->ag_count32, &h->small_bar, &h->small_tab[0], &h->small_tab[1],
+                    &h->small_tab[2], &h->prow, &h->tabP[0], &h->tabP[1],
                     &h->tabP[2], &h->tabTP[0], &h->tabTP[1], &h->tabTP[2]})
     b->release();
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
@@ -1883,10 +1899,11 @@ biofvm_status biofvm_step(biofvm_t *h, int n_steps) {
     a.ny = h->g.ny;
     a.nz = h->g.nz;
     a.S = h->g.n_sub;
-    for (int axis = 0; axis < 3; axis++) a.tab[axis] = static_cast<const double *>(h->tab[axis].p);
-    a.ztab = static_cast<const double *>(h->tabS[2].p);
-    a.zint = static_cast<const double *>(h->stream_const_d.p) + (size_t)2 * 2 * h->g.n_sub;
-    a.zk0 = h->stream_k0[2];
+    for (int axis = 0; axis < 3; axis++) {
+      a.tab[axis] = static_cast<const double *>(h->small_tab[axis].p);
+      a.T[axis] = h->small_T[axis];
+      a.m[axis] = h->small_m[axis];
+    }
     const SrcLists sl = src_lists(h);
     a.src_row_off = sl.row_off;
     a.src_elem = sl.elem;

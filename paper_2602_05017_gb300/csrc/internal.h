@@ -194,10 +194,10 @@ cudaError_t launch_stream_f32(const StreamArgs &a, int grid, cudaStream_t st);
 struct SmallArgs {
   double *rho;
   int nx, ny, nz, S;
-  const double *tab[3];  // per axis: inv [n][S] then mul [n][S]
-  const double *ztab;    // z: the streaming tables inv, mul, q [3][nz][S]
-  const double *zint;    // z: interior constants [2][S] (sigma, r sigma) from position zk0
-  int zk0;
+  // per axis: the host's chunked axis tables (inv, mul, pf, pb [n][S], pc [T][S],
+  // [2][S], cw [T][T][S]) for T chunks of m positions
+  const double *tab[3];
+  int T[3], m[3];
   const int64_t *src_row_off, *src_elem;
   const double *src_alpha, *src_scale;
   int has_src;
@@ -208,7 +208,8 @@ struct SmallArgs {
   unsigned *bar;
   int *status;
 };
-size_t small_smem_bytes(int nx, int ny, int S);
+int small_chunks(int n, int L);
+size_t small_smem_bytes(int nx, int ny, int nz, int S, const int T[3]);
 cudaError_t small_max_blocks(int *blocks_per_sm, size_t smem);
 cudaError_t launch_small_f64(const SmallArgs &a, int grid, size_t smem, cudaStream_t st);
 // Sets the thread-local message biofvm_last_error() returns.
