@@ -669,7 +669,10 @@ void plan_small(biofvm *h) {
     return;
   }
   h->small_smem = smem;
-  h->small_grid = std::min(h->num_sms * per_sm, std::max(nz, h->num_sms));
+  // one CTA per plane (phase 1) or per group of 32 z-lines (phase 2), whichever is more: a grid
+  // barrier's cost grows with its CTAs
+  const int groups = (int)(((int64_t)nx * ny * S + 31) / 32);
+  h->small_grid = std::max(1, std::min(h->num_sms * per_sm, std::max(nz, groups)));
   h->small_use = 1;
 }
 
