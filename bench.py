@@ -51,12 +51,12 @@ KERNEL_SOURCES = ["stream.cuh", "sweeps.cuh", "pipe.cuh", "pipe_args.h", "intern
 # the 400^3 x 4 workload, from one ncu capture; reported only while the kernel sources still
 # hash to `sources_sha256` (otherwise the kernels changed since and traffic is null).
 MEASURED_TRAFFIC = {
-    "sources_sha256": "b1714bc30f9c2cd15d3d997fd14d8b0b67b512bed15d46585035bb2f5002ebc7",
+    "sources_sha256": "35a2fd48ea7fd33a95d4d56c6bfd4ebe2bda90662b2e1fca11e6257ccc0e022e",
     "bytes": {
-        "fp64:x-sweep": 5715298048, "fp64:y-sweep": 5515307520, "fp64:z-sweep": 5539715584,
-        "fp32:x-sweep": 2051327232, "fp32:y-sweep": 1983514624, "fp32:z-sweep": 1983630592,
-        "bf16:x-sweep": 1027097088, "bf16:y-sweep": 966284288, "bf16:z-sweep": 967206400,
-        "fp16:x-sweep": 1027561216, "fp16:y-sweep": 966683136, "fp16:z-sweep": 967169536,
+        "fp64:x-sweep": 5698977280, "fp64:y-sweep": 5499279616, "fp64:z-sweep": 5550959104,
+        "fp32:x-sweep": 2051060480, "fp32:y-sweep": 1983984640, "fp32:z-sweep": 1983558144,
+        "bf16:x-sweep": 1027536384, "bf16:y-sweep": 966321408, "bf16:z-sweep": 967173888,
+        "fp16:x-sweep": 1027404288, "fp16:y-sweep": 966340096, "fp16:z-sweep": 966964224,
     },
 }
 UNIT = "voxel-substrate updates/s"
@@ -152,6 +152,7 @@ class ClockSampler:
 
 
 SHAPE = None  # --shape overrides the grid (profiling a smaller case of the same recipe)
+SUBS = None   # --subs keeps the first substrates of that recipe (profiling)
 
 
 def aggregate(ms_local, world, units_per_rank, steps, device=None):
@@ -171,7 +172,8 @@ def workload_config(with_field=True):
     if SHAPE is None:
         return inputs.workload(2, with_field=with_field)
     nvox = SHAPE[0] * SHAPE[1] * SHAPE[2]
-    return inputs.workload(2, shape=SHAPE, with_field=with_field, n_agents=nvox // 64)
+    w = inputs.workload(2, shape=SHAPE, with_field=with_field, n_agents=nvox // 64)
+    return w if SUBS is None else inputs.first_substrates(w, SUBS)
 
 
 def flush_l2(dev):
@@ -872,11 +874,14 @@ def main():
                     help="run only the batched leg (profiling only; not a bench line)")
     ap.add_argument("--shape", type=int, nargs=3, metavar=("NX", "NY", "NZ"),
                     help="smaller grid of the same recipe (profiling only; not a bench line)")
+    ap.add_argument("--subs", type=int, default=None,
+                    help="with --shape: the recipe's first N substrates (profiling only)")
     ap.add_argument("--only", nargs="+", choices=list(PRECISIONS),
                     help="run only these precisions (profiling only; not a bench line)")
     args = ap.parse_args()
-    global SHAPE
+    global SHAPE, SUBS
     SHAPE = tuple(args.shape) if args.shape else None
+    SUBS = args.subs if args.shape else None
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

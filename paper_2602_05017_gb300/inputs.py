@@ -68,6 +68,21 @@ class Workload:
                     weight=self.weight, dirichlet_nodes=self.dirichlet_nodes)
 
 
+def first_substrates(w: Workload, ns: int) -> Workload:
+    """The same workload with its first `ns` substrates only (parameters, initial field, agent
+    rate columns, Dirichlet flags): e.g. the 400^3 recipe at one substrate for profiling."""
+    ns = int(ns)
+    if not 1 <= ns <= w.ns:
+        raise ValueError(f"ns must be in [1, {w.ns}]")
+    cut = lambda a: None if a is None else np.ascontiguousarray(np.asarray(a)[..., :ns])
+    return Workload(f"{w.name}_s{ns}", w.nx, w.ny, w.nz, ns, w.dx, w.dt, w.D[:ns].copy(),
+                    w.lam[:ns].copy(), w.n_steps, rho0=cut(w.rho0),
+                    dirichlet_on=None if w.dirichlet_on is None else w.dirichlet_on[:ns].copy(),
+                    dirichlet_value=None if w.dirichlet_value is None else w.dirichlet_value[:ns].copy(),
+                    voxel=w.voxel, secretion=cut(w.secretion), target=cut(w.target),
+                    uptake=cut(w.uptake), weight=w.weight, spacing=w.spacing)
+
+
 def _loguniform(rng, lo, hi, size):
     return np.exp(rng.uniform(np.log(lo), np.log(hi), size=size))
 

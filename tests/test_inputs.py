@@ -2,6 +2,7 @@
 import itertools
 
 import numpy as np
+import pytest
 
 from paper_2602_05017_gb300 import inputs
 
@@ -78,3 +79,13 @@ def test_device_blob_evaluator_matches_the_host_one_on_cpu():
     got = inputs.gaussian_blobs_device(w.extra["blobs"], w.nx, w.ny, w.nz, 2, w.dx, "cpu")
     np.testing.assert_allclose(got.numpy(), w.rho0, rtol=1e-13, atol=1e-12 * w.rho0.max())
     assert got.dtype == torch.float64
+
+
+def test_first_substrates_keeps_the_leading_columns():
+    w = inputs.workload(2, shape=(8, 6, 5), n_agents=12)
+    v = inputs.first_substrates(w, 2)
+    assert v.ns == 2 and v.rho0.shape == (5, 6, 8, 2)
+    assert np.array_equal(v.rho0, w.rho0[..., :2]) and np.array_equal(v.D, w.D[:2])
+    assert np.array_equal(v.secretion, w.secretion[:, :2]) and np.array_equal(v.voxel, w.voxel)
+    with pytest.raises(ValueError):
+        inputs.first_substrates(w, 5)
