@@ -298,7 +298,8 @@ typedef struct biofvm_batch biofvm_batch_t;
  * per-environment mode): NULL or [n_env][3] tile shapes along
  * x, y, z per environment -- the shapes an autotuner chooses: a value >= the
  * axis length solves whole lines (one warp streams 32 lines, no chunks; FP32
- * then allocates a field-sized scratch for the environment); a smaller value
+ * then allocates a scratch of one [n][32] tile per 32-line tile of the
+ * largest sweep, about the field's size); a smaller value
  * is the chunk length of the partitioned solve (at most 8 chunks of at most
  * 48 positions); <= 0 picks a default (whole lines, except chunks along x
  * when n_sub <= 2).  All environments share `prec` and the stream.

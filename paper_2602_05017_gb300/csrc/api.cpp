@@ -2164,7 +2164,9 @@ struct biofvm_batch {
   cudaStream_t stream = nullptr, cap_stream = nullptr;
   int device = 0, maxm = 8, grid = 0;
   int64_t per_step = 0;
-  DevBuf envs_d, tile_off_d, done_d, flags_d;  // flags: [0] abort, [1] status
+  DevBuf envs_d, tile_off_d, done_d, flags_d;  // flags: [0] abort, [1] status, [2..3] claims
+  int dynamic = 1;  // work items claimed from a counter (else static round robin)
+  int ctas_cap = 0;  // CTAs per SM of the persistent launch at most (0: as many as fit)
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
   int graph_steps = -1;
@@ -2290,6 +2292,28 @@ biofvm_status batch_capture_graph_mode(biofvm_batch *b, int K) {
   return BIOFVM_OK;
 }
 
+// Tiles of 32 lines per sweep of a batched environment: x tiles hold
+// floor(32/S) rows of S lines, y and z tiles 32 consecutive columns.
+void batch_tiles(const biofvm *h, int64_t tiles[3]) {
+  const int S = h->g.n_sub, rpt = 32 / S;
+  const int64_t nrows = (int64_t)h->g.ny * h->g.nz, rowlen = (int64_t)h->g.nx * S;
+  tiles[0] = (nrows + rpt - 1) / rpt;
+  tiles[1] = (int64_t)h->g.nz * ((rowlen + 31) / 32);
+  tiles[2] = (rowlen * h->g.ny + 31) / 32;
+}
+
+// Scratch bytes of an FP32 environment with whole-line axes: one [n][32]
+// tile per tile of the largest sweep (the single-grid streaming sweep's
+// field-sized scratch is never larger).
+size_t batch_scratch_bytes(const biofvm *h) {
+  int64_t tiles[3];
+  batch_tiles(h, tiles);
+  const int64_t ns[3] = {h->g.nx, h->g.ny, h->g.nz};
+  int64_t el = (int64_t)h->nel;
+  for (int a = 0; a < 3; a++) el = std::max(el, tiles[a] * ns[a] * 32);
+  return (size_t)el * h->esz;
+}
+
 // Environment descriptors (device pointers of every environment's field,
 // constants and sources) and the tile prefix sums.
 biofvm_status batch_upload(biofvm_batch *b) {
@@ -2313,10 +2337,7 @@ biofvm_status batch_upload(biofvm_batch *b) {
       x.m[axis] = t.m;
     }
     x.rows_per_tile = 32 / x.S;
-    const int64_t nrows = (int64_t)x.ny * x.nz, rowlen = (int64_t)x.nx * x.S;
-    x.tiles[0] = (nrows + x.rows_per_tile - 1) / x.rows_per_tile;
-    x.tiles[1] = (int64_t)x.nz * ((rowlen + 31) / 32);
-    x.tiles[2] = (rowlen * x.ny + 31) / 32;
+    batch_tiles(h, x.tiles);
     const bool fp64 = h->prec == BIOFVM_FP64;
     for (int ph = 0; ph < 3; ph++) {
       x.whole[ph] = b->whole[e][ph];
@@ -2375,6 +2396,8 @@ biofvm_status biofvm_batch_create(int n_env, const biofvm_grid *grids, const dou
       b->graph_mode = total / n_env >= 1048576.0;
     }
   }
+  if (const char *env = getenv("BIOFVM_BATCH_DYNAMIC")) b->dynamic = atoi(env) != 0;
+  if (const char *env = getenv("BIOFVM_BATCH_CTAS")) b->ctas_cap = std::max(0, atoi(env));
   int64_t off = 0;
   for (int e = 0; e < n_env; e++) {
     const biofvm_grid &g = grids[e];
@@ -2403,8 +2426,9 @@ biofvm_status biofvm_batch_create(int n_env, const biofvm_grid *grids, const dou
     b->env_gen.push_back(0);
     b->whole.push_back({whole[0], whole[1], whole[2]});
     for (int a = 0; a < 3; a++) b->maxm = std::max(b->maxm, m[a]);
-    if ((whole[0] || whole[1] || whole[2]) && prec == BIOFVM_FP32 && !h->scratch.p &&
-        dev_alloc(h->scratch, h->nel * h->esz) != cudaSuccess) {
+    if ((whole[0] || whole[1] || whole[2]) && prec == BIOFVM_FP32 &&
+        h->scratch.bytes < batch_scratch_bytes(h) &&
+        dev_alloc(h->scratch, batch_scratch_bytes(h)) != cudaSuccess) {
       batch_destroy_impl(b);
       return fail(BIOFVM_ERR_OOM, "environment %d: scratch field allocation failed", e);
     }
@@ -2455,16 +2479,17 @@ biofvm_status biofvm_batch_create(int n_env, const biofvm_grid *grids, const dou
     batch_destroy_impl(b);
     return fail(BIOFVM_ERR_CUDA, "batched kernel occupancy query failed");
   }
+  if (b->ctas_cap > 0) per_sm = std::min(per_sm, b->ctas_cap);
   b->grid = per_sm * b->env[0]->num_sms;  // every CTA resident (the schedule relies on it)
   if (dev_alloc(b->envs_d, (size_t)n_env * sizeof(BatchEnv)) != cudaSuccess ||
       dev_alloc(b->tile_off_d, 3 * (size_t)(n_env + 1) * 8) != cudaSuccess ||
       dev_alloc(b->done_d, 3 * (size_t)n_env * sizeof(unsigned)) != cudaSuccess ||
-      dev_alloc(b->flags_d, 2 * sizeof(int)) != cudaSuccess) {
+      dev_alloc(b->flags_d, 4 * sizeof(int)) != cudaSuccess) {
     batch_destroy_impl(b);
     return fail(BIOFVM_ERR_OOM, "device allocation of the batch descriptors failed");
   }
   if ((e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking)) != cudaSuccess ||
-      (e = cudaMemset(b->flags_d.p, 0, 2 * sizeof(int))) != cudaSuccess) {
+      (e = cudaMemset(b->flags_d.p, 0, 4 * sizeof(int))) != cudaSuccess) {
     batch_destroy_impl(b);
     return fail(BIOFVM_ERR_CUDA, "batch set-up failed: %s", cudaGetErrorString(e));
   }
@@ -2534,11 +2559,15 @@ biofvm_status biofvm_batch_step(biofvm_batch_t *b, int n_steps) {
     a.abort_flag = static_cast<int *>(b->flags_d.p);
     a.status = static_cast<int *>(b->flags_d.p) + 1;
     a.stall_test = b->stall_test;
+    a.next = b->dynamic ? reinterpret_cast<unsigned long long *>(
+                              static_cast<int *>(b->flags_d.p) + 2)
+                        : nullptr;
     a.maxm = b->maxm;
     const int grid = (int)std::min<int64_t>(b->grid, b->per_step * n_steps);
     CK(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e1 = cudaMemsetAsync(b->done_d.p, 0, 3 * (size_t)ne * sizeof(unsigned), b->cap_stream);
     cudaError_t e2 = cudaMemsetAsync(b->flags_d.p, 0, sizeof(int), b->cap_stream);  // abort flag
+    if (e2 == cudaSuccess && a.next) e2 = cudaMemsetAsync(a.next, 0, 8, b->cap_stream);
     cudaError_t e3 = b->prec == BIOFVM_FP64 ? launch_batch_f64(a, b->maxm, grid, b->cap_stream)
                                             : launch_batch_f32(a, b->maxm, grid, b->cap_stream);
     cudaGraph_t graph = nullptr;
@@ -2611,8 +2640,9 @@ biofvm_status biofvm_batch_set_tiles(biofvm_batch_t *b, const int *tile_m) {
   }
   for (size_t e = 0; e < b->env.size(); e++) {  // scratch fields for FP32 whole-line axes
     biofvm *h = b->env[e];
-    if ((whole[e][0] || whole[e][1] || whole[e][2]) && !fp64 && !h->scratch.p &&
-        dev_alloc(h->scratch, h->nel * h->esz) != cudaSuccess)
+    if ((whole[e][0] || whole[e][1] || whole[e][2]) && !fp64 &&
+        h->scratch.bytes < batch_scratch_bytes(h) &&
+        dev_alloc(h->scratch, batch_scratch_bytes(h)) != cudaSuccess)
       return fail(BIOFVM_ERR_OOM, "environment %zu: scratch field allocation failed", e);
   }
   for (int c : kBatchMaxm)
@@ -2632,6 +2662,7 @@ biofvm_status biofvm_batch_set_tiles(biofvm_batch_t *b, const int *tile_m) {
   }
   b->maxm = maxm;
   b->whole = whole;
+  if (b->ctas_cap > 0) per_sm = std::min(per_sm, b->ctas_cap);
   b->grid = std::max(per_sm, 1) * b->env[0]->num_sms;
   return batch_upload(b);
 }

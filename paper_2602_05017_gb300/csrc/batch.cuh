@@ -6,7 +6,9 @@
 // one environment, in the order (step, phase x/y/z, environment, item): a
 // line cut into T chunks takes T warps, so the 8 warps of a CTA solve
 // floor(8/T) tiles at once.  CTA b takes items b, b + G, b + 2G, ...
-// (G = gridDim.x, every CTA resident).
+// (G = gridDim.x, every CTA resident), or, with a claim counter, the next
+// unclaimed item each time it is free (items are claimed in order, so the
+// argument below holds for both).
 // Before an item, its dependency on the previous phase of the same
 // environment is checked on a per-(phase, environment) completion counter:
 //     x of step k   needs all z tiles of step k-1 (k > 0)
@@ -21,8 +23,10 @@
 // shared memory, carries across the CTA's warps) or whole (m >= n: each
 // warp streams its 32 lines as the single-grid streaming kernels do, no
 // carries; an item is then 8 tiles, one per warp), with the arithmetic of the
-// single-grid kernels: App. A system, FP32 in defect-correction form, the
-// source update applied to an x item's rows before its solve.  Zero-flux
+// single-grid kernels: App. A system, FP32 in defect-correction form (the
+// forward intermediate of whole lines in a scratch tile per warp, discarded
+// from L2 once read back), the source update applied to an x item's rows
+// before its solve.  Zero-flux
 // boundaries (the batched microenvironments have no Dirichlet faces).
 #pragma once
 #include <cuda_runtime.h>
@@ -66,6 +70,7 @@ __device__ __forceinline__ void cp_async_elem(void *smem, const void *gmem, int 
 // positions.
 constexpr int kBatchKS = 24;
 constexpr int kBatchR = 4;
+constexpr int kBatchWarpFloats = 2 * kBatchKS * 32;  // a warp's share of the line slabs
 
 // 256-thread CTAs, FP32 held to 64 registers (three or four per SM, as the
 // chunk rows' shared memory allows), FP64 to 80: the kernel is latency-bound,
@@ -83,8 +88,18 @@ __global__ void __launch_bounds__(kBatchWarps * 32, sizeof(E) == 4 ? 4 : 3)
   __shared__ int s_go;
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   const int64_t total = a.per_step * a.n_steps;
-  int last_env = -1, last_phase = -1, last_step = -1;  // last dependency known satisfied
-  for (int64_t g = blockIdx.x; g < total; g += gridDim.x) {
+  // (step, phase, environment) whose dependency thread 0 last saw satisfied
+  // (shared memory: only thread 0 uses it, so it takes no register of the others)
+  __shared__ long long s_last;
+  if (threadIdx.x == 0) s_last = -1;
+  __shared__ long long s_claim;
+  for (int64_t g = blockIdx.x;; g += gridDim.x) {
+    if (a.next) {  // claimed in order from the shared counter instead of every G-th item
+      if (threadIdx.x == 0) s_claim = (long long)atomicAdd(a.next, 1ull);
+      __syncthreads();
+      g = s_claim;  // read by every thread before the dependency barrier below
+    }
+    if (g >= total) break;
     const int step = (int)(g / a.per_step);
     int64_t r = g - (int64_t)step * a.per_step;
     int phase = 0;
@@ -106,8 +121,9 @@ __global__ void __launch_bounds__(kBatchWarps * 32, sizeof(E) == 4 ? 4 : 3)
     if (threadIdx.x == 0) {
       int go = 1;
       if (ld_relaxed_int(a.abort_flag)) go = 0;
-      const bool need = !(ei == last_env && phase == last_phase && step == last_step) &&
-                        !(phase == 0 && step == 0);
+      const long long key = ((long long)step * 3 + phase) * a.n_env + ei;
+      const bool need = key != s_last && !(phase == 0 && step == 0);
+      s_last = key;
       if (go && need) {
         const int dep_phase = phase == 0 ? 2 : phase - 1;
         unsigned want = (unsigned)(E_.items[dep_phase] * (phase == 0 ? step : step + 1));
@@ -132,9 +148,6 @@ __global__ void __launch_bounds__(kBatchWarps * 32, sizeof(E) == 4 ? 4 : 3)
     }
     __syncthreads();
     if (!s_go) return;
-    last_env = ei;
-    last_phase = phase;
-    last_step = step;
 
     const int S = E_.S, nx = E_.nx, ny = E_.ny;
     const int n = phase == 0 ? nx : phase == 1 ? ny : E_.nz;
@@ -177,10 +190,11 @@ __global__ void __launch_bounds__(kBatchWarps * 32, sizeof(E) == 4 ? 4 : 3)
         } else {
           cf.om = ldg<E>(E_.cfix[phase], L.s);
           cf.clo = ldg<E>(E_.cfix[phase], S + L.s);
-          E *sline = static_cast<E *>(E_.scratch) + (L.active ? L.base : 0);
-          float *gsm = reinterpret_cast<float *>(batch_smem) + (size_t)wp * 2 * kBatchKS * 32 + lane;
-          solve_lines_f32<kBatchR, kBatchKS>(line, sline, n, st, L.active, cf, dr, E(0), E(0), gsm,
-                                       gsm + kBatchKS * 32);
+          // the warp's scratch tile: [position][lane], tiles in tile order
+          E *sline = static_cast<E *>(E_.scratch) + tile * n * 32 + lane;
+          float *wsm = reinterpret_cast<float *>(batch_smem) + (size_t)wp * kBatchWarpFloats + lane;
+          solve_lines_f32<kBatchR, kBatchKS, true>(line, sline, n, st, L.active, cf, dr, E(0),
+                                                   E(0), wsm, wsm + kBatchKS * 32);
         }
       }
       __syncthreads();

@@ -23,7 +23,8 @@ struct BatchEnv {
   // whole-line axes (tile shape m >= n): streaming solve, one warp per tile
   // (stream.cuh), coefficients position-major [n][S] (FP64: inv, mul, q;
   // FP32: inv', mul of the defect form), interior constants [2][S] from
-  // position k0 on, FP32 c_hi/c_lo and a field-sized scratch
+  // position k0 on, FP32 c_hi/c_lo and a scratch of one [n][32] tile per
+  // whole-line tile (batch_scratch_elems)
   int whole[3];
   const void *stab[3], *sint[3], *cfix[3];
   int k0[3];
@@ -38,6 +39,7 @@ struct BatchArgs {
   int64_t per_step;         // work items of one step
   unsigned int *done;       // [3][n_env] completed work items (cumulative over steps)
   int *abort_flag, *status;
+  unsigned long long *next;  // claim counter (zero at launch), or NULL: static round robin
   int stall_test;           // test hook: the first y tile of environment 0 waits for a count
                             // that never comes, so its bounded wait expires
 };
