@@ -51,12 +51,12 @@ KERNEL_SOURCES = ["stream.cuh", "sweeps.cuh", "pipe.cuh", "pipe_args.h", "intern
 # the 400^3 x 4 workload, from one ncu capture; reported only while the kernel sources still
 # hash to `sources_sha256` (otherwise the kernels changed since and traffic is null).
 MEASURED_TRAFFIC = {
-    "sources_sha256": "35a2fd48ea7fd33a95d4d56c6bfd4ebe2bda90662b2e1fca11e6257ccc0e022e",
+    "sources_sha256": "dfdfcfc5517b3db62d07efd51e965a28556916ae6b5369129c40901f2a165b99",
     "bytes": {
-        "fp64:x-sweep": 5698977280, "fp64:y-sweep": 5499279616, "fp64:z-sweep": 5550959104,
-        "fp32:x-sweep": 2051060480, "fp32:y-sweep": 1983984640, "fp32:z-sweep": 1983558144,
-        "bf16:x-sweep": 1027536384, "bf16:y-sweep": 966321408, "bf16:z-sweep": 967173888,
-        "fp16:x-sweep": 1027404288, "fp16:y-sweep": 966340096, "fp16:z-sweep": 966964224,
+        "fp64:x-sweep": 5710992896, "fp64:y-sweep": 5504968192, "fp64:z-sweep": 5532824320,
+        "fp32:x-sweep": 2051157248, "fp32:y-sweep": 1983586816, "fp32:z-sweep": 1984059904,
+        "bf16:x-sweep": 1027370496, "bf16:y-sweep": 965999616, "bf16:z-sweep": 966979072,
+        "fp16:x-sweep": 1027427840, "fp16:y-sweep": 966120448, "fp16:z-sweep": 967207424,
     },
 }
 UNIT = "voxel-substrate updates/s"

@@ -32,6 +32,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "batch_args.h"
 #include "stream.cuh"
 #include "sweeps.cuh"
@@ -71,6 +73,202 @@ __device__ __forceinline__ void cp_async_elem(void *smem, const void *gmem, int 
 constexpr int kBatchKS = 24;
 constexpr int kBatchR = 4;
 constexpr int kBatchWarpFloats = 2 * kBatchKS * 32;  // a warp's share of the line slabs
+
+// Drops one 128-byte line (128-byte aligned) from L2 without writing it back;
+// its contents become undefined.
+__device__ __forceinline__ void discard_l2(const void *p) {
+  asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory");
+}
+// Hinted store at a compile-time byte offset from p (no address arithmetic).
+template <int OFF>
+__device__ __forceinline__ void st_hint_at(float *p, float v, unsigned long long pol) {
+  asm volatile("st.global.L2::cache_hint.f32 [%0+%3], %1, %2;" ::"l"(p), "f"(v), "l"(pol),
+               "n"(OFF));
+}
+template <int K, int N, typename F>
+__device__ __forceinline__ void static_for(F &&f) {
+  if constexpr (K < N) {
+    f(std::integral_constant<int, K>{});
+    static_for<K + 1, N>(f);
+  }
+}
+
+// FP32 whole lines of the batched kernel: the arithmetic of solve_lines_f32
+// (defect form, e = L_N d one position behind the loads with mirrored ends,
+// g_i = mul_i g_{i-1} + inv'_i e_i, y_i = g_i + mul_i y_{i+1},
+// x_i = c_hi d_i + (c_lo d_i + y_i)), for lines without Dirichlet faces.
+//   * The forward intermediate goes to the warp's own scratch tile
+//     [position][32 lanes] (sline: this lane's column), so every position of
+//     the warp is one 128-byte line; the backward pass discards each line from
+//     L2 once all lanes have read it, and the dead intermediate is never
+//     written back to DRAM.
+//   * Positions below KS keep g and d in shared-memory slabs (gsm, dsm).
+//   * The kernel is issue-bound on these tiles, so a block of R positions
+//     that lies inside the line past k0 (interior constants), wholly in the
+//     slabs or wholly past them, takes a path with no per-position test,
+//     table load or address increment of the scratch; other blocks (the
+//     first, the one across KS, the last) take the general path.
+//     Lanes without a line (active false) run the plain blocks too, on valid
+//     addresses of their own (line = the field's start, their own scratch
+//     column), and store nothing to the field.
+template <int R, int KS>
+__device__ __forceinline__ void batch_lines_f32(float *line, float *sline, int n, long long st,
+                                                bool active, const LineCoef<float> &cf,
+                                                float *gsm, float *dsm) {
+  const int S = cf.S, ngrp = (n + R - 1) / R;
+  const int plain_lo = max(KS, cf.k0);  // plain blocks emit or read positions >= plain_lo
+  const L2Pol pol = make_l2pol();
+  float g = 0.f, dm1 = 0.f, dm2 = 0.f;
+  // ---- forward
+  auto load_f = [&](float(&buf)[R], int gi) {
+    const int i0 = gi * R;
+    if (i0 + R <= n) {
+      const float *q = line + (long long)i0 * st;
+#pragma unroll
+      for (int k = 0; k < R; k++) {
+        buf[k] = *q;
+        q += st;
+      }
+    } else {
+      load_block<float, R>(buf, line, st, i0, true, n, active);
+    }
+  };
+  auto emit = [&](int p, float e) {  // general: g of position p from its defect e
+    const bool in = p >= cf.k0 && p < n - 1;
+    const float iv = in ? cf.c0 : __ldg(cf.inv + (size_t)p * S);
+    const float mu = in ? cf.c1 : __ldg(cf.mul + (size_t)p * S);
+    g = fmaf(mu, g, e * iv);
+    if (p < KS) gsm[p * 32] = g; else st_hint(sline + (long long)p * 32, g, pol.keep);
+  };
+  auto fwd = [&](int gi, const float(&buf)[R]) {
+    const int i0 = gi * R;
+    if (i0 - 1 >= plain_lo && i0 + R - 1 < n) {  // emits positions i0-1 .. i0+R-2
+      float *sq = sline + (long long)(i0 - 1) * 32;
+      static_for<0, R>([&](auto kc) {
+        constexpr int k = decltype(kc)::value;
+        const float d = buf[k];
+        g = fmaf(cf.c1, g, ((dm1 - dm2) + (dm1 - d)) * cf.c0);
+        st_hint_at<k * 128>(sq, g, pol.keep);
+        dm2 = dm1;
+        dm1 = d;
+      });
+      return;
+    }
+    if (i0 >= 1 && i0 - 1 >= cf.k0 && i0 + R <= KS && i0 + R - 1 < n) {  // inside the slabs
+      float *gq = gsm + (i0 - 1) * 32, *dq = dsm + i0 * 32;
+#pragma unroll
+      for (int k = 0; k < R; k++) {
+        const float d = buf[k];
+        dq[k * 32] = d;
+        g = fmaf(cf.c1, g, ((dm1 - dm2) + (dm1 - d)) * cf.c0);
+        gq[k * 32] = g;
+        dm2 = dm1;
+        dm1 = d;
+      }
+      return;
+    }
+    if (!active) return;
+#pragma unroll
+    for (int k = 0; k < R; k++) {
+      const int i = i0 + k;
+      if (i < n) {
+        const float d = buf[k];
+        if (i < KS) dsm[i * 32] = d;
+        if (i == 0) {
+          dm1 = d;
+          dm2 = d;  // mirrored start: d_{-1} = d_0
+        } else {
+          emit(i - 1, (dm1 - dm2) + (dm1 - d));
+          dm2 = dm1;
+          dm1 = d;
+        }
+      }
+    }
+  };
+  {
+    float A[R], B[R];
+    load_f(A, 0);
+    for (int gi = 0; gi < ngrp; gi += 2) {
+      load_f(B, gi + 1);
+      fwd(gi, A);
+      load_f(A, gi + 2);
+      if (gi + 1 < ngrp) fwd(gi + 1, B);
+    }
+    if (active && n > 0) emit(n - 1, dm1 - dm2);
+  }
+  pass_barrier();
+  // ---- backward
+  float y = 0.f;
+  auto load_b = [&](float(&gb)[R], float(&db)[R], int gi) {
+    const int i1 = n - 1 - gi * R;
+    if (i1 - R + 1 >= KS && i1 - R + 1 >= 0) {  // the whole block in global memory
+      const float *qs = sline + (long long)i1 * 32, *qd = line + (long long)i1 * st;
+#pragma unroll
+      for (int k = 0; k < R; k++) {
+        gb[k] = qs[-k * 32];
+        db[k] = *qd;
+        qd -= st;
+      }
+    } else if (i1 < KS && i1 - R + 1 >= 0) {  // the whole block in the slabs
+#pragma unroll
+      for (int k = 0; k < R; k++) {
+        gb[k] = gsm[(i1 - k) * 32];
+        db[k] = dsm[(i1 - k) * 32];
+      }
+    } else {
+      const float *qs = sline + (long long)i1 * 32, *qd = line + (long long)i1 * st;
+#pragma unroll
+      for (int k = 0; k < R; k++) {
+        const int i = i1 - k;
+        const bool ok = active && i >= 0 && i < n;
+        gb[k] = !ok ? 0.f : (i < KS ? gsm[i * 32] : *qs);
+        db[k] = !ok ? 0.f : (i < KS ? dsm[i * 32] : *qd);
+        qs -= 32;
+        qd -= st;
+      }
+    }
+  };
+  auto bwd = [&](int gi, const float(&gb)[R], const float(&db)[R]) {
+    const int i1 = n - 1 - gi * R;
+    float *q = line + (long long)i1 * st;
+    if (gi >= 1 && i1 - R + 1 >= max(cf.k0, 0)) {  // interior positions i1 .. i1-R+1
+#pragma unroll
+      for (int k = 0; k < R; k++) {
+        y = fmaf(cf.c1, y, gb[k]);
+        const float xv = fmaf(cf.om, db[k], fmaf(cf.clo, db[k], y));
+        if (active) st_hint(q, xv, pol.drop);
+        q -= st;
+      }
+    } else if (active) {
+#pragma unroll
+      for (int k = 0; k < R; k++) {
+        const int i = i1 - k;
+        if (i >= 0) {
+          const bool in = i >= cf.k0 && i < n - 1;
+          const float mu = in ? cf.c1 : __ldg(cf.mul + (size_t)i * S);
+          y = fmaf(mu, y, gb[k]);
+          st_hint(q, fmaf(cf.om, db[k], fmaf(cf.clo, db[k], y)), pol.drop);
+        }
+        q -= st;
+      }
+    }
+    // every lane has read block gi's scratch line: lane k discards position i1 - k's
+    __syncwarp();
+    const int lane = threadIdx.x & 31;
+    if (lane < R && i1 - lane >= KS && i1 - lane >= 0)
+      discard_l2(sline + ((long long)i1 * 32 - 33 * lane));
+  };
+  {
+    float GA[R], DA[R], GB[R], DB[R];
+    load_b(GA, DA, 0);
+    for (int gi = 0; gi < ngrp; gi += 2) {
+      load_b(GB, DB, gi + 1);
+      bwd(gi, GA, DA);
+      load_b(GA, DA, gi + 2);
+      if (gi + 1 < ngrp) bwd(gi + 1, GB, DB);
+    }
+  }
+}
 
 // 256-thread CTAs, FP32 held to 64 registers (three or four per SM, as the
 // chunk rows' shared memory allows), FP64 to 80: the kernel is latency-bound,
@@ -193,8 +391,8 @@ __global__ void __launch_bounds__(kBatchWarps * 32, sizeof(E) == 4 ? 4 : 3)
           // the warp's scratch tile: [position][lane], tiles in tile order
           E *sline = static_cast<E *>(E_.scratch) + tile * n * 32 + lane;
           float *wsm = reinterpret_cast<float *>(batch_smem) + (size_t)wp * kBatchWarpFloats + lane;
-          solve_lines_f32<kBatchR, kBatchKS, true>(line, sline, n, st, L.active, cf, dr, E(0),
-                                                   E(0), wsm, wsm + kBatchKS * 32);
+          batch_lines_f32<kBatchR, kBatchKS>(line, sline, n, st, L.active, cf, wsm,
+                                             wsm + kBatchKS * 32);
         }
       }
       __syncthreads();

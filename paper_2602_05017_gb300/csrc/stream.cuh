@@ -129,11 +129,6 @@ __device__ __forceinline__ void st_hint(double *p, double v, unsigned long long 
 __device__ __forceinline__ void st_hint(float *p, float v, unsigned long long pol) {
   asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(pol));
 }
-// Drops one 128-byte line (128-byte aligned) from L2 without writing it back;
-// its contents become undefined.
-__device__ __forceinline__ void discard_l2(const void *p) {
-  asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory");
-}
 // Compiler barrier between the passes: the hinted stores are asm statements,
 // so the backward pass's ordinary loads must not move above them.
 __device__ __forceinline__ void pass_barrier() { asm volatile("" ::: "memory"); }
@@ -433,24 +428,17 @@ __device__ __forceinline__ void solve_rows_f64(double *wbase, long long rowlen, 
   }
 }
 
-// FP32 defect-correction solve of a warp's lines (see the header).  sline:
-// this lane's forward intermediate, either in a scratch field at the same
-// offset as line (TILED false: position i at sline[i * st]) or in the warp's
-// own scratch tile [position][32 lanes] (TILED true: position i at
-// sline[i * 32], every position of the warp one 128-byte line).  A tiled
-// scratch line is dead once the backward pass has read it, so it is discarded
-// from L2 without a write-back (the intermediate then costs no DRAM writes
-// unless L2 evicts it before the backward pass).  KS > 0: for positions below
+// FP32 defect-correction solve of a warp's lines (see the header); sline is
+// the scratch field at the same offset as line.  KS > 0: for positions below
 // KS (a multiple of R) both g and d stay in shared memory (gsm, dsm: this
 // lane's slabs, position i at [i * 32]), since they live longest between the
 // two passes.
-template <int R = kStreamR, int KS = 0, bool TILED = false>
+template <int R = kStreamR, int KS = 0>
 __device__ __forceinline__ void solve_lines_f32(float *line, float *sline, int n, long long st,
                                                 bool active, const LineCoef<float> &cf,
                                                 const LineDir &dr, float dval_in, float dval,
                                                 float *gsm = nullptr, float *dsm = nullptr) {
   const int S = cf.S, k0 = cf.k0, ngrp = (n + R - 1) / R;
-  const long long sst = TILED ? 32 : st;  // scratch stride between positions
   const L2Pol pol = make_l2pol();
   auto dmod = [&](float v, int i) {
     return (dr.before && (dr.face || i == 0 || i == n - 1)) ? dval_in : v;
@@ -467,7 +455,7 @@ __device__ __forceinline__ void solve_lines_f32(float *line, float *sline, int n
     if (!active) return;
     const int i0 = gi * R;
     const bool interior = i0 - 1 >= k0 && i0 + R - 2 < n - 1;
-    float *sq = sline + (long long)(i0 - 1) * sst;  // position i - 1
+    float *sq = sline + (long long)(i0 - 1) * st;  // position i - 1
 #pragma unroll
     for (int k = 0; k < R; k++) {
       const int i = i0 + k;
@@ -483,7 +471,7 @@ __device__ __forceinline__ void solve_lines_f32(float *line, float *sline, int n
           dm1 = d;
         }
       }
-      sq += sst;
+      sq += st;
     }
   };
   // ---- backward: y_i = g_i + mul_i y_{i+1}, x_i = c_hi d_i + (c_lo d_i + y_i)
@@ -515,37 +503,26 @@ __device__ __forceinline__ void solve_lines_f32(float *line, float *sline, int n
       load_block<float, R>(A, line, st, (gi + 2) * R, true, n, active);
       if (gi + 1 < ngrp) fwd_group(gi + 1, B);
     }
-    if (active && n > 0) emit(n - 1, dm1 - dm2, false, sline + (long long)(n - 1) * sst);
+    if (active && n > 0) emit(n - 1, dm1 - dm2, false, sline + (long long)(n - 1) * st);
   }
   pass_barrier();
   {
     // backward blocks: shared memory below KS, global above
     auto load2 = [&](float(&gb)[R], float(&db)[R], int i1) {
       if (KS == 0 || i1 - R + 1 >= KS) {
-        load_block<float, R>(gb, sline, sst, i1, false, n, active);
+        load_block<float, R>(gb, sline, st, i1, false, n, active);
         load_block<float, R>(db, line, st, i1, false, n, active);
       } else {
-        const float *qs = sline + (long long)i1 * sst, *qd = line + (long long)i1 * st;
+        const float *qs = sline + (long long)i1 * st, *qd = line + (long long)i1 * st;
 #pragma unroll
         for (int k = 0; k < R; k++) {
           const int i = i1 - k;
           const bool ok = active && i >= 0 && i < n;
           gb[k] = !ok ? 0.f : (i < KS ? gsm[i * 32] : *qs);
           db[k] = !ok ? 0.f : (i < KS ? dsm[i * 32] : *qd);
-          qs -= sst;
+          qs -= st;
           qd -= st;
         }
-      }
-    };
-    // block gi has been read by every lane of the warp (its values are
-    // consumed): lane k discards the scratch line of its position i1 - k
-    auto discard = [&](int gi) {
-      if constexpr (TILED) {
-        __syncwarp();
-        const int lane = threadIdx.x & 31, i1 = n - 1 - gi * R;
-        // position i1 - lane's line starts at sline - lane + (i1 - lane) * 32
-        if (lane < R && i1 - lane >= KS && i1 - lane >= 0)
-          discard_l2(sline + ((long long)i1 * 32 - 33 * lane));
       }
     };
     float GA[R], DA[R], GB[R], DB[R];
@@ -553,12 +530,8 @@ __device__ __forceinline__ void solve_lines_f32(float *line, float *sline, int n
     for (int gi = 0; gi < ngrp; gi += 2) {
       load2(GB, DB, n - 1 - (gi + 1) * R);
       bwd_group(gi, GA, DA);
-      discard(gi);
       load2(GA, DA, n - 1 - (gi + 2) * R);
-      if (gi + 1 < ngrp) {
-        bwd_group(gi + 1, GB, DB);
-        discard(gi + 1);
-      }
+      if (gi + 1 < ngrp) bwd_group(gi + 1, GB, DB);
     }
   }
 }
