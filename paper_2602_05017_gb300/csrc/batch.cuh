@@ -68,10 +68,13 @@ __device__ __forceinline__ void cp_async_elem(void *smem, const void *gmem, int 
 }
 
 // FP32 whole-line tiles keep the first kBatchKS positions of g and d in shared
-// memory (48 KB per CTA), streaming the rest in register blocks of kBatchR
-// positions.
+// memory (48 KB per CTA), streaming the rest in register blocks of kBatchRF
+// positions (forward pass: one array per block) and kBatchR positions
+// (backward pass: g and d), double-buffered, at 64 registers without spills;
+// forward blocks of 8 measured 4% faster than blocks of 4.
 constexpr int kBatchKS = 24;
 constexpr int kBatchR = 4;
+constexpr int kBatchRF = 8;
 constexpr int kBatchWarpFloats = 2 * kBatchKS * 32;  // a warp's share of the line slabs
 
 // Drops one 128-byte line (128-byte aligned) from L2 without writing it back;
@@ -111,93 +114,99 @@ __device__ __forceinline__ void static_for(F &&f) {
 //     Lanes without a line (active false) run the plain blocks too, on valid
 //     addresses of their own (line = the field's start, their own scratch
 //     column), and store nothing to the field.
-template <int R, int KS>
+template <int RF, int RB, int KS>
 __device__ __forceinline__ void batch_lines_f32(float *line, float *sline, int n, long long st,
                                                 bool active, const LineCoef<float> &cf,
                                                 float *gsm, float *dsm) {
-  const int S = cf.S, ngrp = (n + R - 1) / R;
+  const int S = cf.S;
   const int plain_lo = max(KS, cf.k0);  // plain blocks emit or read positions >= plain_lo
   const L2Pol pol = make_l2pol();
   float g = 0.f, dm1 = 0.f, dm2 = 0.f;
-  // ---- forward
-  auto load_f = [&](float(&buf)[R], int gi) {
-    const int i0 = gi * R;
-    if (i0 + R <= n) {
-      const float *q = line + (long long)i0 * st;
+  // ---- forward, blocks of R = RF positions (its own scope: R is redefined below)
+  {
+    constexpr int R = RF;
+    const int ngrp = (n + R - 1) / R;
+    auto load_f = [&](float(&buf)[R], int gi) {
+      const int i0 = gi * R;
+      if (i0 + R <= n) {
+        const float *q = line + (long long)i0 * st;
 #pragma unroll
-      for (int k = 0; k < R; k++) {
-        buf[k] = *q;
-        q += st;
+        for (int k = 0; k < R; k++) {
+          buf[k] = *q;
+          q += st;
+        }
+      } else {
+        load_block<float, R>(buf, line, st, i0, true, n, active);
       }
-    } else {
-      load_block<float, R>(buf, line, st, i0, true, n, active);
-    }
-  };
-  auto emit = [&](int p, float e) {  // general: g of position p from its defect e
-    const bool in = p >= cf.k0 && p < n - 1;
-    const float iv = in ? cf.c0 : __ldg(cf.inv + (size_t)p * S);
-    const float mu = in ? cf.c1 : __ldg(cf.mul + (size_t)p * S);
-    g = fmaf(mu, g, e * iv);
-    if (p < KS) gsm[p * 32] = g; else st_hint(sline + (long long)p * 32, g, pol.keep);
-  };
-  auto fwd = [&](int gi, const float(&buf)[R]) {
-    const int i0 = gi * R;
-    if (i0 - 1 >= plain_lo && i0 + R - 1 < n) {  // emits positions i0-1 .. i0+R-2
-      float *sq = sline + (long long)(i0 - 1) * 32;
-      static_for<0, R>([&](auto kc) {
-        constexpr int k = decltype(kc)::value;
-        const float d = buf[k];
-        g = fmaf(cf.c1, g, ((dm1 - dm2) + (dm1 - d)) * cf.c0);
-        st_hint_at<k * 128>(sq, g, pol.keep);
-        dm2 = dm1;
-        dm1 = d;
-      });
-      return;
-    }
-    if (i0 >= 1 && i0 - 1 >= cf.k0 && i0 + R <= KS && i0 + R - 1 < n) {  // inside the slabs
-      float *gq = gsm + (i0 - 1) * 32, *dq = dsm + i0 * 32;
-#pragma unroll
-      for (int k = 0; k < R; k++) {
-        const float d = buf[k];
-        dq[k * 32] = d;
-        g = fmaf(cf.c1, g, ((dm1 - dm2) + (dm1 - d)) * cf.c0);
-        gq[k * 32] = g;
-        dm2 = dm1;
-        dm1 = d;
-      }
-      return;
-    }
-    if (!active) return;
-#pragma unroll
-    for (int k = 0; k < R; k++) {
-      const int i = i0 + k;
-      if (i < n) {
-        const float d = buf[k];
-        if (i < KS) dsm[i * 32] = d;
-        if (i == 0) {
+    };
+    auto emit = [&](int p, float e) {  // general: g of position p from its defect e
+      const bool in = p >= cf.k0 && p < n - 1;
+      const float iv = in ? cf.c0 : __ldg(cf.inv + (size_t)p * S);
+      const float mu = in ? cf.c1 : __ldg(cf.mul + (size_t)p * S);
+      g = fmaf(mu, g, e * iv);
+      if (p < KS) gsm[p * 32] = g; else st_hint(sline + (long long)p * 32, g, pol.keep);
+    };
+    auto fwd = [&](int gi, const float(&buf)[R]) {
+      const int i0 = gi * R;
+      if (i0 - 1 >= plain_lo && i0 + R - 1 < n) {  // emits positions i0-1 .. i0+R-2
+        float *sq = sline + (long long)(i0 - 1) * 32;
+        static_for<0, R>([&](auto kc) {
+          constexpr int k = decltype(kc)::value;
+          const float d = buf[k];
+          g = fmaf(cf.c1, g, ((dm1 - dm2) + (dm1 - d)) * cf.c0);
+          st_hint_at<k * 128>(sq, g, pol.keep);
+          dm2 = dm1;
           dm1 = d;
-          dm2 = d;  // mirrored start: d_{-1} = d_0
-        } else {
-          emit(i - 1, (dm1 - dm2) + (dm1 - d));
+        });
+        return;
+      }
+      if (i0 >= 1 && i0 - 1 >= cf.k0 && i0 + R <= KS && i0 + R - 1 < n) {  // inside the slabs
+        float *gq = gsm + (i0 - 1) * 32, *dq = dsm + i0 * 32;
+#pragma unroll
+        for (int k = 0; k < R; k++) {
+          const float d = buf[k];
+          dq[k * 32] = d;
+          g = fmaf(cf.c1, g, ((dm1 - dm2) + (dm1 - d)) * cf.c0);
+          gq[k * 32] = g;
           dm2 = dm1;
           dm1 = d;
         }
+        return;
       }
+      if (!active) return;
+#pragma unroll
+      for (int k = 0; k < R; k++) {
+        const int i = i0 + k;
+        if (i < n) {
+          const float d = buf[k];
+          if (i < KS) dsm[i * 32] = d;
+          if (i == 0) {
+            dm1 = d;
+            dm2 = d;  // mirrored start: d_{-1} = d_0
+          } else {
+            emit(i - 1, (dm1 - dm2) + (dm1 - d));
+            dm2 = dm1;
+            dm1 = d;
+          }
+        }
+      }
+    };
+    {
+      float A[R], B[R];
+      load_f(A, 0);
+      for (int gi = 0; gi < ngrp; gi += 2) {
+        load_f(B, gi + 1);
+        fwd(gi, A);
+        load_f(A, gi + 2);
+        if (gi + 1 < ngrp) fwd(gi + 1, B);
+      }
+      if (active && n > 0) emit(n - 1, dm1 - dm2);
     }
-  };
-  {
-    float A[R], B[R];
-    load_f(A, 0);
-    for (int gi = 0; gi < ngrp; gi += 2) {
-      load_f(B, gi + 1);
-      fwd(gi, A);
-      load_f(A, gi + 2);
-      if (gi + 1 < ngrp) fwd(gi + 1, B);
-    }
-    if (active && n > 0) emit(n - 1, dm1 - dm2);
   }
   pass_barrier();
-  // ---- backward
+  // ---- backward, blocks of R = RB positions
+  constexpr int R = RB;
+  const int ngrp = (n + R - 1) / R;
   float y = 0.f;
   auto load_b = [&](float(&gb)[R], float(&db)[R], int gi) {
     const int i1 = n - 1 - gi * R;
@@ -391,7 +400,7 @@ __global__ void __launch_bounds__(kBatchWarps * 32, sizeof(E) == 4 ? 4 : 3)
           // the warp's scratch tile: [position][lane], tiles in tile order
           E *sline = static_cast<E *>(E_.scratch) + tile * n * 32 + lane;
           float *wsm = reinterpret_cast<float *>(batch_smem) + (size_t)wp * kBatchWarpFloats + lane;
-          batch_lines_f32<kBatchR, kBatchKS>(line, sline, n, st, L.active, cf, wsm,
+          batch_lines_f32<kBatchRF, kBatchR, kBatchKS>(line, sline, n, st, L.active, cf, wsm,
                                              wsm + kBatchKS * 32);
         }
       }
