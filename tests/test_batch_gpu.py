@@ -238,3 +238,35 @@ def test_batch_mode_follows_environment_size(binding):
     big = binding.BioFVMBatch(_envs(23, [(128, 128, 64, 1), (64, 64, 64, 8)], agents=False))
     assert big.mode() == "graph"
     big.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_batch_item_claims_and_grid_sizes_give_identical_fields(binding, prec, monkeypatch):
+    """The persistent kernel's schedule does not touch the arithmetic: items claimed from the
+    counter (default), statically strided (BIOFVM_BATCH_DYNAMIC=0) and on one CTA per SM
+    (BIOFVM_BATCH_CTAS=1) give bit-identical fields, whole-line and chunked axes mixed, long
+    lines included; the first also against the oracle."""
+    envs = _envs(31, [(150, 40, 36, 3), (33, 96, 17, 5), (64, 9, 130, 1), (7, 5, 3, 8)])
+    tiles = [[w.nx, 16, w.nz] for w in envs]
+    fields, grids = [], []
+    for knobs in ({}, {"BIOFVM_BATCH_DYNAMIC": "0"}, {"BIOFVM_BATCH_CTAS": "1"}):
+        for k in ("BIOFVM_BATCH_DYNAMIC", "BIOFVM_BATCH_CTAS"):
+            monkeypatch.delenv(k, raising=False)
+        for k, v in knobs.items():
+            monkeypatch.setenv(k, v)
+        b = binding.BioFVMBatch(envs, precision=prec, tile_m=tiles, mode="persistent")
+        grids.append(b.grid())
+        for sim, w in zip(b.envs, envs):
+            sim.set_density(w.rho0)
+            sim.set_sources(w.voxel, w.secretion, w.target, w.uptake, w.weight)
+        b.step(3)
+        b.sync()
+        fields.append([np.asarray(sim.density()).copy() for sim in b.envs])
+        b.close()
+    assert grids[0] == grids[1] and grids[0] % grids[2] == 0 and grids[2] < grids[0]
+    for other in fields[1:]:
+        for a, c in zip(fields[0], other):
+            assert np.array_equal(a, c)
+    for got, w in zip(fields[0], envs):
+        ref = oracle.Problem(**w.oracle_kwargs()).step(w.rho0, 3)
+        assert rel(got, ref) <= TOL[prec], w.name
