@@ -26,8 +26,8 @@
 // single-grid kernels: App. A system, FP32 in defect-correction form (the
 // forward intermediate of whole lines in a scratch tile per warp, discarded
 // from L2 once read back), the source update applied to an x item's rows
-// before its solve.  Zero-flux
-// boundaries (the batched microenvironments have no Dirichlet faces).
+// before its solve.  Zero-flux boundaries (the batched microenvironments have
+// no Dirichlet faces).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
