@@ -286,7 +286,10 @@ biofvm_status biofvm_probe_fma_rate(biofvm_precision prec, uintptr_t cuda_stream
  *     enough to fill the GPU in a few concurrent launches.
  * The mode is taken from the environment variable BIOFVM_BATCH_MODE (graph or
  * persistent) if set, else mode 1 when the mean environment holds at least
- * 2^20 voxel-substrates.  Each environment is an ordinary handle (zero-flux
+ * 2^20 voxel-substrates.  The persistent kernel's CTAs claim work items in
+ * order from a counter (BIOFVM_BATCH_DYNAMIC=0: a static stride instead) and
+ * fill every SM with as many CTAs as fit (BIOFVM_BATCH_CTAS caps the CTAs per
+ * SM); the results do not depend on either.  Each environment is an ordinary handle (zero-flux
  * boundaries) reachable through biofvm_batch_env, so biofvm_set_density,
  * biofvm_set_sources, biofvm_density (and even biofvm_step) work on it.
  * ---------------------------------------------------------------------- */
